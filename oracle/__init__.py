@@ -1,0 +1,334 @@
+"""FP64 CPU oracle of the seismic saliency method (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may
+import this package.  It shares no code with the CUDA path: the stencil builder,
+the normalisation, the weight fits and the gradients below are written here from
+the paper, independently of the product.
+
+Pipeline (Sec. 2 of the paper, Fig. 2 block diagram):
+  V --local 3D DFT (Eq. 2)--> F --projection (Eq. 1)--> F_m --abs mean (step 3)--> E_m
+    --directional center-surround (Eq. 3)--> S_m --min-max--> S^_m
+    --weighted sum (Eq. 4; equal, given, LS fit to a desired map D, or LMS/NLMS/RLS)--> S.
+
+Readings where the paper is silent (each an argument here):
+  * stride 1 (a window around every voxel), window offsets [-n/2, n/2-1];
+  * rectangular taper (the cube C_n as is); Hann optional;
+  * E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]|;
+  * DCS stencil: direction groups t, x and t-x (Fig. 4), offsets s*d for s in +-1..+-R,
+    Gaussian weights w_o = alpha_d exp(-|o|^2 / (2 sigma^2)) multiplying the neighbour
+    inside |.| as Eq. 3 is written, Q = number of offsets;
+  * borders: symmetric extension (edge sample repeated) of V and of E;
+  * per-map min-max before combining and a final min-max of S (a flat map is all 0);
+  * LS weights (G + delta I)^-1 b in FP64 (the fixed point the LMS family approaches;
+    RLS with lambda = 1 and P0 = I/delta reaches it exactly).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+BOUNDARY = {"symmetric": 0, "periodic": 1, "zero": 2}
+TAPER = {"rect": 0, "hann": 1}
+
+_lib = None
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_i64_p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L_ = ctypes.c_long
+        i = ctypes.c_int
+        L.sal_oracle_local_spectrum.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, L_, L_, L_, _c_dbl_p]
+        L.sal_oracle_projected_spectra.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, L_, L_, L_, _c_dbl_p]
+        L.sal_oracle_features.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_dbl_p, i]
+        L.sal_oracle_features_at.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_i64_p, L_, _c_dbl_p, i]
+        L.sal_oracle_center_surround.argtypes = [_c_dbl_p, L_, L_, L_, i, i, _c_int_p, _c_dbl_p, _c_dbl_p, i]
+        L.sal_oracle_center_surround_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, _c_int_p, _c_dbl_p,
+                                                         _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.sal_oracle_features_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_dbl_p, _c_dbl_p, i]
+        L.sal_oracle_lms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, _c_dbl_p, _c_dbl_p]
+        L.sal_oracle_nlms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, ctypes.c_double, _c_dbl_p,
+                                      _c_dbl_p]
+        L.sal_oracle_rls.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, ctypes.c_double, _c_dbl_p,
+                                     _c_dbl_p]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_c_dbl_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed (code {rc})")
+
+
+# ----------------------------------------------------------------------------------------------
+# Steps 1-3: local spectrum, projection, features (Eq. 1, Eq. 2, step 3)
+# ----------------------------------------------------------------------------------------------
+
+def local_spectrum(V, t: int, x: int, y: int, n: int, boundary="symmetric", taper="rect") -> np.ndarray:
+    """Complex [n][n][n] spectrum of the cube around voxel (t,x,y) (Eq. 2)."""
+    V = _f64(V)
+    out = np.empty((n, n, n, 2), dtype=np.float64)
+    _check(lib().sal_oracle_local_spectrum(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper],
+                                           t, x, y, _dp(out)), "local_spectrum")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def projected_spectra(V, t: int, x: int, y: int, n: int, boundary="symmetric", taper="rect") -> np.ndarray:
+    """Complex [3][n][n][n] projected spectra F_t, F_x, F_y of Eq. 1 (DC = 0)."""
+    V = _f64(V)
+    out = np.empty((3, n, n, n, 2), dtype=np.float64)
+    _check(lib().sal_oracle_projected_spectra(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper],
+                                              t, x, y, _dp(out)), "projected_spectra")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
+    """E [3][T][X][Y] (E_t, E_x, E_y) at every voxel."""
+    V = _f64(V)
+    E = np.empty((3,) + V.shape, dtype=np.float64)
+    _check(lib().sal_oracle_features(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], _dp(E),
+                                     threads), "features")
+    return E
+
+
+def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
+    """E at listed voxels: pts [count][3] -> [count][3]."""
+    V = _f64(V)
+    pts = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((pts.shape[0], 3), dtype=np.float64)
+    if pts.shape[0] == 0:
+        return out
+    _check(lib().sal_oracle_features_at(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper],
+                                        pts.ctypes.data_as(_c_i64_p), pts.shape[0], _dp(out), threads),
+           "features_at")
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# Step 4: directional center-surround (Eq. 3, Fig. 4)
+# ----------------------------------------------------------------------------------------------
+
+DEFAULT_DIRECTIONS = ((1, 0, 0), (0, 1, 0), (1, 1, 0))  # t, x and t-x (Fig. 4)
+
+
+def dcs_stencil(directions: Sequence[Sequence[int]] = DEFAULT_DIRECTIONS, R: int = 3, sigma: float = 1.5,
+                alpha: Optional[Sequence[float]] = None):
+    """Directional window: offsets o = s*d (s = +-1..+-R) per direction d, Gaussian factor
+    g_o = exp(-|o|^2 / (2 sigma^2)), weight w_o = alpha_d g_o.  Returns
+    (offsets [Q][3] int32, g [Q], dir_id [Q] int32, w [Q])."""
+    alpha = np.ones(len(directions)) if alpha is None else np.asarray(alpha, dtype=np.float64)
+    offs, g, did = [], [], []
+    for d_i, d in enumerate(directions):
+        for s in list(range(-R, 0)) + list(range(1, R + 1)):
+            o = (s * d[0], s * d[1], s * d[2])
+            offs.append(o)
+            g.append(math.exp(-(o[0] ** 2 + o[1] ** 2 + o[2] ** 2) / (2.0 * sigma * sigma)))
+            did.append(d_i)
+    offs = np.asarray(offs, dtype=np.int32)
+    g = np.asarray(g, dtype=np.float64)
+    did = np.asarray(did, dtype=np.int32)
+    return offs, g, did, alpha[did] * g
+
+
+def center_surround(E, offsets, w, boundary="symmetric", threads: int = 0) -> np.ndarray:
+    """S [3][T][X][Y] per Eq. 3 (raw, before normalisation)."""
+    E = _f64(E)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    w = _f64(w)
+    S = np.empty_like(E)
+    _check(lib().sal_oracle_center_surround(_dp(E), *E.shape[1:], BOUNDARY[boundary], len(w),
+                                            offsets.ctypes.data_as(_c_int_p), _dp(w), _dp(S), threads),
+           "center_surround")
+    return S
+
+
+def ext_index(i, N: int, boundary: str):
+    """Boundary extension of one axis (array version); -1 where the zero extension applies."""
+    i = np.asarray(i, dtype=np.int64)
+    if boundary == "periodic":
+        return np.mod(i, N)
+    if boundary == "zero":
+        return np.where((i >= 0) & (i < N), i, -1)
+    r = np.mod(i, 2 * N)
+    return np.where(r < N, r, 2 * N - 1 - r)
+
+
+def center_surround_at(V, pts, n: int, offsets, w, boundary="symmetric", taper="rect",
+                       threads: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """(E at pts [count][3], raw S at pts [count][3]) computed from V one voxel at a time."""
+    pts = np.asarray(pts, dtype=np.int64).reshape(-1, 3)
+    shape = np.asarray(V).shape
+    offsets = np.asarray(offsets, dtype=np.int64)
+    nb = pts[:, None, :] + offsets[None, :, :]                 # [count][Q][3]
+    idx = np.stack([ext_index(nb[..., a], shape[a], boundary) for a in range(3)], axis=-1)
+    valid = np.all(idx >= 0, axis=-1)
+    allp = np.concatenate([pts, np.where(valid[..., None], idx, 0).reshape(-1, 3)], axis=0)
+    uniq, inv = np.unique(allp, axis=0, return_inverse=True)
+    Eu = features_at(V, uniq, n, boundary, taper, threads)
+    Eall = Eu[inv.reshape(-1)]
+    Ec = Eall[: len(pts)]                                      # [count][3]
+    Enb = Eall[len(pts):].reshape(len(pts), len(w), 3)
+    Enb = np.where(valid[..., None], Enb, 0.0)
+    S = np.abs(Ec[:, None, :] - np.asarray(w)[None, :, None] * Enb).sum(axis=1) / len(w)
+    return Ec, S
+
+
+# ----------------------------------------------------------------------------------------------
+# Step 5: normalisation and combination (Eq. 4)
+# ----------------------------------------------------------------------------------------------
+
+def minmax_bounds(A) -> Tuple[float, float]:
+    return float(np.min(A)), float(np.max(A))
+
+
+def minmax(A, lo: Optional[float] = None, hi: Optional[float] = None) -> np.ndarray:
+    """(A - min) / (max - min); a flat map (span <= 1e-30 max(1,|max|)) maps to 0."""
+    A = _f64(A)
+    if lo is None:
+        lo, hi = minmax_bounds(A)
+    span = hi - lo
+    if span <= 1e-30 * max(1.0, abs(hi)):
+        return np.zeros_like(A)
+    return (A - lo) / span
+
+
+def ls_weights(Shat, D, delta: float = 1e-6) -> np.ndarray:
+    """W = (G + delta I)^-1 b with G = sum_p x_p x_p^T, b = sum_p x_p D_p, x_p = Shat[:, p]."""
+    X = _f64(Shat).reshape(3, -1)
+    d = _f64(D).reshape(-1)
+    G = X @ X.T
+    b = X @ d
+    return np.linalg.solve(G + delta * np.eye(3), b)
+
+
+def _seq_order(A) -> np.ndarray:
+    """Voxel order of the sequential filters: inline sections (y) outermost, then x, then t."""
+    A = np.asarray(A)
+    if A.ndim == 4:
+        return np.ascontiguousarray(np.transpose(A, (0, 3, 2, 1)).reshape(3, -1), dtype=np.float64)
+    return np.ascontiguousarray(np.transpose(A, (2, 1, 0)).reshape(-1), dtype=np.float64)
+
+
+def adapt_weights(Shat, D, method: str = "nlms", W0=(1 / 3, 1 / 3, 1 / 3), mu: float = 0.5, eps: float = 1e-8,
+                  lam: float = 1.0, delta: float = 1e-6, return_trace: bool = False):
+    """One sequential pass of LMS / NLMS / RLS (paper: NLMS for all results)."""
+    X = _seq_order(Shat)
+    d = _seq_order(D)
+    N = d.size
+    W = np.array(W0 if method != "rls" else (0.0, 0.0, 0.0), dtype=np.float64)
+    err2 = np.empty(N, dtype=np.float64)
+    L = lib()
+    if method == "lms":
+        rc = L.sal_oracle_lms(_dp(X), _dp(d), N, mu, _dp(W), _dp(err2))
+    elif method == "nlms":
+        rc = L.sal_oracle_nlms(_dp(X), _dp(d), N, mu, eps, _dp(W), _dp(err2))
+    elif method == "rls":
+        rc = L.sal_oracle_rls(_dp(X), _dp(d), N, lam, delta, _dp(W), _dp(err2))
+    else:
+        raise ValueError(method)
+    _check(rc, method)
+    return (W, err2) if return_trace else W
+
+
+def combine(S3, weights="equal", D=None, delta: float = 1e-6, bounds=None) -> Dict[str, np.ndarray]:
+    """Normalise each S_m, fit or take the weights, weighted sum, final min-max.
+
+    weights: 'equal' | 'ls' (needs D) | 'nlms' | 'lms' | 'rls' (need D) | array of 3.
+    bounds: optional frozen (lo[3], hi[3], loC, hiC) for the normalisations.
+    """
+    S3 = _f64(S3)
+    if bounds is None:
+        lo = np.array([S3[m].min() for m in range(3)])
+        hi = np.array([S3[m].max() for m in range(3)])
+    else:
+        lo, hi = np.asarray(bounds[0], float), np.asarray(bounds[1], float)
+    Shat = np.stack([minmax(S3[m], lo[m], hi[m]) for m in range(3)])
+    if isinstance(weights, str):
+        if weights == "equal":
+            W = np.full(3, 1.0 / 3.0)
+        elif weights == "ls":
+            W = ls_weights(Shat, D, delta)
+        else:
+            W = adapt_weights(Shat, D, method=weights, delta=delta)
+    else:
+        W = np.asarray(weights, dtype=np.float64)
+    C = np.tensordot(W, Shat, axes=1)
+    if bounds is None:
+        loC, hiC = minmax_bounds(C)
+    else:
+        loC, hiC = float(bounds[2]), float(bounds[3])
+    S = minmax(C, loC, hiC)
+    return {"S": S, "W": W, "Shat": Shat, "C": C, "lo": lo, "hi": hi, "loC": loC, "hiC": hiC}
+
+
+def saliency(V, n: int, boundary="symmetric", taper="rect", stencil=None, weights="equal", D=None,
+             delta: float = 1e-6, threads: int = 0, bounds=None) -> Dict[str, np.ndarray]:
+    """Whole forward pass: E, raw S_m, weights and the consolidated map S."""
+    if stencil is None:
+        stencil = dcs_stencil()
+    offsets, g, did, w = stencil
+    E = features(V, n, boundary, taper, threads)
+    S3 = center_surround(E, offsets, w, boundary, threads)
+    out = combine(S3, weights, D, delta, bounds)
+    out.update({"E": E, "S3": S3})
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# Gradient (analytic adjoint; normalisation bounds held constant)
+# ----------------------------------------------------------------------------------------------
+
+def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", stencil=None, fwd=None,
+                      threads: int = 0) -> Dict[str, np.ndarray]:
+    """Gradients of sum_p gS_p S_p with respect to V, the 3 weights W and the per-direction
+    alpha_d, with the min-max bounds of the forward pass held constant."""
+    if stencil is None:
+        stencil = dcs_stencil()
+    offsets, g, did, w = stencil
+    W = np.asarray(W, dtype=np.float64)
+    if fwd is None:
+        fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads)
+    gS = _f64(gS)
+    spanC = fwd["hiC"] - fwd["loC"]
+    gC = gS / spanC if spanC > 1e-30 * max(1.0, abs(fwd["hiC"])) else np.zeros_like(gS)
+    gW = np.array([np.sum(gC * fwd["Shat"][m]) for m in range(3)])
+    gS3 = np.empty((3,) + gS.shape)
+    for m in range(3):
+        span = fwd["hi"][m] - fwd["lo"][m]
+        gS3[m] = W[m] * gC / span if span > 1e-30 * max(1.0, abs(fwd["hi"][m])) else 0.0
+    E = _f64(fwd["E"])
+    gE = np.empty_like(E)
+    gw = np.empty(len(w), dtype=np.float64)
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    wv = _f64(w)
+    _check(lib().sal_oracle_center_surround_adjoint(_dp(E), *E.shape[1:], BOUNDARY[boundary], len(wv),
+                                                    offs.ctypes.data_as(_c_int_p), _dp(wv), _dp(gS3),
+                                                    _dp(gE), _dp(gw)), "center_surround_adjoint")
+    ndir = int(did.max()) + 1
+    galpha = np.zeros(ndir)
+    for o in range(len(wv)):
+        galpha[did[o]] += gw[o] * g[o]
+    V64 = _f64(V)
+    gV = np.empty_like(V64)
+    _check(lib().sal_oracle_features_adjoint(_dp(V64), *V64.shape, n, BOUNDARY[boundary], TAPER[taper],
+                                             _dp(gE), _dp(gV), threads), "features_adjoint")
+    return {"gV": gV, "gW": gW, "galpha": galpha, "gE": gE, "gS3": gS3, "gw": gw}
