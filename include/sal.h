@@ -1,0 +1,141 @@
+/*
+ * sal.h — C ABI of the GB300 (sm_103a) seismic saliency library, libsal.so.
+ *
+ * Method: Shafiq, Long, Di, AlRegib, "A novel attention model for salient structure
+ * detection in seismic volumes" (Applied Computing and Intelligence, 2021).  The
+ * paper's problem statement (Sec. 2): given a seismic volume V of size T x X x Y
+ * (T time/depth, X crossline, Y inline), compute a saliency map S of the same size
+ * by (1) a local 3D DFT of an n^3 cube around every voxel (Eq. 2), (2) a spectral
+ * projection of each local spectrum onto the t, x and y dimensions (Eq. 1),
+ * (3) per-dimension features E_m, (4) a directional center-surround comparison
+ * giving S_m (Eq. 3, Fig. 4) and (5) a weighted combination of S_t, S_x, S_y with
+ * equal, given or template-fitted weights (Eq. 4).
+ *
+ * Conventions for every entry point:
+ *   - Volumes are C-contiguous float32 [T][X][Y] (Y fastest).  Stacked maps are
+ *     [3][T][X][Y] with the planes in the order t, x, y.
+ *   - All data pointers are DEVICE pointers owned by the caller, unless a comment
+ *     says otherwise.  The handle owns only its constant tables and scratch.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous: they return after enqueueing the work.
+ *   - Every call returns a sal_status.  Argument errors are reported before any
+ *     work is enqueued.  Errors found on the device set an error word that the
+ *     next call on the handle reports as SAL_ERR_DEVICE_CHECK.  Nothing traps on
+ *     the device.  sal_last_error() gives a one-line message for the last error.
+ *   - Results are deterministic for a fixed handle configuration: reductions
+ *     use fixed-order trees, never floating-point atomics.
+ *   - A handle is not thread-safe: calls on one handle must not overlap in time.
+ */
+#ifndef SAL_H
+#define SAL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sal_handle sal_handle;
+
+typedef enum {
+    SAL_OK = 0,
+    SAL_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad parameter          */
+    SAL_ERR_UNSUPPORTED = 2,   /* valid but not built (e.g. a window size)        */
+    SAL_ERR_OOM = 3,           /* scratch does not fit the HBM budget or device   */
+    SAL_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed            */
+    SAL_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up              */
+    SAL_ERR_DEVICE_CHECK = 6   /* a device-side check set the error word          */
+} sal_status;
+
+typedef enum { SAL_FP32 = 0, SAL_BF16 = 1, SAL_FP16 = 2 } sal_precision;
+
+/* Border extension of V (for the DFT cubes) and of E (for the center-surround). */
+typedef enum {
+    SAL_BND_SYMMETRIC = 0,  /* edge sample repeated: -1 -> 0, -2 -> 1, T -> T-1 */
+    SAL_BND_PERIODIC = 1,
+    SAL_BND_ZERO = 2
+} sal_boundary;
+
+typedef struct {
+    int n;                  /* cube side of the local DFT (Sec. 2 step 1, Eq. 2); even,
+                               2 <= n <= 16 for SAL_FP32, n in {8,16} for BF16/FP16   */
+    int stride;             /* window stride; must be 1 (a cube around every voxel)   */
+    int taper;              /* 0 = rectangular (the cube as is), 1 = periodic Hann    */
+    int boundary;           /* sal_boundary                                           */
+    int feature;            /* 0 = E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (step 3)  */
+    /* Directional center-surround window (Eq. 3, Fig. 4): Q = n_offsets neighbours
+       o = (dt,dx,dy), |dt|,|dx|,|dy| <= 8, with weight w_o = alpha[dir_id[o]] * gauss_w[o].
+       Host pointers; copied by sal_create. */
+    int n_offsets;          /* Q, 1 <= Q <= 64                                         */
+    const int* offsets;     /* [Q][3]                                                  */
+    const float* gauss_w;   /* [Q]  Gaussian factor of each neighbour                  */
+    const int* dir_id;      /* [Q]  direction group of each neighbour, < n_dirs        */
+    int n_dirs;             /* 1 <= n_dirs <= 16                                       */
+    const float* alpha;     /* [n_dirs] per-direction weights (host)                   */
+    int prec;               /* sal_precision of the local DFT contraction              */
+    double ls_delta;        /* ridge delta of the template fit (G + delta I)^-1 b      */
+    size_t hbm_budget_bytes;/* upper bound on the handle's device scratch (0 = none)   */
+} sal_params;
+
+/* Creates a handle for volumes of size T x X x Y on the current CUDA device.
+ * Validates `p`, builds the DFT tables and allocates scratch (E, S_m and gradient
+ * planes, reduction partials) within p->hbm_budget_bytes.  *out receives the
+ * handle; on error *out is NULL.  Synchronous. */
+sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out);
+
+/* Frees the handle and its scratch.  NULL is accepted.  Synchronises the device. */
+sal_status sal_destroy(sal_handle* h);
+
+/* Bytes of device scratch the handle holds (host pointer `bytes`). */
+sal_status sal_workspace_size(const sal_handle* h, size_t* bytes);
+
+/* Replaces the per-direction weights alpha[n_dirs] (host pointer).  Takes effect
+ * for calls enqueued after it returns. */
+sal_status sal_set_alpha(sal_handle* h, const float* alpha);
+
+/* Steps 1-3 (Sec. 2; Eq. 2 local DFT, Eq. 1 projection, step 3 feature):
+ *   E[m][p] = (1/n^3) sum_{k != 0} r_m(k) |F_p[k]|,  m in {t,x,y},
+ *   F_p[k] = sum_u h(u) Vext[p + u - n/2] exp(-2 pi i k.u / n),  u,k in [0,n)^3,
+ *   r_t = sqrt(j^2+k^2)/|kappa|, r_x = sqrt(i^2+k^2)/|kappa|, r_y = sqrt(i^2+j^2)/|kappa|,
+ * with signed bins (i,j,k) and the zero-frequency bin left out.
+ * V: [T][X][Y] float32 (device).  E: [3][T][X][Y] float32 (device, written). */
+sal_status sal_local_spectra_project(sal_handle* h, const float* V, float* E, void* stream);
+
+/* Step 4, directional center-surround (Eq. 3):
+ *   S3[m][p] = (1/Q) sum_o | E[m][p] - w_o * Eext[m][p + o] |.
+ * E: [3][T][X][Y] (device).  S3: [3][T][X][Y] raw maps (device, written). */
+sal_status sal_center_surround(sal_handle* h, const float* E, float* S3, void* stream);
+
+/* Step 5, combination (Eq. 4): each S_m is min-max normalised to [0,1] (a flat map
+ * becomes 0); the weights are W_in (device [3]) if D is NULL and W_in is not, equal
+ * (1/3) if both are NULL, or, if D (device [T][X][Y], the desired map) is given, the
+ * least-squares fit W = (G + delta I)^-1 b with G = sum_p x_p x_p^T, b = sum_p x_p D_p,
+ * x_p = (S^_t, S^_x, S^_y)(p), accumulated in FP64.  S = minmax(sum_m W_m S^_m).
+ * W_out: device [3], receives the weights used (nullable).  S: [T][X][Y] (written). */
+sal_status sal_combine(sal_handle* h, const float* S3, const float* D, const float* W_in,
+                       float* W_out, float* S, void* stream);
+
+/* Steps 1-5 in one call.  S3_opt and E_opt (nullable, device [3][T][X][Y]) receive
+ * the intermediate maps when given; otherwise the handle's scratch holds them. */
+sal_status sal_saliency(sal_handle* h, const float* V, const float* D, const float* W_in,
+                        float* S, float* S3_opt, float* E_opt, float* W_out, void* stream);
+
+/* Gradient of L = sum_p gS[p] * S[p] for S = sal_saliency(V, weights W) with the
+ * min-max bounds of the forward pass held constant (the paper has no backward pass;
+ * this is the adjoint of Eq. 1-4).  Recomputes the forward pass and the local
+ * spectra brick by brick; no spectra are stored.
+ * V: [T][X][Y], W: device [3] (the weights of the forward pass), gS: [T][X][Y].
+ * Outputs (device, each nullable): gV [T][X][Y], gW [3], galpha [n_dirs]. */
+sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, const float* gS,
+                                 float* gV, float* gW, float* galpha, void* stream);
+
+/* Message of the last error on the handle ("" if none).  h may be NULL (then the
+ * last sal_create error of this thread is returned).  The string lives until the
+ * next call on the handle. */
+const char* sal_last_error(const sal_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAL_H */

@@ -1,0 +1,89 @@
+// K2: directional center-surround comparison (Sec. 2 step 4, Eq. 3; windows of Fig. 4)
+//   S_m[p] = (1/Q) sum_o | E_m[p] - w_o * Eext_m[p + o] |,   m in {t, x, y},
+// with the difference formed by one FMA (fmaf(-w, e_nb, e_c): the product is not rounded
+// before the subtraction).  HBM-bound: 12 B read + 12 B written per voxel; neighbours come
+// from L1/L2.  Fused per-block min/max of each S_m for the normalisation in K3.
+#include <cfloat>
+
+#include "sal_internal.cuh"
+
+namespace sal {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k2_dcs(const float* __restrict__ E, float* __restrict__ S3, int T, int X, int Y, int bnd,
+       const __grid_constant__ Stencil st, float* __restrict__ mm_part) {
+    const long long NV = (long long)T * X * Y;
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV;
+         p += (long long)gridDim.x * kThreads) {
+        const int y = (int)(p % Y);
+        const int x = (int)((p / Y) % X);
+        const int t = (int)(p / ((long long)X * Y));
+        float ec[3], acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) ec[m] = __ldg(E + m * NV + p);
+        for (int o = 0; o < st.Q; ++o) {
+            const int tt = ext_index(t + st.off[o][0], T, bnd);
+            const int xx = ext_index(x + st.off[o][1], X, bnd);
+            const int yy = ext_index(y + st.off[o][2], Y, bnd);
+            const bool ok = tt >= 0 && xx >= 0 && yy >= 0;
+            const long long q = ok ? ((long long)tt * X + xx) * Y + yy : 0;
+            const float w = st.w[o];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float nb = ok ? __ldg(E + m * NV + q) : 0.f;
+                acc[m] += fabsf(fmaf(-w, nb, ec[m]));
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float s = acc[m] * st.invQ;
+            S3[m * NV + p] = s;
+            mn[m] = fminf(mn[m], s);
+            mx[m] = fmaxf(mx[m], s);
+        }
+    }
+    __shared__ float red[kThreads / 32][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float a = warp_min(mn[m]), b = warp_max(mx[m]);
+        if (lane == 0) {
+            red[wid][m] = a;
+            red[wid][3 + m] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        float v = red[0][c];
+        for (int w = 1; w < kThreads / 32; ++w) v = c < 3 ? fminf(v, red[w][c]) : fmaxf(v, red[w][c]);
+        mm_part[blockIdx.x * 8 + c] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, const Stencil& st,
+                       float* mm_part, cudaStream_t s) {
+    const long long NV = (long long)T * X * Y;
+    const int blocks = red_blocks(NV);  // K3 reduces exactly this many min/max partials
+    k2_dcs<<<blocks, kThreads, 0, s>>>(E, S3, T, X, Y, bnd, st, mm_part);
+    return cudaGetLastError();
+}
+
+}  // namespace sal

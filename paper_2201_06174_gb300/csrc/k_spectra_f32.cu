@@ -1,0 +1,260 @@
+// K1-F32: local 3D DFT around every voxel, spectral projection and feature, in FP32 on
+// the SIMT pipes (Sec. 2 steps 1-3; Eq. 2 separable DFT, Eq. 1 projection).
+//
+// One CTA owns a line of BY output voxels (t0, x0, y_start .. y_start+BY-1).  It stages the
+// halo brick V[t0-n/2 .. t0+n/2-1][x0-n/2 .. x0+n/2-1][y_start-n/2 .. y_start+BY+n/2-2] in
+// shared memory (border extension applied at load) and runs the separable sliding DFT:
+//   stage 1 (t, real input):  G1[k_t][x][y]  = sum_u c/s(k_t,u) V[t0-n/2+u][x][y],   k_t in [0,n/2]
+//   stage 2 (x, complex):     G2[k_t][k_x][y] = sum_u c/s(k_x,u) G1[k_t][u][y],      k_x in [0,n)
+//   stage 3 (y, complex):     F[k_t][k_x][k_y](y0) = sum_u c/s(k_y,u) G2[k_t][k_x][y0-n/2+u]
+// Hermitian symmetry of a real cube keeps only k_t in [0, n/2] (multiplicity 2 for
+// 0 < k_t < n/2).  Each one-axis DFT pairs bins k and n-k: with P = sum g cos, Q = sum g sin,
+// F[k] = P - iQ and F[n-k] = P + iQ, which halves the multiplies.
+// Stage 3 is fused with the feature epilogue: |F| per bin, weighted by the projection ratios
+// r_m(k) of Eq. 1 (zero at DC), summed over k_y in registers and over (k_t,k_x) rows through
+// shared memory in a fixed order.  Per-voxel spectra never leave the SM.
+#include <cstdio>
+
+#include "sal_internal.cuh"
+
+namespace sal {
+namespace {
+
+template <int N> struct Cfg;
+template <> struct Cfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
+template <> struct Cfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
+template <> struct Cfg<8>  { static constexpr int BY = 32, YC = 4, MINB = 2; };
+template <> struct Cfg<16> { static constexpr int BY = 16, YC = 8, MINB = 2; };
+
+template <int N> struct Tw {
+    float c[N / 2 + 1][N];
+    float s[N / 2 + 1][N];
+};
+
+template <int N> struct Geo {
+    static constexpr int H = N / 2 + 1;
+    static constexpr int BY = Cfg<N>::BY;
+    static constexpr int YC = Cfg<N>::YC;
+    static constexpr int YH = BY + N - 1;          // y extent of the halo brick
+    static constexpr int ROWS = H * N;             // (k_t, k_x) rows of stage 3
+    static constexpr int NT = ROWS * (BY / YC);    // threads per CTA
+    static constexpr int IN_FLOATS = N * N * YH;
+    static constexpr int G_FLOAT2 = H * N * YH;
+    static constexpr int PART_FLOATS = BY * 3 * ROWS;
+    static constexpr size_t A_BYTES_IN = (size_t)IN_FLOATS * 4 + (size_t)G_FLOAT2 * 8;
+    static constexpr size_t A_BYTES = A_BYTES_IN > (size_t)PART_FLOATS * 4 ? A_BYTES_IN : (size_t)PART_FLOATS * 4;
+    static constexpr size_t SMEM = A_BYTES + (size_t)G_FLOAT2 * 8;
+    static_assert(BY % YC == 0, "BY/YC");
+    static_assert(NT <= 1024, "threads");
+};
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
+k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
+               const __grid_constant__ Tw<N> tw) {
+    using G = Geo<N>;
+    constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_in = reinterpret_cast<float*>(smem_raw);                        // [N][N][YH]
+    float2* s_g1 = reinterpret_cast<float2*>(smem_raw + (size_t)G::IN_FLOATS * 4);  // [H][N][YH]
+    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::A_BYTES);         // [H][N][YH]
+    float* s_part = reinterpret_cast<float*>(smem_raw);                      // [BY][3][ROWS] (aliases A)
+
+    const int tid = threadIdx.x;
+    const int y_start = blockIdx.x * BY;
+    const int x0 = blockIdx.y;
+    const int t0 = blockIdx.z;
+
+    // ---- brick staging with border extension -------------------------------------------------
+    for (int idx = tid; idx < G::IN_FLOATS; idx += NT) {
+        int ut = idx / (N * YH);
+        int ux = (idx / YH) % N;
+        int yy = idx % YH;
+        int gt = ext_index(t0 - N / 2 + ut, T, bnd);
+        int gx = ext_index(x0 - N / 2 + ux, X, bnd);
+        int gy = ext_index(y_start - N / 2 + yy, Y, bnd);
+        float v = 0.f;
+        if (gt >= 0 && gx >= 0 && gy >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
+        s_in[idx] = v;
+    }
+    __syncthreads();
+
+    // ---- stage 1: DFT along t of the real cube, bins k_t in [0, n/2] -------------------------
+    for (int it = tid; it < N * YH; it += NT) {
+        const int ux = it / YH, yy = it % YH;
+        float v[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) v[u] = s_in[(u * N + ux) * YH + yy];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float P = 0.f, Q = 0.f;
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+                P = fmaf(v[u], tw.c[k][u], P);
+                Q = fmaf(v[u], tw.s[k][u], Q);
+            }
+            s_g1[(k * N + ux) * YH + yy] = make_float2(P, -Q);
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 2: DFT along x (complex), all k_x --------------------------------------------
+    for (int it = tid; it < H * YH; it += NT) {
+        const int kt = it / YH, yy = it % YH;
+        float2 g[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) g[u] = s_g1[(kt * N + u) * YH + yy];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+                pr = fmaf(g[u].x, tw.c[k][u], pr);
+                pi = fmaf(g[u].y, tw.c[k][u], pi);
+                if (k != 0 && 2 * k != N) {
+                    qr = fmaf(g[u].x, tw.s[k][u], qr);
+                    qi = fmaf(g[u].y, tw.s[k][u], qi);
+                }
+            }
+            s_g2[(kt * N + k) * YH + yy] = make_float2(pr + qi, pi - qr);
+            if (k != 0 && 2 * k != N) s_g2[(kt * N + (N - k)) * YH + yy] = make_float2(pr - qi, pi + qr);
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 3 + projection/feature epilogue ----------------------------------------------
+    const int row = tid % ROWS;           // (k_t, k_x)
+    const int ych = tid / ROWS;           // chunk of YC outputs
+    const int kt = row / N, kx = row % N;
+    float wt[3][H];                       // r_m(k_t,k_x,+-k_y) * multiplicity / n^3
+    {
+        const int i = kt;
+        const int j = kx < N / 2 ? kx : kx - N;
+        const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
+        const float scale = mult / (float)(N * N * N);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float r2 = (float)(i * i + j * j + k * k);
+            if (r2 == 0.f) {
+                wt[0][k] = wt[1][k] = wt[2][k] = 0.f;
+            } else {
+                const float inv = scale / sqrtf(r2);
+                wt[0][k] = sqrtf((float)(j * j + k * k)) * inv;
+                wt[1][k] = sqrtf((float)(i * i + k * k)) * inv;
+                wt[2][k] = sqrtf((float)(i * i + j * j)) * inv;
+            }
+        }
+    }
+    __syncthreads();  // s_part aliases s_in / s_g1
+    const float2* grow = s_g2 + (size_t)row * YH;
+    for (int yl = ych * YC; yl < ych * YC + YC; ++yl) {
+        float pr[H], pi[H], qr[H], qi[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const float2 g = grow[yl + u];
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                pr[k] = fmaf(g.x, tw.c[k][u], pr[k]);
+                pi[k] = fmaf(g.y, tw.c[k][u], pi[k]);
+                if (k != 0 && 2 * k != N) {
+                    qr[k] = fmaf(g.x, tw.s[k][u], qr[k]);
+                    qi[k] = fmaf(g.y, tw.s[k][u], qi[k]);
+                }
+            }
+        }
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float a;
+            if (k == 0 || 2 * k == N) {
+                a = sqrtf(fmaf(pr[k], pr[k], pi[k] * pi[k]));
+            } else {
+                const float ar = pr[k] + qi[k], ai = pi[k] - qr[k];   // F[k]   = P - iQ
+                const float br = pr[k] - qi[k], bi = pi[k] + qr[k];   // F[n-k] = P + iQ
+                a = sqrtf(fmaf(ar, ar, ai * ai)) + sqrtf(fmaf(br, br, bi * bi));
+            }
+            e0 = fmaf(wt[0][k], a, e0);
+            e1 = fmaf(wt[1][k], a, e1);
+            e2 = fmaf(wt[2][k], a, e2);
+        }
+        s_part[(yl * 3 + 0) * ROWS + row] = e0;
+        s_part[(yl * 3 + 1) * ROWS + row] = e1;
+        s_part[(yl * 3 + 2) * ROWS + row] = e2;
+    }
+    __syncthreads();
+
+    // ---- fixed-order reduction over the (k_t, k_x) rows ---------------------------------------
+    const size_t NV = (size_t)T * X * Y;
+    for (int it = tid; it < BY * 3; it += NT) {
+        const int yl = it / 3, m = it % 3;
+        const int y = y_start + yl;
+        if (y >= Y) continue;
+        const float* p = s_part + (size_t)(yl * 3 + m) * ROWS;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        int r = 0;
+        for (; r + 4 <= ROWS; r += 4) {
+            acc0 += p[r];
+            acc1 += p[r + 1];
+            acc2 += p[r + 2];
+            acc3 += p[r + 3];
+        }
+        for (; r < ROWS; ++r) acc0 += p[r];
+        E[m * NV + ((size_t)t0 * X + x0) * Y + y] = (acc0 + acc1) + (acc2 + acc3);
+    }
+}
+
+template <int N>
+Tw<N> make_tw(const TwiddleTable& t) {
+    Tw<N> w;
+    for (int k = 0; k <= N / 2; ++k)
+        for (int u = 0; u < N; ++u) {
+            w.c[k][u] = t.c[k][u];
+            w.s[k][u] = t.s[k][u];
+        }
+    return w;
+}
+
+template <int N>
+cudaError_t prepare() {
+    return cudaFuncSetAttribute(k1_spectra_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Geo<N>::SMEM);
+}
+
+template <int N>
+cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd,
+                   cudaStream_t s) {
+    using G = Geo<N>;
+    dim3 grid((Y + G::BY - 1) / G::BY, X, T);
+    k1_spectra_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, make_tw<N>(t));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool spectra_f32_supported(int n) { return n == 2 || n == 4 || n == 8 || n == 16; }
+
+cudaError_t spectra_f32_prepare(int n) {
+    switch (n) {
+        case 2: return prepare<2>();
+        case 4: return prepare<4>();
+        case 8: return prepare<8>();
+        case 16: return prepare<16>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
+                               int Y, int bnd, cudaStream_t s) {
+    if (T > 65535 || X > 65535) return cudaErrorInvalidConfiguration;
+    switch (n) {
+        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, s);
+        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, s);
+        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, s);
+        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sal

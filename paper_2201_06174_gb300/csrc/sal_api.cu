@@ -1,0 +1,256 @@
+// Host side of the C ABI declared in include/sal.h: parameter validation, handle-owned tables
+// and scratch, and stream-ordered launches of the kernels K1 (local spectra + features),
+// K2 (center-surround) and K3 (normalisation + combination).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sal_internal.cuh"
+
+struct sal_handle {
+    int device = 0;
+    int T = 0, X = 0, Y = 0;
+    long long N = 0;
+    int n = 0, taper = 0, boundary = 0, feature = 0, prec = 0;
+    double ls_delta = 1e-6;
+    size_t budget = 0;
+    sal::Stencil st{};
+    std::vector<float> alpha;
+    sal::TwiddleTable tw{};
+    float* E = nullptr;      // [3][N] feature scratch
+    float* S3 = nullptr;     // [3][N] raw center-surround scratch
+    sal::Reduce red{};
+    void* small = nullptr;   // one allocation holding the reduction scratch
+    size_t bytes = 0;
+    std::string last;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+sal_status fail(sal_handle* h, sal_status s, const std::string& msg) {
+    if (h) h->last = msg; else g_create_error = msg;
+    return s;
+}
+
+sal_status cuda_fail(sal_handle* h, cudaError_t e, const char* where) {
+    return fail(h, SAL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void free_scratch(sal_handle* h) {
+    if (h->E) cudaFree(h->E);
+    if (h->S3) cudaFree(h->S3);
+    if (h->small) cudaFree(h->small);
+    h->E = h->S3 = nullptr;
+    h->small = nullptr;
+}
+
+void build_twiddles(sal_handle* h) {
+    const int n = h->n;
+    h->tw.n = n;
+    for (int k = 0; k <= n / 2; ++k)
+        for (int u = 0; u < n; ++u) {
+            const int m = (k * u) % n;
+            const double hu = h->taper ? 0.5 - 0.5 * std::cos(2.0 * M_PI * u / n) : 1.0;
+            h->tw.c[k][u] = (float)(hu * std::cos(2.0 * M_PI * m / n));
+            h->tw.s[k][u] = (float)(hu * std::sin(2.0 * M_PI * m / n));
+        }
+}
+
+void refresh_weights(sal_handle* h) {
+    for (int o = 0; o < h->st.Q; ++o) h->st.w[o] = h->alpha[h->st.dir[o]] * h->st.g[o];
+}
+
+sal_status check_handle(sal_handle* h) {
+    if (!h) return SAL_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    h->last.clear();
+    return SAL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, SAL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, SAL_ERR_INVALID_ARG, "params is NULL");
+    if (T < 1 || X < 1 || Y < 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "T, X, Y must be >= 1");
+    if (T > 65535 || X > 65535) return fail(nullptr, SAL_ERR_UNSUPPORTED, "T and X must be <= 65535");
+    if (p->n < 2 || (p->n & 1) || p->n > sal::kMaxN)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "n must be even, 2 <= n <= 32");
+    if (p->stride != 1) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only stride 1 is built");
+    if (p->taper != 0 && p->taper != 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "taper must be 0 or 1");
+    if (p->boundary < 0 || p->boundary > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad boundary");
+    if (p->feature != 0) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only feature 0 is built");
+    if (p->prec < 0 || p->prec > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad precision");
+    if (p->prec == SAL_FP32 && !sal::spectra_f32_supported(p->n))
+        return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16}");
+    if (p->prec != SAL_FP32) return fail(nullptr, SAL_ERR_UNSUPPORTED, "precision not built");
+    if (p->n_offsets < 1 || p->n_offsets > sal::kMaxOffsets)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "n_offsets must be in [1, 64]");
+    if (p->n_dirs < 1 || p->n_dirs > sal::kMaxDirs)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "n_dirs must be in [1, 16]");
+    if (!p->offsets || !p->gauss_w || !p->dir_id || !p->alpha)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "stencil arrays must not be NULL");
+    if (!(p->ls_delta >= 0.0) || !std::isfinite(p->ls_delta))
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "ls_delta must be finite and >= 0");
+
+    sal_handle* h = new sal_handle();
+    h->T = T; h->X = X; h->Y = Y;
+    h->N = (long long)T * X * Y;
+    h->n = p->n; h->taper = p->taper; h->boundary = p->boundary; h->feature = p->feature;
+    h->prec = p->prec; h->ls_delta = p->ls_delta; h->budget = p->hbm_budget_bytes;
+    h->st.Q = p->n_offsets;
+    h->st.n_dirs = p->n_dirs;
+    h->st.invQ = 1.0f / (float)p->n_offsets;
+    for (int o = 0; o < p->n_offsets; ++o) {
+        for (int a = 0; a < 3; ++a) {
+            const int v = p->offsets[3 * o + a];
+            if (v < -sal::kMaxHalo || v > sal::kMaxHalo) {
+                delete h;
+                return fail(nullptr, SAL_ERR_INVALID_ARG, "stencil offset component beyond +-8");
+            }
+            h->st.off[o][a] = v;
+        }
+        if (p->dir_id[o] < 0 || p->dir_id[o] >= p->n_dirs) {
+            delete h;
+            return fail(nullptr, SAL_ERR_INVALID_ARG, "dir_id out of range");
+        }
+        if (!std::isfinite(p->gauss_w[o])) {
+            delete h;
+            return fail(nullptr, SAL_ERR_INVALID_ARG, "gauss_w must be finite");
+        }
+        h->st.dir[o] = p->dir_id[o];
+        h->st.g[o] = p->gauss_w[o];
+    }
+    h->alpha.assign(p->alpha, p->alpha + p->n_dirs);
+    for (float a : h->alpha)
+        if (!std::isfinite(a)) {
+            delete h;
+            return fail(nullptr, SAL_ERR_INVALID_ARG, "alpha must be finite");
+        }
+    refresh_weights(h);
+    build_twiddles(h);
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    e = sal::spectra_f32_prepare(h->n);
+    if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
+
+    const size_t plane3 = (size_t)3 * h->N * sizeof(float);
+    const size_t small = (size_t)sal::kRedBlocks * 8 * sizeof(float) + (size_t)sal::kRedBlocks * 16 * sizeof(double)
+                         + 16 * sizeof(float) + 16 * sizeof(double) + 256;
+    const size_t need = 2 * plane3 + small;
+    if (h->budget && need > h->budget) {
+        delete h;
+        return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
+    }
+    if ((e = cudaMalloc(&h->E, plane3)) != cudaSuccess || (e = cudaMalloc(&h->S3, plane3)) != cudaSuccess ||
+        (e = cudaMalloc(&h->small, small)) != cudaSuccess) {
+        free_scratch(h);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    char* b = static_cast<char*>(h->small);
+    h->red.g_part = reinterpret_cast<double*>(b);
+    b += (size_t)sal::kRedBlocks * 16 * sizeof(double);
+    h->red.wsum = reinterpret_cast<double*>(b);
+    b += 16 * sizeof(double);
+    h->red.mm_part = reinterpret_cast<float*>(b);
+    b += (size_t)sal::kRedBlocks * 8 * sizeof(float);
+    h->red.norm = reinterpret_cast<float*>(b);
+    h->bytes = need;
+    *out = h;
+    return SAL_OK;
+}
+
+sal_status sal_destroy(sal_handle* h) {
+    if (!h) return SAL_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    free_scratch(h);
+    delete h;
+    return SAL_OK;
+}
+
+sal_status sal_workspace_size(const sal_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SAL_ERR_INVALID_ARG;
+    *bytes = h->bytes;
+    return SAL_OK;
+}
+
+sal_status sal_set_alpha(sal_handle* h, const float* alpha) {
+    if (!h) return SAL_ERR_INVALID_ARG;
+    if (!alpha) return fail(h, SAL_ERR_INVALID_ARG, "alpha is NULL");
+    for (int d = 0; d < h->st.n_dirs; ++d)
+        if (!std::isfinite(alpha[d])) return fail(h, SAL_ERR_INVALID_ARG, "alpha must be finite");
+    h->alpha.assign(alpha, alpha + h->st.n_dirs);
+    refresh_weights(h);
+    return SAL_OK;
+}
+
+sal_status sal_local_spectra_project(sal_handle* h, const float* V, float* E, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!V || !E) return fail(h, SAL_ERR_INVALID_ARG, "V and E must not be NULL");
+    cudaError_t e = sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
+                                            static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "local_spectra_project launch");
+}
+
+sal_status sal_center_surround(sal_handle* h, const float* E, float* S3, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!E || !S3) return fail(h, SAL_ERR_INVALID_ARG, "E and S3 must not be NULL");
+    cudaError_t e = sal::dcs_launch(E, S3, h->T, h->X, h->Y, h->boundary, h->st, h->red.mm_part,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "center_surround launch");
+}
+
+sal_status sal_combine(sal_handle* h, const float* S3, const float* D, const float* W_in, float* W_out, float* S,
+                       void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!S3 || !S) return fail(h, SAL_ERR_INVALID_ARG, "S3 and S must not be NULL");
+    cudaError_t e = sal::combine_launch(S3, D, W_in, W_out, S, h->N, h->ls_delta, false, h->red,
+                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "combine launch");
+}
+
+sal_status sal_saliency(sal_handle* h, const float* V, const float* D, const float* W_in, float* S, float* S3_opt,
+                        float* E_opt, float* W_out, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!V || !S) return fail(h, SAL_ERR_INVALID_ARG, "V and S must not be NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* E = E_opt ? E_opt : h->E;
+    float* S3 = S3_opt ? S3_opt : h->S3;
+    cudaError_t e = sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "local_spectra_project launch");
+    e = sal::dcs_launch(E, S3, h->T, h->X, h->Y, h->boundary, h->st, h->red.mm_part, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "center_surround launch");
+    e = sal::combine_launch(S3, D, W_in, W_out, S, h->N, h->ls_delta, true, h->red, st);
+    return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "combine launch");
+}
+
+sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, const float* gS, float* gV,
+                                 float* gW, float* galpha, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    (void)V; (void)W; (void)gS; (void)gV; (void)gW; (void)galpha; (void)stream;
+    return fail(h, SAL_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+const char* sal_last_error(const sal_handle* h) {
+    return h ? h->last.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal declarations shared by the libsal.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sal.h"
+
+namespace sal {
+
+constexpr int kMaxOffsets = 64;
+constexpr int kMaxDirs = 16;
+constexpr int kMaxHalo = 8;      // |dt|,|dx|,|dy| bound of a center-surround offset
+constexpr int kMaxN = 32;        // largest DFT side the tables hold
+constexpr int kRedBlocks = 1216; // 152 SMs x 8: grid of the grid-stride reduction kernels
+
+// Center-surround window of Eq. 3, passed by value as a kernel parameter.
+struct Stencil {
+    int Q;
+    int n_dirs;
+    float invQ;
+    int off[kMaxOffsets][3];
+    float g[kMaxOffsets];     // Gaussian factor of each neighbour
+    int dir[kMaxOffsets];     // direction group
+    float w[kMaxOffsets];     // effective weight alpha[dir] * g
+};
+
+// Real DFT twiddles with the taper folded in: c[k][u] = h(u) cos(2 pi k u / n),
+// s[k][u] = h(u) sin(2 pi k u / n), for k in [0, n/2], u in [0, n).
+struct TwiddleTable {
+    int n;
+    float c[kMaxN / 2 + 1][kMaxN];
+    float s[kMaxN / 2 + 1][kMaxN];
+};
+
+enum : int { BND_SYMMETRIC = 0, BND_PERIODIC = 1, BND_ZERO = 2 };
+
+// Border extension of one axis; -1 where the zero extension applies.
+__host__ __device__ __forceinline__ int ext_index(int i, int n, int mode) {
+    if ((unsigned)i < (unsigned)n) return i;
+    if (mode == BND_PERIODIC) {
+        int r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    if (mode == BND_ZERO) return -1;
+    int P = 2 * n;  // symmetric, edge sample repeated
+    int r = i % P;
+    if (r < 0) r += P;
+    return r < n ? r : P - 1 - r;
+}
+
+// Scratch for the volume-wide reductions (device memory owned by the handle).
+struct Reduce {
+    float* mm_part;     // [kRedBlocks][8]  per-block min/max partials
+    double* g_part;     // [kRedBlocks][16] per-block FP64 partial sums
+    float* norm;        // [16]: lo[3], inv[3], W[3], loC, invC, flags
+    double* wsum;       // [16]: reduced FP64 sums (Gram, gradient of W)
+};
+
+// ---- K1: local spectra + projection + features ----------------------------------------------
+bool spectra_f32_supported(int n);
+cudaError_t spectra_f32_prepare(int n);
+cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
+                               int Y, int bnd, cudaStream_t s);
+
+// ---- K2: directional center-surround ----------------------------------------------------------
+cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, const Stencil& st,
+                       float* mm_part, cudaStream_t s);
+
+// ---- K3: normalisation + combination ----------------------------------------------------------
+int red_blocks(long long NV);  // grid of the grid-stride reduction kernels (<= kRedBlocks)
+cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, float* W_out, float* S,
+                           long long N, double delta, bool s3_partials_ready, const Reduce& r, cudaStream_t s);
+
+}  // namespace sal

@@ -1,0 +1,279 @@
+"""Thin Python binding of libsal.so (the C ABI in include/sal.h).
+
+Argument marshalling only: every step of the saliency path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  The functions keep the
+C names (sal_create, sal_local_spectra_project, ...); `Saliency` is a small convenience
+wrapper that owns a handle and allocates the outputs.
+
+There is no CPU fallback: if libsal.so cannot be built or loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsal.so")
+
+SAL_OK, SAL_ERR_INVALID_ARG, SAL_ERR_UNSUPPORTED, SAL_ERR_OOM, SAL_ERR_CUDA, SAL_ERR_TIMEOUT, \
+    SAL_ERR_DEVICE_CHECK = range(7)
+STATUS_NAMES = ["SAL_OK", "SAL_ERR_INVALID_ARG", "SAL_ERR_UNSUPPORTED", "SAL_ERR_OOM", "SAL_ERR_CUDA",
+                "SAL_ERR_TIMEOUT", "SAL_ERR_DEVICE_CHECK"]
+PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
+BOUNDARY = {"symmetric": 0, "periodic": 1, "zero": 2}
+TAPER = {"rect": 0, "hann": 1}
+
+# Exported entry points (must match include/sal.h).
+ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
+                "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error")
+
+
+class SalError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class sal_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("stride", ctypes.c_int), ("taper", ctypes.c_int),
+                ("boundary", ctypes.c_int), ("feature", ctypes.c_int), ("n_offsets", ctypes.c_int),
+                ("offsets", ctypes.POINTER(ctypes.c_int)), ("gauss_w", ctypes.POINTER(ctypes.c_float)),
+                ("dir_id", ctypes.POINTER(ctypes.c_int)), ("n_dirs", ctypes.c_int),
+                ("alpha", ctypes.POINTER(ctypes.c_float)), ("prec", ctypes.c_int),
+                ("ls_delta", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libsal.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise SalError(SAL_ERR_UNSUPPORTED, f"{LIB_PATH} is missing (CUDA extension not built)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    L.sal_create.argtypes = [ctypes.POINTER(sal_params), i, i, i, ctypes.POINTER(vp)]
+    L.sal_destroy.argtypes = [vp]
+    L.sal_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.sal_set_alpha.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.sal_local_spectra_project.argtypes = [vp, vp, vp, vp]
+    L.sal_center_surround.argtypes = [vp, vp, vp, vp]
+    L.sal_combine.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.sal_saliency.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.sal_saliency_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.sal_last_error.argtypes = [vp]
+    L.sal_last_error.restype = ctypes.c_char_p
+    for name in ENTRY_POINTS:
+        if name != "sal_last_error":
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _check(status: int, handle=None):
+    if status != SAL_OK:
+        msg = load().sal_last_error(handle).decode()
+        raise SalError(status, msg)
+
+
+# ------------------------------------------------------------------------------------------------
+# Parameters and the default directional window (Fig. 4: t, x and t-x directions)
+# ------------------------------------------------------------------------------------------------
+
+def directional_window(directions: Sequence[Sequence[int]] = ((1, 0, 0), (0, 1, 0), (1, 1, 0)), R: int = 3,
+                       sigma: float = 1.5):
+    """Neighbour offsets s*d for s in +-1..+-R along each direction d, their Gaussian factors
+    exp(-|o|^2 / (2 sigma^2)) and direction ids."""
+    offs, g, did = [], [], []
+    for di, d in enumerate(directions):
+        for s in range(-R, R + 1):
+            if s == 0:
+                continue
+            o = [s * int(c) for c in d]
+            offs.append(o)
+            g.append(math.exp(-float(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) / (2.0 * sigma * sigma)))
+            did.append(di)
+    return np.asarray(offs, np.int32), np.asarray(g, np.float32), np.asarray(did, np.int32)
+
+
+@dataclasses.dataclass
+class Params:
+    n: int = 16
+    boundary: str = "symmetric"
+    taper: str = "rect"
+    directions: Tuple[Tuple[int, int, int], ...] = ((1, 0, 0), (0, 1, 0), (1, 1, 0))
+    R: int = 3
+    sigma: float = 1.5
+    alpha: Optional[Sequence[float]] = None
+    prec: str = "fp32"
+    ls_delta: float = 1e-6
+    hbm_budget_bytes: int = 0
+    offsets: Optional[np.ndarray] = None   # explicit window overrides directions/R/sigma
+    gauss_w: Optional[np.ndarray] = None
+    dir_id: Optional[np.ndarray] = None
+
+    def window(self):
+        if self.offsets is not None:
+            return (np.ascontiguousarray(self.offsets, np.int32).reshape(-1, 3),
+                    np.ascontiguousarray(self.gauss_w, np.float32), np.ascontiguousarray(self.dir_id, np.int32))
+        return directional_window(self.directions, self.R, self.sigma)
+
+
+def sal_create(params: Params, shape: Sequence[int]):
+    """Creates a handle on the current CUDA device and returns it."""
+    L = load()
+    offs, g, did = params.window()
+    ndirs = int(did.max()) + 1 if len(did) else 0
+    alpha = np.ones(ndirs, np.float32) if params.alpha is None else np.ascontiguousarray(params.alpha, np.float32)
+    p = sal_params(n=params.n, stride=1, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary], feature=0,
+                   n_offsets=len(g), offsets=offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                   gauss_w=g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                   dir_id=did.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n_dirs=len(alpha),
+                   alpha=alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), prec=PRECISION[params.prec],
+                   ls_delta=params.ls_delta, hbm_budget_bytes=params.hbm_budget_bytes)
+    h = ctypes.c_void_p()
+    T, X, Y = (int(s) for s in shape)
+    _check(L.sal_create(ctypes.byref(p), T, X, Y, ctypes.byref(h)), None)
+    return h
+
+
+def sal_destroy(h):
+    if h:
+        load().sal_destroy(h)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def sal_local_spectra_project(h, V, E, stream=None):
+    _check(load().sal_local_spectra_project(h, _ptr(V), _ptr(E), _stream(stream)), h)
+
+
+def sal_center_surround(h, E, S3, stream=None):
+    _check(load().sal_center_surround(h, _ptr(E), _ptr(S3), _stream(stream)), h)
+
+
+def sal_combine(h, S3, D, W_in, W_out, S, stream=None):
+    _check(load().sal_combine(h, _ptr(S3), _ptr(D), _ptr(W_in), _ptr(W_out), _ptr(S), _stream(stream)), h)
+
+
+def sal_saliency(h, V, D, W_in, S, S3_opt=None, E_opt=None, W_out=None, stream=None):
+    _check(load().sal_saliency(h, _ptr(V), _ptr(D), _ptr(W_in), _ptr(S), _ptr(S3_opt), _ptr(E_opt), _ptr(W_out),
+                               _stream(stream)), h)
+
+
+def sal_saliency_backward(h, V, W, gS, gV=None, gW=None, galpha=None, stream=None):
+    _check(load().sal_saliency_backward(h, _ptr(V), _ptr(W), _ptr(gS), _ptr(gV), _ptr(gW), _ptr(galpha),
+                                        _stream(stream)), h)
+
+
+def sal_set_alpha(h, alpha):
+    a = np.ascontiguousarray(alpha, np.float32)
+    _check(load().sal_set_alpha(h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), h)
+
+
+def sal_workspace_size(h) -> int:
+    b = ctypes.c_size_t()
+    _check(load().sal_workspace_size(h, ctypes.byref(b)), h)
+    return int(b.value)
+
+
+class Saliency:
+    """Owns a handle for one volume shape; allocates outputs with torch on the handle's device."""
+
+    def __init__(self, shape: Sequence[int], params: Optional[Params] = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise SalError(SAL_ERR_CUDA, "no CUDA device: the saliency path runs only on the GPU")
+        self.params = params or Params()
+        self.shape = tuple(int(s) for s in shape)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.h = sal_create(self.params, self.shape)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *lead):
+        import torch
+        return torch.empty(lead + self.shape, dtype=torch.float32, device=self.device)
+
+    def _in(self, t):
+        import torch
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor):
+            t = torch.as_tensor(np.ascontiguousarray(t, np.float32))
+        return t.to(self.device, torch.float32).contiguous()
+
+    def local_spectra_project(self, V):
+        E = self._empty(3)
+        sal_local_spectra_project(self.h, self._in(V), E)
+        return E
+
+    def center_surround(self, E):
+        S3 = self._empty(3)
+        sal_center_surround(self.h, self._in(E), S3)
+        return S3
+
+    def combine(self, S3, D=None, W=None):
+        import torch
+        S = self._empty()
+        W_out = torch.empty(3, dtype=torch.float32, device=self.device)
+        sal_combine(self.h, self._in(S3), self._in(D), self._in(W), W_out, S)
+        return S, W_out
+
+    def saliency(self, V, D=None, W=None, intermediates: bool = False) -> Dict[str, "torch.Tensor"]:
+        import torch
+        S = self._empty()
+        W_out = torch.empty(3, dtype=torch.float32, device=self.device)
+        E = self._empty(3) if intermediates else None
+        S3 = self._empty(3) if intermediates else None
+        sal_saliency(self.h, self._in(V), self._in(D), self._in(W), S, S3, E, W_out)
+        out = {"S": S, "W": W_out}
+        if intermediates:
+            out.update({"E": E, "S3": S3})
+        return out
+
+    def backward(self, V, W, gS):
+        import torch
+        gV = self._empty()
+        gW = torch.empty(3, dtype=torch.float32, device=self.device)
+        nd = len(self.params.window()[2]) and int(self.params.window()[2].max()) + 1
+        galpha = torch.empty(nd, dtype=torch.float32, device=self.device)
+        sal_saliency_backward(self.h, self._in(V), self._in(W), self._in(gS), gV, gW, galpha)
+        return gV, gW, galpha
+
+    def set_alpha(self, alpha):
+        sal_set_alpha(self.h, alpha)
+
+
+def sal_last_error_text(h=None) -> str:
+    """sal_last_error: message of the last error on the handle (or of the last sal_create)."""
+    return load().sal_last_error(h).decode()
