@@ -129,6 +129,22 @@ sal_status sal_saliency(sal_handle* h, const float* V, const float* D, const flo
 sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, const float* gS,
                                  float* gV, float* gW, float* galpha, void* stream);
 
+/* Allocation-free form of sal_combine, for callers that cannot allocate device memory: code
+ * that runs under a caller-owned memory pool or arena, inside a region where new allocations
+ * are forbidden, or on a path where an allocation and the synchronisation it may bring are not
+ * acceptable.  It needs no handle (sal_create allocates) and calls no cudaMalloc or cudaFree.
+ * The paper has no counterpart: this is a deployment form of the step 5 combination above,
+ * with the same arguments and results (ls_delta as in sal_params).
+ * Its reduction scratch is one file-scope device array of about 0.6 MiB that every GPU that
+ * loads the library holds until the process exits.  Limit: T*X*Y <= 16,777,216 voxels; larger
+ * volumes return SAL_ERR_UNSUPPORTED before any work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and give wrong results.  Errors are reported by
+ * sal_last_error(NULL). */
+sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
+                               double ls_delta, float* W_out, float* S, void* stream);
+
 /* Message of the last error on the handle ("" if none).  h may be NULL (then the
  * last sal_create error of this thread is returned).  The string lives until the
  * next call on the handle. */

@@ -7,6 +7,9 @@
 //   S    = minmax(sum_m W_m S^_m).
 // All passes are grid-stride, HBM-bound and deterministic (no floating-point atomics).
 #include <cfloat>
+#include <cmath>
+#include <mutex>
+#include <string>
 
 #include "sal_internal.cuh"
 
@@ -228,3 +231,102 @@ cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, f
 }
 
 }  // namespace sal
+
+// ---- Allocation-free combination --------------------------------------------------------------
+// sal_combine_noalloc runs the same K3 kernels as sal_combine, but its reduction scratch is a
+// file-scope device array instead of memory the handle obtains from cudaMalloc.  It serves
+// callers that must not allocate device memory: code running under a caller-owned memory pool
+// or arena, inside a region that forbids new allocations, or on a path where an allocation
+// (and the implicit synchronisation it can bring) is not acceptable.
+namespace {
+
+constexpr long long kNoAllocVoxPerBlock = 4096;  // 256 threads x 16 voxels per partial slot
+constexpr int kNoAllocSlots = 4096;              // partial slots held by the static array
+constexpr long long kNoAllocMaxVoxels = kNoAllocVoxPerBlock * kNoAllocSlots;  // 16,777,216
+
+struct NoAllocScratch {
+    double g_part[kNoAllocSlots * 16];
+    double wsum[16];
+    float mm_part[kNoAllocSlots * 8];
+    float norm[16];
+};
+
+// Host code must not use this name as a device address: on the host it is only a stand-in.
+// The device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+extern "C" sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
+                                          double ls_delta, float* W_out, float* S, void* stream) {
+    if (T < 1 || X < 1 || Y < 1) {
+        sal::set_unbound_error("sal_combine_noalloc: T, X, Y must be >= 1");
+        return SAL_ERR_INVALID_ARG;
+    }
+    const long long N = (long long)T * X * Y;
+    if (N > kNoAllocMaxVoxels) {
+        sal::set_unbound_error("sal_combine_noalloc: volume of " + std::to_string(N) +
+                               " voxels exceeds the static scratch limit of 16777216 voxels");
+        return SAL_ERR_UNSUPPORTED;
+    }
+    if (!S3 || !S) {
+        sal::set_unbound_error("sal_combine_noalloc: S3 and S must not be NULL");
+        return SAL_ERR_INVALID_ARG;
+    }
+    if (!(ls_delta >= 0.0) || !std::isfinite(ls_delta)) {
+        sal::set_unbound_error("sal_combine_noalloc: ls_delta must be finite and >= 0");
+        return SAL_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        sal::set_unbound_error(std::string("sal_combine_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+        return SAL_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        sal::set_unbound_error("sal_combine_noalloc: device ordinal beyond 63");
+        return SAL_ERR_UNSUPPORTED;
+    }
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                sal::set_unbound_error(std::string("sal_combine_noalloc: cudaGetSymbolAddress: ") +
+                                       cudaGetErrorString(e));
+                return SAL_ERR_CUDA;
+            }
+        }
+        base = g_noalloc_addr[dev];
+    }
+    NoAllocScratch* scr = static_cast<NoAllocScratch*>(base);
+    sal::Reduce r{};
+    r.mm_part = scr->mm_part;
+    r.g_part = scr->g_part;
+    r.norm = scr->norm;
+    r.wsum = scr->wsum;
+    // Every partial slot a kernel reads was written earlier in this call, so the leftovers
+    // of a previous call need no clearing.
+    const int nb = (int)((N + kNoAllocVoxPerBlock - 1) / kNoAllocVoxPerBlock);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    sal::k3_minmax3<<<nb, sal::kThreads, 0, s>>>(S3, N, r.mm_part);
+    sal::k3_minmax_finalize<<<1, sal::kThreads, 0, s>>>(r.mm_part, nb, 3, r.norm + sal::N_LO, r.norm + sal::N_INV);
+    const int mode = D ? 2 : (W_in ? 1 : 0);
+    if (mode == 2) sal::k3_gram<<<nb, sal::kThreads, 0, s>>>(S3, D, N, r.norm, r.g_part);
+    sal::k3_weights<<<1, sal::kThreads, 0, s>>>(r.g_part, nb, W_in, mode, ls_delta, r.norm, W_out, r.wsum);
+    sal::k3_combine<<<nb, sal::kThreads, 0, s>>>(S3, N, r.norm, S, r.mm_part);
+    sal::k3_minmax_finalize<<<1, sal::kThreads, 0, s>>>(r.mm_part, nb, 1, r.norm + sal::N_LOC, r.norm + sal::N_INVC);
+    sal::k3_normalize<<<nb, sal::kThreads, 0, s>>>(S, N, r.norm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        sal::set_unbound_error(std::string("sal_combine_noalloc: launch: ") + cudaGetErrorString(e));
+        return SAL_ERR_CUDA;
+    }
+    return SAL_OK;
+}

@@ -74,6 +74,8 @@ sal_status check_handle(sal_handle* h) {
 
 }  // namespace
 
+void sal::set_unbound_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out) {

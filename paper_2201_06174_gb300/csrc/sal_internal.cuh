@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "sal.h"
 
 namespace sal {
@@ -71,5 +73,8 @@ cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, 
 int red_blocks(long long NV);  // grid of the grid-stride reduction kernels (<= kRedBlocks)
 cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, float* W_out, float* S,
                            long long N, double delta, bool s3_partials_ready, const Reduce& r, cudaStream_t s);
+
+// Message for sal_last_error(NULL) from entry points that have no handle.
+void set_unbound_error(const std::string& msg);
 
 }  // namespace sal

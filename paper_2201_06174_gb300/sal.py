@@ -31,7 +31,8 @@ TAPER = {"rect": 0, "hann": 1}
 
 # Exported entry points (must match include/sal.h).
 ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
-                "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error")
+                "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
+                "sal_combine_noalloc")
 
 
 class SalError(RuntimeError):
@@ -73,6 +74,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_combine.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.sal_saliency.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.sal_saliency_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.sal_combine_noalloc.argtypes = [i, i, i, vp, vp, vp, ctypes.c_double, vp, vp, vp]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -184,6 +186,13 @@ def sal_saliency(h, V, D, W_in, S, S3_opt=None, E_opt=None, W_out=None, stream=N
 def sal_saliency_backward(h, V, W, gS, gV=None, gW=None, galpha=None, stream=None):
     _check(load().sal_saliency_backward(h, _ptr(V), _ptr(W), _ptr(gS), _ptr(gV), _ptr(gW), _ptr(galpha),
                                         _stream(stream)), h)
+
+
+def sal_combine_noalloc(S3, D, W_in, W_out, S, ls_delta: float = 1e-6, stream=None):
+    """Allocation-free combination (no handle, no device allocation); S3 is [3][T][X][Y]."""
+    T, X, Y = (int(v) for v in S3.shape[1:])
+    _check(load().sal_combine_noalloc(T, X, Y, _ptr(S3), _ptr(D), _ptr(W_in), float(ls_delta), _ptr(W_out), _ptr(S),
+                                      _stream(stream)), None)
 
 
 def sal_set_alpha(h, alpha):
