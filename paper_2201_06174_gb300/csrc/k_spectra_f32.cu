@@ -20,6 +20,14 @@
 namespace sal {
 namespace {
 
+// Square root on the MUFU pipe (sqrt.approx: one instruction, relative error about 2^-22,
+// far inside the 1e-5 budget of the FP32 form).
+__device__ __forceinline__ float fast_sqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int N> struct Cfg;
 template <> struct Cfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
 template <> struct Cfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
@@ -46,6 +54,7 @@ template <int N> struct Geo {
     static constexpr size_t SMEM = A_BYTES + (size_t)G_FLOAT2 * 8;
     static_assert(BY % YC == 0, "BY/YC");
     static_assert(NT <= 1024, "threads");
+    static_assert(NT % 32 == 0 && NT >= YH, "halo load mapping");
 };
 
 template <int N>
@@ -66,16 +75,22 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     const int t0 = blockIdx.z;
 
     // ---- brick staging with border extension -------------------------------------------------
-    for (int idx = tid; idx < G::IN_FLOATS; idx += NT) {
-        int ut = idx / (N * YH);
-        int ux = (idx / YH) % N;
-        int yy = idx % YH;
-        int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-        int gx = ext_index(x0 - N / 2 + ux, X, bnd);
-        int gy = ext_index(y_start - N / 2 + yy, Y, bnd);
-        float v = 0.f;
-        if (gt >= 0 && gx >= 0 && gy >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-        s_in[idx] = v;
+    {
+        // thread -> (y position, first row); rows (u_t, u_x) advance by NT / YH per trip
+        constexpr int RSTEP = NT / YH;
+        const int yy = tid % YH;
+        const int r0 = tid / YH;
+        const int gy = ext_index(y_start - N / 2 + yy, Y, bnd);
+        if (r0 < RSTEP) {
+            for (int r = r0; r < N * N; r += RSTEP) {
+                const int ut = r / N, ux = r % N;
+                const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
+                const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
+                float v = 0.f;
+                if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
+                s_in[r * YH + yy] = v;
+            }
+        }
     }
     __syncthreads();
 
@@ -169,11 +184,11 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
         for (int k = 0; k < H; ++k) {
             float a;
             if (k == 0 || 2 * k == N) {
-                a = sqrtf(fmaf(pr[k], pr[k], pi[k] * pi[k]));
+                a = fast_sqrt(fmaf(pr[k], pr[k], pi[k] * pi[k]));
             } else {
                 const float ar = pr[k] + qi[k], ai = pi[k] - qr[k];   // F[k]   = P - iQ
                 const float br = pr[k] - qi[k], bi = pi[k] + qr[k];   // F[n-k] = P + iQ
-                a = sqrtf(fmaf(ar, ar, ai * ai)) + sqrtf(fmaf(br, br, bi * bi));
+                a = fast_sqrt(fmaf(ar, ar, ai * ai)) + fast_sqrt(fmaf(br, br, bi * bi));
             }
             e0 = fmaf(wt[0][k], a, e0);
             e1 = fmaf(wt[1][k], a, e1);
@@ -187,21 +202,16 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
 
     // ---- fixed-order reduction over the (k_t, k_x) rows ---------------------------------------
     const size_t NV = (size_t)T * X * Y;
-    for (int it = tid; it < BY * 3; it += NT) {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int it = warp; it < BY * 3; it += NT / 32) {
         const int yl = it / 3, m = it % 3;
-        const int y = y_start + yl;
-        if (y >= Y) continue;
         const float* p = s_part + (size_t)(yl * 3 + m) * ROWS;
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-        int r = 0;
-        for (; r + 4 <= ROWS; r += 4) {
-            acc0 += p[r];
-            acc1 += p[r + 1];
-            acc2 += p[r + 2];
-            acc3 += p[r + 3];
-        }
-        for (; r < ROWS; ++r) acc0 += p[r];
-        E[m * NV + ((size_t)t0 * X + x0) * Y + y] = (acc0 + acc1) + (acc2 + acc3);
+        float acc = 0.f;
+        for (int r = lane; r < ROWS; r += 32) acc += p[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int y = y_start + yl;
+        if (lane == 0 && y < Y) E[m * NV + ((size_t)t0 * X + x0) * Y + y] = acc;
     }
 }
 
