@@ -145,6 +145,28 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
 sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
                                double ls_delta, float* W_out, float* S, void* stream);
 
+/* Stepwise backward calls (adjoints of the three forward steps; the fused call above is
+ * their composition).  The paper has no backward pass: these follow from Eq. 1-4.
+ *
+ * sal_local_spectra_project_backward: gV = (dE/dV)^T gE for E = sal_local_spectra_project(V):
+ *   gVext[p + u - n/2] += Re sum_k h(u) exp(+2 pi i k.u / n) (sum_m gE_m[p] r_m(k)/n^3) F_p[k]/|F_p[k]|
+ *   folded back through the border extension.  V, gV: [T][X][Y]; gE: [3][T][X][Y].
+ *   The first backward call on a handle allocates its backward scratch. */
+sal_status sal_local_spectra_project_backward(sal_handle* h, const float* V, const float* gE, float* gV,
+                                              void* stream);
+
+/* sal_center_surround_backward: adjoint of Eq. 3 with respect to E and the per-direction
+ * weights: gE = (dS3/dE)^T gS3 (nullable), galpha[d] = sum_{o in d} gauss_w[o] dL/dw_o
+ * (nullable).  sgn(0) = 0 at the kinks of |.|.  E, gS3, gE: [3][T][X][Y]. */
+sal_status sal_center_surround_backward(sal_handle* h, const float* E, const float* gS3, float* gE, float* galpha,
+                                        void* stream);
+
+/* sal_combine_backward: adjoint of Eq. 4 and the two min-max normalisations (bounds held
+ * constant) for S = sal_combine(S3, W): gS3[m] = W_m gS / ((max C - min C)(max S_m - min S_m)),
+ * gW (nullable, device [3]).  S3, gS3: [3][T][X][Y]; W: device [3]; gS: [T][X][Y]. */
+sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, const float* gS, float* gS3,
+                                float* gW, void* stream);
+
 /* Message of the last error on the handle ("" if none).  h may be NULL (then the
  * last sal_create error of this thread is returned).  The string lives until the
  * next call on the handle. */

@@ -297,6 +297,55 @@ def saliency(V, n: int, boundary="symmetric", taper="rect", stencil=None, weight
 # Gradient (analytic adjoint; normalisation bounds held constant)
 # ----------------------------------------------------------------------------------------------
 
+def combine_backward(fwd, W, gS):
+    """Adjoint of the normalisations and Eq. 4 with the forward bounds held constant:
+    returns (gS3 [3][T][X][Y], gW [3])."""
+    W = np.asarray(W, dtype=np.float64)
+    gS = _f64(gS)
+    spanC = fwd["hiC"] - fwd["loC"]
+    gC = gS / spanC if spanC > 1e-30 * max(1.0, abs(fwd["hiC"])) else np.zeros_like(gS)
+    gW = np.array([np.sum(gC * fwd["Shat"][m]) for m in range(3)])
+    gS3 = np.empty((3,) + gS.shape)
+    for m in range(3):
+        span = fwd["hi"][m] - fwd["lo"][m]
+        gS3[m] = W[m] * gC / span if span > 1e-30 * max(1.0, abs(fwd["hi"][m])) else 0.0
+    return gS3, gW
+
+
+def center_surround_adjoint(E, gS3, offsets, w, boundary="symmetric"):
+    """Adjoint of Eq. 3: returns (gE [3][T][X][Y], gw [Q]) with gw the gradient of each
+    neighbour weight w_o."""
+    E = _f64(E)
+    gS3 = _f64(gS3)
+    gE = np.empty_like(E)
+    wv = _f64(w)
+    gw = np.empty(len(wv), dtype=np.float64)
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    _check(lib().sal_oracle_center_surround_adjoint(_dp(E), *E.shape[1:], BOUNDARY[boundary], len(wv),
+                                                    offs.ctypes.data_as(_c_int_p), _dp(wv), _dp(gS3),
+                                                    _dp(gE), _dp(gw)), "center_surround_adjoint")
+    return gE, gw
+
+
+def direction_gradient(gw, g, did):
+    """galpha_d = sum_{o in direction d} g_o gw_o  (w_o = alpha_d g_o)."""
+    ndir = int(np.max(did)) + 1
+    galpha = np.zeros(ndir)
+    for o in range(len(gw)):
+        galpha[did[o]] += gw[o] * g[o]
+    return galpha
+
+
+def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
+    """gV = (dE/dV)^T gE through the extension (adjoint of the feature step)."""
+    V64 = _f64(V)
+    gE = _f64(gE)
+    gV = np.empty_like(V64)
+    _check(lib().sal_oracle_features_adjoint(_dp(V64), *V64.shape, n, BOUNDARY[boundary], TAPER[taper],
+                                             _dp(gE), _dp(gV), threads), "features_adjoint")
+    return gV
+
+
 def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", stencil=None, fwd=None,
                       threads: int = 0) -> Dict[str, np.ndarray]:
     """Gradients of sum_p gS_p S_p with respect to V, the 3 weights W and the per-direction
@@ -307,28 +356,8 @@ def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", sten
     W = np.asarray(W, dtype=np.float64)
     if fwd is None:
         fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads)
-    gS = _f64(gS)
-    spanC = fwd["hiC"] - fwd["loC"]
-    gC = gS / spanC if spanC > 1e-30 * max(1.0, abs(fwd["hiC"])) else np.zeros_like(gS)
-    gW = np.array([np.sum(gC * fwd["Shat"][m]) for m in range(3)])
-    gS3 = np.empty((3,) + gS.shape)
-    for m in range(3):
-        span = fwd["hi"][m] - fwd["lo"][m]
-        gS3[m] = W[m] * gC / span if span > 1e-30 * max(1.0, abs(fwd["hi"][m])) else 0.0
-    E = _f64(fwd["E"])
-    gE = np.empty_like(E)
-    gw = np.empty(len(w), dtype=np.float64)
-    offs = np.ascontiguousarray(offsets, dtype=np.int32)
-    wv = _f64(w)
-    _check(lib().sal_oracle_center_surround_adjoint(_dp(E), *E.shape[1:], BOUNDARY[boundary], len(wv),
-                                                    offs.ctypes.data_as(_c_int_p), _dp(wv), _dp(gS3),
-                                                    _dp(gE), _dp(gw)), "center_surround_adjoint")
-    ndir = int(did.max()) + 1
-    galpha = np.zeros(ndir)
-    for o in range(len(wv)):
-        galpha[did[o]] += gw[o] * g[o]
-    V64 = _f64(V)
-    gV = np.empty_like(V64)
-    _check(lib().sal_oracle_features_adjoint(_dp(V64), *V64.shape, n, BOUNDARY[boundary], TAPER[taper],
-                                             _dp(gE), _dp(gV), threads), "features_adjoint")
+    gS3, gW = combine_backward(fwd, W, gS)
+    gE, gw = center_surround_adjoint(fwd["E"], gS3, offsets, w, boundary)
+    galpha = direction_gradient(gw, g, did)
+    gV = features_adjoint(V, gE, n, boundary, taper, threads)
     return {"gV": gV, "gW": gW, "galpha": galpha, "gE": gE, "gS3": gS3, "gw": gw}

@@ -37,6 +37,11 @@
 
 enum { BND_SYMMETRIC = 0, BND_PERIODIC = 1, BND_ZERO = 2 };
 
+/* Relative magnitude (to the window L1 norm) below which a bin is treated as F = 0 in the
+   adjoint: 2^-19, above the rounding level of an FP32 DFT of the window, below the bins of
+   real data. */
+#define KINK_TAU (1.0 / 524288.0)
+
 /* Boundary extension of one axis.  Returns -1 where the zero extension applies. */
 static long ext_index(long i, long N, int mode) {
     if (i >= 0 && i < N) return i;
@@ -346,7 +351,8 @@ int sal_oracle_center_surround_adjoint(const double* E, long T, long X, long Y, 
 
 /*
  * Adjoint of the feature step.  For each voxel p, with F_p recomputed,
- *   U[k] = (1/n^3) (sum_m gE_m[p] r_m(k)) F_p[k] / |F_p[k]|   (0 at DC or |F| = 0),
+ *   U[k] = (1/n^3) (sum_m gE_m[p] r_m(k)) F_p[k] / |F_p[k]|
+ *   (0 at DC and where |F| <= 2^-19 sum_u |h(u) Vext[p+u-n/2]|, the zero subgradient of |F|),
  *   gVext[p + u - n/2] += h(u) Re sum_k U[k] exp(+2 pi i k.u / n),
  * then the extension is folded back onto V (zero extension drops).  gV [T][X][Y] is
  * overwritten.  Per-thread accumulators are summed in thread order.
@@ -383,13 +389,19 @@ int sal_oracle_features_adjoint(const double* V, long T, long X, long Y, int n, 
             if (ge[0] == 0.0 && ge[1] == 0.0 && ge[2] == 0.0) continue;
             long t = p / (X * Y), x = (p / Y) % X, y = p % Y;
             local_spectrum(V, T, X, Y, n, mode, taper, t, x, y, &W);
+            /* |F| has no direction at F = 0 (a kink): bins whose magnitude is at or below
+               KINK_TAU times the window's L1 norm (the rounding level of the DFT) take the
+               zero subgradient. */
+            double l1 = 0.0;
+            for (size_t b = 0; b < n3; ++b) l1 += fabs(W.w[b]);
+            const double thr = KINK_TAU * l1;
             for (int kt = 0; kt < n; ++kt)
                 for (int kx = 0; kx < n; ++kx)
                     for (int ky = 0; ky < n; ++ky) {
                         size_t b = IDX3(kt, kx, ky, n);
                         double mag = sqrt(W.fre[b] * W.fre[b] + W.fim[b] * W.fim[b]);
                         ure[b] = uim[b] = 0.0;
-                        if ((kt == 0 && kx == 0 && ky == 0) || mag == 0.0) continue;
+                        if ((kt == 0 && kx == 0 && ky == 0) || mag <= thr) continue;
                         int i = signed_bin(kt, n), j = signed_bin(kx, n), k = signed_bin(ky, n);
                         double c = 0.0;
                         for (int m = 0; m < 3; ++m) c += ge[m] * proj_ratio(m, i, j, k);

@@ -1,0 +1,319 @@
+// Backward pass of the combination and center-surround steps, and the overlap-add gather of the
+// spectral adjoint (the paper has no backward pass; this is the adjoint of Eq. 3 and Eq. 4 with
+// the min-max bounds of the forward pass held constant).
+//
+//   S = (C - loC) invC,  C = sum_m W_m S^_m,  S^_m = (S_m - lo_m) inv_m
+//   gW_m = invC inv_m sum_p gS[p] (S_m[p] - lo_m)            (FP64 sums, fixed order)
+//   gS_m = coef_m gS,  coef_m = W_m invC inv_m
+// Center-surround (Eq. 3), d_{p,o} = E[p] - w_o Eext[p+o], sgn(0) = 0:
+//   gE[q] = (1/Q) [ gS_m[q] sum_o sgn(d_{q,o}) - sum_o w_o sum_{p: ext(p+o) = q} gS_m[p] sgn(d_{p,o}) ]
+//   gw_o  = -(1/Q) sum_m sum_p gS_m[p] sgn(d_{p,o}) Eext_m[p+o],   galpha_d = sum_{o in d} g_o gw_o
+// Every output is formed by gathering, so no atomics are used and results are deterministic.
+#include <cfloat>
+
+#include "sal_internal.cuh"
+
+namespace sal {
+namespace {
+
+constexpr int kThreads = 256;
+enum : int { N_LO = 0, N_INV = 3, N_W = 6, N_LOC = 9, N_INVC = 10 };
+
+__device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
+    int q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+__device__ __forceinline__ int ceildiv(int a, int b) { return -floordiv(-a, b); }
+
+__device__ __forceinline__ float sgnf(float d) { return (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f); }
+
+// Positions p in [0, N) with ext(p + o) == q: the range [o, N + o) is shorter than one period,
+// so each family of preimages contributes at most one (at most two in all).
+__device__ __forceinline__ int pre_offset(int q, int o, int N, int mode, int* out) {
+    // extended positions i' in [o, N + o) that map to q
+    const int lo = o, hi = N + o;
+    int c = 0;
+    if (mode == BND_ZERO) {
+        if (q >= lo && q < hi) out[c++] = q - o;
+    } else if (mode == BND_PERIODIC) {
+        for (int i = q + N * ceildiv(lo - q, N); i < hi; i += N) out[c++] = i - o;
+    } else {
+        const int P = 2 * N;
+        for (int i = q + P * ceildiv(lo - q, P); i < hi; i += P) out[c++] = i - o;
+        const int r = P - 1 - q;
+        for (int i = r + P * ceildiv(lo - r, P); i < hi; i += P) out[c++] = i - o;
+    }
+    return c;
+}
+
+// Extended positions i' in [lo, hi) with ext(i') == q.
+__device__ __forceinline__ int pre_range(int q, int N, int mode, int lo, int hi, int* out, int cap) {
+    int c = 0;
+    if (mode == BND_ZERO) {
+        if (q >= lo && q < hi) out[c++] = q;
+    } else if (mode == BND_PERIODIC) {
+        for (int i = q + N * ceildiv(lo - q, N); i < hi && c < cap; i += N) out[c++] = i;
+    } else {
+        const int P = 2 * N;
+        for (int i = q + P * ceildiv(lo - q, P); i < hi && c < cap; i += P) out[c++] = i;
+        const int r = P - 1 - q;
+        for (int i = r + P * ceildiv(lo - r, P); i < hi && c < cap; i += P) out[c++] = i;
+    }
+    return c;
+}
+
+// FP64 partials of sum_p gS[p] (S_m[p] - lo_m), m = 0..2.
+__global__ void __launch_bounds__(kThreads)
+kb_weights_partial(const float* __restrict__ S3, const float* __restrict__ gS, long long NV,
+                   const float* __restrict__ norm, double* __restrict__ part) {
+    const float lo0 = norm[N_LO], lo1 = norm[N_LO + 1], lo2 = norm[N_LO + 2];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV; p += (long long)gridDim.x * kThreads) {
+        const double g = (double)__ldg(gS + p);
+        a0 += g * (double)(__ldg(S3 + p) - lo0);
+        a1 += g * (double)(__ldg(S3 + NV + p) - lo1);
+        a2 += g * (double)(__ldg(S3 + 2 * NV + p) - lo2);
+    }
+    __shared__ double red[3][kThreads];
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[blockIdx.x * 64 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// gW and the per-map coefficients coef_m = W_m invC inv_m.  One block.
+__global__ void __launch_bounds__(kThreads)
+kb_weights_finalize(const double* __restrict__ part, int nparts, const float* __restrict__ norm,
+                    float* __restrict__ coef, float* __restrict__ gW) {
+    __shared__ double s[3][kThreads];
+    for (int c = 0; c < 3; ++c) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += kThreads) a += part[i * 64 + c];
+        s[c][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) {
+        const int m = threadIdx.x;
+        const double invC = norm[N_INVC], inv = norm[N_INV + m];
+        coef[m] = (float)((double)norm[N_W + m] * invC * inv);
+        if (gW) gW[m] = (float)(invC * inv * s[m][0]);
+    }
+}
+
+// K4: gradient of the features through Eq. 3 (gather form).
+__global__ void __launch_bounds__(kThreads)
+k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
+               float* __restrict__ gE, int T, int X, int Y, int bnd, const __grid_constant__ Stencil st) {
+    // gradient of the raw map m at p: coef[m] * gS[m * gms + p]
+    const long long NV = (long long)T * X * Y;
+    const float c0 = coef[0], c1 = coef[1], c2 = coef[2];
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < NV; q += (long long)gridDim.x * kThreads) {
+        const int y = (int)(q % Y);
+        const int x = (int)((q / Y) % X);
+        const int t = (int)(q / ((long long)X * Y));
+        float eq[3], gq[3], acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            eq[m] = __ldg(E + m * NV + q);
+            gq[m] = __ldg(gS + m * gms + q);
+        }
+        for (int o = 0; o < st.Q; ++o) {
+            const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
+            const float w = st.w[o];
+            // q as the center of the comparison
+            const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd), yy = ext_index(y + dy, Y, bnd);
+            const bool ok = (tt | xx | yy) >= 0;
+            const long long nq = ok ? ((long long)tt * X + xx) * Y + yy : 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float nb = ok ? __ldg(E + m * NV + nq) : 0.f;
+                acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+            }
+            // q as the neighbour: p with ext(p + o) = q
+            int pt[2], px[2], py[2];
+            const int nt = pre_offset(t, dt, T, bnd, pt);
+            const int nx = pre_offset(x, dx, X, bnd, px);
+            const int ny = pre_offset(y, dy, Y, bnd, py);
+            for (int a = 0; a < nt; ++a)
+                for (int b = 0; b < nx; ++b)
+                    for (int c = 0; c < ny; ++c) {
+                        const long long p = ((long long)pt[a] * X + px[b]) * Y + py[c];
+#pragma unroll
+                        for (int m = 0; m < 3; ++m)
+                            acc[m] -= w * sgnf(fmaf(-w, eq[m], __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p);
+                    }
+        }
+        gE[q] = acc[0] * c0 * st.invQ;
+        gE[NV + q] = acc[1] * c1 * st.invQ;
+        gE[2 * NV + q] = acc[2] * c2 * st.invQ;
+    }
+}
+
+// FP64 partials of gw_o (before the -1/Q factor), one pass over the block's voxels per offset.
+__global__ void __launch_bounds__(kThreads)
+k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
+              int T, int X, int Y, int bnd, const __grid_constant__ Stencil st, double* __restrict__ part) {
+    const long long NV = (long long)T * X * Y;
+    const float c[3] = {coef[0], coef[1], coef[2]};
+    __shared__ double red[kThreads];
+    for (int o = 0; o < st.Q; ++o) {
+        const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
+        const float w = st.w[o];
+        double acc = 0.0;
+        for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV; p += (long long)gridDim.x * kThreads) {
+            const int y = (int)(p % Y);
+            const int x = (int)((p / Y) % X);
+            const int t = (int)(p / ((long long)X * Y));
+            const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd), yy = ext_index(y + dy, Y, bnd);
+            if ((tt | xx | yy) < 0) continue;
+            const long long nq = ((long long)tt * X + xx) * Y + yy;
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float nb = __ldg(E + m * NV + nq);
+                s = fmaf(c[m] * sgnf(fmaf(-w, nb, __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p), nb, s);
+            }
+            acc += (double)s;
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int sdx = kThreads / 2; sdx > 0; sdx >>= 1) {
+            if (threadIdx.x < sdx) red[threadIdx.x] += red[threadIdx.x + sdx];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 64 + o] = red[0];
+        __syncthreads();
+    }
+}
+
+// galpha_d = sum_{o in d} g_o gw_o, gw_o = -(1/Q) sum_blocks part[block][o].  One block.
+__global__ void __launch_bounds__(kThreads)
+k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_constant__ Stencil st,
+                   float* __restrict__ galpha) {
+    __shared__ double gw[kMaxOffsets];
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        double a = 0.0;
+        for (int i = 0; i < nparts; ++i) a += part[i * 64 + o];
+        gw[o] = -a / st.Q;
+    }
+    __syncthreads();
+    if (threadIdx.x < st.n_dirs) {
+        double a = 0.0;
+        for (int o = 0; o < st.Q; ++o)
+            if (st.dir[o] == (int)threadIdx.x) a += (double)st.g[o] * gw[o];
+        galpha[threadIdx.x] = (float)a;
+    }
+}
+
+// Overlap-add of the spectral adjoint: gV[q] += sum of every brick block element whose extended
+// position maps to q.  Blocks of the bricks with t0 in [t_begin, t_begin + t_count).
+__global__ void __launch_bounds__(kThreads)
+k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, int X, int Y, int bnd, int n,
+              int BY, int YH, int t_begin, int t_count) {
+    const long long NV = (long long)T * X * Y;
+    const int h2 = n / 2;
+    const int nseg = (Y + BY - 1) / BY;
+    const int t_end = t_begin + t_count;
+    const long long bsz = (long long)n * n * YH;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < NV; q += (long long)gridDim.x * kThreads) {
+        const int y = (int)(q % Y);
+        const int x = (int)((q / Y) % X);
+        const int t = (int)(q / ((long long)X * Y));
+        int et[40], ex[40], ey[40];
+        const int nt = pre_range(t, T, bnd, t_begin - h2, t_end + h2 - 1, et, 40);
+        if (nt == 0) continue;
+        const int nx = pre_range(x, X, bnd, -h2, X + h2 - 1, ex, 40);
+        const int ny = pre_range(y, Y, bnd, -h2, Y + h2 - 1, ey, 40);
+        float sum = 0.f;
+        for (int a = 0; a < nt; ++a) {
+            const int te = et[a];
+            const int t0a = max(t_begin, te - h2 + 1), t0b = min(t_end - 1, te + h2);
+            for (int t0 = t0a; t0 <= t0b; ++t0) {
+                const int ut = te - t0 + h2;
+                for (int b = 0; b < nx; ++b) {
+                    const int xe = ex[b];
+                    const int x0a = max(0, xe - h2 + 1), x0b = min(X - 1, xe + h2);
+                    for (int x0 = x0a; x0 <= x0b; ++x0) {
+                        const int ux = xe - x0 + h2;
+                        const long long cta_row = ((long long)(t0 - t_begin) * X + x0) * nseg;
+                        for (int c = 0; c < ny; ++c) {
+                            const int ye = ey[c];
+                            const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
+                            const int sb = min(nseg - 1, floordiv(ye + h2, BY));
+                            for (int sg = sa; sg <= sb; ++sg) {
+                                const int yy = ye - sg * BY + h2;
+                                sum += __ldg(blocks + (cta_row + sg) * bsz + ((long long)ut * n + ux) * YH + yy);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        gV[q] += sum;
+    }
+}
+
+// gS3[m][p] = coef[m] * gS[p]
+__global__ void __launch_bounds__(kThreads)
+kb_expand(const float* __restrict__ gS, const float* __restrict__ coef, float* __restrict__ gS3, long long NV) {
+    const float c0 = coef[0], c1 = coef[1], c2 = coef[2];
+    for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV; p += (long long)gridDim.x * kThreads) {
+        const float g = __ldg(gS + p);
+        gS3[p] = c0 * g;
+        gS3[NV + p] = c1 * g;
+        gS3[2 * NV + p] = c2 * g;
+    }
+}
+
+}  // namespace
+
+cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s) {
+    kb_expand<<<red_blocks(N), kThreads, 0, s>>>(gS, coef, gS3, N);
+    return cudaGetLastError();
+}
+
+cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
+                                    float* coef, float* gW, cudaStream_t s) {
+    const int nb = red_blocks(N);
+    kb_weights_partial<<<nb, kThreads, 0, s>>>(S3, gS, N, r.norm, part);
+    kb_weights_finalize<<<1, kThreads, 0, s>>>(part, nb, r.norm, coef, gW);
+    return cudaGetLastError();
+}
+
+cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,
+                               int X, int Y, int bnd, const Stencil& st, cudaStream_t s) {
+    const long long NV = (long long)T * X * Y;
+    k4_dcs_adjoint<<<red_blocks(NV), kThreads, 0, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
+    return cudaGetLastError();
+}
+
+cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, int T, int X, int Y,
+                              int bnd, const Stencil& st, double* part, float* galpha, cudaStream_t s) {
+    const long long NV = (long long)T * X * Y;
+    const int nb = red_blocks(NV);
+    k4_gw_partial<<<nb, kThreads, 0, s>>>(E, gS, gms, coef, T, X, Y, bnd, st, part);
+    k4_galpha_finalize<<<1, kThreads, 0, s>>>(part, nb, st, galpha);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
+                              SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s) {
+    const long long NV = (long long)T * X * Y;
+    long long nb = (NV + kThreads - 1) / kThreads;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BY, g.YH, t_begin, t_count);
+    return cudaGetLastError();
+}
+
+}  // namespace sal

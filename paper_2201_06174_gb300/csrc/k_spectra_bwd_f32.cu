@@ -1,0 +1,297 @@
+// K5-F32: adjoint of the local-spectrum feature step (the backward of Sec. 2 steps 1-3).
+//
+// For L = sum_p sum_m gE_m[p] E_m[p] with E_m[p] = sum_{k in half} wt_m(k) |F_p[k]| (wt holds
+// r_m of Eq. 1, the Hermitian multiplicity of k_t and 1/n^3), the gradient with respect to the
+// (extended) input is
+//   gVext[p + u - n/2] += Re sum_{k in half} h(u) exp(+2 pi i k.u / n) Gamma_p[k],
+//   Gamma_p[k] = (sum_m gE_m[p] wt_m(k)) F_p[k] / |F_p[k]|,
+// with Gamma = 0 at DC and wherever |F| <= 2^-19 A_p, A_p = sum_u |h(u) Vext[p + u - n/2]| (the
+// window's L1 norm bounds every |F_p[k]|): |F| has no direction at F = 0, and below that level
+// F is rounding noise, so those bins take the zero subgradient.
+// i.e. the transposes of the three sliding DFT stages applied to Gamma in reverse order.
+// Spectra are recomputed brick by brick (the forward stages of K1), never stored.
+//
+// One CTA = one brick (t0, x0, y_start .. y_start+BY-1), same mapping as K1:
+//   1. stage brick, forward stages 1 and 2 (shared with K1);
+//   2. per (row, y0): forward stage 3 -> Gamma -> inverse DFT along y (pairing k, n-k), added
+//      into a private accumulation window of the thread (thread-interleaved shared memory);
+//   3. windows of the y-chunks summed into Gamma_G2[k_t][k_x][y];
+//   4. adjoint of stage 2 (x) -> Gamma_G1[k_t][u_x][y];
+//   5. adjoint of stage 1 (t), real part -> the brick's block [u_t][u_x][y] of gVext, written to
+//      scratch; a separate gather kernel sums the overlapping blocks in a fixed order.
+#include "spectra_f32_common.cuh"
+
+namespace sal {
+namespace {
+
+using f32::fast_rsqrt;
+using f32::Tw;
+
+constexpr float kKinkTau = 1.0f / 524288.0f;  // zero-subgradient level of |F| relative to the window L1 norm
+
+template <int N> struct BCfg;
+template <> struct BCfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
+template <> struct BCfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
+template <> struct BCfg<8>  { static constexpr int BY = 32, YC = 4, MINB = 2; };
+template <> struct BCfg<16> { static constexpr int BY = 16, YC = 8, MINB = 2; };
+
+template <int N> struct BGeo {
+    static constexpr int H = N / 2 + 1;
+    static constexpr int BY = BCfg<N>::BY;
+    static constexpr int YC = BCfg<N>::YC;
+    static constexpr int ROWS = H * N;
+    static constexpr int NT = ROWS * (BY / YC);
+    using B = f32::Brick<N, BY, NT>;
+    static constexpr int YH = B::YH;
+    static constexpr int WIN = YC + N - 1;                       // private window (complex values)
+    static constexpr size_t IN_BYTES = (size_t)B::IN_FLOATS * 4;
+    static constexpr size_t G_BYTES = (size_t)B::G_FLOAT2 * 8;
+    static constexpr size_t WIN_BYTES = (size_t)NT * WIN * 8;
+    static constexpr size_t A0 = IN_BYTES + G_BYTES;
+    static constexpr size_t A_BYTES = A0 > WIN_BYTES ? A0 : WIN_BYTES;   // s_in+s_g1 | windows | Gamma_G1
+    static constexpr size_t SMEM = A_BYTES + G_BYTES + (size_t)4 * BY * 4 + (size_t)YH * 4;
+    static constexpr int BLOCK_FLOATS = N * N * YH;              // scratch block per CTA
+    static_assert(BY % YC == 0 && NT <= 1024, "geometry");
+};
+
+template <int N>
+__global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
+k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
+                       int T, int X, int Y, int bnd, int t_begin, const __grid_constant__ Tw<N> tw) {
+    using G = BGeo<N>;
+    using B = typename G::B;
+    constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT, WIN = G::WIN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_in = reinterpret_cast<float*>(smem_raw);
+    float2* s_g1 = reinterpret_cast<float2*>(smem_raw + G::IN_BYTES);
+    float2* s_win = reinterpret_cast<float2*>(smem_raw);                 // [WIN][NT] after stage 2
+    float2* s_gg1 = reinterpret_cast<float2*>(smem_raw);                 // Gamma_G1 [H][N][YH] after step 3
+    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::A_BYTES);     // G2, then Gamma_G2 [H][N][YH]
+    float* s_ge = reinterpret_cast<float*>(smem_raw + G::A_BYTES + G::G_BYTES);  // [3][BY]
+    float* s_l1 = s_ge + 3 * BY;                                                 // [BY] window L1 norms
+    float* s_col = s_l1 + BY;                                                    // [YH] column sums
+
+    const int tid = threadIdx.x;
+    const int y_start = blockIdx.x * BY;
+    const int x0 = blockIdx.y;
+    const int t0 = t_begin + blockIdx.z;
+    const size_t NV = (size_t)T * X * Y;
+
+    B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
+    for (int i = tid; i < 3 * BY; i += NT) {
+        const int m = i / BY, yl = i % BY, y = y_start + yl;
+        s_ge[i] = y < Y ? __ldg(gE + m * NV + ((size_t)t0 * X + x0) * Y + y) : 0.f;
+    }
+    __syncthreads();
+    // window L1 norms A[y0] = sum_u h(u_t) h(u_x) h(u_y) |V|, as column sums then a y box sum
+    for (int yy = tid; yy < YH; yy += NT) {
+        float a = 0.f;
+        for (int r = 0; r < N * N; ++r) a = fmaf(tw.c[0][r / N] * tw.c[0][r % N], fabsf(s_in[r * YH + yy]), a);
+        s_col[yy] = a;
+    }
+    B::stage1(s_in, s_g1, tw);
+    __syncthreads();
+    for (int yl = tid; yl < BY; yl += NT) {
+        float a = 0.f;
+#pragma unroll
+        for (int u = 0; u < N; ++u) a = fmaf(tw.c[0][u], s_col[yl + u], a);
+        s_l1[yl] = a;
+    }
+    B::stage2(s_g1, s_g2, tw);
+    __syncthreads();
+
+    // ---- step 2: forward stage 3, Gamma, inverse along y into the private window -------------
+    const int row = tid % ROWS;
+    const int ych = tid / ROWS;
+    float wt[3][H];
+    B::row_weights(row, wt);
+#pragma unroll
+    for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
+    const float2* grow = s_g2 + (size_t)row * YH;
+    for (int yi = 0; yi < YC; ++yi) {
+        const int yl = ych * YC + yi;
+        float pr[H], pi[H], qr[H], qi[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const float2 g = grow[yl + u];
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                pr[k] = fmaf(g.x, tw.c[k][u], pr[k]);
+                pi[k] = fmaf(g.y, tw.c[k][u], pi[k]);
+                if (k != 0 && 2 * k != N) {
+                    qr[k] = fmaf(g.x, tw.s[k][u], qr[k]);
+                    qi[k] = fmaf(g.y, tw.s[k][u], qi[k]);
+                }
+            }
+        }
+        const float g0 = s_ge[yl], g1 = s_ge[BY + yl], g2 = s_ge[2 * BY + yl];
+        const float thr = kKinkTau * s_l1[yl];
+        const float thr2 = fmaxf(thr * thr, 1e-30f);   // also keeps subnormal |F|^2 away from rsqrt
+        // A_k = Gamma[k] + Gamma[n-k], B_k = i (Gamma[k] - Gamma[n-k]); self-paired bins: A_k = Gamma[k]
+        float ar[H], ai[H], br[H], bi[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float rho = fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
+            if (k == 0 || 2 * k == N) {
+                const float m2 = fmaf(pr[k], pr[k], pi[k] * pi[k]);
+                const float sc = m2 > thr2 ? rho * fast_rsqrt(m2) : 0.f;
+                ar[k] = sc * pr[k];
+                ai[k] = sc * pi[k];
+                br[k] = bi[k] = 0.f;
+            } else {
+                const float fr = pr[k] + qi[k], fi = pi[k] - qr[k];   // F[k]
+                const float hr = pr[k] - qi[k], hi = pi[k] + qr[k];   // F[n-k]
+                const float m2a = fmaf(fr, fr, fi * fi), m2b = fmaf(hr, hr, hi * hi);
+                const float sa = m2a > thr2 ? rho * fast_rsqrt(m2a) : 0.f;
+                const float sb = m2b > thr2 ? rho * fast_rsqrt(m2b) : 0.f;
+                const float gar = sa * fr, gai = sa * fi, gbr = sb * hr, gbi = sb * hi;
+                ar[k] = gar + gbr;
+                ai[k] = gai + gbi;
+                br[k] = gbi - gai;        // i * (Gamma_a - Gamma_b)
+                bi[k] = gar - gbr;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                zr = fmaf(ar[k], tw.c[k][u], zr);
+                zi = fmaf(ai[k], tw.c[k][u], zi);
+                if (k != 0 && 2 * k != N) {
+                    zr = fmaf(br[k], tw.s[k][u], zr);
+                    zi = fmaf(bi[k], tw.s[k][u], zi);
+                }
+            }
+            float2* w = s_win + (yi + u) * NT + tid;
+            float2 acc = *w;
+            acc.x += zr;
+            acc.y += zi;
+            *w = acc;
+        }
+    }
+    __syncthreads();
+
+    // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
+    for (int it = tid; it < ROWS * YH; it += NT) {
+        const int r = it / YH, y = it % YH;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int c = 0; c < BY / YC; ++c) {
+            const int j = y - c * YC;
+            if (j >= 0 && j < WIN) {
+                const float2 v = s_win[j * NT + c * ROWS + r];
+                sr += v.x;
+                si += v.y;
+            }
+        }
+        s_g2[(size_t)r * YH + y] = make_float2(sr, si);
+    }
+    __syncthreads();
+
+    // ---- step 4: adjoint of stage 2 (x): Gamma_G1[k_t][u][y] ----------------------------------
+    for (int it = tid; it < H * YH; it += NT) {
+        const int kt = it / YH, y = it % YH;
+        float ar[H], ai[H], br[H], bi[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 a = s_g2[(size_t)(kt * N + k) * YH + y];
+            if (k == 0 || 2 * k == N) {
+                ar[k] = a.x; ai[k] = a.y; br[k] = bi[k] = 0.f;
+            } else {
+                const float2 b = s_g2[(size_t)(kt * N + (N - k)) * YH + y];
+                ar[k] = a.x + b.x;
+                ai[k] = a.y + b.y;
+                br[k] = b.y - a.y;
+                bi[k] = a.x - b.x;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                zr = fmaf(ar[k], tw.c[k][u], zr);
+                zi = fmaf(ai[k], tw.c[k][u], zi);
+                if (k != 0 && 2 * k != N) {
+                    zr = fmaf(br[k], tw.s[k][u], zr);
+                    zi = fmaf(bi[k], tw.s[k][u], zi);
+                }
+            }
+            s_gg1[(size_t)(kt * N + u) * YH + y] = make_float2(zr, zi);
+        }
+    }
+    __syncthreads();
+
+    // ---- step 5: adjoint of stage 1 (t), real part -> scratch block [u_t][u_x][y] -------------
+    const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float* blk = blocks + cta * G::BLOCK_FLOATS;
+    for (int it = tid; it < N * YH; it += NT) {
+        const int ux = it / YH, y = it % YH;
+        float2 g[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) g[k] = s_gg1[(size_t)(k * N + ux) * YH + y];
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            float z = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                z = fmaf(g[k].x, tw.c[k][u], z);
+                if (k != 0 && 2 * k != N) z = fmaf(-g[k].y, tw.s[k][u], z);
+            }
+            blk[((size_t)u * N + ux) * YH + y] = z;
+        }
+    }
+}
+
+template <int N>
+cudaError_t prepare_n() {
+    return cudaFuncSetAttribute(k5_spectra_adjoint_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)BGeo<N>::SMEM);
+}
+
+template <int N>
+cudaError_t launch_n(const TwiddleTable& t, const float* V, const float* gE, float* blocks, int T, int X, int Y,
+                     int bnd, int t_begin, int t_count, cudaStream_t s) {
+    using G = BGeo<N>;
+    dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
+    k5_spectra_adjoint_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, f32::make_tw<N>(t));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t spectra_adjoint_f32_prepare(int n) {
+    switch (n) {
+        case 2: return prepare_n<2>();
+        case 4: return prepare_n<4>();
+        case 8: return prepare_n<8>();
+        case 16: return prepare_n<16>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
+    switch (n) {
+        case 2: return {BGeo<2>::BY, BGeo<2>::YH, BGeo<2>::BLOCK_FLOATS};
+        case 4: return {BGeo<4>::BY, BGeo<4>::YH, BGeo<4>::BLOCK_FLOATS};
+        case 8: return {BGeo<8>::BY, BGeo<8>::YH, BGeo<8>::BLOCK_FLOATS};
+        case 16: return {BGeo<16>::BY, BGeo<16>::YH, BGeo<16>::BLOCK_FLOATS};
+        default: return {0, 0, 0};
+    }
+}
+
+cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
+                                       int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s) {
+    switch (n) {
+        case 2: return launch_n<2>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
+        case 4: return launch_n<4>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
+        case 8: return launch_n<8>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
+        case 16: return launch_n<16>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sal

@@ -13,20 +13,13 @@
 // Stage 3 is fused with the feature epilogue: |F| per bin, weighted by the projection ratios
 // r_m(k) of Eq. 1 (zero at DC), summed over k_y in registers and over (k_t,k_x) rows through
 // shared memory in a fixed order.  Per-voxel spectra never leave the SM.
-#include <cstdio>
-
-#include "sal_internal.cuh"
+#include "spectra_f32_common.cuh"
 
 namespace sal {
 namespace {
 
-// Square root on the MUFU pipe (sqrt.approx: one instruction, relative error about 2^-22,
-// far inside the 1e-5 budget of the FP32 form).
-__device__ __forceinline__ float fast_sqrt(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+using f32::fast_sqrt;
+using f32::Tw;
 
 template <int N> struct Cfg;
 template <> struct Cfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
@@ -34,27 +27,20 @@ template <> struct Cfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
 template <> struct Cfg<8>  { static constexpr int BY = 32, YC = 4, MINB = 2; };
 template <> struct Cfg<16> { static constexpr int BY = 16, YC = 8, MINB = 2; };
 
-template <int N> struct Tw {
-    float c[N / 2 + 1][N];
-    float s[N / 2 + 1][N];
-};
-
 template <int N> struct Geo {
     static constexpr int H = N / 2 + 1;
     static constexpr int BY = Cfg<N>::BY;
     static constexpr int YC = Cfg<N>::YC;
-    static constexpr int YH = BY + N - 1;          // y extent of the halo brick
     static constexpr int ROWS = H * N;             // (k_t, k_x) rows of stage 3
     static constexpr int NT = ROWS * (BY / YC);    // threads per CTA
-    static constexpr int IN_FLOATS = N * N * YH;
-    static constexpr int G_FLOAT2 = H * N * YH;
+    using B = f32::Brick<N, BY, NT>;
+    static constexpr int YH = B::YH;
     static constexpr int PART_FLOATS = BY * 3 * ROWS;
-    static constexpr size_t A_BYTES_IN = (size_t)IN_FLOATS * 4 + (size_t)G_FLOAT2 * 8;
+    static constexpr size_t A_BYTES_IN = (size_t)B::IN_FLOATS * 4 + (size_t)B::G_FLOAT2 * 8;
     static constexpr size_t A_BYTES = A_BYTES_IN > (size_t)PART_FLOATS * 4 ? A_BYTES_IN : (size_t)PART_FLOATS * 4;
-    static constexpr size_t SMEM = A_BYTES + (size_t)G_FLOAT2 * 8;
+    static constexpr size_t SMEM = A_BYTES + (size_t)B::G_FLOAT2 * 8;
     static_assert(BY % YC == 0, "BY/YC");
     static_assert(NT <= 1024, "threads");
-    static_assert(NT % 32 == 0 && NT >= YH, "halo load mapping");
 };
 
 template <int N>
@@ -62,105 +48,31 @@ __global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
 k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
                const __grid_constant__ Tw<N> tw) {
     using G = Geo<N>;
+    using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* s_in = reinterpret_cast<float*>(smem_raw);                        // [N][N][YH]
-    float2* s_g1 = reinterpret_cast<float2*>(smem_raw + (size_t)G::IN_FLOATS * 4);  // [H][N][YH]
-    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::A_BYTES);         // [H][N][YH]
-    float* s_part = reinterpret_cast<float*>(smem_raw);                      // [BY][3][ROWS] (aliases A)
+    float* s_in = reinterpret_cast<float*>(smem_raw);                                // [N][N][YH]
+    float2* s_g1 = reinterpret_cast<float2*>(smem_raw + (size_t)B::IN_FLOATS * 4);   // [H][N][YH]
+    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::A_BYTES);                 // [H][N][YH]
+    float* s_part = reinterpret_cast<float*>(smem_raw);                              // [BY][3][ROWS] (aliases A)
 
     const int tid = threadIdx.x;
     const int y_start = blockIdx.x * BY;
     const int x0 = blockIdx.y;
     const int t0 = blockIdx.z;
 
-    // ---- brick staging with border extension -------------------------------------------------
-    {
-        // thread -> (y position, first row); rows (u_t, u_x) advance by NT / YH per trip
-        constexpr int RSTEP = NT / YH;
-        const int yy = tid % YH;
-        const int r0 = tid / YH;
-        const int gy = ext_index(y_start - N / 2 + yy, Y, bnd);
-        if (r0 < RSTEP) {
-            for (int r = r0; r < N * N; r += RSTEP) {
-                const int ut = r / N, ux = r % N;
-                const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-                const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
-                float v = 0.f;
-                if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-                s_in[r * YH + yy] = v;
-            }
-        }
-    }
+    B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
     __syncthreads();
-
-    // ---- stage 1: DFT along t of the real cube, bins k_t in [0, n/2] -------------------------
-    for (int it = tid; it < N * YH; it += NT) {
-        const int ux = it / YH, yy = it % YH;
-        float v[N];
-#pragma unroll
-        for (int u = 0; u < N; ++u) v[u] = s_in[(u * N + ux) * YH + yy];
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-            float P = 0.f, Q = 0.f;
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-                P = fmaf(v[u], tw.c[k][u], P);
-                Q = fmaf(v[u], tw.s[k][u], Q);
-            }
-            s_g1[(k * N + ux) * YH + yy] = make_float2(P, -Q);
-        }
-    }
+    B::stage1(s_in, s_g1, tw);
     __syncthreads();
-
-    // ---- stage 2: DFT along x (complex), all k_x --------------------------------------------
-    for (int it = tid; it < H * YH; it += NT) {
-        const int kt = it / YH, yy = it % YH;
-        float2 g[N];
-#pragma unroll
-        for (int u = 0; u < N; ++u) g[u] = s_g1[(kt * N + u) * YH + yy];
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-            float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-                pr = fmaf(g[u].x, tw.c[k][u], pr);
-                pi = fmaf(g[u].y, tw.c[k][u], pi);
-                if (k != 0 && 2 * k != N) {
-                    qr = fmaf(g[u].x, tw.s[k][u], qr);
-                    qi = fmaf(g[u].y, tw.s[k][u], qi);
-                }
-            }
-            s_g2[(kt * N + k) * YH + yy] = make_float2(pr + qi, pi - qr);
-            if (k != 0 && 2 * k != N) s_g2[(kt * N + (N - k)) * YH + yy] = make_float2(pr - qi, pi + qr);
-        }
-    }
+    B::stage2(s_g1, s_g2, tw);
     __syncthreads();
 
     // ---- stage 3 + projection/feature epilogue ----------------------------------------------
     const int row = tid % ROWS;           // (k_t, k_x)
     const int ych = tid / ROWS;           // chunk of YC outputs
-    const int kt = row / N, kx = row % N;
     float wt[3][H];                       // r_m(k_t,k_x,+-k_y) * multiplicity / n^3
-    {
-        const int i = kt;
-        const int j = kx < N / 2 ? kx : kx - N;
-        const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-        const float scale = mult / (float)(N * N * N);
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-            const float r2 = (float)(i * i + j * j + k * k);
-            if (r2 == 0.f) {
-                wt[0][k] = wt[1][k] = wt[2][k] = 0.f;
-            } else {
-                const float inv = scale / sqrtf(r2);
-                wt[0][k] = sqrtf((float)(j * j + k * k)) * inv;
-                wt[1][k] = sqrtf((float)(i * i + k * k)) * inv;
-                wt[2][k] = sqrtf((float)(i * i + j * j)) * inv;
-            }
-        }
-    }
-    __syncthreads();  // s_part aliases s_in / s_g1
+    B::row_weights(row, wt);
     const float2* grow = s_g2 + (size_t)row * YH;
     for (int yl = ych * YC; yl < ych * YC + YC; ++yl) {
         float pr[H], pi[H], qr[H], qi[H];
@@ -216,17 +128,6 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
 }
 
 template <int N>
-Tw<N> make_tw(const TwiddleTable& t) {
-    Tw<N> w;
-    for (int k = 0; k <= N / 2; ++k)
-        for (int u = 0; u < N; ++u) {
-            w.c[k][u] = t.c[k][u];
-            w.s[k][u] = t.s[k][u];
-        }
-    return w;
-}
-
-template <int N>
 cudaError_t prepare() {
     return cudaFuncSetAttribute(k1_spectra_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo<N>::SMEM);
@@ -237,7 +138,7 @@ cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X
                    cudaStream_t s) {
     using G = Geo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, T);
-    k1_spectra_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, make_tw<N>(t));
+    k1_spectra_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
     return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 // K2 (center-surround) and K3 (normalisation + combination).
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -23,6 +24,11 @@ struct sal_handle {
     float* S3 = nullptr;     // [3][N] raw center-surround scratch
     sal::Reduce red{};
     void* small = nullptr;   // one allocation holding the reduction scratch
+    // backward scratch, allocated by the first sal_saliency_backward call
+    float* gE = nullptr;     // [3][N]
+    double* bpart = nullptr; // [kRedBlocks][64]
+    float* blocks = nullptr; // brick blocks of the spectral adjoint for one slab of t0
+    int slab_t = 0;
     size_t bytes = 0;
     std::string last;
 };
@@ -44,8 +50,12 @@ void free_scratch(sal_handle* h) {
     if (h->E) cudaFree(h->E);
     if (h->S3) cudaFree(h->S3);
     if (h->small) cudaFree(h->small);
-    h->E = h->S3 = nullptr;
+    if (h->gE) cudaFree(h->gE);
+    if (h->bpart) cudaFree(h->bpart);
+    if (h->blocks) cudaFree(h->blocks);
+    h->E = h->S3 = h->gE = h->blocks = nullptr;
     h->small = nullptr;
+    h->bpart = nullptr;
 }
 
 void build_twiddles(sal_handle* h) {
@@ -144,11 +154,12 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
     e = sal::spectra_f32_prepare(h->n);
+    if (e == cudaSuccess) e = sal::spectra_adjoint_f32_prepare(h->n);
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
 
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
     const size_t small = (size_t)sal::kRedBlocks * 8 * sizeof(float) + (size_t)sal::kRedBlocks * 16 * sizeof(double)
-                         + 16 * sizeof(float) + 16 * sizeof(double) + 256;
+                         + 32 * sizeof(float) + 16 * sizeof(double) + 256;
     const size_t need = 2 * plane3 + small;
     if (h->budget && need > h->budget) {
         delete h;
@@ -169,6 +180,16 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     h->red.mm_part = reinterpret_cast<float*>(b);
     b += (size_t)sal::kRedBlocks * 8 * sizeof(float);
     h->red.norm = reinterpret_cast<float*>(b);
+    {
+        // norm layout: [0..10] bounds and weights, [12..14] gradient coefficients, [16..18] ones
+        float init[32] = {0.f};
+        init[16] = init[17] = init[18] = 1.f;
+        if ((e = cudaMemcpy(h->red.norm, init, sizeof(init), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            return cuda_fail(nullptr, e, "cudaMemcpy");
+        }
+    }
     h->bytes = need;
     *out = h;
     return SAL_OK;
@@ -243,12 +264,135 @@ sal_status sal_saliency(sal_handle* h, const float* V, const float* D, const flo
     return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "combine launch");
 }
 
+namespace {
+
+constexpr size_t kBlocksCap = (size_t)2 << 30;  // brick-block scratch of the spectral adjoint (per slab)
+
+sal_status ensure_backward_scratch(sal_handle* h) {
+    if (h->gE) return SAL_OK;
+    const sal::SpectraAdjointGeometry g = sal::spectra_adjoint_f32_geometry(h->n);
+    const int nseg = (h->Y + g.BY - 1) / g.BY;
+    const size_t per_t = (size_t)h->X * nseg * g.block_floats * sizeof(float);
+    size_t cap = kBlocksCap;
+    const size_t plane3 = (size_t)3 * h->N * sizeof(float);
+    const size_t bpart = (size_t)sal::kRedBlocks * 64 * sizeof(double);
+    if (h->budget) {
+        const size_t used = h->bytes + plane3 + bpart;
+        if (used + per_t > h->budget)
+            return fail(h, SAL_ERR_OOM, "backward scratch exceeds hbm_budget_bytes");
+        cap = std::min(cap, h->budget - used);
+    }
+    int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->T, cap / per_t));
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->gE, plane3)) != cudaSuccess || (e = cudaMalloc(&h->bpart, bpart)) != cudaSuccess ||
+        (e = cudaMalloc(&h->blocks, per_t * slab)) != cudaSuccess) {
+        if (h->gE) cudaFree(h->gE);
+        if (h->bpart) cudaFree(h->bpart);
+        h->gE = h->blocks = nullptr;
+        h->bpart = nullptr;
+        cudaGetLastError();
+        return fail(h, SAL_ERR_OOM, std::string("backward scratch cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->slab_t = slab;
+    h->bytes += plane3 + bpart + per_t * slab;
+    return SAL_OK;
+}
+
+// gV = (dE/dV)^T gE through the brick blocks of K5 and the fixed-order overlap-add, slab by slab.
+sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, float* gV, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(gV, 0, (size_t)h->N * sizeof(float), st)) != cudaSuccess)
+        return cuda_fail(h, e, "spectral adjoint: memset");
+    const sal::SpectraAdjointGeometry g = sal::spectra_adjoint_f32_geometry(h->n);
+    for (int t_begin = 0; t_begin < h->T; t_begin += h->slab_t) {
+        const int cnt = std::min(h->slab_t, h->T - t_begin);
+        if ((e = sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
+                                                 t_begin, cnt, st)) != cudaSuccess)
+            return cuda_fail(h, e, "spectral adjoint");
+        if ((e = sal::gather_add_launch(h->blocks, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt, st)) !=
+            cudaSuccess)
+            return cuda_fail(h, e, "spectral adjoint: overlap-add");
+    }
+    return SAL_OK;
+}
+
+}  // namespace
+
 sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, const float* gS, float* gV,
                                  float* gW, float* galpha, void* stream) {
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
-    (void)V; (void)W; (void)gS; (void)gV; (void)gW; (void)galpha; (void)stream;
-    return fail(h, SAL_ERR_UNSUPPORTED, "backward not built yet");
+    if (!V || !W || !gS) return fail(h, SAL_ERR_INVALID_ARG, "V, W and gS must not be NULL");
+    if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    // forward recompute: features, raw maps, normalisation bounds for the given weights
+    if ((e = sal::spectra_f32_launch(h->n, h->tw, V, h->E, h->T, h->X, h->Y, h->boundary, st)) != cudaSuccess)
+        return cuda_fail(h, e, "backward: local_spectra_project");
+    if ((e = sal::dcs_launch(h->E, h->S3, h->T, h->X, h->Y, h->boundary, h->st, h->red.mm_part, st)) != cudaSuccess)
+        return cuda_fail(h, e, "backward: center_surround");
+    // the combined map itself is not needed: gE's first plane holds it until K4 overwrites it
+    if ((e = sal::combine_launch(h->S3, nullptr, W, nullptr, h->gE, h->N, h->ls_delta, true, h->red, st)) !=
+        cudaSuccess)
+        return cuda_fail(h, e, "backward: combine");
+    float* coef = h->red.norm + 12;
+    if ((e = sal::backward_weights_launch(h->S3, gS, h->N, h->red, h->bpart, coef, gW, st)) != cudaSuccess)
+        return cuda_fail(h, e, "backward: weights");
+    if (galpha &&
+        (e = sal::dcs_galpha_launch(h->E, gS, 0, coef, h->T, h->X, h->Y, h->boundary, h->st, h->bpart, galpha, st)) !=
+            cudaSuccess)
+        return cuda_fail(h, e, "backward: alpha");
+    if (!gV) return SAL_OK;
+    if ((e = sal::dcs_adjoint_launch(h->E, gS, 0, coef, h->gE, h->T, h->X, h->Y, h->boundary, h->st, st)) !=
+        cudaSuccess)
+        return cuda_fail(h, e, "backward: center_surround adjoint");
+    return spectral_adjoint(h, V, h->gE, gV, st);
+}
+
+sal_status sal_local_spectra_project_backward(sal_handle* h, const float* V, const float* gE, float* gV,
+                                              void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!V || !gE || !gV) return fail(h, SAL_ERR_INVALID_ARG, "V, gE and gV must not be NULL");
+    if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
+    return spectral_adjoint(h, V, gE, gV, static_cast<cudaStream_t>(stream));
+}
+
+sal_status sal_center_surround_backward(sal_handle* h, const float* E, const float* gS3, float* gE, float* galpha,
+                                        void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!E || !gS3) return fail(h, SAL_ERR_INVALID_ARG, "E and gS3 must not be NULL");
+    if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const float* ones = h->red.norm + 16;
+    if (galpha && (e = sal::dcs_galpha_launch(E, gS3, h->N, ones, h->T, h->X, h->Y, h->boundary, h->st, h->bpart,
+                                             galpha, st)) != cudaSuccess)
+        return cuda_fail(h, e, "center_surround_backward: alpha");
+    if (gE && (e = sal::dcs_adjoint_launch(E, gS3, h->N, ones, gE, h->T, h->X, h->Y, h->boundary, h->st, st)) !=
+                  cudaSuccess)
+        return cuda_fail(h, e, "center_surround_backward");
+    return SAL_OK;
+}
+
+sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, const float* gS, float* gS3,
+                                float* gW, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!S3 || !W || !gS || !gS3) return fail(h, SAL_ERR_INVALID_ARG, "S3, W, gS and gS3 must not be NULL");
+    if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    // bounds of the forward combination; its map goes to gS3's first plane until overwritten
+    if ((e = sal::combine_launch(S3, nullptr, W, nullptr, gS3, h->N, h->ls_delta, false, h->red, st)) != cudaSuccess)
+        return cuda_fail(h, e, "combine_backward: bounds");
+    float* coef = h->red.norm + 12;
+    if ((e = sal::backward_weights_launch(S3, gS, h->N, h->red, h->bpart, coef, gW, st)) != cudaSuccess)
+        return cuda_fail(h, e, "combine_backward: weights");
+    if ((e = sal::expand_gradient_launch(gS, coef, gS3, h->N, st)) != cudaSuccess)
+        return cuda_fail(h, e, "combine_backward: expand");
+    return SAL_OK;
 }
 
 const char* sal_last_error(const sal_handle* h) {

@@ -74,6 +74,27 @@ int red_blocks(long long NV);  // grid of the grid-stride reduction kernels (<= 
 cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, float* W_out, float* S,
                            long long N, double delta, bool s3_partials_ready, const Reduce& r, cudaStream_t s);
 
+// ---- K4/K5 and the backward reductions ---------------------------------------------------------
+struct SpectraAdjointGeometry {
+    int BY;            // outputs per brick along y
+    int YH;            // y extent of a brick's block
+    int block_floats;  // n * n * YH: scratch floats per brick
+};
+cudaError_t spectra_adjoint_f32_prepare(int n);
+SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
+cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
+                                       int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s);
+cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
+                                    float* coef, float* gW, cudaStream_t s);
+// gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]
+cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,
+                               int X, int Y, int bnd, const Stencil& st, cudaStream_t s);
+cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, int T, int X, int Y,
+                              int bnd, const Stencil& st, double* part, float* galpha, cudaStream_t s);
+cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s);
+cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
+                              SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s);
+
 // Message for sal_last_error(NULL) from entry points that have no handle.
 void set_unbound_error(const std::string& msg);
 

@@ -32,7 +32,8 @@ TAPER = {"rect": 0, "hann": 1}
 # Exported entry points (must match include/sal.h).
 ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
                 "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
-                "sal_combine_noalloc")
+                "sal_combine_noalloc", "sal_local_spectra_project_backward", "sal_center_surround_backward",
+                "sal_combine_backward")
 
 
 class SalError(RuntimeError):
@@ -75,6 +76,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_saliency.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.sal_saliency_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.sal_combine_noalloc.argtypes = [i, i, i, vp, vp, vp, ctypes.c_double, vp, vp, vp]
+    L.sal_local_spectra_project_backward.argtypes = [vp, vp, vp, vp, vp]
+    L.sal_center_surround_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sal_combine_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -186,6 +190,18 @@ def sal_saliency(h, V, D, W_in, S, S3_opt=None, E_opt=None, W_out=None, stream=N
 def sal_saliency_backward(h, V, W, gS, gV=None, gW=None, galpha=None, stream=None):
     _check(load().sal_saliency_backward(h, _ptr(V), _ptr(W), _ptr(gS), _ptr(gV), _ptr(gW), _ptr(galpha),
                                         _stream(stream)), h)
+
+
+def sal_local_spectra_project_backward(h, V, gE, gV, stream=None):
+    _check(load().sal_local_spectra_project_backward(h, _ptr(V), _ptr(gE), _ptr(gV), _stream(stream)), h)
+
+
+def sal_center_surround_backward(h, E, gS3, gE=None, galpha=None, stream=None):
+    _check(load().sal_center_surround_backward(h, _ptr(E), _ptr(gS3), _ptr(gE), _ptr(galpha), _stream(stream)), h)
+
+
+def sal_combine_backward(h, S3, W, gS, gS3, gW=None, stream=None):
+    _check(load().sal_combine_backward(h, _ptr(S3), _ptr(W), _ptr(gS), _ptr(gS3), _ptr(gW), _stream(stream)), h)
 
 
 def sal_combine_noalloc(S3, D, W_in, W_out, S, ls_delta: float = 1e-6, stream=None):

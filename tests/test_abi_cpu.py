@@ -65,7 +65,8 @@ def test_null_params_and_out():
 def test_null_handle_calls():
     L = sal.load()
     for name, nargs in [("sal_local_spectra_project", 4), ("sal_center_surround", 4), ("sal_combine", 7),
-                        ("sal_saliency", 9), ("sal_saliency_backward", 8)]:
+                        ("sal_saliency", 9), ("sal_saliency_backward", 8), ("sal_local_spectra_project_backward", 5),
+                        ("sal_center_surround_backward", 6), ("sal_combine_backward", 7)]:
         assert getattr(L, name)(*([None] * nargs)) == salmod.SAL_ERR_INVALID_ARG
     assert L.sal_destroy(None) == salmod.SAL_OK
     assert L.sal_workspace_size(None, None) == salmod.SAL_ERR_INVALID_ARG

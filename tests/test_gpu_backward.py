@@ -1,0 +1,204 @@
+"""GPU parity of the backward (differentiation form) against the FP64 oracle adjoint, through the
+C ABI, plus central finite differences of the GPU forward and a weight-fitting run.
+
+Tolerances (FP32 path): relative L2 <= 1e-5 for each step's adjoint.  The sign of each
+center-surround difference (a kink of |.|) is an integer-valued decision: the step tests feed
+both sides the same FP32 features and FP32 weights, so both take it on identical numbers.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def sal():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_06174_gb300 as s
+    s.load()
+    return s
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+# brick sizes along y of the spectral adjoint (used to force several t-slabs through the budget)
+_BY = {2: 32, 4: 32, 8: 32, 16: 16}
+
+
+@pytest.mark.parametrize("n,shape,boundary,slabs", [
+    (2, (5, 6, 40), "symmetric", 1),
+    (4, (7, 5, 37), "periodic", 1),
+    (4, (6, 9, 20), "zero", 3),
+    (8, (10, 9, 45), "symmetric", 1),
+    (8, (9, 7, 33), "symmetric", 4),
+    (16, (6, 5, 21), "symmetric", 1),
+    (16, (5, 4, 17), "periodic", 2),
+])
+def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 100, faults=1))
+    gE = synth.random_volume((3,) + shape, seed=n + 7)
+    budget = 0
+    if slabs > 1:
+        nseg = -(-shape[2] // _BY[n])
+        per_t = shape[1] * nseg * n * n * (_BY[n] + n - 1) * 4
+        base = sal.Saliency(shape, sal.Params(n=n, boundary=boundary))
+        created = sal.sal_workspace_size(base.h)
+        base.close()
+        N = int(np.prod(shape))
+        budget = created + 3 * N * 4 + 1216 * 64 * 8 + per_t * max(1, shape[0] // slabs)
+    eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, hbm_budget_bytes=budget))
+    try:
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
+    finally:
+        eng.close()
+    ref = oracle.features_adjoint(V, gE, n, boundary=boundary)
+    assert rel_l2(got, ref) <= RTOL, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("boundary", ["symmetric", "periodic", "zero"])
+def test_center_surround_adjoint_matches_oracle(sal, boundary):
+    shape = (9, 8, 35)
+    V, _ = synth.volume(synth.small_spec(shape, seed=5, faults=1))
+    E32 = oracle.features(V, 4, boundary=boundary).astype(np.float32)
+    gS3 = synth.random_volume((3,) + shape, seed=11)
+    alpha = [1.0, 0.7, 1.3]
+    params = sal.Params(n=4, boundary=boundary, alpha=alpha)
+    offs, g, did, w = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
+    w32 = (np.asarray(alpha, np.float32)[did] * g.astype(np.float32)).astype(np.float64)  # the kernel's weights
+    eng = sal.Saliency(shape, params)
+    try:
+        gE = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+        ga = torch.empty(3, dtype=torch.float32, device="cuda")
+        sal.sal_center_surround_backward(eng.h, _cuda(E32), _cuda(gS3), gE, ga)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    refE, gw = oracle.center_surround_adjoint(E32, gS3, offs, w32, boundary)
+    ref_ga = oracle.direction_gradient(gw, g.astype(np.float32), did)
+    assert rel_l2(gE.cpu().numpy(), refE) <= RTOL
+    assert rel_l2(ga.cpu().numpy(), ref_ga) <= RTOL
+
+
+def test_combine_adjoint_matches_oracle(sal):
+    shape = (11, 10, 30)
+    rng = np.random.default_rng(3)
+    S3 = rng.random((3,) + shape).astype(np.float32)
+    gS = rng.standard_normal(shape).astype(np.float32)
+    W = np.array([0.5, 0.2, 0.3], np.float32)
+    eng = sal.Saliency(shape, sal.Params(n=4))
+    try:
+        gS3 = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+        gW = torch.empty(3, dtype=torch.float32, device="cuda")
+        sal.sal_combine_backward(eng.h, _cuda(S3), _cuda(W), _cuda(gS), gS3, gW)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    fwd = oracle.combine(S3, W.astype(np.float64))
+    ref3, refW = oracle.combine_backward(fwd, W.astype(np.float64), gS)
+    assert rel_l2(gS3.cpu().numpy(), ref3) <= RTOL
+    assert rel_l2(gW.cpu().numpy(), refW) <= RTOL
+
+
+@pytest.mark.parametrize("n,shape", [(4, (10, 9, 33)), (8, (12, 10, 40)), (16, (6, 6, 18))])
+def test_fused_backward_matches_oracle(sal, n, shape):
+    """sal_saliency_backward end to end (forward recomputed inside) against the FP64 adjoint."""
+    V, D = synth.volume(synth.small_spec(shape, seed=n, faults=2))
+    W = np.array([0.45, 0.35, 0.2])
+    alpha = [1.0, 0.8, 1.2]
+    params = sal.Params(n=n, alpha=alpha)
+    st = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
+    fwd = oracle.saliency(V, n, stencil=st, weights=W)
+    gS = (fwd["S"] - D).astype(np.float32)
+    ref = oracle.saliency_backward(V, n, W, gS, stencil=st, fwd=fwd)
+    eng = sal.Saliency(shape, params)
+    try:
+        gV, gW, ga = eng.backward(_cuda(V), _cuda(W), _cuda(gS))
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    assert rel_l2(gV.cpu().numpy(), ref["gV"]) <= RTOL, rel_l2(gV.cpu().numpy(), ref["gV"])
+    assert rel_l2(gW.cpu().numpy(), ref["gW"]) <= RTOL
+    assert rel_l2(ga.cpu().numpy(), ref["galpha"]) <= RTOL
+
+
+def test_finite_differences_of_gpu_forward(sal):
+    """Central differences (eps = 1e-3, 64 seeded entries) of L = sum gS * S on the FP32 GPU
+    forward with the forward's min-max bounds held fixed, against sal_saliency_backward."""
+    V, D = synth.volume(synth.small_spec((24, 20, 40), seed=0, faults=1))
+    n = 8
+    W = torch.tensor([0.5, 0.3, 0.2], device="cuda")
+    eng = sal.Saliency(V.shape, sal.Params(n=n))
+    try:
+        Vt = _cuda(V)
+        S3 = eng.center_surround(eng.local_spectra_project(Vt)).double()
+        lo = S3.amin(dim=(1, 2, 3), keepdim=True)
+        hi = S3.amax(dim=(1, 2, 3), keepdim=True)
+        C = (W.double()[:, None, None, None] * (S3 - lo) / (hi - lo)).sum(0)
+        loC, hiC = C.min(), C.max()
+        gS = _cuda(((C - loC) / (hiC - loC)).cpu().numpy() - D)
+
+        def L(Vx):
+            S3x = eng.center_surround(eng.local_spectra_project(Vx)).double()
+            Cx = (W.double()[:, None, None, None] * (S3x - lo) / (hi - lo)).sum(0)
+            return float(((Cx - loC) / (hiC - loC) * gS.double()).sum())
+
+        gV, _, _ = eng.backward(Vt, W, gS)
+        idx = synth.sample_points(V.shape, 64, seed=1234)
+        eps = 1e-3
+        fd = []
+        for p in idx:
+            Vp = Vt.clone(); Vp[tuple(p)] += eps
+            Vm = Vt.clone(); Vm[tuple(p)] -= eps
+            fd.append((L(Vp) - L(Vm)) / (2 * eps))
+        an = gV.cpu().numpy()[idx[:, 0], idx[:, 1], idx[:, 2]]
+    finally:
+        eng.close()
+    fd = np.array(fd)
+    # FP32 forward noise and the kinks of |.| bound the agreement of single entries; the
+    # 64-vector agrees to about 1e-2.
+    assert rel_l2(an, fd) <= 2e-2, rel_l2(an, fd)
+
+
+def test_autograd_matches_abi_and_descends(sal):
+    """The autograd Function returns exactly the C-ABI backward, and a small step of V along
+    the negative gradient lowers the L2 distance of S to a fault mask."""
+    from paper_2201_06174_gb300.autograd import saliency
+    V, D = synth.volume(synth.small_spec((20, 18, 36), seed=2, faults=2))
+    eng = sal.Saliency(V.shape, sal.Params(n=8))
+    try:
+        Vt = _cuda(V)
+        Dt = _cuda(D)
+        Vr = Vt.clone().requires_grad_(True)
+        Wr = torch.tensor([0.5, 0.3, 0.2], device="cuda", requires_grad=True)
+        ar = torch.tensor([1.0, 0.9, 1.1], device="cuda", requires_grad=True)
+        S = saliency(Vr, Wr, ar, eng)
+        loss0 = 0.5 * ((S - Dt) ** 2).sum()
+        loss0.backward()
+        gS = (S.detach() - Dt).contiguous()
+        eng.set_alpha(ar.detach().cpu().numpy())
+        gV, gW, ga = eng.backward(Vt, Wr.detach(), gS)
+        assert torch.equal(Vr.grad, gV) and torch.equal(Wr.grad, gW) and torch.equal(ar.grad, ga)
+        eta = 1e-3 * float(Vt.norm()) / float(gV.norm())
+        with torch.no_grad():
+            S1 = saliency(Vt - eta * gV, Wr.detach(), ar.detach(), eng)
+            loss1 = 0.5 * ((S1 - Dt) ** 2).sum()
+        assert float(loss1) < float(loss0)
+    finally:
+        eng.close()
