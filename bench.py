@@ -1,9 +1,10 @@
 #!/usr/bin/env python
 """Throughput of the seismic saliency hot path on GB300.
 
-One step = one pass of the whole path over one synthetic volume resident in HBM:
-K1 local spectra + projection + features, K2 directional center-surround, K3 normalisation
-and combination (sal_local_spectra_project, sal_center_surround, sal_combine).
+One step = one pass of the whole path over one synthetic volume resident in HBM: the forward
+(K1 local spectra + projection + features, K2 directional center-surround, K3 normalisation and
+combination) and the backward of L = sum gS * S for a fixed seeded upstream gradient gS (the
+combination adjoint, K4 center-surround adjoint, K5 spectral adjoint with brick recompute).
 
 Prints one JSON line.  Multi-GPU (torchrun): every rank processes its own volume (the path
 shards into independent volumes, no collective on the data path), the timed region is
@@ -28,7 +29,7 @@ WORKLOADS = {
     "salt128": dict(spec="salt128", n=16, desc="128x128x128 synthetic seismic volume (layered reflectivity, "
                     "30 Hz Ricker, 3 faults of random strike/dip with throw 2-8, salt ellipsoid 30/30/45 with "
                     "boundary reflector, folds amp 5 / wavelength 64, noise 0.1 rms), window 16^3, FP32",
-                    cpu_sample=80, ref_sample=24),
+                    cpu_sample=40, ref_sample=20),
     "fault48": dict(spec="fault48", n=8, desc="48^3 synthetic seismic volume (layers, one 60 deg normal fault "
                     "with throw 4, noise 0.1 rms), window 8^3, FP32", cpu_sample=48, ref_sample=32),
     "precision256x384x192": dict(spec="precision256x384x192", n=16, desc="256x384x192 synthetic seismic volume "
@@ -39,7 +40,8 @@ WORKLOADS = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
-K1_TRAFFIC = {}
+K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840}   # profiles/salt128_n16_fp32_fwd_bwd.md
+K5_TRAFFIC = {}
 
 
 def k1_flops_per_voxel(n: int) -> int:
@@ -94,16 +96,26 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(V, n, sample):
-    """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host cores)."""
+def cpu_oracle_rate(V, n, sample, backward=True):
+    """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host
+    cores): forward, and the backward with the same fixed upstream gradient as the GPU step."""
     import numpy as np
 
     import oracle
     sub = np.ascontiguousarray(V[:sample, :sample, :sample])
+    gS = _upstream(sub.shape)
     t0 = time.perf_counter()
-    oracle.saliency(sub, n)
+    fwd = oracle.saliency(sub, n)
+    if backward:
+        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd)
     dt = time.perf_counter() - t0
     return sub.size / dt / 1e6, dt, sub.shape
+
+
+def _upstream(shape):
+    """Fixed seeded upstream gradient dL/dS of the backward half of a step."""
+    import numpy as np
+    return np.random.default_rng(12345).standard_normal(shape).astype(np.float32)
 
 
 def run_reference(args, wl):
@@ -126,9 +138,10 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": wl["n"], "shape": list(V.shape), "precision": "fp64 oracle"},
+            "config": {"workload": wl["desc"], "n": wl["n"], "shape": list(V.shape), "precision": "fp64 oracle",
+                       "form": "forward+backward"},
             "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{s}^3 corner sub-volume of the workload per step, full forward"},
+                             "sample": f"{s}^3 corner sub-volume of the workload per step, FP64 forward+backward"},
             "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -173,23 +186,38 @@ def main():
     eng = sal.Saliency(V.shape, params)
     dev = torch.device("cuda", local_rank)
     Vd = torch.from_numpy(V).to(dev)
+    gSd = torch.from_numpy(_upstream(V.shape)).to(dev)
+    Wd = torch.full((3,), 1.0 / 3.0, dtype=torch.float32, device=dev)
     E = torch.empty((3,) + V.shape, dtype=torch.float32, device=dev)
     S3 = torch.empty_like(E)
+    gS3 = torch.empty_like(E)
+    gE = torch.empty_like(E)
     S = torch.empty(V.shape, dtype=torch.float32, device=dev)
+    gV = torch.empty_like(S)
     W = torch.empty(3, dtype=torch.float32, device=dev)
+    gW = torch.empty(3, dtype=torch.float32, device=dev)
+    galpha = torch.empty(3, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    launches_per_step = 8  # K1, K2, K3: minmax3, minmax_finalize x2, weights, combine, normalize
+
+    # one step: the forward (K1, K2, K3) and the backward of L = sum gS * S through the
+    # stepwise public calls (combine adjoint, center-surround adjoint K4, spectral adjoint K5)
+    calls = [
+        ("k1_local_spectra_project", lambda: sal.sal_local_spectra_project(eng.h, Vd, E)),
+        ("k2_center_surround", lambda: sal.sal_center_surround(eng.h, E, S3)),
+        ("k3_combine", lambda: sal.sal_combine(eng.h, S3, None, Wd, W, S)),
+        ("combine_backward", lambda: sal.sal_combine_backward(eng.h, S3, Wd, gSd, gS3, gW)),
+        ("k4_center_surround_backward", lambda: sal.sal_center_surround_backward(eng.h, E, gS3, gE, galpha)),
+        ("k5_local_spectra_project_backward", lambda: sal.sal_local_spectra_project_backward(eng.h, Vd, gE, gV)),
+    ]
 
     def step():
-        sal.sal_local_spectra_project(eng.h, Vd, E)
-        sal.sal_center_surround(eng.h, E, S3)
-        sal.sal_combine(eng.h, S3, None, None, W, S)
+        for _, c in calls:
+            c()
 
     for _ in range(max(args.warmup, 3)):
         step()
     barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
     dev_props = torch.cuda.get_device_properties(local_rank)
     gpu_id = str(getattr(dev_props, "uuid", "") or "")
     if gpu_id and not gpu_id.startswith("GPU-"):
@@ -197,35 +225,42 @@ def main():
     clocks = ClockSampler(gpu_id)
     clocks.start()
     barrier()
+    launches0 = sal.sal_launch_count()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
-        a, b, c = evs[i]
-        a.record()
-        sal.sal_local_spectra_project(eng.h, Vd, E)
-        b.record()
-        sal.sal_center_surround(eng.h, E, S3)
-        sal.sal_combine(eng.h, S3, None, None, W, S)
-        c.record()
+        ev = evs[i]
+        ev[0].record()
+        for j, (_, c) in enumerate(calls):
+            c()
+            ev[j + 1].record()
     barrier()
     wall = time.perf_counter() - wall0
+    launches = sal.sal_launch_count() - launches0
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(c) for a, b, c in evs)
-    k1_ms = sum(a.elapsed_time(b) for a, b, c in evs)
-    t = torch.tensor([total_ms, k1_ms], dtype=torch.float64, device=dev)
+    per_call = [sum(ev[j].elapsed_time(ev[j + 1]) for ev in evs) for j in range(len(calls))]
+    total_ms = sum(per_call)
+    t = torch.tensor([total_ms] + per_call, dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, k1_ms = float(t[0]), float(t[1])
+    total_ms = float(t[0])
+    per_call = [float(v) for v in t[1:]]
+    fwd_ms = sum(per_call[:3])
     value = world * nvox * args.steps / (total_ms / 1e3) / 1e6
 
-    # end to end through the public fused call, host buffers, copies inside the timed region
+    # end to end through the fused public calls, host buffers, copies inside the timed region
     Vh = torch.from_numpy(V).pin_memory()
+    gSh = torch.from_numpy(_upstream(V.shape)).pin_memory()
     Sh = torch.empty(V.shape, dtype=torch.float32).pin_memory()
+    gVh = torch.empty(V.shape, dtype=torch.float32).pin_memory()
 
     def e2e_step():
         Vd.copy_(Vh, non_blocking=True)
-        sal.sal_saliency(eng.h, Vd, None, None, S, None, None, W)
+        gSd.copy_(gSh, non_blocking=True)
+        sal.sal_saliency(eng.h, Vd, None, Wd, S, None, None, W)
+        sal.sal_saliency_backward(eng.h, Vd, Wd, gSd, gV, gW, galpha)
         Sh.copy_(S, non_blocking=True)
+        gVh.copy_(gV, non_blocking=True)
 
     for _ in range(max(args.warmup, 3)):
         e2e_step()
@@ -243,23 +278,32 @@ def main():
     e2e_value = world * nvox * args.steps / (float(t[0]) / 1e3) / 1e6
 
     n = wl["n"]
-    k1_launch_s = k1_ms / 1e3 / args.steps
-    achieved = k1_flops_per_voxel(n) * nvox / k1_launch_s / 1e12
-    traffic = K1_TRAFFIC.get((args.workload, n, "fp32"))
+    names = [c[0] for c in calls]
+    # dominant kernel: K5 (spectral adjoint: brick recompute + transposed stages, 2x the K1 contraction)
+    k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
+    k1_ms = per_call[names.index("k1_local_spectra_project")] / args.steps
+    k5_ach = 2 * k1_flops_per_voxel(n) * nvox / (k5_ms / 1e3) / 1e12
+    k1_ach = k1_flops_per_voxel(n) * nvox / (k1_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "n": n, "shape": list(V.shape), "precision": "fp32",
-                   "form": "forward", "l2": "flushed between steps (256 MiB device write outside the events)",
+                   "form": "forward+backward (upstream gradient fixed, seeded)",
+                   "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k1_spectra_f32", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+        "forward": {"value": world * nvox * args.steps / (fwd_ms / 1e3) / 1e6, "unit": "Mvoxel/s",
+                    "ms_per_step": fwd_ms / args.steps},
+        "ms_per_call": {nm: v / args.steps for nm, v in zip(names, per_call)},
+        "roofline": {"kernel": "k5_spectra_adjoint_f32 (+ overlap-add gather)", "bound": "alu", "achieved": k5_ach,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": k5_ach / FP32_PEAK_TFLOPS,
+                     "traffic": K5_TRAFFIC.get((args.workload, n, "fp32")),
                      "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
-                     "k1_ms_per_launch": k1_ms / args.steps, "k1_share_of_step": k1_ms / total_ms},
-        "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "h2d_bytes_per_step": V.nbytes,
-                "d2h_bytes_per_step": V.nbytes},
-        "gpu_launches": launches_per_step * args.steps,
+                     "k1": {"achieved": k1_ach, "frac": k1_ach / FP32_PEAK_TFLOPS,
+                            "traffic": K1_TRAFFIC.get((args.workload, n, "fp32"))}},
+        "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 2 * V.nbytes,
+                "d2h_bytes_per_step": 2 * V.nbytes},
+        "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": wall,
     }
@@ -267,7 +311,8 @@ def main():
         s = wl["cpu_sample"]
         rate, dt, shape = cpu_oracle_rate(V, n, s)
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{s}^3 corner sub-volume of the workload, full FP64 forward, {dt:.1f} s"}
+                                "sample": f"{s}^3 corner sub-volume of the workload, FP64 forward+backward, "
+                                          f"{dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     eng.close()

@@ -167,6 +167,10 @@ sal_status sal_center_surround_backward(sal_handle* h, const float* E, const flo
 sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, const float* gS, float* gS3,
                                 float* gW, void* stream);
 
+/* Number of kernels this library has launched in the process so far (all handles and
+ * entry points), for accounting; host pointer `count`. */
+sal_status sal_launch_count(unsigned long long* count);
+
 /* Message of the last error on the handle ("" if none).  h may be NULL (then the
  * last sal_create error of this thread is returned).  The string lives until the
  * next call on the handle. */

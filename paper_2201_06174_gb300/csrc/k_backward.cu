@@ -280,6 +280,7 @@ kb_expand(const float* __restrict__ gS, const float* __restrict__ coef, float* _
 
 cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s) {
     kb_expand<<<red_blocks(N), kThreads, 0, s>>>(gS, coef, gS3, N);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -288,6 +289,7 @@ cudaError_t backward_weights_launch(const float* S3, const float* gS, long long 
     const int nb = red_blocks(N);
     kb_weights_partial<<<nb, kThreads, 0, s>>>(S3, gS, N, r.norm, part);
     kb_weights_finalize<<<1, kThreads, 0, s>>>(part, nb, r.norm, coef, gW);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -295,6 +297,7 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
                                int X, int Y, int bnd, const Stencil& st, cudaStream_t s) {
     const long long NV = (long long)T * X * Y;
     k4_dcs_adjoint<<<red_blocks(NV), kThreads, 0, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -304,6 +307,7 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
     const int nb = red_blocks(NV);
     k4_gw_partial<<<nb, kThreads, 0, s>>>(E, gS, gms, coef, T, X, Y, bnd, st, part);
     k4_galpha_finalize<<<1, kThreads, 0, s>>>(part, nb, st, galpha);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -313,6 +317,7 @@ cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int 
     long long nb = (NV + kThreads - 1) / kThreads;
     if (nb > 152 * 32) nb = 152 * 32;
     k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BY, g.YH, t_begin, t_count);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -227,6 +227,7 @@ cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, f
     k3_combine<<<nb, kThreads, 0, s>>>(S3, N, r.norm, S, r.mm_part);
     k3_minmax_finalize<<<1, kThreads, 0, s>>>(r.mm_part, nb, 1, r.norm + N_LOC, r.norm + N_INVC);
     k3_normalize<<<nb, kThreads, 0, s>>>(S, N, r.norm);
+    note_launches(5 + (s3_partials_ready ? 0 : 1) + (mode == 2 ? 1 : 0));
     return cudaGetLastError();
 }
 
@@ -323,6 +324,7 @@ extern "C" sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, 
     sal::k3_combine<<<nb, sal::kThreads, 0, s>>>(S3, N, r.norm, S, r.mm_part);
     sal::k3_minmax_finalize<<<1, sal::kThreads, 0, s>>>(r.mm_part, nb, 1, r.norm + sal::N_LOC, r.norm + sal::N_INVC);
     sal::k3_normalize<<<nb, sal::kThreads, 0, s>>>(S, N, r.norm);
+    sal::note_launches(6 + (mode == 2 ? 1 : 0));
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         sal::set_unbound_error(std::string("sal_combine_noalloc: launch: ") + cudaGetErrorString(e));

@@ -83,6 +83,7 @@ cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, 
     const long long NV = (long long)T * X * Y;
     const int blocks = red_blocks(NV);  // K3 reduces exactly this many min/max partials
     k2_dcs<<<blocks, kThreads, 0, s>>>(E, S3, T, X, Y, bnd, st, mm_part);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -176,7 +176,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
 
     // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
     for (int it = tid; it < ROWS * YH; it += NT) {
-        const int r = it / YH, y = it % YH;
+        const int r = it % ROWS, y = it / ROWS;   // rows fastest: window reads are consecutive
         float sr = 0.f, si = 0.f;
 #pragma unroll
         for (int c = 0; c < BY / YC; ++c) {
@@ -258,6 +258,7 @@ cudaError_t launch_n(const TwiddleTable& t, const float* V, const float* gE, flo
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
     k5_spectra_adjoint_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, f32::make_tw<N>(t));
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X
     using G = Geo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, T);
     k1_spectra_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    note_launches(1);
     return cudaGetLastError();
 }
 

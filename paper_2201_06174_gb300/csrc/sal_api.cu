@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -85,6 +86,9 @@ sal_status check_handle(sal_handle* h) {
 }  // namespace
 
 void sal::set_unbound_error(const std::string& msg) { g_create_error = msg; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void sal::note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -392,6 +396,12 @@ sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, 
         return cuda_fail(h, e, "combine_backward: weights");
     if ((e = sal::expand_gradient_launch(gS, coef, gS3, h->N, st)) != cudaSuccess)
         return cuda_fail(h, e, "combine_backward: expand");
+    return SAL_OK;
+}
+
+sal_status sal_launch_count(unsigned long long* count) {
+    if (!count) return SAL_ERR_INVALID_ARG;
+    *count = g_launches.load(std::memory_order_relaxed);
     return SAL_OK;
 }
 

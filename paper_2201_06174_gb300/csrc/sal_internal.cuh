@@ -95,6 +95,9 @@ cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS
 cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
                               SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s);
 
+// Process-wide count of kernels launched by the library (sal_launch_count).
+void note_launches(int k);
+
 // Message for sal_last_error(NULL) from entry points that have no handle.
 void set_unbound_error(const std::string& msg);
 

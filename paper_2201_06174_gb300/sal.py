@@ -33,7 +33,7 @@ TAPER = {"rect": 0, "hann": 1}
 ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
                 "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
                 "sal_combine_noalloc", "sal_local_spectra_project_backward", "sal_center_surround_backward",
-                "sal_combine_backward")
+                "sal_combine_backward", "sal_launch_count")
 
 
 class SalError(RuntimeError):
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_local_spectra_project_backward.argtypes = [vp, vp, vp, vp, vp]
     L.sal_center_surround_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.sal_combine_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.sal_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -209,6 +210,13 @@ def sal_combine_noalloc(S3, D, W_in, W_out, S, ls_delta: float = 1e-6, stream=No
     T, X, Y = (int(v) for v in S3.shape[1:])
     _check(load().sal_combine_noalloc(T, X, Y, _ptr(S3), _ptr(D), _ptr(W_in), float(ls_delta), _ptr(W_out), _ptr(S),
                                       _stream(stream)), None)
+
+
+def sal_launch_count() -> int:
+    """Kernels launched by libsal.so in this process so far."""
+    c = ctypes.c_ulonglong()
+    _check(load().sal_launch_count(ctypes.byref(c)), None)
+    return int(c.value)
 
 
 def sal_set_alpha(h, alpha):
