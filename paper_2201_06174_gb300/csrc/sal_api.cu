@@ -30,6 +30,8 @@ struct sal_handle {
     double* bpart = nullptr; // [kRedBlocks][64]
     float* blocks = nullptr; // brick blocks of the spectral adjoint for one slab of t0
     int slab_t = 0;
+    volatile int* err_host = nullptr;  // mapped host word set by bounded device waits that gave up
+    int* err_dev = nullptr;
     size_t bytes = 0;
     std::string last;
 };
@@ -51,6 +53,9 @@ void free_scratch(sal_handle* h) {
     if (h->E) cudaFree(h->E);
     if (h->S3) cudaFree(h->S3);
     if (h->small) cudaFree(h->small);
+    if (h->err_host) cudaFreeHost((void*)h->err_host);
+    h->err_host = nullptr;
+    h->err_dev = nullptr;
     if (h->gE) cudaFree(h->gE);
     if (h->bpart) cudaFree(h->bpart);
     if (h->blocks) cudaFree(h->blocks);
@@ -80,7 +85,18 @@ sal_status check_handle(sal_handle* h) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     h->last.clear();
+    if (h->err_host && *h->err_host) {
+        *h->err_host = 0;
+        return fail(h, SAL_ERR_TIMEOUT, "a bounded tensor-core wait gave up in an earlier call; its outputs are invalid");
+    }
     return SAL_OK;
+}
+
+// K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.
+cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) {
+    if (h->prec == SAL_FP32) return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+    return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
+                                  h->err_dev, st);
 }
 
 }  // namespace
@@ -106,9 +122,10 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     if (p->boundary < 0 || p->boundary > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad boundary");
     if (p->feature != 0) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only feature 0 is built");
     if (p->prec < 0 || p->prec > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad precision");
-    if (p->prec == SAL_FP32 && !sal::spectra_f32_supported(p->n))
+    if (!sal::spectra_f32_supported(p->n))
         return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16}");
-    if (p->prec != SAL_FP32) return fail(nullptr, SAL_ERR_UNSUPPORTED, "precision not built");
+    if (p->prec != SAL_FP32 && !sal::spectra_tc_supported(p->n))
+        return fail(nullptr, SAL_ERR_UNSUPPORTED, "BF16/FP16 tensor-core path is built for n in {8,16}");
     if (p->n_offsets < 1 || p->n_offsets > sal::kMaxOffsets)
         return fail(nullptr, SAL_ERR_INVALID_ARG, "n_offsets must be in [1, 64]");
     if (p->n_dirs < 1 || p->n_dirs > sal::kMaxDirs)
@@ -159,6 +176,7 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
     e = sal::spectra_f32_prepare(h->n);
     if (e == cudaSuccess) e = sal::spectra_adjoint_f32_prepare(h->n);
+    if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
 
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
@@ -175,6 +193,18 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
         delete h;
         cudaGetLastError();
         return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    {
+        void* hp = nullptr;
+        if ((e = cudaHostAlloc(&hp, sizeof(int), cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer((void**)&h->err_dev, hp, 0)) != cudaSuccess) {
+            if (hp) cudaFreeHost(hp);
+            free_scratch(h);
+            delete h;
+            return cuda_fail(nullptr, e, "error word");
+        }
+        h->err_host = static_cast<volatile int*>(hp);
+        *h->err_host = 0;
     }
     char* b = static_cast<char*>(h->small);
     h->red.g_part = reinterpret_cast<double*>(b);
@@ -228,8 +258,7 @@ sal_status sal_local_spectra_project(sal_handle* h, const float* V, float* E, vo
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !E) return fail(h, SAL_ERR_INVALID_ARG, "V and E must not be NULL");
-    cudaError_t e = sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
-                                            static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_k1(h, V, E, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SAL_OK : cuda_fail(h, e, "local_spectra_project launch");
 }
 
@@ -260,7 +289,7 @@ sal_status sal_saliency(sal_handle* h, const float* V, const float* D, const flo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float* E = E_opt ? E_opt : h->E;
     float* S3 = S3_opt ? S3_opt : h->S3;
-    cudaError_t e = sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+    cudaError_t e = launch_k1(h, V, E, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "local_spectra_project launch");
     e = sal::dcs_launch(E, S3, h->T, h->X, h->Y, h->boundary, h->st, h->red.mm_part, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "center_surround launch");
@@ -331,8 +360,7 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     // forward recompute: features, raw maps, normalisation bounds for the given weights
-    if ((e = sal::spectra_f32_launch(h->n, h->tw, V, h->E, h->T, h->X, h->Y, h->boundary, st)) != cudaSuccess)
-        return cuda_fail(h, e, "backward: local_spectra_project");
+    if ((e = launch_k1(h, V, h->E, st)) != cudaSuccess) return cuda_fail(h, e, "backward: local_spectra_project");
     if ((e = sal::dcs_launch(h->E, h->S3, h->T, h->X, h->Y, h->boundary, h->st, h->red.mm_part, st)) != cudaSuccess)
         return cuda_fail(h, e, "backward: center_surround");
     // the combined map itself is not needed: gE's first plane holds it until K4 overwrites it

@@ -65,6 +65,12 @@ cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
                                int Y, int bnd, cudaStream_t s);
 
+// K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word
+bool spectra_tc_supported(int n);
+cudaError_t spectra_tc_prepare(int n, int fmt);
+cudaError_t spectra_tc_launch(int n, int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
+                              int bnd, int* err, cudaStream_t s);
+
 // ---- K2: directional center-surround ----------------------------------------------------------
 cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, const Stencil& st,
                        float* mm_part, cudaStream_t s);

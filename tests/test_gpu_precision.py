@@ -1,0 +1,80 @@
+"""Precision form: the local-DFT contraction on the tensor cores in BF16 / FP16 with FP32
+accumulation, against the FP64 oracle.
+
+Tolerance (the benchmark spec, BF16/FP16 form): relative L2 <= 1e-2 per map and max-abs <= 2e-2 on the
+normalised [0, 1] map S.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def sal():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_06174_gb300 as s
+    s.load()
+    return s
+
+
+def _run(sal, V, params, D=None):
+    eng = sal.Saliency(V.shape, params)
+    try:
+        out = eng.saliency(torch.from_numpy(V).cuda(), None if D is None else torch.from_numpy(D).cuda(),
+                           intermediates=True)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        eng.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,shape,boundary", [
+    (8, (9, 21, 37), "symmetric"),
+    (8, (6, 16, 16), "periodic"),
+    (16, (6, 11, 35), "symmetric"),
+    (16, (5, 8, 16), "zero"),
+])
+def test_tensor_core_forward_matches_oracle(sal, prec, n, shape, boundary):
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + shape[1], faults=2))
+    p = sal.Params(n=n, boundary=boundary, prec=prec)
+    g = _run(sal, V, p)
+    ref = oracle.saliency(V, n, boundary=boundary,
+                          stencil=oracle.dcs_stencil(p.directions, p.R, p.sigma))
+    errs = {f"E{m}": rel_l2(g["E"][m], ref["E"][m]) for m in range(3)}
+    errs.update({f"S{m}": rel_l2(g["S3"][m], ref["S3"][m]) for m in range(3)})
+    errs["S"] = rel_l2(g["S"], ref["S"])
+    print(prec, n, shape, {k: f"{v:.2e}" for k, v in errs.items()}, "maxabs", np.abs(g["S"] - ref["S"]).max())
+    for k, v in errs.items():
+        assert v <= 1e-2, (k, v)
+    assert np.abs(g["S"] - ref["S"]).max() <= 2e-2
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tensor_core_salt128_n16_sampled(sal, prec):
+    """The 128^3 workload: raw maps at seeded voxels against the oracle, and the normalised map
+    against the FP32 GPU form."""
+    V, _ = synth.volume("salt128")
+    g = _run(sal, V, sal.Params(n=16, prec=prec))
+    g32 = _run(sal, V, sal.Params(n=16, prec="fp32"))
+    p = sal.Params(n=16)
+    st = oracle.dcs_stencil(p.directions, p.R, p.sigma)
+    pts = synth.sample_points(V.shape, 40, seed=5)
+    Ec, Sc = oracle.center_surround_at(V, pts, 16, st[0], st[3])
+    for m in range(3):
+        assert rel_l2(g["E"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Ec[:, m]) <= 1e-2
+        assert rel_l2(g["S3"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Sc[:, m]) <= 1e-2
+    assert rel_l2(g["S"], g32["S"]) <= 1e-2
+    assert np.abs(g["S"] - g32["S"]).max() <= 2e-2
