@@ -40,8 +40,31 @@ WORKLOADS = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
-K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840}   # profiles/salt128_n16_fp32_fwd_bwd.md
+K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840}   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
 K5_TRAFFIC = {}
+
+
+def measured_peaks():
+    """Measured peaks of the GB300s, if present."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def k1_roofline(prec, achieved, traffic):
+    """K1's contraction flops against the pipe they run on: FP32 FMA (SIMT form) or the tensor
+    cores (BF16/FP16 form, where the SIMT stages and the |F| epilogue bind instead)."""
+    if prec == "fp32":
+        return {"pipe": "fp32 fma", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic}
+    pk = measured_peaks().get("bf16_tflops", 1900.0)
+    return {"pipe": "tensor (kind::f16)", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense "
+            "rate is the same", "binding": "SIMT stages 1-2 and the |F| epilogue (FMA/MUFU), see profiles/",
+            "traffic": traffic}
 
 
 def k1_flops_per_voxel(n: int) -> int:
@@ -112,6 +135,23 @@ def cpu_oracle_rate(V, n, sample, backward=True):
     return sub.size / dt / 1e6, dt, sub.shape
 
 
+def sampled_error(V, n, params, E, S3, count=48, seed=7):
+    """Relative L2 error of the GPU's raw maps E_m and S_m against the FP64 oracle at seeded voxels
+    (the oracle computes them one voxel at a time)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    st = oracle.dcs_stencil(params.directions, params.R, params.sigma)
+    pts = synth.sample_points(V.shape, count, seed=seed)
+    Ec, Sc = oracle.center_surround_at(V, pts, n, st[0], st[3])
+    Eg = E.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
+    Sg = S3.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"voxels": count, "E_rel_l2": [rel(Eg[:, m], Ec[:, m]) for m in range(3)],
+            "S_m_rel_l2": [rel(Sg[:, m], Sc[:, m]) for m in range(3)]}
+
+
 def _upstream(shape):
     """Fixed seeded upstream gradient dL/dS of the backward half of a step."""
     import numpy as np
@@ -153,6 +193,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="salt128", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp32"],
+                    help="arithmetic of the local-DFT contraction (bf16/fp16: tensor cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
@@ -182,7 +224,7 @@ def main():
 
     V, _ = synth.volume(wl["spec"], with_mask=False)
     nvox = V.size
-    params = sal.Params(n=wl["n"])
+    params = sal.Params(n=wl["n"], prec=args.prec)
     eng = sal.Saliency(V.shape, params)
     dev = torch.device("cuda", local_rank)
     Vd = torch.from_numpy(V).to(dev)
@@ -277,6 +319,26 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_value = world * nvox * args.steps / (float(t[0]) / 1e3) / 1e6
 
+    # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
+    k1_fp32_ms = None
+    if args.prec != "fp32":
+        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32"))
+        E32 = torch.empty_like(E)
+        for _ in range(3):
+            sal.sal_local_spectra_project(eng32.h, Vd, E32)
+        barrier()
+        tot = 0.0
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sal.sal_local_spectra_project(eng32.h, Vd, E32)
+            b.record()
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        k1_fp32_ms = tot / args.steps
+        eng32.close()
+
     n = wl["n"]
     names = [c[0] for c in calls]
     # dominant kernel: K5 (spectral adjoint: brick recompute + transposed stages, 2x the K1 contraction)
@@ -287,20 +349,24 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "n": n, "shape": list(V.shape), "precision": "fp32",
+        "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[args.prec], "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": n, "shape": list(V.shape),
+                   "precision": args.prec + (" tensor-core local DFT (FP32 accumulate), FP32 backward"
+                                             if args.prec != "fp32" else " SIMT"),
                    "form": "forward+backward (upstream gradient fixed, seeded)",
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "forward": {"value": world * nvox * args.steps / (fwd_ms / 1e3) / 1e6, "unit": "Mvoxel/s",
                     "ms_per_step": fwd_ms / args.steps},
         "ms_per_call": {nm: v / args.steps for nm, v in zip(names, per_call)},
+        "k1_vs_fp32": None if k1_fp32_ms is None else {
+            "k1_ms": k1_ms, "k1_fp32_ms": k1_fp32_ms, "speedup": k1_fp32_ms / k1_ms,
+            "forward_fp32_Mvoxel_s": world * nvox / ((k1_fp32_ms + sum(per_call[1:3]) / args.steps) / 1e3) / 1e6},
         "roofline": {"kernel": "k5_spectra_adjoint_f32 (+ overlap-add gather)", "bound": "alu", "achieved": k5_ach,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": k5_ach / FP32_PEAK_TFLOPS,
                      "traffic": K5_TRAFFIC.get((args.workload, n, "fp32")),
                      "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
-                     "k1": {"achieved": k1_ach, "frac": k1_ach / FP32_PEAK_TFLOPS,
-                            "traffic": K1_TRAFFIC.get((args.workload, n, "fp32"))}},
+                     "k1": k1_roofline(args.prec, k1_ach, K1_TRAFFIC.get((args.workload, n, args.prec)))},
         "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 2 * V.nbytes,
                 "d2h_bytes_per_step": 2 * V.nbytes},
         "gpu_launches": launches,
@@ -312,7 +378,8 @@ def main():
         rate, dt, shape = cpu_oracle_rate(V, n, s)
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{s}^3 corner sub-volume of the workload, FP64 forward+backward, "
-                                          f"{dt:.1f} s"}
+                                          f"{dt:.1f} s",
+                                "sampled_error_vs_fp64": sampled_error(V, n, params, E, S3)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     eng.close()
