@@ -217,15 +217,17 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
 }
 
 // Overlap-add of the spectral adjoint: gV[q] += sum of every brick block element whose extended
-// position maps to q.  Blocks of the bricks with t0 in [t_begin, t_begin + t_count).
+// position maps to q.  Blocks of the bricks with t0 in [t_begin, t_begin + t_count); brick (xs, ys)
+// covers x_ext in [xs*BX - n/2, xs*BX + BX + n/2 - 1), y_ext likewise with BY.
 __global__ void __launch_bounds__(kThreads)
 k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, int X, int Y, int bnd, int n,
-              int BY, int YH, int t_begin, int t_count) {
+              int BX, int XH, int BY, int YH, int t_begin, int t_count) {
     const long long NV = (long long)T * X * Y;
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
+    const int nxs = (X + BX - 1) / BX;
     const int t_end = t_begin + t_count;
-    const long long bsz = (long long)n * n * YH;
+    const long long bsz = (long long)n * XH * YH;
     for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < NV; q += (long long)gridDim.x * kThreads) {
         const int y = (int)(q % Y);
         const int x = (int)((q / Y) % X);
@@ -243,17 +245,17 @@ k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, i
                 const int ut = te - t0 + h2;
                 for (int b = 0; b < nx; ++b) {
                     const int xe = ex[b];
-                    const int x0a = max(0, xe - h2 + 1), x0b = min(X - 1, xe + h2);
-                    for (int x0 = x0a; x0 <= x0b; ++x0) {
-                        const int ux = xe - x0 + h2;
-                        const long long cta_row = ((long long)(t0 - t_begin) * X + x0) * nseg;
+                    const int xa = max(0, ceildiv(xe + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(xe + h2, BX));
+                    for (int xs = xa; xs <= xb; ++xs) {
+                        const int ux = xe - xs * BX + h2;
+                        const long long cta_row = ((long long)(t0 - t_begin) * nxs + xs) * nseg;
                         for (int c = 0; c < ny; ++c) {
                             const int ye = ey[c];
                             const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
                             const int sb = min(nseg - 1, floordiv(ye + h2, BY));
                             for (int sg = sa; sg <= sb; ++sg) {
                                 const int yy = ye - sg * BY + h2;
-                                sum += __ldg(blocks + (cta_row + sg) * bsz + ((long long)ut * n + ux) * YH + yy);
+                                sum += __ldg(blocks + (cta_row + sg) * bsz + ((long long)ut * XH + ux) * YH + yy);
                             }
                         }
                     }
@@ -316,7 +318,7 @@ cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int 
     const long long NV = (long long)T * X * Y;
     long long nb = (NV + kThreads - 1) / kThreads;
     if (nb > 152 * 32) nb = 152 * 32;
-    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BY, g.YH, t_begin, t_count);
+    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -276,11 +276,11 @@ cudaError_t spectra_adjoint_f32_prepare(int n) {
 
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
     switch (n) {
-        case 2: return {BGeo<2>::BY, BGeo<2>::YH, BGeo<2>::BLOCK_FLOATS};
-        case 4: return {BGeo<4>::BY, BGeo<4>::YH, BGeo<4>::BLOCK_FLOATS};
-        case 8: return {BGeo<8>::BY, BGeo<8>::YH, BGeo<8>::BLOCK_FLOATS};
-        case 16: return {BGeo<16>::BY, BGeo<16>::YH, BGeo<16>::BLOCK_FLOATS};
-        default: return {0, 0, 0};
+        case 2: return {BGeo<2>::BY, BGeo<2>::YH, 1, 2, BGeo<2>::BLOCK_FLOATS};
+        case 4: return {BGeo<4>::BY, BGeo<4>::YH, 1, 4, BGeo<4>::BLOCK_FLOATS};
+        case 8: return {BGeo<8>::BY, BGeo<8>::YH, 1, 8, BGeo<8>::BLOCK_FLOATS};
+        case 16: return {BGeo<16>::BY, BGeo<16>::YH, 1, 16, BGeo<16>::BLOCK_FLOATS};
+        default: return {0, 0, 0, 0, 0};
     }
 }
 

@@ -177,6 +177,7 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     e = sal::spectra_f32_prepare(h->n);
     if (e == cudaSuccess) e = sal::spectra_adjoint_f32_prepare(h->n);
     if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
+    if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_adjoint_tc_prepare(h->n, 0);
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
 
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
@@ -301,11 +302,16 @@ namespace {
 
 constexpr size_t kBlocksCap = (size_t)2 << 30;  // brick-block scratch of the spectral adjoint (per slab)
 
+// Brick geometry of the spectral adjoint in the handle's precision.
+sal::SpectraAdjointGeometry adjoint_geometry(const sal_handle* h) {
+    return h->prec == SAL_FP32 ? sal::spectra_adjoint_f32_geometry(h->n) : sal::spectra_adjoint_tc_geometry(h->n);
+}
+
 sal_status ensure_backward_scratch(sal_handle* h) {
     if (h->gE) return SAL_OK;
-    const sal::SpectraAdjointGeometry g = sal::spectra_adjoint_f32_geometry(h->n);
+    const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     const int nseg = (h->Y + g.BY - 1) / g.BY;
-    const size_t per_t = (size_t)h->X * nseg * g.block_floats * sizeof(float);
+    const size_t per_t = (size_t)((h->X + g.BX - 1) / g.BX) * nseg * g.block_floats * sizeof(float);
     size_t cap = kBlocksCap;
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
     const size_t bpart = (size_t)sal::kRedBlocks * 64 * sizeof(double);
@@ -336,12 +342,17 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     cudaError_t e;
     if ((e = cudaMemsetAsync(gV, 0, (size_t)h->N * sizeof(float), st)) != cudaSuccess)
         return cuda_fail(h, e, "spectral adjoint: memset");
-    const sal::SpectraAdjointGeometry g = sal::spectra_adjoint_f32_geometry(h->n);
+    const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     for (int t_begin = 0; t_begin < h->T; t_begin += h->slab_t) {
         const int cnt = std::min(h->slab_t, h->T - t_begin);
-        if ((e = sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
-                                                 t_begin, cnt, st)) != cudaSuccess)
-            return cuda_fail(h, e, "spectral adjoint");
+        e = h->prec == SAL_FP32
+                ? sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
+                                                  t_begin, cnt, st)
+                // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
+                // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
+                : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
+                                                 t_begin, cnt, h->err_dev, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
         if ((e = sal::gather_add_launch(h->blocks, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt, st)) !=
             cudaSuccess)
             return cuda_fail(h, e, "spectral adjoint: overlap-add");

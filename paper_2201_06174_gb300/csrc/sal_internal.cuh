@@ -81,15 +81,25 @@ cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, f
                            long long N, double delta, bool s3_partials_ready, const Reduce& r, cudaStream_t s);
 
 // ---- K4/K5 and the backward reductions ---------------------------------------------------------
+// Brick of the spectral adjoint: outputs x0 in [xs*BX, xs*BX+BX), y0 in [ys*BY, ys*BY+BY) at one t0;
+// its block of gVext is [u_t in n][XH = BX+n-1][YH = BY+n-1] floats.
 struct SpectraAdjointGeometry {
     int BY;            // outputs per brick along y
     int YH;            // y extent of a brick's block
-    int block_floats;  // n * n * YH: scratch floats per brick
+    int BX;            // outputs per brick along x
+    int XH;            // x extent of a brick's block
+    int block_floats;  // n * XH * YH: scratch floats per brick
 };
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
                                        int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s);
+// K5 on the tensor cores (FP16 operands: fmt must be 0)
+cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
+SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
+cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const float* V, const float* gE,
+                                      float* blocks, int T, int X, int Y, int bnd, int t_begin, int t_count, int* err,
+                                      cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]

@@ -78,3 +78,66 @@ def test_tensor_core_salt128_n16_sampled(sal, prec):
         assert rel_l2(g["S3"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Sc[:, m]) <= 1e-2
     assert rel_l2(g["S"], g32["S"]) <= 1e-2
     assert np.abs(g["S"] - g32["S"]).max() <= 2e-2
+
+
+# ---- backward on the tensor cores ------------------------------------------------------------------
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,shape,boundary,slabs", [
+    (8, (7, 21, 37), "symmetric", 1),
+    (8, (9, 16, 20), "zero", 3),
+    (16, (6, 11, 35), "symmetric", 1),
+    (16, (5, 9, 18), "periodic", 2),
+])
+def test_tensor_core_spectral_adjoint_matches_oracle(sal, prec, n, shape, boundary, slabs):
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 3, faults=1))
+    gE = synth.random_volume((3,) + shape, seed=n + 9)
+    budget = 0
+    if slabs > 1:
+        P = 128 // n
+        nxs, nys = -(-shape[1] // P), -(-shape[2] // 16)
+        per_t = nxs * nys * n * (P + n - 1) * (16 + n - 1) * 4
+        base = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, prec=prec))
+        created = sal.sal_workspace_size(base.h)
+        base.close()
+        N = int(np.prod(shape))
+        budget = created + 3 * N * 4 + 1216 * 64 * 8 + per_t * max(1, shape[0] // slabs)
+    eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, prec=prec, hbm_budget_bytes=budget))
+    try:
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
+    finally:
+        eng.close()
+    ref = oracle.features_adjoint(V, gE, n, boundary=boundary)
+    err = rel_l2(got, ref)
+    print(prec, n, shape, boundary, "gV rel-L2", f"{err:.2e}")
+    assert err <= 1e-2
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,shape", [(8, (10, 18, 33)), (16, (6, 10, 20))])
+def test_tensor_core_fused_backward(sal, prec, n, shape):
+    V, D = synth.volume(synth.small_spec(shape, seed=n, faults=2))
+    W = np.array([0.45, 0.35, 0.2])
+    alpha = [1.0, 0.8, 1.2]
+    params = sal.Params(n=n, alpha=alpha, prec=prec)
+    st = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
+    fwd = oracle.saliency(V, n, stencil=st, weights=W)
+    gS = (fwd["S"] - D).astype(np.float32)
+    ref = oracle.saliency_backward(V, n, W, gS, stencil=st, fwd=fwd)
+    eng = sal.Saliency(shape, params)
+    try:
+        gV, gW, ga = eng.backward(_cuda(V), _cuda(W), _cuda(gS))
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    errs = (rel_l2(gV.cpu().numpy(), ref["gV"]), rel_l2(gW.cpu().numpy(), ref["gW"]),
+            rel_l2(ga.cpu().numpy(), ref["galpha"]))
+    print(prec, n, shape, "gV gW galpha rel-L2", [f"{e:.2e}" for e in errs])
+    assert max(errs) <= 1e-2
