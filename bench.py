@@ -28,7 +28,7 @@ METRIC = "Mvoxel/s full saliency map (fwd, fwd+bwd), BF16-TC vs FP32 at stated e
 WORKLOADS = {
     "salt128": dict(spec="salt128", n=16, desc="128x128x128 synthetic seismic volume (layered reflectivity, "
                     "30 Hz Ricker, 3 faults of random strike/dip with throw 2-8, salt ellipsoid 30/30/45 with "
-                    "boundary reflector, folds amp 5 / wavelength 64, noise 0.1 rms), window 16^3, FP32",
+                    "boundary reflector, folds amp 5 / wavelength 64, noise 0.1 rms), window 16^3",
                     cpu_sample=40, ref_sample=20),
     "fault48": dict(spec="fault48", n=8, desc="48^3 synthetic seismic volume (layers, one 60 deg normal fault "
                     "with throw 4, noise 0.1 rms), window 8^3, FP32", cpu_sample=48, ref_sample=32),
@@ -54,17 +54,32 @@ def measured_peaks():
         return {}
 
 
-def k1_roofline(prec, achieved, traffic):
-    """K1's contraction flops against the pipe they run on: FP32 FMA (SIMT form) or the tensor
-    cores (BF16/FP16 form, where the SIMT stages and the |F| epilogue bind instead)."""
+# MUFU (XU) pipe: 16 ops / clk / SM x 152 SMs x 2.07 GHz (derived from unit counts and the max clock)
+MUFU_PEAK_TOPS = 16 * 152 * 2.070e9 / 1e12
+
+
+def bins_per_voxel(n: int) -> int:
+    """abs(F) bins per voxel of the half spectrum (k_t in [0, n/2]): h n^2, one sqrt each."""
+    return (n // 2 + 1) * n * n
+
+
+def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic):
+    """Roofline of a spectral kernel.  FP32 form: its contraction flops (the per-voxel figure
+    4hn + 8hn^2 + 8hn^3, x2 for the adjoint) on the FP32 FMA pipe.  BF16/FP16 form: the
+    contraction runs on the tensor cores (reported as `tensor`), and the binding pipe is the
+    abs(F) epilogue, h n^2 square roots per voxel on the MUFU pipe."""
+    flops = flops_mult * k1_flops_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     if prec == "fp32":
-        return {"pipe": "fp32 fma", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic}
-    pk = measured_peaks().get("bf16_tflops", 1900.0)
-    return {"pipe": "tensor (kind::f16)", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-            "frac": achieved / pk, "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense "
-            "rate is the same", "binding": "SIMT stages 1-2 and the |F| epilogue (FMA/MUFU), see profiles/",
-            "traffic": traffic}
+        return {"kernel": kernel, "bound": "alu", "pipe": "fp32 fma", "achieved": flops, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": flops / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
+    bins = bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
+    tpk = measured_peaks().get("bf16_tflops", 1900.0)
+    return {"kernel": kernel, "bound": "alu", "pipe": "MUFU (abs(F) epilogue: one sqrt per bin)", "achieved": bins,
+            "peak": MUFU_PEAK_TOPS, "unit": "Tsqrt/s", "frac": bins / MUFU_PEAK_TOPS, "traffic": traffic,
+            "peak_note": "MUFU 16/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
+            "tensor": {"achieved_tflops": flops, "peak_tflops": tpk, "frac": flops / tpk,
+                       "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}}
 
 
 def k1_flops_per_voxel(n: int) -> int:
@@ -341,18 +356,21 @@ def main():
 
     n = wl["n"]
     names = [c[0] for c in calls]
-    # dominant kernel: K5 (spectral adjoint: brick recompute + transposed stages, 2x the K1 contraction)
+    # dominant kernel: K5 (spectral adjoint with brick recompute, incl. its overlap-add gather)
     k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
     k1_ms = per_call[names.index("k1_local_spectra_project")] / args.steps
-    k5_ach = 2 * k1_flops_per_voxel(n) * nvox / (k5_ms / 1e3) / 1e12
-    k1_ach = k1_flops_per_voxel(n) * nvox / (k1_ms / 1e3) / 1e12
+    tag = "tc" if args.prec != "fp32" else "f32"
+    rl = roofline(f"k5_spectra_adjoint_{tag} (+ k5_gather_add)", args.prec, n, nvox, k5_ms, 2,
+                  K5_TRAFFIC.get((args.workload, n, args.prec)))
+    rl["k1"] = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1,
+                        K1_TRAFFIC.get((args.workload, n, args.prec)))
     line = {
         "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[args.prec], "data": "synthetic",
         "config": {"workload": wl["desc"], "n": n, "shape": list(V.shape),
-                   "precision": args.prec + (" tensor-core local DFT (FP32 accumulate), FP32 backward"
-                                             if args.prec != "fp32" else " SIMT"),
+                   "precision": args.prec + (" tensor-core local DFT (FP32 accumulate); the adjoint's "
+                                             "tensor-core operands are FP16" if args.prec != "fp32" else " SIMT"),
                    "form": "forward+backward (upstream gradient fixed, seeded)",
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
@@ -362,11 +380,7 @@ def main():
         "k1_vs_fp32": None if k1_fp32_ms is None else {
             "k1_ms": k1_ms, "k1_fp32_ms": k1_fp32_ms, "speedup": k1_fp32_ms / k1_ms,
             "forward_fp32_Mvoxel_s": world * nvox / ((k1_fp32_ms + sum(per_call[1:3]) / args.steps) / 1e3) / 1e6},
-        "roofline": {"kernel": "k5_spectra_adjoint_f32 (+ overlap-add gather)", "bound": "alu", "achieved": k5_ach,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": k5_ach / FP32_PEAK_TFLOPS,
-                     "traffic": K5_TRAFFIC.get((args.workload, n, "fp32")),
-                     "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
-                     "k1": k1_roofline(args.prec, k1_ach, K1_TRAFFIC.get((args.workload, n, args.prec)))},
+        "roofline": rl,
         "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 2 * V.nbytes,
                 "d2h_bytes_per_step": 2 * V.nbytes},
         "gpu_launches": launches,
