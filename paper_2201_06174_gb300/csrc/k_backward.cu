@@ -197,17 +197,25 @@ k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long lo
     }
 }
 
-// galpha_d = sum_{o in d} g_o gw_o, gw_o = -(1/Q) sum_blocks part[block][o].  One block.
+// galpha_d = sum_{o in d} g_o gw_o, gw_o = -(1/Q) sum_blocks part[block][o].  One block; each
+// offset's partials are summed by a fixed-order tree.
 __global__ void __launch_bounds__(kThreads)
 k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_constant__ Stencil st,
                    float* __restrict__ galpha) {
+    __shared__ double red[kThreads];
     __shared__ double gw[kMaxOffsets];
-    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+    for (int o = 0; o < st.Q; ++o) {
         double a = 0.0;
-        for (int i = 0; i < nparts; ++i) a += part[i * 64 + o];
-        gw[o] = -a / st.Q;
+        for (int i = threadIdx.x; i < nparts; i += kThreads) a += part[i * 64 + o];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int s = kThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) gw[o] = -red[0] / st.Q;
+        __syncthreads();
     }
-    __syncthreads();
     if (threadIdx.x < st.n_dirs) {
         double a = 0.0;
         for (int o = 0; o < st.Q; ++o)

@@ -28,7 +28,8 @@ namespace {
 using f32::fast_rsqrt;
 using f32::Tw;
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;             // 16 warps: 4 per TMEM lane quarter
+constexpr int kGroups = kThreads / 128;   // warp groups sharing a lane quarter
 constexpr int kBY = 16;
 constexpr int kKRows = kBY + 15;
 constexpr uint32_t kTmemCols = 512;       // [0,256) forward F of 8 outputs; [256,320) inverse re/im
@@ -62,6 +63,7 @@ template <int N> struct BtGeo {
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * P * kBY * 4;
     static constexpr size_t OFF_MISC = OFF_L1 + (size_t)P * kBY * 4;
     static constexpr size_t SMEM_USED = OFF_MISC + 64 + 2 * (kThreads / 32) * 4;
+    static_assert(4 % kGroups == 0, "operand slots per warp group");
     // one CTA per SM: it holds all 512 tensor-memory columns
     static constexpr size_t SMEM = SMEM_USED > (size_t)120 * 1024 ? SMEM_USED : (size_t)120 * 1024;
     static constexpr int BLOCK_FLOATS = N * XH * YH;
@@ -225,7 +227,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const float inv_scale = 1.f / (bmax > 0.f ? bmax : 1.f);
     const float sigma = bgmax > 0.f ? (float)(N * N * N) / (8.f * bgmax) : 1.f;  // Gamma' operand scale
 
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, grp = warp >> 2;   // lane quarter, warp group
     const int m = 32 * q + lane;                 // TMEM lane = stage-3 row (x0l, k_x)
     const int x0l = m / N, kx = m % N;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
@@ -337,8 +339,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             for (int batch = 0; batch < 2; ++batch) {
                 if (ok) {
 #pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        const int slot = half * 2 + jj;            // operand slot in this batch
+                    for (int jj = 0; jj < 4 / kGroups; ++jj) {
+                        const int slot = grp * (4 / kGroups) + jj;  // operand slot in this batch
                         const int j = batch * 4 + slot;            // TMEM output slot of this pass
                         const int y0 = pass * 8 + j;
                         float v[32];
@@ -413,7 +415,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             __syncthreads();
         }
         // ---- Gamma_G2[row][y] from the accumulator (unscaled) ----------------------------------------
-        if (half == 0 && !*s_fail) {
+        if (grp == 0 && !*s_fail) {
             float vr[32], vi[32];
             tc::tmem_ld32(tmem + lane_base + kInvCol, vr);
             tc::tmem_ld32(tmem + lane_base + kInvCol + 32, vi);
