@@ -33,8 +33,11 @@ WORKLOADS = {
     "fault48": dict(spec="fault48", n=8, desc="48^3 synthetic seismic volume (layers, one 60 deg normal fault "
                     "with throw 4, noise 0.1 rms), window 8^3, FP32", cpu_sample=48, ref_sample=32),
     "precision256x384x192": dict(spec="precision256x384x192", n=16, desc="256x384x192 synthetic seismic volume "
-                                 "(6 faults, 2 salt bodies, SNR 5 dB), window 16^3, FP32", cpu_sample=48,
-                                 ref_sample=24),
+                                 "(6 faults, 2 salt bodies, SNR 5 dB, folds), window 16^3", cpu_sample=40,
+                                 ref_sample=20),
+    "full462x951x651": dict(spec="full462x951x651", n=16, desc="462x951x651 synthetic seismic volume (20 faults, "
+                            "3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3", cpu_sample=40,
+                            ref_sample=20),
 }
 # Peak of the binding pipe of K1 (FP32 SIMT form): 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
