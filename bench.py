@@ -85,6 +85,20 @@ def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic):
                        "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}}
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise max of per-rank timings (the slowest rank bounds the job)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_throughput(world: int, voxels_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job Mvoxel/s: every rank processes its own volume per step (weak scaling)."""
+    return world * voxels_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
 def k1_flops_per_voxel(n: int) -> int:
     """Algorithmic flops per voxel of the separable sliding local DFT (stages along t, x, y with
     h = n/2+1 retained t-bins): 4hn + 8hn^2 + 8hn^3."""
@@ -300,13 +314,10 @@ def main():
     clk = clocks.stop()
     per_call = [sum(ev[j].elapsed_time(ev[j + 1]) for ev in evs) for j in range(len(calls))]
     total_ms = sum(per_call)
-    t = torch.tensor([total_ms] + per_call, dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t[0])
-    per_call = [float(v) for v in t[1:]]
+    red = max_over_ranks([total_ms] + per_call, dist, dev)
+    total_ms, per_call = red[0], red[1:]
     fwd_ms = sum(per_call[:3])
-    value = world * nvox * args.steps / (total_ms / 1e3) / 1e6
+    value = job_throughput(world, nvox, args.steps, total_ms)
 
     # end to end through the fused public calls, host buffers, copies inside the timed region
     Vh = torch.from_numpy(V).pin_memory()
@@ -331,11 +342,8 @@ def main():
         e2e_step()
     e1.record()
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * nvox * args.steps / (float(t[0]) / 1e3) / 1e6
+    e2e_ms = max_over_ranks([e0.elapsed_time(e1)], dist, dev)[0]
+    e2e_value = job_throughput(world, nvox, args.steps, e2e_ms)
 
     # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
     k1_fp32_ms = None

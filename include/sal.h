@@ -57,8 +57,9 @@ typedef enum {
 } sal_boundary;
 
 typedef struct {
-    int n;                  /* cube side of the local DFT (Sec. 2 step 1, Eq. 2); even,
-                               2 <= n <= 16 for SAL_FP32, n in {8,16} for BF16/FP16   */
+    int n;                  /* cube side of the local DFT (Sec. 2 step 1, Eq. 2): n in
+                               {2,4,8,16,32} for SAL_FP32, {8,16,32} for BF16/FP16; the
+                               backward calls are built for n <= 16                      */
     int stride;             /* window stride; must be 1 (a cube around every voxel)   */
     int taper;              /* 0 = rectangular (the cube as is), 1 = periodic Hann    */
     int boundary;           /* sal_boundary                                           */

@@ -94,6 +94,11 @@ sal_status check_handle(sal_handle* h) {
 
 // K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.
 cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) {
+    if (h->n == 32) {
+        if (h->prec == SAL_FP32) return sal::spectra_f32_n32_launch(h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+        return sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
+                                        h->err_dev, st);
+    }
     if (h->prec == SAL_FP32) return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
     return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
                                   h->err_dev, st);
@@ -122,10 +127,10 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     if (p->boundary < 0 || p->boundary > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad boundary");
     if (p->feature != 0) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only feature 0 is built");
     if (p->prec < 0 || p->prec > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad precision");
-    if (!sal::spectra_f32_supported(p->n))
-        return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16}");
-    if (p->prec != SAL_FP32 && !sal::spectra_tc_supported(p->n))
-        return fail(nullptr, SAL_ERR_UNSUPPORTED, "BF16/FP16 tensor-core path is built for n in {8,16}");
+    if (!sal::spectra_f32_supported(p->n) && p->n != 32)
+        return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16,32}");
+    if (p->prec != SAL_FP32 && !sal::spectra_tc_supported(p->n) && p->n != 32)
+        return fail(nullptr, SAL_ERR_UNSUPPORTED, "BF16/FP16 tensor-core path is built for n in {8,16,32}");
     if (p->n_offsets < 1 || p->n_offsets > sal::kMaxOffsets)
         return fail(nullptr, SAL_ERR_INVALID_ARG, "n_offsets must be in [1, 64]");
     if (p->n_dirs < 1 || p->n_dirs > sal::kMaxDirs)
@@ -174,10 +179,15 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
-    e = sal::spectra_f32_prepare(h->n);
-    if (e == cudaSuccess) e = sal::spectra_adjoint_f32_prepare(h->n);
-    if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
-    if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_adjoint_tc_prepare(h->n, 0);
+    if (h->n == 32) {
+        // forward only: the backward of the 32^3 window is not built
+        e = h->prec == SAL_FP32 ? sal::spectra_f32_n32_prepare() : sal::spectra_tc32_prepare(h->prec == SAL_BF16 ? 1 : 0);
+    } else {
+        e = sal::spectra_f32_prepare(h->n);
+        if (e == cudaSuccess) e = sal::spectra_adjoint_f32_prepare(h->n);
+        if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
+        if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_adjoint_tc_prepare(h->n, 0);
+    }
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
 
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
@@ -308,6 +318,7 @@ sal::SpectraAdjointGeometry adjoint_geometry(const sal_handle* h) {
 }
 
 sal_status ensure_backward_scratch(sal_handle* h) {
+    if (h->n == 32) return fail(h, SAL_ERR_UNSUPPORTED, "the backward is built for n in {2,4,8,16}");
     if (h->gE) return SAL_OK;
     const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     const int nseg = (h->Y + g.BY - 1) / g.BY;

@@ -65,6 +65,14 @@ cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
                                int Y, int bnd, cudaStream_t s);
 
+// K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
+cudaError_t spectra_f32_n32_prepare();
+cudaError_t spectra_f32_n32_launch(const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y, int bnd,
+                                   cudaStream_t s);
+cudaError_t spectra_tc32_prepare(int fmt);
+cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
+                                int bnd, int* err, cudaStream_t s);
+
 // K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word
 bool spectra_tc_supported(int n);
 cudaError_t spectra_tc_prepare(int n, int fmt);

@@ -40,6 +40,7 @@ def _create(**kw):
     (dict(n=0), salmod.SAL_ERR_INVALID_ARG),
     (dict(n=34), salmod.SAL_ERR_INVALID_ARG),
     (dict(n=6), salmod.SAL_ERR_UNSUPPORTED),
+    (dict(n=32, prec="bf16", shape=(70000, 4, 4)), salmod.SAL_ERR_UNSUPPORTED),
     (dict(shape=(0, 4, 4)), salmod.SAL_ERR_INVALID_ARG),
     (dict(shape=(70000, 4, 4)), salmod.SAL_ERR_UNSUPPORTED),
     (dict(offsets=np.array([[9, 0, 0]]), gauss_w=np.array([1.0]), dir_id=np.array([0])), salmod.SAL_ERR_INVALID_ARG),

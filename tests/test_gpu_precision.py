@@ -141,3 +141,33 @@ def test_tensor_core_fused_backward(sal, prec, n, shape):
             rel_l2(ga.cpu().numpy(), ref["galpha"]))
     print(prec, n, shape, "gV gW galpha rel-L2", [f"{e:.2e}" for e in errs])
     assert max(errs) <= 1e-2
+
+
+# ---- the 32^3 window -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 1e-2), ("fp16", 1e-2)])
+def test_window32_forward_matches_oracle(sal, prec, tol):
+    shape = (5, 9, 21)
+    V, _ = synth.volume(synth.small_spec(shape, seed=32, faults=2))
+    p = sal.Params(n=32, prec=prec)
+    g = _run(sal, V, p)
+    ref = oracle.saliency(V, 32, stencil=oracle.dcs_stencil(p.directions, p.R, p.sigma))
+    errs = {f"E{m}": rel_l2(g["E"][m], ref["E"][m]) for m in range(3)}
+    errs.update({f"S{m}": rel_l2(g["S3"][m], ref["S3"][m]) for m in range(3)})
+    errs["S"] = rel_l2(g["S"], ref["S"])
+    print(prec, 32, shape, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= tol, (k, v)
+    if prec != "fp32":
+        assert np.abs(g["S"] - ref["S"]).max() <= 2e-2
+
+
+def test_window32_backward_is_not_built(sal):
+    eng = sal.Saliency((4, 4, 8), sal.Params(n=32))
+    try:
+        with pytest.raises(sal.SalError) as ei:
+            eng.backward(torch.zeros((4, 4, 8), device="cuda"), torch.ones(3, device="cuda") / 3,
+                         torch.zeros((4, 4, 8), device="cuda"))
+        assert ei.value.status == 2  # SAL_ERR_UNSUPPORTED
+    finally:
+        eng.close()
