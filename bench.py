@@ -151,7 +151,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(V, n, sample, backward=True):
+def cpu_oracle_rate(V, n, sample, backward=True):  # noqa: C901
     """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host
     cores): forward, and the backward with the same fixed upstream gradient as the GPU step."""
     import numpy as np
@@ -198,11 +198,12 @@ def run_reference(args, wl):
     import synth
     V, _ = synth.volume(wl["spec"], with_mask=False)
     s = wl["ref_sample"]
+    bwd = getattr(args, "form", "fwdbwd") == "fwdbwd"
     for _ in range(args.warmup):
-        cpu_oracle_rate(V, wl["n"], s)
+        cpu_oracle_rate(V, wl["n"], s, backward=bwd)
     times = []
     for _ in range(args.steps):
-        _, dt, shape = cpu_oracle_rate(V, wl["n"], s)
+        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd)
         times.append(dt)
     vox = s ** 3
     value = vox * args.steps / sum(times) / 1e6
@@ -227,9 +228,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp32"],
                     help="arithmetic of the local-DFT contraction (bf16/fp16: tensor cores)")
+    ap.add_argument("--n", type=int, default=None, help="window side (overrides the workload's)")
+    ap.add_argument("--form", default="fwdbwd", choices=["fwdbwd", "fwd"],
+                    help="fwdbwd: forward + backward step (default); fwd: forward only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.n is not None:
+        wl["n"] = args.n
+        wl["desc"] = wl["desc"].replace("window 16^3", f"window {args.n}^3")
+    if wl["n"] >= 32:  # the FP64 oracle costs 12 n^4 flop per voxel: keep its sample to ~30 s
+        wl["cpu_sample"], wl["ref_sample"] = 16, 12
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -284,6 +293,9 @@ def main():
         ("k5_local_spectra_project_backward", lambda: sal.sal_local_spectra_project_backward(eng.h, Vd, gE, gV)),
     ]
 
+    if args.form == "fwd":
+        calls = calls[:3]
+
     def step():
         for _, c in calls:
             c()
@@ -327,11 +339,14 @@ def main():
 
     def e2e_step():
         Vd.copy_(Vh, non_blocking=True)
-        gSd.copy_(gSh, non_blocking=True)
+        if args.form == "fwdbwd":
+            gSd.copy_(gSh, non_blocking=True)
         sal.sal_saliency(eng.h, Vd, None, Wd, S, None, None, W)
-        sal.sal_saliency_backward(eng.h, Vd, Wd, gSd, gV, gW, galpha)
+        if args.form == "fwdbwd":
+            sal.sal_saliency_backward(eng.h, Vd, Wd, gSd, gV, gW, galpha)
         Sh.copy_(S, non_blocking=True)
-        gVh.copy_(gV, non_blocking=True)
+        if args.form == "fwdbwd":
+            gVh.copy_(gV, non_blocking=True)
 
     for _ in range(max(args.warmup, 3)):
         e2e_step()
@@ -367,14 +382,18 @@ def main():
 
     n = wl["n"]
     names = [c[0] for c in calls]
-    # dominant kernel: K5 (spectral adjoint with brick recompute, incl. its overlap-add gather)
-    k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
+    # dominant kernel: K5 (spectral adjoint with brick recompute, incl. its overlap-add gather);
+    # K1 in the forward-only form
     k1_ms = per_call[names.index("k1_local_spectra_project")] / args.steps
     tag = "tc" if args.prec != "fp32" else "f32"
-    rl = roofline(f"k5_spectra_adjoint_{tag} (+ k5_gather_add)", args.prec, n, nvox, k5_ms, 2,
-                  K5_TRAFFIC.get((args.workload, n, args.prec)))
-    rl["k1"] = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1,
-                        K1_TRAFFIC.get((args.workload, n, args.prec)))
+    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1, K1_TRAFFIC.get((args.workload, n, args.prec)))
+    if args.form == "fwdbwd":
+        k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
+        rl = roofline(f"k5_spectra_adjoint_{tag} (+ k5_gather_add)", args.prec, n, nvox, k5_ms, 2,
+                      K5_TRAFFIC.get((args.workload, n, args.prec)))
+        rl["k1"] = k1_rl
+    else:
+        rl = k1_rl
     line = {
         "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -382,7 +401,8 @@ def main():
         "config": {"workload": wl["desc"], "n": n, "shape": list(V.shape),
                    "precision": args.prec + (" tensor-core local DFT (FP32 accumulate); the adjoint's "
                                              "tensor-core operands are FP16" if args.prec != "fp32" else " SIMT"),
-                   "form": "forward+backward (upstream gradient fixed, seeded)",
+                   "form": "forward+backward (upstream gradient fixed, seeded)" if args.form == "fwdbwd"
+                   else "forward",
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "forward": {"value": world * nvox * args.steps / (fwd_ms / 1e3) / 1e6, "unit": "Mvoxel/s",
@@ -392,18 +412,19 @@ def main():
             "k1_ms": k1_ms, "k1_fp32_ms": k1_fp32_ms, "speedup": k1_fp32_ms / k1_ms,
             "forward_fp32_Mvoxel_s": world * nvox / ((k1_fp32_ms + sum(per_call[1:3]) / args.steps) / 1e3) / 1e6},
         "roofline": rl,
-        "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 2 * V.nbytes,
-                "d2h_bytes_per_step": 2 * V.nbytes},
+        "e2e": {"value": e2e_value, "unit": "Mvoxel/s",
+                "h2d_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes,
+                "d2h_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes},
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = wl["cpu_sample"]
-        rate, dt, shape = cpu_oracle_rate(V, n, s)
+        rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd")
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{s}^3 corner sub-volume of the workload, FP64 forward+backward, "
-                                          f"{dt:.1f} s",
+                                "sample": f"{s}^3 corner sub-volume of the workload, FP64 "
+                                          f"{'forward+backward' if args.form == 'fwdbwd' else 'forward'}, {dt:.1f} s",
                                 "sampled_error_vs_fp64": sampled_error(V, n, params, E, S3)}
     if rank == 0:
         print(json.dumps(line), flush=True)
