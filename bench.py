@@ -14,6 +14,7 @@ bracketed by barriers and the max over ranks is taken; value = all voxels / that
 """
 import argparse
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -31,7 +32,9 @@ WORKLOADS = {
                     "boundary reflector, folds amp 5 / wavelength 64, noise 0.1 rms), window 16^3",
                     cpu_sample=40, ref_sample=20),
     "fault48": dict(spec="fault48", n=8, desc="48^3 synthetic seismic volume (layers, one 60 deg normal fault "
-                    "with throw 4, noise 0.1 rms), window 8^3, FP32", cpu_sample=48, ref_sample=32),
+                    "with throw 4, noise 0.1 rms), window 8^3", cpu_sample=48, ref_sample=32),
+    "fault128": dict(spec="fault128", n=8, desc="128x128x128 synthetic seismic volume (layers, one 60 deg "
+                     "normal fault with throw 4, noise 0.1 rms), window 8^3", cpu_sample=48, ref_sample=32),
     "precision256x384x192": dict(spec="precision256x384x192", n=16, desc="256x384x192 synthetic seismic volume "
                                  "(6 faults, 2 salt bodies, SNR 5 dB, folds), window 16^3", cpu_sample=40,
                                  ref_sample=20),
@@ -236,7 +239,7 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:
         wl["n"] = args.n
-        wl["desc"] = wl["desc"].replace("window 16^3", f"window {args.n}^3")
+        wl["desc"] = re.sub(r"window \d+\^3", f"window {args.n}^3", wl["desc"])
     if wl["n"] >= 32:  # the FP64 oracle costs 12 n^4 flop per voxel: keep its sample to ~30 s
         wl["cpu_sample"], wl["ref_sample"] = 16, 12
     if args.impl == "reference":
