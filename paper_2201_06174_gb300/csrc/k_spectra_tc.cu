@@ -1,21 +1,27 @@
-// K1-TC: local 3D DFT + projection + feature (Sec. 2 steps 1-3; Eq. 2, Eq. 1) with the dominant
-// contraction -- stage 3, the DFT along y of every (k_t, k_x) row -- on the 5th-generation tensor
-// cores (tcgen05.mma, kind::f16, BF16 or FP16 operands, FP32 accumulation in tensor memory).
+// K1-TC: local 3D DFT + projection + feature (Sec. 2 steps 1-3; Eq. 2, Eq. 1) with all three
+// separable DFT stages on the 5th-generation tensor cores (tcgen05.mma, kind::f16, BF16 or FP16
+// operands, FP32 accumulation in tensor memory).  Only the abs(F) / Eq. 1 epilogue runs on the SIMT
+// pipes.
 //
-// CTA brick: t0, x0 in [xb, xb + P) with P = 128/n, y0 in [yb, yb + 16).
-// For each k_t tile (k_t = 0 .. n/2):
-//   stage 1 (SIMT, FP32):  G1[x][y]     = sum_u h(u) exp(-2 pi i k_t u / n) V[t0-n/2+u][x][y]
-//   stage 2 (SIMT, FP32):  G2[x0][k_x][y] = sum_u h(u) exp(-2 pi i k_x u / n) G1[x0-n/2+u][y]
-//            rounded (after a per-brick scale 1/max|V|) to BF16/FP16 into the A operand:
-//            row m = (x0 - xb) * n + k_x (128 rows), K = y, MN-major, no swizzle, 16-byte K rows
-//   stage 3 (tensor cores): per output y0, D = A[:, y0 .. y0+15] x B, B = [cos | sin] twiddles
-//            (pairing k_y with n-k_y: P = sum g cos, Q = sum g sin, F = P -+ iQ); the window of y0
-//            is the same descriptor moved by 16*y0 bytes.  Real and imaginary parts of A are two
-//            MMAs of N = 16 columns into tensor memory.
-//   epilogue (tcgen05.ld): |F| for every bin, weighted by r_m of Eq. 1 (table in shared memory),
-//            summed over k_y in registers, over k_t across tiles, over k_x by warp shuffles.
-// Every wait on the tensor cores is bounded; on timeout the CTA sets the error word and leaves
-// after releasing its tensor memory.
+// CTA brick: t0, x0 in [xb, xb + P) with P = 128/n, y0 in [yb, yb + 16).  Positions of the halo are
+// pos = x * YP + y (x < 24, y < YP = 8 ceil(YH / 8)).
+//   stage 1 (t), once for all k_t:  D1[pos][c] = sum_u V[t0-n/2+u][x][y] T1[u][c],
+//            c = [cos k_t = 0..n/2 | sin k_t = 1..n/2-1]; A = the brick scaled by 1/max|V| and
+//            rounded to 16 bits (MN-major: 8 consecutive y per 16-byte row), one MMA per 128 positions.
+//            D1 is read back once and scattered into one stage-2 B operand per k_t:
+//            G1 = P - iQ  ->  B2[(re|im, y)][(cos|sin, x)] = [[G1r, G1i], [G1i, -G1r]].
+//   stage 2 (x), per k_t:  D2[(x0, k_x)][(re|im, y)] = sum_x A2[(x0, k_x)][(cos|sin, x)] B2[..][..],
+//            A2 = the Toeplitz twiddles h(x - x0) [cos | sin](2 pi k_x (x - x0) / n): the sliding
+//            window along x is built into A2, so G2 = sum (c - i s)(G1r + i G1i) for all 16 k_x.
+//            D2 is rounded to 16 bits into the stage-3 A operands (real, imaginary), MN-major with
+//            16-byte K rows: the window of output y0 is the same descriptor moved by 16 y0 bytes.
+//   stage 3 (y), per k_t and output y0:  D3[(x0, k_x)][(re|im, k_y)] = Are(y0) B3a + Aim(y0) B3b,
+//            B3a = [c | -s], B3b = [s | c] over all k_y: the accumulator holds Re F and Im F.
+//   epilogue (tcgen05.ld): abs(F) per bin, bins k_y and n - k_y summed (same Eq. 1 ratios), weighted
+//            by r_m / |k| of Eq. 1, summed over k_y in registers, over k_t across tiles, over k_x by
+//            warp shuffles; E = sum * max|V|.
+// Every wait on the tensor cores is bounded; on timeout the CTA sets the error word and leaves after
+// releasing its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -30,8 +36,10 @@ using f32::Tw;
 
 constexpr int kThreads = 256;
 constexpr int kBY = 16;                 // outputs per CTA along y
-constexpr int kKRows = kBY + 15;        // K rows of the A operand: window start + 16 taps
-constexpr uint32_t kTmemCols = 256;     // 8 outputs x (16 + 16) FP32 columns
+constexpr int kKRows = kBY + 15;        // K rows of the stage-3 A operand: window start + 16 taps
+constexpr int kXHP = 24;                // halo rows along x staged (>= P + n - 1, multiple of 8)
+constexpr int kK2 = 2 * kXHP;           // stage-2 K: 24 cos taps + 24 sin taps
+constexpr uint32_t kTmemCols = 256;     // two 128-column accumulator buffers
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <int N> struct TcGeo {
@@ -39,22 +47,43 @@ template <int N> struct TcGeo {
     static constexpr int P = 128 / N;          // x0 positions per CTA
     static constexpr int XH = P + N - 1;       // x extent of the halo
     static constexpr int YH = kBY + N - 1;     // y extent of the halo
-    static constexpr uint32_t SBO_A = kKRows * 16;           // bytes between 8-row groups of A
-    static constexpr size_t IN_B = (size_t)N * XH * YH * 4;
-    static constexpr size_t G1_B = (size_t)XH * YH * 8;
-    static constexpr size_t A_B = (size_t)16 * SBO_A;        // one of A_re / A_im
-    static constexpr size_t B_B = 512;
-    static constexpr size_t WT_B = (size_t)H * N * H * 3 * 4;
-    static constexpr size_t OFF_G1 = IN_B;
-    static constexpr size_t OFF_A = (OFF_G1 + G1_B + 127) / 128 * 128;
-    static constexpr size_t OFF_B = OFF_A + 2 * A_B;
-    static constexpr size_t OFF_WT = OFF_B + B_B;
-    static constexpr size_t OFF_MISC = OFF_WT + WT_B;
-    static constexpr size_t SMEM_USED = OFF_MISC + 64 + kThreads / 32 * 4;
-    // at most two CTAs per SM: two x 256 tensor-memory columns fill the 512 of an SM
-    static constexpr size_t SMEM = SMEM_USED > (size_t)80 * 1024 ? SMEM_USED : (size_t)80 * 1024;
-    static_assert(2 * H - 2 <= 16, "B columns");
-    static_assert(YH <= kKRows, "window rows");
+    static constexpr int YG = (YH + 7) / 8;
+    static constexpr int YP = 8 * YG;          // y positions per halo row
+    static constexpr int NB1 = (kXHP * YP + 127) / 128;   // stage-1 MMAs (128 positions each)
+    static constexpr int N2 = 2 * YP;          // stage-2 N: re | im over y
+    static constexpr int N3 = 2 * N;           // stage-3 N per output: re | im over k_y
+    static constexpr int OPC = 32 / N3;        // outputs per 32-column TMEM chunk (1 or 2)
+    static constexpr int OPP = 128 / N3;       // outputs per pass (one 128-column buffer)
+    static constexpr int PASSES = kBY / OPP;   // 4 (n = 16) or 2 (n = 8), alternating buffers
+    static constexpr uint32_t SBO_A3 = kKRows * 16;
+    static constexpr uint32_t SBO_K2 = kK2 / 8 * 128;    // 8-row group stride of the K-major A2 / B2
+    static constexpr size_t A1_B = (size_t)NB1 * 4096;
+    static constexpr size_t B2_B = (size_t)N2 / 8 * SBO_K2;   // one k_t tile
+    static constexpr size_t B2ALL_B = (size_t)H * B2_B;
+    static constexpr size_t R0_B = A1_B > B2ALL_B ? A1_B : B2ALL_B;   // A1 then the B2 tiles (aliased)
+    // constant operands, built once per handle and bulk-copied into every CTA:
+    // [A2 | B1 | B3a | B3b | Eq. 1 weight table]
+    static constexpr size_t A2_B = (size_t)16 * SBO_K2;
+    static constexpr size_t B3_B = (size_t)N3 / 8 * 256;
+    static constexpr size_t WT_B = ((size_t)H * H * H * 3 * 4 + 15) / 16 * 16;
+    static constexpr size_t TAB_B1 = A2_B;
+    static constexpr size_t TAB_B3A = TAB_B1 + 512;
+    static constexpr size_t TAB_B3B = TAB_B3A + B3_B;
+    static constexpr size_t TAB_WT = TAB_B3B + B3_B;
+    static constexpr size_t TAB_B = TAB_WT + WT_B;
+    static constexpr size_t A3_B = (size_t)16 * SBO_A3;
+    static constexpr size_t OFF_TAB = (R0_B + 127) / 128 * 128;
+    static constexpr size_t OFF_A3 = OFF_TAB + TAB_B;
+    static constexpr size_t OFF_MISC = OFF_A3 + 2 * A3_B;
+    static constexpr size_t SMEM = OFF_MISC + 64 + kThreads / 32 * 4;
+    static constexpr int STAGE_ITEMS = 16 * NB1 * 16;   // (u, 8-position group) items of the A1 fill
+    static constexpr int STAGE_PER_THREAD = (STAGE_ITEMS + kThreads - 1) / kThreads;
+    static_assert(XH <= kXHP && YH <= 32 && YP <= 32, "halo");
+    static_assert(2 * H - 2 <= 16, "stage-1 columns");
+    static_assert(NB1 * 16 <= (int)kTmemCols && N2 <= 128, "tensor memory");
+    static_assert(PASSES * OPP == kBY && PASSES % 2 == 0 && PASSES * OPC * 2 == 8, "passes");
+    static_assert(TAB_B % 16 == 0 && OFF_TAB % 16 == 0 && OFF_A3 % 16 == 0, "bulk copy alignment");
+    static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
 };
 
 template <int FMT> struct Pack;
@@ -79,22 +108,89 @@ template <> struct Pack<0> {  // FP16
     }
 };
 
+// Twiddles of any bin k in [0, n): h(u) cos(2 pi k u / n) and h(u) sin(2 pi k u / n); 0 outside [0, n).
+template <int N> __device__ __forceinline__ float twc(const Tw<N>& tw, int k, int u) {
+    if (u < 0 || u >= N) return 0.f;
+    return k <= N / 2 ? tw.c[k][u] : tw.c[N - k][u];
+}
+template <int N> __device__ __forceinline__ float tws(const Tw<N>& tw, int k, int u) {
+    if (u < 0 || u >= N) return 0.f;
+    return k <= N / 2 ? tw.s[k][u] : -tw.s[N - k][u];
+}
+
+// The constant operands of one (n, operand type): A2 (Toeplitz stage-2 twiddles, K-major), B1
+// (stage-1 twiddles), B3a / B3b (stage-3 twiddles), the Eq. 1 weight table [k_t][|k_x|][|k_y|][3].
+template <int N, int FMT>
+__global__ void k1_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out) {
+    using G = TcGeo<N>;
+    constexpr int H = G::H;
+    unsigned char* a2 = out;
+    unsigned char* b1 = out + G::TAB_B1;
+    unsigned char* b3a = out + G::TAB_B3A;
+    unsigned char* b3b = out + G::TAB_B3B;
+    float* wt = reinterpret_cast<float*>(out + G::TAB_WT);
+    const int tid = threadIdx.x;
+    // B1[c][u]: c < H: cos k_t = c; H <= c < 2H-2: sin k_t = c-H+1.  byte = (c/8)256 + (u/8)128 + (c%8)16 + (u%8)2
+    for (int i = tid; i < 256; i += blockDim.x) {
+        const int c = i / 16, u = i % 16;
+        float v = 0.f;
+        if (c < H) v = twc<N>(tw, c, u);
+        else if (c < 2 * H - 2) v = tws<N>(tw, c - H + 1, u);
+        *reinterpret_cast<uint16_t*>(b1 + (c / 8) * 256 + (u / 8) * 128 + (c % 8) * 16 + (u % 8) * 2) =
+            Pack<FMT>::one(v);
+    }
+    // B3a[ncol][u] = [c | -s], B3b[ncol][u] = [s | c] over k_y = ncol % n (K-major, K = u)
+    for (int i = tid; i < G::N3 * 16; i += blockDim.x) {
+        const int ncol = i / 16, u = i % 16, k = ncol % N;
+        const bool re = ncol < N;
+        const float c = twc<N>(tw, k, u), sn = tws<N>(tw, k, u);
+        const size_t off = (ncol / 8) * 256 + (u / 8) * 128 + (ncol % 8) * 16 + (u % 8) * 2;
+        *reinterpret_cast<uint16_t*>(b3a + off) = Pack<FMT>::one(re ? c : -sn);
+        *reinterpret_cast<uint16_t*>(b3b + off) = Pack<FMT>::one(re ? sn : c);
+    }
+    // A2[(x0l, k_x)][k2]: k2 < 24: cos, else sin, of (k_x, x - x0l) with x = k2 % 24 (K-major)
+    for (int i = tid; i < 128 * kK2; i += blockDim.x) {
+        const int m = i / kK2, k2 = i % kK2;
+        const int x0l = m / N, kx = m % N, x = k2 % kXHP, u = x - x0l;
+        const float v = k2 < kXHP ? twc<N>(tw, kx, u) : tws<N>(tw, kx, u);
+        *reinterpret_cast<uint16_t*>(a2 + (m / 8) * G::SBO_K2 + (k2 / 8) * 128 + (m % 8) * 16 + (k2 % 8) * 2) =
+            Pack<FMT>::one(v);
+    }
+    // Eq. 1 weights r_m(k) / |k| (k_t multiplicity folded in) over (k_t, |k_x|, |k_y|)
+    for (int i = tid; i < H * H * H; i += blockDim.x) {
+        const int k = i % H, aj = (i / H) % H, kt = i / (H * H);
+        const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
+        const float r2 = (float)(kt * kt + aj * aj + k * k);
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+        if (r2 > 0.f) {
+            const float inv = mult / (float)(N * N * N) / sqrtf(r2);
+            w0 = sqrtf((float)(aj * aj + k * k)) * inv;
+            w1 = sqrtf((float)(kt * kt + k * k)) * inv;
+            w2 = sqrtf((float)(kt * kt + aj * aj)) * inv;
+        }
+        wt[i * 3 + 0] = w0;
+        wt[i * 3 + 1] = w1;
+        wt[i * 3 + 2] = w2;
+    }
+}
+
 template <int N, int FMT>
 __global__ void __launch_bounds__(kThreads, 2)
 k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
-              const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
+              const unsigned char* __restrict__ tables, int* __restrict__ err) {
     using G = TcGeo<N>;
-    constexpr int H = G::H, P = G::P, XH = G::XH, YH = G::YH;
+    constexpr int H = G::H, P = G::P, XH = G::XH, YH = G::YH, YG = G::YG, YP = G::YP;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* s_in = reinterpret_cast<float*>(smem);                       // [N][XH][YH]
-    float2* s_g1 = reinterpret_cast<float2*>(smem + G::OFF_G1);         // [XH][YH]
-    unsigned char* s_are = smem + G::OFF_A;                             // A real part
-    unsigned char* s_aim = smem + G::OFF_A + G::A_B;                    // A imaginary part
-    unsigned char* s_b = smem + G::OFF_B;                               // B [16 x 16], K-major
-    float* s_wt = reinterpret_cast<float*>(smem + G::OFF_WT);           // [k_t][k_x][k][3]
+    unsigned char* s_a1 = smem;                              // stage-1 A (MN-major), then:
+    unsigned char* s_b2 = smem;                              // stage-2 B tiles, one per k_t (K-major)
+    unsigned char* s_tab = smem + G::OFF_TAB;                // constant operands (bulk copy)
+    unsigned char* s_are = smem + G::OFF_A3;                 // stage-3 A, real part (MN-major)
+    unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;       // stage-3 A, imaginary part
+    const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);   // [k_t][|k_x|][|k_y|][3]
+    // mbarriers: [0], [1] accumulator buffer full (MMA commit), [2] constant operands landed
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 8);
-    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 16);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 48);
+    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 52);
     float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 64);   // [warps]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -102,223 +198,294 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     const int xb = blockIdx.y * P;
     const int t0 = blockIdx.z;
 
-    // ---- set-up: tensor memory, mbarrier, B operand, weight table, halo brick ------------------
+    // ---- set-up: tensor memory, mbarriers, constant operands (bulk copy), stage-3 A zero rows --------
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
     if (tid == 0) {
-        tc::mbar_init(tc::smem_u32(s_mbar), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[2]), 1);
         *s_fail = 0;
+        tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[2]), (uint32_t)G::TAB_B);
+        tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB_B, tc::smem_u32(&s_mbar[2]));
     }
-    for (int i = tid; i < 256; i += kThreads) {
-        const int n = i / 16, k = i % 16;
-        float v = 0.f;
-        if (k < N) {
-            if (n < H) v = tw.c[n][k];
-            else if (n < 2 * H - 2) v = tw.s[n - H + 1][k];
-        }
-        *reinterpret_cast<uint16_t*>(s_b + (n / 8) * 256 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2) =
-            Pack<FMT>::one(v);
-    }
-    for (int i = tid; i < H * N * H; i += kThreads) {
-        const int k = i % H, kx = (i / H) % N, kt = i / (H * N);
-        const int ii = kt, j = kx < N / 2 ? kx : kx - N;
-        const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-        const float r2 = (float)(ii * ii + j * j + k * k);
-        float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-        if (r2 > 0.f) {
-            const float inv = mult / (float)(N * N * N) / sqrtf(r2);
-            w0 = sqrtf((float)(j * j + k * k)) * inv;
-            w1 = sqrtf((float)(ii * ii + k * k)) * inv;
-            w2 = sqrtf((float)(ii * ii + j * j)) * inv;
-        }
-        s_wt[i * 3 + 0] = w0;
-        s_wt[i * 3 + 1] = w1;
-        s_wt[i * 3 + 2] = w2;
-    }
-    // A rows beyond the halo (read by the last windows, multiplied by zero twiddles) stay zero
-    for (int i = tid; i < (int)(2 * G::A_B / 16); i += kThreads)
+    // stage-3 A rows beyond the halo (read by the last windows, multiplied by zero twiddles) stay zero
+    for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
+
+    // ---- the halo brick: registers -> max|V| -> 16-bit stage-1 A operand ---------------------------
+    // item = (u, g): 8 positions pos = 8g .. 8g+7 (x = g / YG, y = 8 (g % YG) + i) at tap u
+    const int ty = yb - N / 2;
+    const bool interior = t0 - N / 2 >= 0 && t0 + N / 2 <= T && xb - N / 2 >= 0 && xb - N / 2 + XH <= X && ty >= 0 &&
+                          ty + YP <= Y && (Y & 3) == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0;
+    float vals[G::STAGE_PER_THREAD][8];
     float vmax = 0.f;
-    for (int r = tid; r < N * XH * YH; r += kThreads) {
-        const int yy = r % YH, xx = (r / YH) % XH, ut = r / (YH * XH);
-        const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-        const int gx = ext_index(xb - N / 2 + xx, X, bnd);
-        const int gy = ext_index(yb - N / 2 + yy, Y, bnd);
-        float v = 0.f;
-        if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-        s_in[r] = v;
-        vmax = fmaxf(vmax, fabsf(v));
+#pragma unroll
+    for (int r = 0; r < G::STAGE_PER_THREAD; ++r) {
+        const int item = tid + r * kThreads;
+        const int u = item / (G::NB1 * 16), g = item % (G::NB1 * 16);
+        const int x = g / YG, y8 = 8 * (g % YG);
+        const bool live = item < G::STAGE_ITEMS && u < N && x < XH;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) vals[r][i] = 0.f;
+        if (interior) {
+            if (live) {
+                const float* src = V + ((size_t)(t0 - N / 2 + u) * X + (xb - N / 2 + x)) * Y + ty + y8;
+                const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(src + 4));
+                vals[r][0] = a.x; vals[r][1] = a.y; vals[r][2] = a.z; vals[r][3] = a.w;
+                vals[r][4] = b.x; vals[r][5] = b.y; vals[r][6] = b.z; vals[r][7] = b.w;
+            }
+        } else {
+            const int gt = ext_index(t0 - N / 2 + u, T, bnd);
+            const int gx = ext_index(xb - N / 2 + x, X, bnd);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int gy = ext_index(ty + y8 + i, Y, bnd);
+                if (live && y8 + i < YH && (gt | gx | gy) >= 0) vals[r][i] = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (y8 + i >= YH) vals[r][i] = 0.f;     // positions past the halo (their outputs are not used)
+            vmax = fmaxf(vmax, fabsf(vals[r][i]));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if (lane == 0) s_red[warp] = vmax;
+    __syncthreads();
+    float bmax = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) bmax = fmaxf(bmax, s_red[w]);
+    const float scale = bmax > 0.f ? bmax : 1.f;     // per-brick scale of the low-precision operands
+    const float inv_scale = 1.f / scale;
+#pragma unroll
+    for (int r = 0; r < G::STAGE_PER_THREAD; ++r) {
+        const int item = tid + r * kThreads;
+        if (item < G::STAGE_ITEMS) {
+            const int u = item / (G::NB1 * 16), g = item % (G::NB1 * 16);
+            uint4 w;
+            w.x = Pack<FMT>::two(vals[r][0] * inv_scale, vals[r][1] * inv_scale);
+            w.y = Pack<FMT>::two(vals[r][2] * inv_scale, vals[r][3] * inv_scale);
+            w.z = Pack<FMT>::two(vals[r][4] * inv_scale, vals[r][5] * inv_scale);
+            w.w = Pack<FMT>::two(vals[r][6] * inv_scale, vals[r][7] * inv_scale);
+            // MN-major: byte(pos, u) = (pos/8) 256 + (u/8) 128 + (u%8) 16 + (pos%8) 2
+            *reinterpret_cast<uint4*>(s_a1 + g * 256 + (u / 8) * 128 + (u % 8) * 16) = w;
+        }
+    }
+    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-    float bmax = 0.f;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) bmax = fmaxf(bmax, s_red[w]);
-    const float scale = bmax > 0.f ? bmax : 1.f;     // per-brick scale of the low-precision operand
-    const float inv_scale = 1.f / scale;
 
-    // epilogue mapping: TMEM lane quarter q, row m = 32 q + lane, output slots of this warp
+    // Every wait is CTA-uniform: thread 0 polls the mbarrier (bounded), the barrier that follows spreads
+    // a give-up (after which no MMA is issued and no tensor memory is read) and, in the k_t loop, also
+    // marks that every warp finished the previous pass.
+    auto wait_cta = [&](int b, uint32_t parity) -> bool {
+        const int failed_before = *s_fail;  // written only before an earlier barrier
+        bool ok = true;
+        if (tid == 0) ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
+        const int bad = __syncthreads_or(!ok || failed_before);
+        if (bad && tid == 0 && !failed_before) {
+            atomicOr(err, 1);
+            *s_fail = 1;  // read by every thread only after a later barrier
+        }
+        tc::fence_after_sync();
+        return !bad;
+    };
+
     const int q = warp & 3, half = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const uint32_t idesc1 = tc::idesc_f16(FMT, 128, 16, 1, 0);
+    const uint32_t idesc2 = tc::idesc_f16(FMT, 128, G::N2, 0, 0);
+    const uint32_t idesc3 = tc::idesc_f16(FMT, 128, G::N3, 1, 0);
+    const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
+    const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
+    const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
+    const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
+    // stage 2 of tile kt into buffer 0 (columns [0, N2)); completion on full[0]
+    auto issue_s2 = [&](int kt) {
+        const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
+#pragma unroll
+        for (int s = 0; s < kK2 / 16; ++s)
+            tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
+                        tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
+        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+    };
+    // stage 3 of one pass (OPP outputs) into buffer pass % 2; completion on full[pass % 2]
+    auto issue_s3 = [&](int pass) {
+        const uint32_t col = (uint32_t)(128 * (pass & 1));
+#pragma unroll
+        for (int j = 0; j < G::OPP; ++j) {
+            const uint32_t y0 = pass * G::OPP + j;
+            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a, idesc3, 0);
+            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b, idesc3, 1);
+        }
+        tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
+    };
+    // D2 (buffer 0) -> stage-3 A operands: warps of half 0 take the real columns, half 1 the imaginary
+    auto convert_d2 = [&]() {
+        float v[32];
+        tc::tmem_ld32(tmem + lane_base + (uint32_t)(half * YP), v);
+        const int m = 32 * q + lane;
+        unsigned char* dst = (half ? s_aim : s_are) + (m / 8) * G::SBO_A3 + (m % 8) * 2;
+#pragma unroll
+        for (int y = 0; y < YH; ++y) *reinterpret_cast<uint16_t*>(dst + y * 16) = Pack<FMT>::one(v[y]);
+        tc::fence_async_smem();
+    };
+
+    // ---- stage 1 on the tensor cores, all k_t at once (after the constant operands landed) ----------
+    bool ok = wait_cta(2, 0);
+    if (tid == 0 && ok) {
+        const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+#pragma unroll
+        for (int i = 0; i < G::NB1; ++i)
+            tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1, idesc1, 0);
+        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+    }
+    ok = wait_cta(0, 0);
+    uint32_t ph0 = 1, ph1 = 0;   // next phase parities of the two buffer barriers
+    // D1 -> one stage-2 B tile per k_t (the A1 region is free once the stage-1 MMAs completed)
+    if (ok) {
+        for (int i = half; i < G::NB1; i += 2) {
+            float v[32];
+            tc::tmem_ld32(tmem + lane_base + (uint32_t)(16 * i), v);   // columns 16 i .. 16 i + 15 used
+            const int pos = 128 * i + 32 * q + lane;
+            const int x = pos / YP, y = pos % YP;
+            if (x < kXHP) {
+                // K-major: byte(ncol, k2) = (ncol/8) SBO_K2 + (k2/8) 128 + (ncol%8) 16 + (k2%8) 2
+                const size_t o_re = (size_t)(y / 8) * G::SBO_K2 + (y % 8) * 16;
+                const size_t o_im = (size_t)((YP + y) / 8) * G::SBO_K2 + ((YP + y) % 8) * 16;
+                const size_t k_c = (size_t)(x / 8) * 128 + (x % 8) * 2;
+                const size_t k_s = (size_t)((kXHP + x) / 8) * 128 + ((kXHP + x) % 8) * 2;
+#pragma unroll
+                for (int kt = 0; kt < H; ++kt) {
+                    const float g1r = v[kt];
+                    const float g1i = (kt == 0 || 2 * kt == N) ? 0.f : -v[H - 1 + kt];
+                    unsigned char* b2 = s_b2 + (size_t)kt * G::B2_B;
+                    *reinterpret_cast<uint16_t*>(b2 + o_re + k_c) = Pack<FMT>::one(g1r);
+                    *reinterpret_cast<uint16_t*>(b2 + o_re + k_s) = Pack<FMT>::one(g1i);
+                    *reinterpret_cast<uint16_t*>(b2 + o_im + k_c) = Pack<FMT>::one(g1i);
+                    *reinterpret_cast<uint16_t*>(b2 + o_im + k_s) = Pack<FMT>::one(-g1r);
+                }
+            }
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && !*s_fail) {
+        tc::fence_after_sync();
+        issue_s2(0);
+    }
+    ok = wait_cta(0, ph0);
+    ph0 ^= 1u;
+    if (ok) convert_d2();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // epilogue mapping: TMEM lane quarter q, row m = 32 q + lane
     const int m = 32 * q + lane;
     const int x0l = m / N, kx = m % N;
+    const int ajx = kx <= N / 2 ? kx : N - kx;
     float acc[8][3];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
 
-    const uint32_t idesc = tc::idesc_f16(FMT, 128, 16, 1, 0);
-    const uint64_t bdesc = tc::desc_noswizzle(tc::smem_u32(s_b), 128, 256);
-    const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
-    uint32_t phase = 0;
-
+    // ---- the k_t loop: one CTA barrier per pass; the MMAs of a pass are issued one pass ahead --------
     for (int kt = 0; kt < H; ++kt) {
-        // ---- stage 1 for this k_t ------------------------------------------------------------
-        {
-            float cr[N], sr[N];
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-                cr[u] = tw.c[kt][u];
-                sr[u] = tw.s[kt][u];
-            }
-            for (int it = tid; it < XH * YH; it += kThreads) {
-                float Pv = 0.f, Qv = 0.f;
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    const float v = s_in[u * XH * YH + it];
-                    Pv = fmaf(v, cr[u], Pv);
-                    Qv = fmaf(v, sr[u], Qv);
-                }
-                s_g1[it] = make_float2(Pv, -Qv);
-            }
+        if (tid == 0 && !*s_fail) {
+            tc::fence_after_sync();
+            issue_s3(0);
+            issue_s3(1);
         }
-        __syncthreads();
-        // ---- stage 2 -> A operand (low precision) --------------------------------------------
-        for (int it = tid; it < P * YH; it += kThreads) {
-            const int xl = it / YH, y = it % YH;
-            float2 g[N];
-#pragma unroll
-            for (int u = 0; u < N; ++u) g[u] = s_g1[(xl + u) * YH + y];
-            float fr[N], fi[N];
-#pragma unroll
-            for (int k = 0; k < H; ++k) {
-                float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    pr = fmaf(g[u].x, tw.c[k][u], pr);
-                    pi = fmaf(g[u].y, tw.c[k][u], pi);
-                    if (k != 0 && 2 * k != N) {
-                        qr = fmaf(g[u].x, tw.s[k][u], qr);
-                        qi = fmaf(g[u].y, tw.s[k][u], qi);
-                    }
-                }
-                fr[k] = (pr + qi) * inv_scale;
-                fi[k] = (pi - qr) * inv_scale;
-                if (k != 0 && 2 * k != N) {
-                    fr[N - k] = (pr - qi) * inv_scale;
-                    fi[N - k] = (pi + qr) * inv_scale;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < N / 8; ++c) {
-                const size_t off = (size_t)(xl * (N / 8) + c) * G::SBO_A + (size_t)y * 16;
-                uint4 vr, vi;
-                vr.x = Pack<FMT>::two(fr[8 * c + 0], fr[8 * c + 1]);
-                vr.y = Pack<FMT>::two(fr[8 * c + 2], fr[8 * c + 3]);
-                vr.z = Pack<FMT>::two(fr[8 * c + 4], fr[8 * c + 5]);
-                vr.w = Pack<FMT>::two(fr[8 * c + 6], fr[8 * c + 7]);
-                vi.x = Pack<FMT>::two(fi[8 * c + 0], fi[8 * c + 1]);
-                vi.y = Pack<FMT>::two(fi[8 * c + 2], fi[8 * c + 3]);
-                vi.z = Pack<FMT>::two(fi[8 * c + 4], fi[8 * c + 5]);
-                vi.w = Pack<FMT>::two(fi[8 * c + 6], fi[8 * c + 7]);
-                *reinterpret_cast<uint4*>(s_are + off) = vr;
-                *reinterpret_cast<uint4*>(s_aim + off) = vi;
-            }
-        }
-        tc::fence_async_smem();
-        __syncthreads();
-        // this lane's projection weights for (k_t, k_x), |k_y| = 0 .. n/2
+        // this lane's Eq. 1 weights for (k_t, |k_x|), |k_y| = 0 .. n/2
         float wt[3][H];
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-            const float* w = s_wt + ((kt * N + kx) * H + k) * 3;
+            const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
             wt[0][k] = w[0];
             wt[1][k] = w[1];
             wt[2][k] = w[2];
         }
-        // ---- stage 3 on the tensor cores, two passes of 8 outputs --------------------------------
-        for (int pass = 0; pass < 2; ++pass) {
-            if (tid == 0 && !*s_fail) {
-                tc::fence_after_sync();
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t y0 = pass * 8 + j;
-                    const uint64_t ar = tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A);
-                    const uint64_t ai = tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A);
-                    tc::mma_f16(tmem + j * 32, ar, bdesc, idesc, 0);
-                    tc::mma_f16(tmem + j * 32 + 16, ai, bdesc, idesc, 0);
-                }
-                tc::mma_commit(tc::smem_u32(s_mbar));
+        for (int pass = 0; pass < G::PASSES; ++pass) {
+            const int b = pass & 1;
+            // pass complete in buffer b, and every warp done with the previous pass (buffer b ^ 1)
+            const bool full = wait_cta(b, b ? ph1 : ph0);
+            if (b) ph1 ^= 1u; else ph0 ^= 1u;
+            if (tid == 0 && !*s_fail && pass >= 1) {
+                if (pass + 1 < G::PASSES) issue_s3(pass + 1);
+                else if (kt + 1 < H) issue_s2(kt + 1);       // buffer 0 free: stage 2 of the next tile
             }
-            // the give-up decision is CTA-uniform: the TMEM loads below are warp-collective
-            const int failed_before = *s_fail;  // written only before the previous barrier
-            const bool ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(s_mbar), phase, kWaitLimit);
-            const int bad = __syncthreads_or(!ok);
-            if (bad && tid == 0 && !failed_before) {
-                atomicOr(err, 1);
-                *s_fail = 1;  // read by every thread only after the barrier that ends this pass
-            }
-            phase ^= 1u;
-            tc::fence_after_sync();
-            if (!bad) {
+            if (full) {
+                // chunks half and half + 2 of this buffer, both loads in flight before the wait
+                uint32_t r[2][32];
+                tc::tmem_ld32_async(tmem + lane_base + (uint32_t)(128 * b + 32 * half), r[0]);
+                tc::tmem_ld32_async(tmem + lane_base + (uint32_t)(128 * b + 32 * (half + 2)), r[1]);
+                tc::tmem_wait_ld(r[0]);
+                tc::tmem_wait_ld(r[1]);
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int j = half + 2 * jj;
-                    float v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * 32), v);
-                    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+                for (int cc = 0; cc < 2; ++cc) {
 #pragma unroll
-                    for (int k = 0; k < H; ++k) {
-                        const float pr = v[k], pi = v[16 + k];
-                        float a;
-                        if (k == 0 || 2 * k == N) {
-                            a = fast_sqrt(fmaf(pr, pr, pi * pi));
-                        } else {
-                            const float qr = v[H + k - 1], qi = v[16 + H + k - 1];
-                            const float ar = pr + qi, ai = pi - qr, br = pr - qi, bi = pi + qr;
-                            a = fast_sqrt(fmaf(ar, ar, ai * ai)) + fast_sqrt(fmaf(br, br, bi * bi));
+                    for (int o = 0; o < G::OPC; ++o) {
+                        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < H; ++k) {
+                            const float re = __uint_as_float(r[cc][o * G::N3 + k]);
+                            const float im = __uint_as_float(r[cc][o * G::N3 + N + k]);
+                            float sm = fast_sqrt(fmaf(re, re, im * im));
+                            if (k != 0 && 2 * k != N) {
+                                const float re2 = __uint_as_float(r[cc][o * G::N3 + N - k]);
+                                const float im2 = __uint_as_float(r[cc][o * G::N3 + 2 * N - k]);
+                                sm += fast_sqrt(fmaf(re2, re2, im2 * im2));
+                            }
+                            e0 = fmaf(wt[0][k], sm, e0);
+                            e1 = fmaf(wt[1][k], sm, e1);
+                            e2 = fmaf(wt[2][k], sm, e2);
                         }
-                        e0 = fmaf(wt[0][k], a, e0);
-                        e1 = fmaf(wt[1][k], a, e1);
-                        e2 = fmaf(wt[2][k], a, e2);
+                        const int slot = (pass * 2 + cc) * G::OPC + o;
+                        acc[slot][0] += e0;
+                        acc[slot][1] += e1;
+                        acc[slot][2] += e2;
                     }
-                    acc[pass * 4 + jj][0] += e0;
-                    acc[pass * 4 + jj][1] += e1;
-                    acc[pass * 4 + jj][2] += e2;
                 }
             }
+            tc::fence_before_sync();
+        }
+        if (kt + 1 < H) {
+            // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
+            ok = wait_cta(0, ph0);
+            ph0 ^= 1u;
+            if (ok) convert_d2();
             tc::fence_before_sync();
             __syncthreads();
         }
     }
+    __syncthreads();
 
     // ---- sum over the n lanes of each x0 (k_x), write E -------------------------------------------
     const size_t NV = (size_t)T * X * Y;
     const int x = xb + x0l;
+    const bool good = *s_fail == 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int y0 = (i / 4) * 8 + half + 2 * (i % 4);
+    for (int pass = 0; pass < G::PASSES; ++pass)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float s = acc[i][c];
+        for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-            for (int o = 1; o < N; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            const int y = yb + y0;
-            if (kx == 0 && x < X && y < Y && !*s_fail) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * scale;
-        }
-    }
+            for (int o = 0; o < G::OPC; ++o) {
+                const int slot = (pass * 2 + cc) * G::OPC + o;
+                const int y0 = pass * G::OPP + (half + 2 * cc) * G::OPC + o;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float s = acc[slot][c];
+#pragma unroll
+                    for (int w = 1; w < N; w <<= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+                    const int y = yb + y0;
+                    if (kx == 0 && x < X && y < Y && good) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * scale;
+                }
+            }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
@@ -331,11 +498,19 @@ cudaError_t prepare_nf() {
 }
 
 template <int N, int FMT>
-cudaError_t launch_nf(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd, int* err,
+cudaError_t tables_nf(const TwiddleTable& t, void* dst, cudaStream_t s) {
+    k1_tc_tables<N, FMT><<<1, 256, 0, s>>>(f32::make_tw<N>(t), static_cast<unsigned char*>(dst));
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int N, int FMT>
+cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int* err,
                       cudaStream_t s) {
     using G = TcGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, T);
-    k1_spectra_tc<N, FMT><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t), err);
+    k1_spectra_tc<N, FMT><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd,
+                                                          static_cast<const unsigned char*>(tables), err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -344,18 +519,30 @@ cudaError_t launch_nf(const TwiddleTable& t, const float* V, float* E, int T, in
 
 bool spectra_tc_supported(int n) { return n == 8 || n == 16; }
 
+size_t spectra_tc_tables_bytes(int n) {
+    if (n == 8) return TcGeo<8>::TAB_B;
+    if (n == 16) return TcGeo<16>::TAB_B;
+    return 0;
+}
+
 cudaError_t spectra_tc_prepare(int n, int fmt) {
     if (n == 8) return fmt == 1 ? prepare_nf<8, 1>() : prepare_nf<8, 0>();
     if (n == 16) return fmt == 1 ? prepare_nf<16, 1>() : prepare_nf<16, 0>();
     return cudaErrorInvalidValue;
 }
 
-cudaError_t spectra_tc_launch(int n, int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
+cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, void* dst, cudaStream_t s) {
+    if (n == 8) return fmt == 1 ? tables_nf<8, 1>(tw, dst, s) : tables_nf<8, 0>(tw, dst, s);
+    if (n == 16) return fmt == 1 ? tables_nf<16, 1>(tw, dst, s) : tables_nf<16, 0>(tw, dst, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
                               int bnd, int* err, cudaStream_t s) {
-    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tw, V, E, T, X, Y, bnd, err, s)
-                                : launch_nf<8, 0>(tw, V, E, T, X, Y, bnd, err, s);
-    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tw, V, E, T, X, Y, bnd, err, s)
-                                 : launch_nf<16, 0>(tw, V, E, T, X, Y, bnd, err, s);
+    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, err, s)
+                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, err, s);
+    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, err, s)
+                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, err, s);
     return cudaErrorInvalidValue;
 }
 

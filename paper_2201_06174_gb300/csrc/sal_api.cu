@@ -25,6 +25,7 @@ struct sal_handle {
     float* S3 = nullptr;     // [3][N] raw center-surround scratch
     sal::Reduce red{};
     void* small = nullptr;   // one allocation holding the reduction scratch
+    void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
     // backward scratch, allocated by the first sal_saliency_backward call
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
@@ -53,6 +54,8 @@ void free_scratch(sal_handle* h) {
     if (h->E) cudaFree(h->E);
     if (h->S3) cudaFree(h->S3);
     if (h->small) cudaFree(h->small);
+    if (h->tc_tables) cudaFree(h->tc_tables);
+    h->tc_tables = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
     h->err_host = nullptr;
     h->err_dev = nullptr;
@@ -100,8 +103,8 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
                                         h->err_dev, st);
     }
     if (h->prec == SAL_FP32) return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
-    return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
-                                  h->err_dev, st);
+    return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, E, h->T, h->X, h->Y,
+                                  h->boundary, h->err_dev, st);
 }
 
 }  // namespace
@@ -193,7 +196,9 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
     const size_t small = (size_t)sal::kRedBlocks * 8 * sizeof(float) + (size_t)sal::kRedBlocks * 16 * sizeof(double)
                          + 32 * sizeof(float) + 16 * sizeof(double) + 256;
-    const size_t need = 2 * plane3 + small;
+    const bool tc_fwd = h->prec != SAL_FP32 && sal::spectra_tc_supported(h->n);
+    const size_t tab_bytes = tc_fwd ? sal::spectra_tc_tables_bytes(h->n) : 0;
+    const size_t need = 2 * plane3 + small + tab_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
@@ -233,6 +238,21 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
             free_scratch(h);
             delete h;
             return cuda_fail(nullptr, e, "cudaMemcpy");
+        }
+    }
+    if (tc_fwd) {
+        if ((e = cudaMalloc(&h->tc_tables, tab_bytes)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            cudaGetLastError();
+            return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        if ((e = sal::spectra_tc_tables_build(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, h->tc_tables, 0)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(0)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            return cuda_fail(nullptr, e, "tensor-core tables");
         }
     }
     h->bytes = need;

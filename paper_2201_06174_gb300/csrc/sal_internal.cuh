@@ -73,10 +73,13 @@ cudaError_t spectra_tc32_prepare(int fmt);
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
                                 int bnd, int* err, cudaStream_t s);
 
-// K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word
+// K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word.  The constant
+// operands (twiddles in the operand layouts, Eq. 1 weights) are built once per handle into `tables`.
 bool spectra_tc_supported(int n);
+size_t spectra_tc_tables_bytes(int n);
 cudaError_t spectra_tc_prepare(int n, int fmt);
-cudaError_t spectra_tc_launch(int n, int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
+cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, void* tables, cudaStream_t s);
+cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
                               int bnd, int* err, cudaStream_t s);
 
 // ---- K2: directional center-surround ----------------------------------------------------------
