@@ -26,6 +26,7 @@ struct sal_handle {
     sal::Reduce red{};
     void* small = nullptr;   // one allocation holding the reduction scratch
     void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
+    void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
     // backward scratch, allocated by the first sal_saliency_backward call
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
@@ -55,7 +56,8 @@ void free_scratch(sal_handle* h) {
     if (h->S3) cudaFree(h->S3);
     if (h->small) cudaFree(h->small);
     if (h->tc_tables) cudaFree(h->tc_tables);
-    h->tc_tables = nullptr;
+    if (h->adj_tables) cudaFree(h->adj_tables);
+    h->tc_tables = h->adj_tables = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
     h->err_host = nullptr;
     h->err_dev = nullptr;
@@ -198,7 +200,8 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
                          + 32 * sizeof(float) + 16 * sizeof(double) + 256;
     const bool tc_fwd = h->prec != SAL_FP32 && sal::spectra_tc_supported(h->n);
     const size_t tab_bytes = tc_fwd ? sal::spectra_tc_tables_bytes(h->n) : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes;
+    const size_t adj_bytes = tc_fwd ? sal::spectra_adjoint_tc_tables_bytes(h->n) : 0;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
@@ -247,8 +250,15 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
             cudaGetLastError();
             return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
+        if ((e = cudaMalloc(&h->adj_tables, adj_bytes)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            cudaGetLastError();
+            return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
         if ((e = sal::spectra_tc_tables_build(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, h->tc_tables, 0)) !=
                 cudaSuccess ||
+            (e = sal::spectra_adjoint_tc_tables_build(h->n, h->tw, h->adj_tables, 0)) != cudaSuccess ||
             (e = cudaStreamSynchronize(0)) != cudaSuccess) {
             free_scratch(h);
             delete h;
@@ -381,8 +391,8 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
                                                   t_begin, cnt, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
-                : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
-                                                 t_begin, cnt, h->err_dev, st);
+                : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,
+                                                 h->boundary, t_begin, cnt, h->err_dev, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
         if ((e = sal::gather_add_launch(h->blocks, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt, st)) !=
             cudaSuccess)

@@ -105,12 +105,14 @@ cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
                                        int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s);
-// K5 on the tensor cores (FP16 operands: fmt must be 0)
+// K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
+size_t spectra_adjoint_tc_tables_bytes(int n);
+cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, void* tables, cudaStream_t s);
 SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
-cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const float* V, const float* gE,
-                                      float* blocks, int T, int X, int Y, int bnd, int t_begin, int t_count, int* err,
-                                      cudaStream_t s);
+cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
+                                      const float* gE, float* blocks, int T, int X, int Y, int bnd, int t_begin,
+                                      int t_count, int* err, cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]
