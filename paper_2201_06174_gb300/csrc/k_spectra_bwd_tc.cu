@@ -14,11 +14,13 @@
 //     of output y0 is the same descriptor moved by 16 (15 - y0) bytes:
 //       Tinv_re[(re|im, k_y)][y] = [c | -s](k_y, y - y0),  Tinv_im = [s | c](k_y, y - y0);
 //   adjoint of stage 2 (x): the stage-2 twiddle matrix A2 [(x0,k_x)][(cos|sin, x)] read as an MN-major
-//     operand is its transpose, so D[(cos|sin, x)][(re|im, y)] = A2^T dG2 (dG2 rounded to FP16) is one
-//     MMA of K = 128; then dG1r = C.re - S.im, dG1i = S.re + C.im on the SIMT pipes;
-//   adjoint of stage 1 (t) on the SIMT pipes, accumulated over k_t into the brick's block of gVext
-//     [u_t][x][y] in shared memory, written to scratch at the end; the fixed-order gather kernel sums
-//     the overlapping blocks.
+//     operand is its transpose; with B_c = [dG2r | dG2i] and B_s = [-dG2i | dG2r] (dG2 rounded to FP16),
+//     D[x][(re|im, y)] = A2_cos^T B_c + A2_sin^T B_s is dG1 = (sum c dG2r - s dG2i, sum c dG2i + s dG2r)
+//     directly (two MMA chains of K = 128, the sin rows selected by moving the start 24 rows);
+//   adjoint of stage 1 (t) on the tensor cores as well: dG1 (scaled, FP16) is written as an MN-major
+//     A operand [pos][(re, im, 0...)] and D_t[pos][u_t] += A_t B_t(k_t), B_t = [c | -s](k_t, u_t),
+//     accumulates the brick's block of gVext over all k_t in tensor memory; at the end it is written to
+//     scratch [u_t][x][y] and the fixed-order gather kernel sums the overlapping blocks.
 // FP16 operands in both 16-bit forms (3 more mantissa bits than BF16: the direction F/|F| of small bins
 // amplifies operand rounding).  Every wait on the tensor cores is bounded; on timeout the CTA sets the
 // error word, skips the remaining MMAs and writes a zero block.
@@ -37,9 +39,11 @@ using tcs::Pack;
 
 constexpr int kFmt = 0;                   // FP16 operands
 constexpr int kThreads = 512;             // 16 warps: 4 per tensor-memory lane quarter
-constexpr uint32_t kTmemCols = 512;       // [0,256) two forward buffers; [256,320) dG2; [320,384) x adjoint
+constexpr uint32_t kTmemCols = 512;       // [0,256) forward buffers; [256,320) dG2; [320,384) dG1; [384,480) gV
 constexpr uint32_t kColY = 256;
 constexpr uint32_t kColX = 320;
+constexpr uint32_t kColT = 384;
+constexpr float kDxScale = 1.f / 64.f;    // keeps the FP16 copy of dG1 far from the FP16 range limit
 constexpr float kKinkTau = 1.0f / 524288.0f;  // zero-subgradient band of |F| (2^-19 of the window L1 norm)
 constexpr int kTR = 48;                   // rows of the shifted inverse twiddle tables (y - y0 + 15)
 
@@ -53,22 +57,22 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr size_t TI_B = (size_t)KG / 8 * TI_LBO;
     static constexpr size_t TAB_TRE = F::TAB_B;
     static constexpr size_t TAB_TIM = TAB_TRE + TI_B;
-    static constexpr size_t TAB5_B = TAB_TIM + TI_B;
-    static constexpr size_t BDG_B = (size_t)8 * 2048;         // dG2 operand [K = 128][N = 64], MN-major
-    static constexpr size_t DX_B = (size_t)48 * 64 * 4;       // x-adjoint rows (cos|sin, x) x (re|im, y)
+    static constexpr size_t TAB_BT = TAB_TIM + TI_B;          // B_t per k_t: [u][(re, im, 0...)], 512 B each
+    static constexpr size_t TAB5_B = TAB_BT + (size_t)F::H * 512;
+    static constexpr size_t BDG_B = (size_t)8 * 2048;         // one dG2 operand [K = 128][N = 64], MN-major
     static constexpr int BLOCK_FLOATS = N * F::XH * F::YH;
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + TAB5_B;
-    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets; later dG2 + x rows
-    static constexpr size_t G_B = 2 * GSET_B > BDG_B + DX_B ? 2 * GSET_B : BDG_B + DX_B;
-    static constexpr size_t OFF_GV = OFF_G + G_B;
-    static constexpr size_t OFF_GE = OFF_GV + (size_t)BLOCK_FLOATS * 4;
+    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets, later B_c | B_s
+    static constexpr size_t G_B = 2 * GSET_B > 2 * BDG_B ? 2 * GSET_B : 2 * BDG_B;
+    static constexpr size_t OFF_AT = OFF_G + G_B;                // t-adjoint A operand [pos][16], MN-major
+    static constexpr size_t OFF_GE = OFF_AT + F::A1_B;
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * F::P * kBY * 4;
     static constexpr size_t OFF_MISC = (OFF_L1 + (size_t)F::P * kBY * 4 + 15) / 16 * 16;
     static constexpr size_t SMEM = OFF_MISC + 64 + 2 * (kThreads / 32) * 4;
-    static_assert(F::OPC * 4 * 32 / F::N3 >= 1 && 4 * 32 == 128, "four 32-column chunks per buffer");
     static_assert((size_t)kXHP * F::YP * 4 <= G_B, "L1 column sums fit in the Gamma region");
-    static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_G % 128 == 0, "alignment");
+    static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
+    static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -89,6 +93,14 @@ __global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __
         *reinterpret_cast<uint16_t*>(tre + off) = Pack<kFmt>::one(k < N ? c : -s);
         *reinterpret_cast<uint16_t*>(tim + off) = Pack<kFmt>::one(k < N ? s : c);
     }
+    // B_t(k_t)[u][k] (K-major, N = u): k = 0: c(k_t, u), k = 1: -s(k_t, u), other K rows zero
+    unsigned char* bt = out + G::TAB_BT;
+    for (int i = threadIdx.x; i < G::H * 256; i += blockDim.x) {
+        const int kt = i / 256, u = (i / 16) % 16, k = i % 16;
+        const float v = k == 0 ? tcs::twc<N>(tw, kt, u) : (k == 1 ? -tcs::tws<N>(tw, kt, u) : 0.f);
+        *reinterpret_cast<uint16_t*>(bt + kt * 512 + (u / 8) * 256 + (k / 8) * 128 + (u % 8) * 16 + (k % 8) * 2) =
+            Pack<kFmt>::one(v);
+    }
 }
 
 template <int N>
@@ -105,10 +117,10 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     unsigned char* s_are = smem + G::OFF_A3;
     unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;
     unsigned char* s_g = smem + G::OFF_G;                        // Gamma operands, two sets
-    unsigned char* s_bdg = smem + G::OFF_G;                      // dG2 operand (after the y adjoint)
-    float* s_dx = reinterpret_cast<float*>(smem + G::OFF_G + G::BDG_B);   // [48][64]
+    unsigned char* s_bc = smem + G::OFF_G;                       // B_c = [dG2r | dG2i] (after the y adjoint)
+    unsigned char* s_bs = smem + G::OFF_G + G::BDG_B;            // B_s = [-dG2i | dG2r]
     float* s_col = reinterpret_cast<float*>(smem + G::OFF_G);    // L1 column sums (set-up only)
-    float* s_gv = reinterpret_cast<float*>(smem + G::OFF_GV);    // [N][XH][YH]
+    unsigned char* s_at = smem + G::OFF_AT;                      // t-adjoint A operand
     float* s_ge = reinterpret_cast<float*>(smem + G::OFF_GE);    // [3][P][16]
     float* s_l1 = reinterpret_cast<float*>(smem + G::OFF_L1);    // [P][16]
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);
@@ -135,7 +147,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     }
     for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = tid; i < G::BLOCK_FLOATS; i += kThreads) s_gv[i] = 0.f;
+    for (int i = tid; i < (int)(G::A1_B / 16); i += kThreads)       // K rows 2..15 of A_t stay zero
+        reinterpret_cast<uint4*>(s_at)[i] = make_uint4(0u, 0u, 0u, 0u);
     float gmax = 0.f;
     for (int i = tid; i < 3 * P * kBY; i += kThreads) {
         const int y0 = i % kBY, xl = (i / kBY) % P, m = i / (kBY * P);
@@ -153,7 +166,6 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) bgmax = fmaxf(bgmax, s_red[kThreads / 32 + w]);
     const float sigma = bgmax > 0.f ? (float)(N * N * N) / (8.f * bgmax) : 1.f;   // Gamma operand scale
-    const float inv_sigma = 1.f / sigma;
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -205,7 +217,9 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const uint32_t idescx = tc::idesc_f16(kFmt, 128, 64, 1, 1);
     const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
     const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
-    const uint32_t gbase = tc::smem_u32(s_g), bdg = tc::smem_u32(s_bdg);
+    const uint32_t gbase = tc::smem_u32(s_g), bc = tc::smem_u32(s_bc), bs = tc::smem_u32(s_bs);
+    const uint32_t at = tc::smem_u32(s_at);
+    const uint32_t idesct = tc::idesc_f16(kFmt, 128, 16, 1, 0);
     const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
     const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
     auto issue_s2 = [&](int kt) {
@@ -357,66 +371,79 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         ok = wait_cta(2, pa);
         pa ^= 1u;
         if (ok) {
-            // warp group grp: columns n = 16 grp .. 16 grp + 15 of (re y 0..31 | im y 0..31)
+            // warp group grp: columns 16 grp .. 16 grp + 15 of (re y 0..31 | im y 0..31) -> B_c at the
+            // same columns, B_s at the other half (re -> the im slot, im -> the re slot, negated)
             float v[16];
             tc::tmem_ld16(tmem + lane_base + kColY + (uint32_t)(16 * grp), v);
+            const float sgn = grp < 2 ? 1.f : -1.f;
             // MN-major [K = m][N = n]: byte(n, k) = (n/8) 2048 + (k/8) 128 + (k%8) 16 + (n%8) 2
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int n = 16 * grp + 8 * h;
-                uint4 w;
+                const int n = 16 * grp + 8 * h, ns = (n + 32) % 64;
+                uint4 w, ws;
                 w.x = Pack<kFmt>::two(v[8 * h + 0], v[8 * h + 1]);
                 w.y = Pack<kFmt>::two(v[8 * h + 2], v[8 * h + 3]);
                 w.z = Pack<kFmt>::two(v[8 * h + 4], v[8 * h + 5]);
                 w.w = Pack<kFmt>::two(v[8 * h + 6], v[8 * h + 7]);
-                *reinterpret_cast<uint4*>(s_bdg + (n / 8) * 2048 + (m / 8) * 128 + (m % 8) * 16) = w;
+                ws.x = Pack<kFmt>::two(sgn * v[8 * h + 0], sgn * v[8 * h + 1]);
+                ws.y = Pack<kFmt>::two(sgn * v[8 * h + 2], sgn * v[8 * h + 3]);
+                ws.z = Pack<kFmt>::two(sgn * v[8 * h + 4], sgn * v[8 * h + 5]);
+                ws.w = Pack<kFmt>::two(sgn * v[8 * h + 6], sgn * v[8 * h + 7]);
+                const size_t row = (size_t)(m / 8) * 128 + (m % 8) * 16;
+                *reinterpret_cast<uint4*>(s_bc + (n / 8) * 2048 + row) = w;
+                *reinterpret_cast<uint4*>(s_bs + (ns / 8) * 2048 + row) = ws;
             }
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        // ---- adjoint of stage 2: A2^T (the stored A2 read MN-major) times dG2 ---------------------------
+        // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------------
         if (tid == 0 && !*s_fail) {
             tc::fence_after_sync();
 #pragma unroll
-            for (int s = 0; s < 8; ++s)
+            for (int s = 0; s < 8; ++s) {
                 tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + 1536 * s, G::SBO_K2, 128),
-                            tc::desc_noswizzle(bdg + 256 * s, 128, 2048), idescx, s > 0 ? 1u : 0u);
+                            tc::desc_noswizzle(bc + 256 * s, 128, 2048), idescx, s > 0 ? 1u : 0u);
+                tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + (kXHP / 8) * 128 + 1536 * s, G::SBO_K2, 128),
+                            tc::desc_noswizzle(bs + 256 * s, 128, 2048), idescx, 1u);
+            }
             tc::mma_commit(tc::smem_u32(&s_mbar[2]));
         }
         ok = wait_cta(2, pa);
         pa ^= 1u;
-        if (ok && q < 2) {
+        // ---- dG1 (rows x of lane quarter 0) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) ----------
+        if (ok && q == 0) {
             float v[16];
-            tc::tmem_ld16(tmem + lane_base + kColX + (uint32_t)(16 * grp), v);
-            if (m < 48) {
+            tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * grp), v);
+            const int x = lane, k = grp >> 1;
+            if (x < kXHP) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) s_dx[m * 64 + 16 * grp + i] = v[i];
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- dG1 = (C.re - S.im, S.re + C.im) / sigma; adjoint of stage 1 into the block ----------------
-        if (ok) {
-            float ct[N], st[N];
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-                ct[u] = tw.c[kt][u];
-                st[u] = tw.s[kt][u];
-            }
-            for (int it = tid; it < XH * YH; it += kThreads) {
-                const int x = it / YH, y = it % YH;
-                const float cr = s_dx[x * 64 + y], ci = s_dx[x * 64 + 32 + y];
-                const float sr = s_dx[(kXHP + x) * 64 + y], si = s_dx[(kXHP + x) * 64 + 32 + y];
-                const float gr = (cr - si) * inv_sigma, gi = (sr + ci) * inv_sigma;
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    float* o = s_gv + (u * XH + x) * YH + y;
-                    *o = fmaf(gr, ct[u], fmaf(-gi, st[u], *o));
+                for (int h = 0; h < 2; ++h) {
+                    const int y8 = 16 * (grp & 1) + 8 * h;
+                    if (y8 < YP) {
+                        // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
+                        uint4 w;
+                        w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
+                        w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
+                        w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
+                        w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
+                        *reinterpret_cast<uint4*>(s_at + ((x * YP + y8) / 8) * 256 + k * 16) = w;
+                    }
                 }
             }
         }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
         __syncthreads();
+        // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ------------
+        if (tid == 0 && !*s_fail) {
+            tc::fence_after_sync();
+            const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
+#pragma unroll
+            for (int i = 0; i < G::NB1; ++i)
+                tc::mma_f16(tmem + kColT + 16 * i, tc::desc_noswizzle(at + 4096 * i, 128, 256), btd, idesct,
+                            kt > 0 ? 1u : 0u);
+        }
         if (kt + 1 < H) {
             // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
             ok = wait_cta(0, ph0);
@@ -427,11 +454,21 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         }
     }
 
-    // ---- the brick's block of gVext to scratch ---------------------------------------------------------
+    // ---- the brick's block of gVext (tensor memory) to scratch [u_t][x][y] ----------------------------------
+    if (tid == 0 && !*s_fail) tc::mma_commit(tc::smem_u32(&s_mbar[2]));
+    ok = wait_cta(2, pa);
     const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float* blk = blocks + cta * G::BLOCK_FLOATS;
-    const bool good = *s_fail == 0;
-    for (int i = tid; i < G::BLOCK_FLOATS; i += kThreads) blk[i] = good ? s_gv[i] : 0.f;
+    const float out_scale = 1.f / (sigma * kDxScale);
+    for (int i = grp; i < G::NB1; i += 4) {
+        float v[16];
+        if (ok) tc::tmem_ld16(tmem + lane_base + kColT + (uint32_t)(16 * i), v);
+        const int pos = 128 * i + m, x = pos / YP, y = pos % YP;
+        if (x < XH && y < YH) {
+#pragma unroll
+            for (int u = 0; u < N; ++u) blk[(u * XH + x) * YH + y] = ok ? v[u] * out_scale : 0.f;
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
