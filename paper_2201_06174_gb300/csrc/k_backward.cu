@@ -128,6 +128,27 @@ k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long l
             eq[m] = __ldg(E + m * NV + q);
             gq[m] = __ldg(gS + m * gms + q);
         }
+        // interior voxels (at least the stencil halo away from every border): the neighbour is q + o and
+        // the only preimage of q under offset o is q - o
+        const bool inner = t >= st.halo[0] && t < T - st.halo[0] && x >= st.halo[1] && x < X - st.halo[1] &&
+                           y >= st.halo[2] && y < Y - st.halo[2];
+        if (inner) {
+            for (int o = 0; o < st.Q; ++o) {
+                const long long d = ((long long)st.off[o][0] * X + st.off[o][1]) * Y + st.off[o][2];
+                const float w = st.w[o];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float nb = __ldg(E + m * NV + q + d);
+                    const float pe = __ldg(E + m * NV + q - d), pg = __ldg(gS + m * gms + q - d);
+                    acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+                    acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
+                }
+            }
+            gE[q] = acc[0] * c0 * st.invQ;
+            gE[NV + q] = acc[1] * c1 * st.invQ;
+            gE[2 * NV + q] = acc[2] * c2 * st.invQ;
+            continue;
+        }
         for (int o = 0; o < st.Q; ++o) {
             const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
             const float w = st.w[o];
@@ -160,40 +181,61 @@ k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long l
     }
 }
 
-// FP64 partials of gw_o (before the -1/Q factor), one pass over the block's voxels per offset.
+// FP64 partials of gw_o (before the -1/Q factor): one pass over the block's voxels; for each offset the
+// warp sums its 32 voxels' terms (fixed shuffle tree) into a warp-private FP64 accumulator, and the
+// warps' accumulators are summed in warp order.
 __global__ void __launch_bounds__(kThreads)
 k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
               int T, int X, int Y, int bnd, const __grid_constant__ Stencil st, double* __restrict__ part) {
     const long long NV = (long long)T * X * Y;
     const float c[3] = {coef[0], coef[1], coef[2]};
-    __shared__ double red[kThreads];
-    for (int o = 0; o < st.Q; ++o) {
-        const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
-        const float w = st.w[o];
-        double acc = 0.0;
-        for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV; p += (long long)gridDim.x * kThreads) {
-            const int y = (int)(p % Y);
-            const int x = (int)((p / Y) % X);
-            const int t = (int)(p / ((long long)X * Y));
-            const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd), yy = ext_index(y + dy, Y, bnd);
-            if ((tt | xx | yy) < 0) continue;
-            const long long nq = ((long long)tt * X + xx) * Y + yy;
-            float s = 0.f;
+    constexpr int kWarps = kThreads / 32;
+    __shared__ double wacc[kWarps][kMaxOffsets];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = lane; o < kMaxOffsets; o += 32) wacc[wid][o] = 0.0;
+    __syncwarp();
+    const long long stride = (long long)gridDim.x * kThreads;
+    const long long first = (long long)blockIdx.x * kThreads + wid * 32;
+    for (long long base = first; base < NV; base += stride) {   // warp-uniform trip count
+        const long long p = base + lane;
+        const bool live = p < NV;
+        int t = 0, x = 0, y = 0;
+        float ep[3] = {0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
+        if (live) {
+            y = (int)(p % Y);
+            x = (int)((p / Y) % X);
+            t = (int)(p / ((long long)X * Y));
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const float nb = __ldg(E + m * NV + nq);
-                s = fmaf(c[m] * sgnf(fmaf(-w, nb, __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p), nb, s);
+                ep[m] = __ldg(E + m * NV + p);
+                gp[m] = c[m] * __ldg(gS + m * gms + p);
             }
-            acc += (double)s;
         }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int sdx = kThreads / 2; sdx > 0; sdx >>= 1) {
-            if (threadIdx.x < sdx) red[threadIdx.x] += red[threadIdx.x + sdx];
-            __syncthreads();
+        for (int o = 0; o < st.Q; ++o) {
+            const float w = st.w[o];
+            float s = 0.f;
+            if (live) {
+                const int tt = ext_index(t + st.off[o][0], T, bnd), xx = ext_index(x + st.off[o][1], X, bnd),
+                          yy = ext_index(y + st.off[o][2], Y, bnd);
+                if ((tt | xx | yy) >= 0) {
+                    const long long nq = ((long long)tt * X + xx) * Y + yy;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const float nb = __ldg(E + m * NV + nq);
+                        s = fmaf(sgnf(fmaf(-w, nb, ep[m])) * gp[m], nb, s);
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+            if (lane == 0) wacc[wid][o] += (double)s;
         }
-        if (threadIdx.x == 0) part[blockIdx.x * 64 + o] = red[0];
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        double a = 0.0;
+        for (int w = 0; w < kWarps; ++w) a += wacc[w][o];
+        part[blockIdx.x * 64 + o] = a;
     }
 }
 

@@ -161,6 +161,7 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
                 return fail(nullptr, SAL_ERR_INVALID_ARG, "stencil offset component beyond +-8");
             }
             h->st.off[o][a] = v;
+            h->st.halo[a] = std::max(h->st.halo[a], v < 0 ? -v : v);
         }
         if (p->dir_id[o] < 0 || p->dir_id[o] >= p->n_dirs) {
             delete h;

@@ -21,6 +21,7 @@ struct Stencil {
     int Q;
     int n_dirs;
     float invQ;
+    int halo[3];              // max |offset component| per axis (t, x, y)
     int off[kMaxOffsets][3];
     float g[kMaxOffsets];     // Gaussian factor of each neighbour
     int dir[kMaxOffsets];     // direction group
