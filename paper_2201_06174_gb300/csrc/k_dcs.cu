@@ -1,8 +1,9 @@
 // K2: directional center-surround comparison (Sec. 2 step 4, Eq. 3; windows of Fig. 4)
 //   S_m[p] = (1/Q) sum_o | E_m[p] - w_o * Eext_m[p + o] |,   m in {t, x, y},
-// with the difference formed by one FMA (fmaf(-w, e_nb, e_c): the product is not rounded
-// before the subtraction).  HBM-bound: 12 B read + 12 B written per voxel; neighbours come
-// from L1/L2.  Fused per-block min/max of each S_m for the normalisation in K3.
+// in compensated FP32: each difference is formed by one FMA (fmaf(-w, e_nb, e_c): the product is
+// not rounded before the subtraction) and the Q distances are summed with Kahan compensation.
+// HBM-bound: 12 B read + 12 B written per voxel; neighbours come from L1/L2.  Fused per-block
+// min/max of each S_m for the normalisation in K3.
 #include <cfloat>
 
 #include "sal_internal.cuh"
@@ -33,7 +34,7 @@ k2_dcs(const float* __restrict__ E, float* __restrict__ S3, int T, int X, int Y,
         const int y = (int)(p % Y);
         const int x = (int)((p / Y) % X);
         const int t = (int)(p / ((long long)X * Y));
-        float ec[3], acc[3] = {0.f, 0.f, 0.f};
+        float ec[3], acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int m = 0; m < 3; ++m) ec[m] = __ldg(E + m * NV + p);
         for (int o = 0; o < st.Q; ++o) {
@@ -46,7 +47,11 @@ k2_dcs(const float* __restrict__ E, float* __restrict__ S3, int T, int X, int Y,
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const float nb = ok ? __ldg(E + m * NV + q) : 0.f;
-                acc[m] += fabsf(fmaf(-w, nb, ec[m]));
+                // Kahan: acc + cmp carries the sum to about twice the FP32 precision
+                const float yv = fabsf(fmaf(-w, nb, ec[m])) - cmp[m];
+                const float tv = acc[m] + yv;
+                cmp[m] = (tv - acc[m]) - yv;
+                acc[m] = tv;
             }
         }
 #pragma unroll
