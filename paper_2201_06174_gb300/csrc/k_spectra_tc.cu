@@ -4,10 +4,12 @@
 // Only the abs(F) / Eq. 1 epilogue runs on the SIMT pipes: abs(F) per bin, bins k_y and n - k_y summed
 // (same Eq. 1 ratios), weighted by r_m / |k| of Eq. 1, summed over k_y in registers, over k_t across
 // tiles, over k_x by warp shuffles; E = sum * max|V|.
-// Two 128-column accumulator buffers alternate; the stage-3 MMAs of a pass are issued one pass ahead, and
-// one CTA barrier per pass both publishes the MMA completion (polled by thread 0) and releases the
-// buffer read in the pass before.  Every wait is bounded; on timeout the CTA sets the error word and
-// leaves after releasing its tensor memory.
+// Warp-specialised: one producer warp issues every MMA; eight consumer warps read the accumulators and
+// run the epilogue.  Two 128-column accumulator buffers alternate; producer and consumers meet only on
+// mbarriers (buffer full: MMA commit; buffer empty and stage-3 A written: one arrival per consumer
+// warp), so the tensor core runs up to two passes ahead and no CTA-wide barrier sits in the k_t loop.
+// Every wait is bounded; on timeout the CTA sets the error word, stops issuing and leaves after
+// releasing its tensor memory.
 #include "tc_spectra_common.cuh"
 
 namespace sal {
@@ -20,7 +22,8 @@ using tcs::kK2;
 using tcs::kWaitLimit;
 using tcs::Pack;
 
-constexpr int kThreads = 256;
+constexpr int kConsumers = 8;           // consumer warps: 2 per tensor-memory lane quarter
+constexpr int kThreads = 32 * (kConsumers + 1);   // + one producer warp
 constexpr uint32_t kTmemCols = 256;     // two 128-column accumulator buffers
 
 template <int N> struct TcGeo : tcs::FwdGeo<N> {
@@ -28,7 +31,7 @@ template <int N> struct TcGeo : tcs::FwdGeo<N> {
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + F::TAB_B;
     static constexpr size_t OFF_MISC = OFF_A3 + 2 * F::A3_B;
-    static constexpr size_t SMEM = OFF_MISC + 64 + kThreads / 32 * 4;
+    static constexpr size_t SMEM = OFF_MISC + 64 + 16 * 4;
     static_assert(F::NB1 * 16 <= (int)kTmemCols, "tensor memory");
     static_assert(F::PASSES * F::OPC * 2 == 8, "accumulator slots");
     static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
@@ -52,10 +55,11 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     unsigned char* s_are = smem + G::OFF_A3;                 // stage-3 A, real part (MN-major)
     unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;       // stage-3 A, imaginary part
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);   // [k_t][|k_x|][|k_y|][3]
-    // mbarriers: [0], [1] accumulator buffer full (MMA commit), [2] constant operands landed
+    // mbarriers: [0], [1] buffer full (MMA commit); [2], [3] buffer empty (one arrival per consumer warp);
+    // [4] stage-3 A written, [5] stage-2 B tiles written (one arrival per consumer warp); [6] constants
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 48);
-    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 52);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 56);
+    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 60);
     float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 64);   // [warps]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -68,10 +72,14 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     if (tid == 0) {
         tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
         tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
-        tc::mbar_init(tc::smem_u32(&s_mbar[2]), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[2]), kConsumers);
+        tc::mbar_init(tc::smem_u32(&s_mbar[3]), kConsumers);
+        tc::mbar_init(tc::smem_u32(&s_mbar[4]), kConsumers);
+        tc::mbar_init(tc::smem_u32(&s_mbar[5]), kConsumers);
+        tc::mbar_init(tc::smem_u32(&s_mbar[6]), 1);
         *s_fail = 0;
-        tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[2]), (uint32_t)G::TAB_B);
-        tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB_B, tc::smem_u32(&s_mbar[2]));
+        tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[6]), (uint32_t)G::TAB_B);
+        tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB_B, tc::smem_u32(&s_mbar[6]));
     }
     // stage-3 A rows beyond the halo (read by the last windows, multiplied by zero twiddles) stay zero
     for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
@@ -84,165 +92,183 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-
-    // Every wait is CTA-uniform: thread 0 polls the mbarrier (bounded), the barrier that follows spreads
-    // a give-up (after which no MMA is issued and no tensor memory is read) and, in the k_t loop, also
-    // marks that every warp finished the previous pass.
-    auto wait_cta = [&](int b, uint32_t parity) -> bool {
-        const int failed_before = *s_fail;  // written only before an earlier barrier
-        bool ok = true;
-        if (tid == 0) ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
-        const int bad = __syncthreads_or(!ok || failed_before);
-        if (bad && tid == 0 && !failed_before) {
-            atomicOr(err, 1);
-            *s_fail = 1;  // read by every thread only after a later barrier
-        }
-        tc::fence_after_sync();
-        return !bad;
+    volatile int* v_fail = s_fail;
+    auto give_up = [&]() {
+        atomicOr(err, 1);
+        atomicExch(s_fail, 1);
     };
 
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, half = (warp >> 2) & 1;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const uint32_t idesc1 = tc::idesc_f16(FMT, 128, 16, 1, 0);
-    const uint32_t idesc2 = tc::idesc_f16(FMT, 128, G::N2, 0, 0);
-    const uint32_t idesc3 = tc::idesc_f16(FMT, 128, G::N3, 1, 0);
-    const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
-    const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
-    const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
-    const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
-    // stage 2 of tile kt into buffer 0 (columns [0, N2)); completion on full[0]
-    auto issue_s2 = [&](int kt) {
-        const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
+
+    if (warp == kConsumers) {
+        // ================================ producer warp: one lane issues every MMA ============================
+        if (lane == 0) {
+            const uint32_t idesc1 = tc::idesc_f16(FMT, 128, 16, 1, 0);
+            const uint32_t idesc2 = tc::idesc_f16(FMT, 128, G::N2, 0, 0);
+            const uint32_t idesc3 = tc::idesc_f16(FMT, 128, G::N3, 1, 0);
+            const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
+            const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
+            const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
+            const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
+            // bounded wait; a give-up (here or in a consumer) stops all further issue
+            auto pwait = [&](int b, uint32_t parity) -> bool {
+                if (*v_fail) return false;
+                const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
+                if (!ok) give_up();
+                tc::fence_after_sync();
+                return ok;
+            };
+            auto issue_s2 = [&](int kt) {
+                const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
 #pragma unroll
-        for (int s = 0; s < kK2 / 16; ++s)
-            tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
-                        tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
-        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
-    };
-    // stage 3 of one pass (OPP outputs) into buffer pass % 2; completion on full[pass % 2]
-    auto issue_s3 = [&](int pass) {
-        const uint32_t col = (uint32_t)(128 * (pass & 1));
+                for (int s = 0; s < kK2 / 16; ++s)
+                    tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
+                                tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
+                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+            };
+            auto issue_s3 = [&](int pass) {
+                const uint32_t col = (uint32_t)(128 * (pass & 1));
 #pragma unroll
-        for (int j = 0; j < G::OPP; ++j) {
-            const uint32_t y0 = pass * G::OPP + j;
-            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a, idesc3, 0);
-            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b, idesc3, 1);
+                for (int j = 0; j < G::OPP; ++j) {
+                    const uint32_t y0 = pass * G::OPP + j;
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a,
+                                idesc3, 0);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b,
+                                idesc3, 1);
+                }
+                tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
+            };
+            bool alive = pwait(6, 0);
+            if (alive) {   // stage 1, all k_t at once
+                const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+#pragma unroll
+                for (int i = 0; i < G::NB1; ++i)
+                    tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1,
+                                idesc1, 0);
+                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+            }
+            alive = alive && pwait(5, 0);             // the stage-2 B tiles are written
+            if (alive) issue_s2(0);
+            uint32_t pa = 0, pe0 = 0, pe1 = 0;
+            for (int kt = 0; kt < H && alive; ++kt) {
+                alive = pwait(4, pa);                 // A3(kt) written; buffer 0 (D2) read
+                pa ^= 1u;
+                if (!alive) break;
+                issue_s3(0);
+                if (kt > 0) {
+                    alive = pwait(3, pe1);            // buffer 1 released by the last pass of kt - 1
+                    pe1 ^= 1u;
+                    if (!alive) break;
+                }
+                issue_s3(1);
+#pragma unroll
+                for (int pass = 2; pass < G::PASSES; ++pass) {
+                    const int b = pass & 1;
+                    alive = pwait(2 + b, b ? pe1 : pe0);   // pass - 2 released buffer b
+                    if (b) pe1 ^= 1u; else pe0 ^= 1u;
+                    if (!alive) break;
+                    issue_s3(pass);
+                }
+                if (!alive || kt + 1 == H) break;
+                alive = pwait(2, pe0);                // pass PASSES - 2 released buffer 0
+                pe0 ^= 1u;
+                if (alive) issue_s2(kt + 1);
+            }
         }
-        tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
-    };
-    // D2 (buffer 0) -> stage-3 A operands: warps of half 0 take the real columns, half 1 the imaginary
-    auto convert_d2 = [&]() { tcs::d2_to_a3<N, FMT>(tmem, s_are, s_aim, q, lane, half); };
-
-    // ---- stage 1 on the tensor cores, all k_t at once (after the constant operands landed) ----------
-    bool ok = wait_cta(2, 0);
-    if (tid == 0 && ok) {
-        const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
-#pragma unroll
-        for (int i = 0; i < G::NB1; ++i)
-            tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1, idesc1, 0);
-        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+        __syncwarp();
     }
-    ok = wait_cta(0, 0);
-    uint32_t ph0 = 1, ph1 = 0;   // next phase parities of the two buffer barriers
-    // D1 -> one stage-2 B tile per k_t (the A1 region is free once the stage-1 MMAs completed)
-    if (ok) tcs::d1_to_b2<N, FMT>(tmem, s_b2, q, lane, half, 2);
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0 && !*s_fail) {
-        tc::fence_after_sync();
-        issue_s2(0);
-    }
-    ok = wait_cta(0, ph0);
-    ph0 ^= 1u;
-    if (ok) convert_d2();
-    tc::fence_before_sync();
-    __syncthreads();
 
-    // epilogue mapping: TMEM lane quarter q, row m = 32 q + lane
+    // ================================ consumer warps ===============================================
     const int m = 32 * q + lane;
     const int x0l = m / N, kx = m % N;
     const int ajx = kx <= N / 2 ? kx : N - kx;
     float acc[8][3];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
-
-    // ---- the k_t loop: one CTA barrier per pass; the MMAs of a pass are issued one pass ahead --------
-    for (int kt = 0; kt < H; ++kt) {
-        if (tid == 0 && !*s_fail) {
+    if (warp < kConsumers) {
+        // warp-uniform bounded wait
+        auto cwait = [&](int b, uint32_t parity) -> bool {
+            bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok && lane == 0 && !*v_fail) give_up();
             tc::fence_after_sync();
-            issue_s3(0);
-            issue_s3(1);
-        }
-        // this lane's Eq. 1 weights for (k_t, |k_x|), |k_y| = 0 .. n/2
-        float wt[3][H];
+            return ok;
+        };
+        auto arrive = [&](int b) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&s_mbar[b]));
+        };
+        uint32_t pf0 = 0, pf1 = 0;
+        // D1 -> one stage-2 B tile per k_t (the A1 region is free once the stage-1 MMAs completed)
+        if (cwait(0, pf0)) tcs::d1_to_b2<N, FMT>(tmem, s_b2, q, lane, half, 2);
+        pf0 ^= 1u;
+        tc::fence_async_smem();
+        arrive(5);
+        // D2 of the first tile -> stage-3 A operands (half 0: real columns, half 1: imaginary)
+        if (cwait(0, pf0)) tcs::d2_to_a3<N, FMT>(tmem, s_are, s_aim, q, lane, half);
+        pf0 ^= 1u;
+        arrive(4);
+        for (int kt = 0; kt < H; ++kt) {
+            // this lane's Eq. 1 weights for (k_t, |k_x|), |k_y| = 0 .. n/2
+            float wt[3][H];
 #pragma unroll
-        for (int k = 0; k < H; ++k) {
-            const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
-            wt[0][k] = w[0];
-            wt[1][k] = w[1];
-            wt[2][k] = w[2];
-        }
-#pragma unroll
-        for (int pass = 0; pass < G::PASSES; ++pass) {
-            const int b = pass & 1;
-            // pass complete in buffer b, and every warp done with the previous pass (buffer b ^ 1)
-            const bool full = wait_cta(b, b ? ph1 : ph0);
-            if (b) ph1 ^= 1u; else ph0 ^= 1u;
-            if (tid == 0 && !*s_fail && pass >= 1) {
-                if (pass + 1 < G::PASSES) issue_s3(pass + 1);
-                else if (kt + 1 < H) issue_s2(kt + 1);       // buffer 0 free: stage 2 of the next tile
+            for (int k = 0; k < H; ++k) {
+                const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
+                wt[0][k] = w[0];
+                wt[1][k] = w[1];
+                wt[2][k] = w[2];
             }
-            if (full) {
-                // chunks half and half + 2 of this buffer, both loads in flight before the wait
-                uint32_t r[2][32];
-                tc::tmem_ld32_async(tmem + lane_base + (uint32_t)(128 * b + 32 * half), r[0]);
-                tc::tmem_ld32_async(tmem + lane_base + (uint32_t)(128 * b + 32 * (half + 2)), r[1]);
-                tc::tmem_wait_ld(r[0]);
-                tc::tmem_wait_ld(r[1]);
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
+            for (int pass = 0; pass < G::PASSES; ++pass) {
+                const int b = pass & 1;
+                const bool full = cwait(b, b ? pf1 : pf0);
+                if (b) pf1 ^= 1u; else pf0 ^= 1u;
+                if (full) {
 #pragma unroll
-                    for (int o = 0; o < G::OPC; ++o) {
-                        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+                    for (int cc = 0; cc < 2; ++cc) {   // chunks half and half + 2 of this buffer
+                        float v[32];
+                        tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * (half + 2 * cc)), v);
 #pragma unroll
-                        for (int k = 0; k < H; ++k) {
-                            const float re = __uint_as_float(r[cc][o * G::N3 + k]);
-                            const float im = __uint_as_float(r[cc][o * G::N3 + N + k]);
-                            float sm = fast_sqrt(fmaf(re, re, im * im));
-                            if (k != 0 && 2 * k != N) {
-                                const float re2 = __uint_as_float(r[cc][o * G::N3 + N - k]);
-                                const float im2 = __uint_as_float(r[cc][o * G::N3 + 2 * N - k]);
-                                sm += fast_sqrt(fmaf(re2, re2, im2 * im2));
+                        for (int o = 0; o < G::OPC; ++o) {
+                            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < H; ++k) {
+                                const float re = v[o * G::N3 + k], im = v[o * G::N3 + N + k];
+                                float sm = fast_sqrt(fmaf(re, re, im * im));
+                                if (k != 0 && 2 * k != N) {
+                                    const float re2 = v[o * G::N3 + N - k], im2 = v[o * G::N3 + 2 * N - k];
+                                    sm += fast_sqrt(fmaf(re2, re2, im2 * im2));
+                                }
+                                e0 = fmaf(wt[0][k], sm, e0);
+                                e1 = fmaf(wt[1][k], sm, e1);
+                                e2 = fmaf(wt[2][k], sm, e2);
                             }
-                            e0 = fmaf(wt[0][k], sm, e0);
-                            e1 = fmaf(wt[1][k], sm, e1);
-                            e2 = fmaf(wt[2][k], sm, e2);
+                            const int slot = (pass * 2 + cc) * G::OPC + o;
+                            acc[slot][0] += e0;
+                            acc[slot][1] += e1;
+                            acc[slot][2] += e2;
                         }
-                        const int slot = (pass * 2 + cc) * G::OPC + o;
-                        acc[slot][0] += e0;
-                        acc[slot][1] += e1;
-                        acc[slot][2] += e2;
                     }
                 }
+                arrive(2 + b);                                 // this warp is done with buffer b
             }
-            tc::fence_before_sync();
-        }
-        if (kt + 1 < H) {
-            // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
-            ok = wait_cta(0, ph0);
-            ph0 ^= 1u;
-            if (ok) convert_d2();
-            tc::fence_before_sync();
-            __syncthreads();
+            if (kt + 1 < H) {
+                // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
+                if (cwait(0, pf0)) tcs::d2_to_a3<N, FMT>(tmem, s_are, s_aim, q, lane, half);
+                pf0 ^= 1u;
+                arrive(4);
+            }
         }
     }
+    tc::fence_before_sync();
     __syncthreads();
 
     // ---- sum over the n lanes of each x0 (k_x), write E -------------------------------------------
     const size_t NV = (size_t)T * X * Y;
     const int x = xb + x0l;
-    const bool good = *s_fail == 0;
+    const bool good = *s_fail == 0 && warp < kConsumers;   // the producer warp holds no results
 #pragma unroll
     for (int pass = 0; pass < G::PASSES; ++pass)
 #pragma unroll
