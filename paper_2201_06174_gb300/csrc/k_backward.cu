@@ -282,6 +282,24 @@ k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, i
         const int y = (int)(q % Y);
         const int x = (int)((q / Y) % X);
         const int t = (int)(q / ((long long)X * Y));
+        if (t >= h2 && t < T - h2 && x >= h2 && x < X - h2 && y >= h2 && y < Y - h2) {
+            // interior voxel: its only extended position is itself
+            const int t0a = max(t_begin, t - h2 + 1), t0b = min(t_end - 1, t + h2);
+            if (t0a > t0b) continue;
+            const int xa = max(0, ceildiv(x + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(x + h2, BX));
+            const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
+            float sum = 0.f;
+            for (int t0 = t0a; t0 <= t0b; ++t0) {
+                const int ut = t - t0 + h2;
+                for (int xs = xa; xs <= xb; ++xs) {
+                    const long long cta_row = ((long long)(t0 - t_begin) * nxs + xs) * nseg;
+                    const long long inner = ((long long)ut * XH + (x - xs * BX + h2)) * YH + y + h2;
+                    for (int sg = sa; sg <= sb; ++sg) sum += __ldg(blocks + (cta_row + sg) * bsz + inner - sg * BY);
+                }
+            }
+            gV[q] += sum;
+            continue;
+        }
         int et[40], ex[40], ey[40];
         const int nt = pre_range(t, T, bnd, t_begin - h2, t_end + h2 - 1, et, 40);
         if (nt == 0) continue;

@@ -70,7 +70,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * F::P * kBY * 4;
     static constexpr size_t OFF_MISC = (OFF_L1 + (size_t)F::P * kBY * 4 + 15) / 16 * 16;
     static constexpr size_t SMEM = OFF_MISC + 64 + 2 * (kThreads / 32) * 4;
-    static_assert((size_t)kXHP * F::YP * 4 <= G_B, "L1 column sums fit in the Gamma region");
+    static_assert((size_t)(kXHP * F::YP + F::XH * kBY) * 4 <= G_B, "L1 sums fit in the Gamma region");
     static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
     static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -182,12 +182,21 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         s_col[pos] = a;
     }
     __syncthreads();
+    // box over y (h(u_y)), rows x of the halo, kept in the upper part of the column-sum area
+    float* s_row = s_col + kXHP * YP;
+    for (int i = tid; i < XH * kBY; i += kThreads) {
+        const int y0 = i % kBY, x = i / kBY;
+        float a = 0.f;
+#pragma unroll
+        for (int uy = 0; uy < N; ++uy) a = fmaf(tw.c[0][uy], s_col[x * YP + y0 + uy], a);
+        s_row[i] = a;
+    }
+    __syncthreads();
     for (int i = tid; i < P * kBY; i += kThreads) {
         const int y0 = i % kBY, xl = i / kBY;
         float a = 0.f;
-        for (int ux = 0; ux < N; ++ux)
 #pragma unroll
-            for (int uy = 0; uy < N; ++uy) a = fmaf(tw.c[0][ux] * tw.c[0][uy], s_col[(xl + ux) * YP + y0 + uy], a);
+        for (int ux = 0; ux < N; ++ux) a = fmaf(tw.c[0][ux], s_row[(xl + ux) * kBY + y0], a);
         s_l1[i] = a;
     }
     tc::fence_after_sync();
