@@ -21,6 +21,9 @@
 //     A operand [pos][(re, im, 0...)] and D_t[pos][u_t] += A_t B_t(k_t), B_t = [c | -s](k_t, u_t),
 //     accumulates the brick's block of gVext over all k_t in tensor memory; at the end it is written to
 //     scratch [u_t][x][y] and the fixed-order gather kernel sums the overlapping blocks.
+// Warp-specialised: one producer warp issues every MMA, sixteen consumer warps compute Gamma and move
+// the adjoint operands; they meet only on mbarriers, and the stage-3 MMAs of the next k_t tile are issued
+// while the consumers still read back the adjoint of the current one.
 // FP16 operands in both 16-bit forms (3 more mantissa bits than BF16: the direction F/|F| of small bins
 // amplifies operand rounding).  Every wait on the tensor cores is bounded; on timeout the CTA sets the
 // error word, skips the remaining MMAs and writes a zero block.
@@ -38,7 +41,8 @@ using tcs::kXHP;
 using tcs::Pack;
 
 constexpr int kFmt = 0;                   // FP16 operands
-constexpr int kThreads = 512;             // 16 warps: 4 per tensor-memory lane quarter
+constexpr int kConsumers = 16;            // consumer warps: 4 per tensor-memory lane quarter
+constexpr int kThreads = 32 * (kConsumers + 1);   // + one producer warp
 constexpr uint32_t kTmemCols = 512;       // [0,256) forward buffers; [256,320) dG2; [320,384) dG1; [384,480) gV
 constexpr uint32_t kColY = 256;
 constexpr uint32_t kColX = 320;
@@ -69,7 +73,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr size_t OFF_GE = OFF_AT + F::A1_B;
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * F::P * kBY * 4;
     static constexpr size_t OFF_MISC = (OFF_L1 + (size_t)F::P * kBY * 4 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_MISC + 64 + 2 * (kThreads / 32) * 4;
+    static constexpr size_t SMEM = OFF_MISC + 128 + 2 * 32 * 4;
     static_assert((size_t)(kXHP * F::YP + F::XH * kBY) * 4 <= G_B, "L1 sums fit in the Gamma region");
     static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
     static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
@@ -124,14 +128,17 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     float* s_ge = reinterpret_cast<float*>(smem + G::OFF_GE);    // [3][P][16]
     float* s_l1 = reinterpret_cast<float*>(smem + G::OFF_L1);    // [P][16]
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);
-    // mbarriers: [0], [1] forward buffers (MMA commit), [2] adjoint MMAs, [3] constant operands landed
+    // mbarriers (arrival counts): [0], [1] forward buffer full (MMA commit); [2], [3] forward buffer read
+    // (16 warps); [4] stage-3 A written (16); [5] stage-2 B tiles written (16); [6], [7] Gamma set written
+    // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete (commit); [11] A_t
+    // written (16); [12] constant operands landed (bulk copy); [13] the brick's gV block complete (commit)
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 32);
-    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 36);
-    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 64);   // [2][warps]
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 112);
+    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 116);
+    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 128);  // [2][32]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int q = warp & 3, grp = warp >> 2;
+    const int q = warp & 3, grp = (warp >> 2) & 3;
     const int yb = blockIdx.x * kBY;
     const int xb = blockIdx.y * P;
     const int t0 = t_begin + blockIdx.z;
@@ -140,10 +147,12 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     // ---- set-up ------------------------------------------------------------------------------------
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
     if (tid == 0) {
-        for (int b = 0; b < 4; ++b) tc::mbar_init(tc::smem_u32(&s_mbar[b]), 1);
+        const uint32_t counts[14] = {1, 1, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, 1,
+                                     kConsumers, 1, kConsumers, 1, 1};
+        for (int b = 0; b < 14; ++b) tc::mbar_init(tc::smem_u32(&s_mbar[b]), counts[b]);
         *s_fail = 0;
-        tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[3]), (uint32_t)G::TAB5_B);
-        tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB5_B, tc::smem_u32(&s_mbar[3]));
+        tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[12]), (uint32_t)G::TAB5_B);
+        tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB5_B, tc::smem_u32(&s_mbar[12]));
     }
     for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -159,12 +168,12 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-    if (lane == 0) s_red[kThreads / 32 + warp] = gmax;
+    if (lane == 0) s_red[32 + warp] = gmax;
     const float scale = tcs::stage_brick<N, kFmt, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid);
     (void)scale;   // the direction F/|F| and the adjoint stages do not depend on the brick scale
     float bgmax = 0.f;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) bgmax = fmaxf(bgmax, s_red[kThreads / 32 + w]);
+    for (int w = 0; w < kThreads / 32; ++w) bgmax = fmaxf(bgmax, s_red[32 + w]);
     const float sigma = bgmax > 0.f ? (float)(N * N * N) / (8.f * bgmax) : 1.f;   // Gamma operand scale
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -199,283 +208,302 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         for (int ux = 0; ux < N; ++ux) a = fmaf(tw.c[0][ux], s_row[(xl + ux) * kBY + y0], a);
         s_l1[i] = a;
     }
+    __syncthreads();   // L1 norms visible; the column-sum area (Gamma region) free again
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-
-    // Every wait is CTA-uniform: thread 0 polls the mbarrier (bounded), the barrier that follows spreads a
-    // give-up (after which no MMA is issued and no tensor memory is read) and, in the k_t loop, also marks
-    // that every warp finished the previous step.
-    auto wait_cta = [&](int b, uint32_t parity) -> bool {
-        const int failed_before = *s_fail;
-        bool ok = true;
-        if (tid == 0) ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
-        const int bad = __syncthreads_or(!ok || failed_before);
-        if (bad && tid == 0 && !failed_before) {
-            atomicOr(err, 1);
-            *s_fail = 1;
-        }
-        tc::fence_after_sync();
-        return !bad;
+    volatile int* v_fail = s_fail;
+    auto give_up = [&]() {
+        atomicOr(err, 1);
+        atomicExch(s_fail, 1);
     };
-
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const uint32_t idesc1 = tc::idesc_f16(kFmt, 128, 16, 1, 0);
-    const uint32_t idesc2 = tc::idesc_f16(kFmt, 128, G::N2, 0, 0);
-    const uint32_t idesc3 = tc::idesc_f16(kFmt, 128, G::N3, 1, 0);
-    const uint32_t idescy = tc::idesc_f16(kFmt, 128, 32, 0, 0);
-    const uint32_t idescx = tc::idesc_f16(kFmt, 128, 64, 1, 1);
-    const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
-    const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
-    const uint32_t gbase = tc::smem_u32(s_g), bc = tc::smem_u32(s_bc), bs = tc::smem_u32(s_bs);
-    const uint32_t at = tc::smem_u32(s_at);
-    const uint32_t idesct = tc::idesc_f16(kFmt, 128, 16, 1, 0);
-    const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
-    const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
-    auto issue_s2 = [&](int kt) {
-        const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
-#pragma unroll
-        for (int s = 0; s < kK2 / 16; ++s)
-            tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
-                        tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
-        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
-    };
-    auto issue_s3 = [&](int pass) {
-        const uint32_t col = (uint32_t)(128 * (pass & 1));
-#pragma unroll
-        for (int j = 0; j < G::OPP; ++j) {
-            const uint32_t y0 = pass * G::OPP + j;
-            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a, idesc3, 0);
-            tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b, idesc3, 1);
-        }
-        tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
-    };
-    // adjoint of stage 3 for the outputs of one pass (Gamma set pass % 2), accumulating into kColY
-    auto issue_inv_y = [&](int pass) {
-        const uint32_t set = gbase + (uint32_t)((pass & 1) * G::GSET_B);
-#pragma unroll
-        for (int j = 0; j < G::OPP; ++j) {
-            const uint32_t y0 = pass * G::OPP + j;
-            const uint32_t slot = set + (uint32_t)(j * G::SLOT_B);
-            const uint32_t shift = (15u - y0) * 16u;
-#pragma unroll
-            for (int s = 0; s < G::KG / 16; ++s) {
-                const uint64_t a = tc::desc_noswizzle(slot + 256 * s, 128, G::SBO_G);
-                const uint32_t acc = (y0 > 0 || s > 0) ? 1u : 0u;
-                tc::mma_f16(tmem + kColY, a,
-                            tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE + shift + 2 * G::TI_LBO * s, G::TI_LBO, 128),
-                            idescy, acc);
-                tc::mma_f16(tmem + kColY + 32, a,
-                            tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM + shift + 2 * G::TI_LBO * s, G::TI_LBO, 128),
-                            idescy, acc);
-            }
-        }
-    };
 
-    // ---- stage 1, D1 -> B2 tiles, stage 2 of the first tile --------------------------------------------
-    bool ok = wait_cta(3, 0);
-    if (tid == 0 && ok) {
-        const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+    if (warp == kConsumers) {
+        // ================================ producer warp: one lane issues every MMA ============================
+        if (lane == 0) {
+            const uint32_t idesc1 = tc::idesc_f16(kFmt, 128, 16, 1, 0);
+            const uint32_t idesc2 = tc::idesc_f16(kFmt, 128, G::N2, 0, 0);
+            const uint32_t idesc3 = tc::idesc_f16(kFmt, 128, G::N3, 1, 0);
+            const uint32_t idescy = tc::idesc_f16(kFmt, 128, 32, 0, 0);
+            const uint32_t idescx = tc::idesc_f16(kFmt, 128, 64, 1, 1);
+            const uint32_t idesct = tc::idesc_f16(kFmt, 128, 16, 1, 0);
+            const uint32_t tab = tc::smem_u32(s_tab), b2base = tc::smem_u32(s_b2);
+            const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
+            const uint32_t gbase = tc::smem_u32(s_g), bc = tc::smem_u32(s_bc), bs = tc::smem_u32(s_bs);
+            const uint32_t at = tc::smem_u32(s_at);
+            const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
+            const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
+            uint32_t ph[14];
 #pragma unroll
-        for (int i = 0; i < G::NB1; ++i)
-            tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1, idesc1, 0);
-        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
-    }
-    ok = wait_cta(0, 0);
-    uint32_t ph0 = 1, ph1 = 0, pa = 0;
-    if (ok) tcs::d1_to_b2<N, kFmt>(tmem, s_b2, q, lane, grp, 4);
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0 && !*s_fail) {
-        tc::fence_after_sync();
-        issue_s2(0);
-    }
-    ok = wait_cta(0, ph0);
-    ph0 ^= 1u;
-    if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
-    tc::fence_before_sync();
-    __syncthreads();
-
-    // Gamma mapping: tensor-memory lane quarter q, row m = 32 q + lane; warp group grp = chunk of a buffer
-    const int m = 32 * q + lane;
-    const int x0l = m / N, kx = m % N;
-    const int ajx = kx <= N / 2 ? kx : N - kx;
-
-    for (int kt = 0; kt < H; ++kt) {
-        if (tid == 0 && !*s_fail) {
-            tc::fence_after_sync();
-            issue_s3(0);
-            issue_s3(1);
-        }
-        float wt[3][H];
+            for (int b = 0; b < 14; ++b) ph[b] = 0;
+            auto commit = [&](int b) { tc::mma_commit(tc::smem_u32(&s_mbar[b])); };
+            // bounded wait; a give-up (here or in a consumer) stops all further issue
+            auto pwait = [&](int b) -> bool {
+                if (*v_fail) return false;
+                const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
+                ph[b] ^= 1u;
+                if (!ok) give_up();
+                tc::fence_after_sync();
+                return ok;
+            };
+            auto issue_s2 = [&](int kt) {
+                const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
 #pragma unroll
-        for (int k = 0; k < H; ++k) {
-            const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
-            wt[0][k] = w[0];
-            wt[1][k] = w[1];
-            wt[2][k] = w[2];
-        }
+                for (int s = 0; s < kK2 / 16; ++s)
+                    tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
+                                tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
+                commit(0);
+            };
+            auto issue_s3 = [&](int pass) {
+                const uint32_t col = (uint32_t)(128 * (pass & 1));
 #pragma unroll
-        for (int pass = 0; pass < G::PASSES; ++pass) {
-            const int b = pass & 1;
-            // pass complete in buffer b; every warp done with the previous pass (its Gamma set written)
-            const bool full = wait_cta(b, b ? ph1 : ph0);
-            if (b) ph1 ^= 1u; else ph0 ^= 1u;
-            if (tid == 0 && !*s_fail && pass >= 1) {
-                issue_inv_y(pass - 1);
-                if (pass + 1 < G::PASSES) issue_s3(pass + 1);
-                else if (kt + 1 < H) issue_s2(kt + 1);       // buffer 0 free: stage 2 of the next tile
-            }
-            if (full) {
-                float v[32];
-                tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * grp), v);
+                for (int j = 0; j < G::OPP; ++j) {
+                    const uint32_t y0 = pass * G::OPP + j;
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a,
+                                idesc3, 0);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b,
+                                idesc3, 1);
+                }
+                commit(pass & 1);
+            };
+            // adjoint of stage 3 for the outputs of one pass (Gamma set pass % 2), accumulating into kColY
+            auto issue_inv_y = [&](int pass) {
+                const uint32_t set = gbase + (uint32_t)((pass & 1) * G::GSET_B);
 #pragma unroll
-                for (int o = 0; o < G::OPC; ++o) {
-                    const int j = grp * G::OPC + o;
-                    const int y0 = pass * G::OPP + j;
-                    const int gi = x0l * kBY + y0;
-                    const float g0 = s_ge[gi], g1 = s_ge[P * kBY + gi], g2 = s_ge[2 * P * kBY + gi];
-                    const float thr = kKinkTau * s_l1[gi];
-                    const float thr2 = fmaxf(thr * thr, 1e-30f);
-                    float rho[H];
+                for (int j = 0; j < G::OPP; ++j) {
+                    const uint32_t y0 = pass * G::OPP + j;
+                    const uint32_t slot = set + (uint32_t)(j * G::SLOT_B);
+                    const uint32_t shift = (15u - y0) * 16u;
 #pragma unroll
-                    for (int k = 0; k < H; ++k) rho[k] = sigma * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
-                    float gr[N], gim[N];
-#pragma unroll
-                    for (int ky = 0; ky < N; ++ky) {
-                        const float re = v[o * G::N3 + ky], im = v[o * G::N3 + N + ky];
-                        const float m2 = fmaf(re, re, im * im);
-                        const float sc = m2 > thr2 ? rho[ky <= N / 2 ? ky : N - ky] * fast_rsqrt(m2) : 0.f;
-                        gr[ky] = sc * re;
-                        gim[ky] = sc * im;
+                    for (int s = 0; s < G::KG / 16; ++s) {
+                        const uint64_t a = tc::desc_noswizzle(slot + 256 * s, 128, G::SBO_G);
+                        const uint32_t accum = (y0 > 0 || s > 0) ? 1u : 0u;
+                        tc::mma_f16(tmem + kColY, a,
+                                    tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE + shift + 2 * G::TI_LBO * s,
+                                                       G::TI_LBO, 128),
+                                    idescy, accum);
+                        tc::mma_f16(tmem + kColY + 32, a,
+                                    tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM + shift + 2 * G::TI_LBO * s,
+                                                       G::TI_LBO, 128),
+                                    idescy, accum);
                     }
-                    // K-major operand: byte(m, k) = (m/8) SBO_G + (k/8) 128 + (m%8) 16 + (k%8) 2, k = [re | im]
-                    unsigned char* dst = s_g + b * G::GSET_B + j * G::SLOT_B + (m / 8) * G::SBO_G + (m % 8) * 16;
+                }
+            };
+            bool alive = pwait(12);
+            if (alive) {   // stage 1, all k_t at once
+                const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
 #pragma unroll
-                    for (int c = 0; c < N / 8; ++c) {
-                        uint4 wr, wi;
-                        wr.x = Pack<kFmt>::two(gr[8 * c + 0], gr[8 * c + 1]);
-                        wr.y = Pack<kFmt>::two(gr[8 * c + 2], gr[8 * c + 3]);
-                        wr.z = Pack<kFmt>::two(gr[8 * c + 4], gr[8 * c + 5]);
-                        wr.w = Pack<kFmt>::two(gr[8 * c + 6], gr[8 * c + 7]);
-                        wi.x = Pack<kFmt>::two(gim[8 * c + 0], gim[8 * c + 1]);
-                        wi.y = Pack<kFmt>::two(gim[8 * c + 2], gim[8 * c + 3]);
-                        wi.z = Pack<kFmt>::two(gim[8 * c + 4], gim[8 * c + 5]);
-                        wi.w = Pack<kFmt>::two(gim[8 * c + 6], gim[8 * c + 7]);
-                        *reinterpret_cast<uint4*>(dst + c * 128) = wr;
-                        *reinterpret_cast<uint4*>(dst + (N / 8 + c) * 128) = wi;
+                for (int i = 0; i < G::NB1; ++i)
+                    tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1,
+                                idesc1, 0);
+                commit(0);
+            }
+            alive = alive && pwait(5);
+            if (alive) issue_s2(0);
+            alive = alive && pwait(4);
+            if (alive) {
+                issue_s3(0);
+                issue_s3(1);
+            }
+            for (int kt = 0; kt < H && alive; ++kt) {
+#pragma unroll
+                for (int pass = 0; pass < G::PASSES; ++pass) {
+                    const int b = pass & 1;
+                    if (!(alive = pwait(6 + b))) break;     // Gamma of this pass written
+                    issue_inv_y(pass);
+                    if (pass == G::PASSES - 1) commit(8);
+                    if (pass + 2 < G::PASSES) {
+                        if (!(alive = pwait(2 + b))) break; // the pass read buffer b
+                        issue_s3(pass + 2);
+                    } else if (pass + 2 == G::PASSES) {
+                        if (!(alive = pwait(2))) break;     // buffer 0 released
+                        if (kt + 1 < H) issue_s2(kt + 1);
+                    }
+                }
+                if (!alive) break;
+                if (kt + 1 < H) {
+                    if (!(alive = pwait(4))) break;          // A3(kt + 1) written (buffer 0's D2 read)
+                    issue_s3(0);
+                    if (!(alive = pwait(3))) break;          // buffer 1 released by the last pass of kt
+                    issue_s3(1);
+                }
+                // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------
+                if (!(alive = pwait(9))) break;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + 1536 * s, G::SBO_K2, 128),
+                                tc::desc_noswizzle(bc + 256 * s, 128, 2048), idescx, s > 0 ? 1u : 0u);
+                    tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + (kXHP / 8) * 128 + 1536 * s, G::SBO_K2, 128),
+                                tc::desc_noswizzle(bs + 256 * s, 128, 2048), idescx, 1u);
+                }
+                commit(10);
+                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
+                if (!(alive = pwait(11))) break;
+                const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
+#pragma unroll
+                for (int i = 0; i < G::NB1; ++i)
+                    tc::mma_f16(tmem + kColT + 16 * i, tc::desc_noswizzle(at + 4096 * i, 128, 256), btd, idesct,
+                                kt > 0 ? 1u : 0u);
+            }
+            if (alive) commit(13);
+        }
+        __syncwarp();
+    } else {
+        // ================================ consumer warps ===============================================
+        uint32_t ph[14];
+#pragma unroll
+        for (int b = 0; b < 14; ++b) ph[b] = 0;
+        // warp-uniform bounded wait
+        auto cwait = [&](int b) -> bool {
+            bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
+            ph[b] ^= 1u;
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok && lane == 0 && !*v_fail) give_up();
+            tc::fence_after_sync();
+            return ok;
+        };
+        auto arrive = [&](int b) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&s_mbar[b]));
+        };
+        const int m = 32 * q + lane;
+        const int x0l = m / N, kx = m % N;
+        const int ajx = kx <= N / 2 ? kx : N - kx;
+        bool ok = cwait(0);
+        if (ok) tcs::d1_to_b2<N, kFmt>(tmem, s_b2, q, lane, grp, 4);
+        tc::fence_async_smem();
+        arrive(5);
+        ok = cwait(0);
+        if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
+        arrive(4);
+        for (int kt = 0; kt < H; ++kt) {
+            float wt[3][H];
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
+                wt[0][k] = w[0];
+                wt[1][k] = w[1];
+                wt[2][k] = w[2];
+            }
+#pragma unroll
+            for (int pass = 0; pass < G::PASSES; ++pass) {
+                const int b = pass & 1;
+                if (cwait(b)) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * grp), v);
+#pragma unroll
+                    for (int o = 0; o < G::OPC; ++o) {
+                        const int j = grp * G::OPC + o;
+                        const int y0 = pass * G::OPP + j;
+                        const int gi = x0l * kBY + y0;
+                        const float g0 = s_ge[gi], g1 = s_ge[P * kBY + gi], g2 = s_ge[2 * P * kBY + gi];
+                        const float thr = kKinkTau * s_l1[gi];
+                        const float thr2 = fmaxf(thr * thr, 1e-30f);
+                        float rho[H];
+#pragma unroll
+                        for (int k = 0; k < H; ++k)
+                            rho[k] = sigma * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
+                        float gr[N], gim[N];
+#pragma unroll
+                        for (int ky = 0; ky < N; ++ky) {
+                            const float re = v[o * G::N3 + ky], im = v[o * G::N3 + N + ky];
+                            const float m2 = fmaf(re, re, im * im);
+                            const float sc = m2 > thr2 ? rho[ky <= N / 2 ? ky : N - ky] * fast_rsqrt(m2) : 0.f;
+                            gr[ky] = sc * re;
+                            gim[ky] = sc * im;
+                        }
+                        // K-major operand: byte(m, k) = (m/8) SBO_G + (k/8) 128 + (m%8) 16 + (k%8) 2, k = [re | im]
+                        unsigned char* dst = s_g + b * G::GSET_B + j * G::SLOT_B + (m / 8) * G::SBO_G + (m % 8) * 16;
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) {
+                            uint4 wr, wi;
+                            wr.x = Pack<kFmt>::two(gr[8 * c + 0], gr[8 * c + 1]);
+                            wr.y = Pack<kFmt>::two(gr[8 * c + 2], gr[8 * c + 3]);
+                            wr.z = Pack<kFmt>::two(gr[8 * c + 4], gr[8 * c + 5]);
+                            wr.w = Pack<kFmt>::two(gr[8 * c + 6], gr[8 * c + 7]);
+                            wi.x = Pack<kFmt>::two(gim[8 * c + 0], gim[8 * c + 1]);
+                            wi.y = Pack<kFmt>::two(gim[8 * c + 2], gim[8 * c + 3]);
+                            wi.z = Pack<kFmt>::two(gim[8 * c + 4], gim[8 * c + 5]);
+                            wi.w = Pack<kFmt>::two(gim[8 * c + 6], gim[8 * c + 7]);
+                            *reinterpret_cast<uint4*>(dst + c * 128) = wr;
+                            *reinterpret_cast<uint4*>(dst + (N / 8 + c) * 128) = wi;
+                        }
+                    }
+                }
+                tc::fence_async_smem();
+                arrive(2 + b);   // buffer b read
+                arrive(6 + b);   // Gamma set b written
+            }
+            if (kt + 1 < H) {
+                // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
+                ok = cwait(0);
+                if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
+                arrive(4);
+            }
+            // ---- dG2 (all adjoint-y MMAs of kt done) -> B_c | B_s (FP16, MN-major [K = m][N = 64]) -------
+            if (cwait(8)) {
+                // warp group grp: columns 16 grp .. 16 grp + 15 of (re y 0..31 | im y 0..31) -> B_c at the same
+                // columns, B_s at the other half (re -> the im slot, im -> the re slot, negated)
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + kColY + (uint32_t)(16 * grp), v);
+                const float sgn = grp < 2 ? 1.f : -1.f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int n = 16 * grp + 8 * h, ns = (n + 32) % 64;
+                    uint4 w, ws;
+                    w.x = Pack<kFmt>::two(v[8 * h + 0], v[8 * h + 1]);
+                    w.y = Pack<kFmt>::two(v[8 * h + 2], v[8 * h + 3]);
+                    w.z = Pack<kFmt>::two(v[8 * h + 4], v[8 * h + 5]);
+                    w.w = Pack<kFmt>::two(v[8 * h + 6], v[8 * h + 7]);
+                    ws.x = Pack<kFmt>::two(sgn * v[8 * h + 0], sgn * v[8 * h + 1]);
+                    ws.y = Pack<kFmt>::two(sgn * v[8 * h + 2], sgn * v[8 * h + 3]);
+                    ws.z = Pack<kFmt>::two(sgn * v[8 * h + 4], sgn * v[8 * h + 5]);
+                    ws.w = Pack<kFmt>::two(sgn * v[8 * h + 6], sgn * v[8 * h + 7]);
+                    const size_t row = (size_t)(m / 8) * 128 + (m % 8) * 16;
+                    *reinterpret_cast<uint4*>(s_bc + (n / 8) * 2048 + row) = w;
+                    *reinterpret_cast<uint4*>(s_bs + (ns / 8) * 2048 + row) = ws;
+                }
+            }
+            tc::fence_async_smem();
+            arrive(9);
+            // ---- dG1 (rows x of lane quarter 0) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) --------
+            if (cwait(10) && q == 0) {
+                float v[16];
+                tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * grp), v);
+                const int x = lane, k = grp >> 1;
+                if (x < kXHP) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int y8 = 16 * (grp & 1) + 8 * h;
+                        if (y8 < YP) {
+                            // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
+                            uint4 w;
+                            w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
+                            w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
+                            w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
+                            w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
+                            *reinterpret_cast<uint4*>(s_at + ((x * YP + y8) / 8) * 256 + k * 16) = w;
+                        }
                     }
                 }
             }
             tc::fence_async_smem();
-            tc::fence_before_sync();
+            arrive(11);
         }
-        // ---- adjoint of stage 3 for the last pass, then dG2 -> FP16 operand --------------------------------
-        __syncthreads();
-        if (tid == 0 && !*s_fail) {
-            tc::fence_after_sync();
-            issue_inv_y(G::PASSES - 1);
-            tc::mma_commit(tc::smem_u32(&s_mbar[2]));
-        }
-        ok = wait_cta(2, pa);
-        pa ^= 1u;
-        if (ok) {
-            // warp group grp: columns 16 grp .. 16 grp + 15 of (re y 0..31 | im y 0..31) -> B_c at the
-            // same columns, B_s at the other half (re -> the im slot, im -> the re slot, negated)
+        // ---- the brick's block of gVext (tensor memory) to scratch [u_t][x][y] --------------------------------
+        ok = cwait(13);
+        const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        float* blk = blocks + cta * G::BLOCK_FLOATS;
+        const float out_scale = 1.f / (sigma * kDxScale);
+        for (int i = grp; i < G::NB1; i += 4) {
             float v[16];
-            tc::tmem_ld16(tmem + lane_base + kColY + (uint32_t)(16 * grp), v);
-            const float sgn = grp < 2 ? 1.f : -1.f;
-            // MN-major [K = m][N = n]: byte(n, k) = (n/8) 2048 + (k/8) 128 + (k%8) 16 + (n%8) 2
+            if (ok) tc::tmem_ld16(tmem + lane_base + kColT + (uint32_t)(16 * i), v);
+            const int pos = 128 * i + m, x = pos / YP, y = pos % YP;
+            if (x < XH && y < YH) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int n = 16 * grp + 8 * h, ns = (n + 32) % 64;
-                uint4 w, ws;
-                w.x = Pack<kFmt>::two(v[8 * h + 0], v[8 * h + 1]);
-                w.y = Pack<kFmt>::two(v[8 * h + 2], v[8 * h + 3]);
-                w.z = Pack<kFmt>::two(v[8 * h + 4], v[8 * h + 5]);
-                w.w = Pack<kFmt>::two(v[8 * h + 6], v[8 * h + 7]);
-                ws.x = Pack<kFmt>::two(sgn * v[8 * h + 0], sgn * v[8 * h + 1]);
-                ws.y = Pack<kFmt>::two(sgn * v[8 * h + 2], sgn * v[8 * h + 3]);
-                ws.z = Pack<kFmt>::two(sgn * v[8 * h + 4], sgn * v[8 * h + 5]);
-                ws.w = Pack<kFmt>::two(sgn * v[8 * h + 6], sgn * v[8 * h + 7]);
-                const size_t row = (size_t)(m / 8) * 128 + (m % 8) * 16;
-                *reinterpret_cast<uint4*>(s_bc + (n / 8) * 2048 + row) = w;
-                *reinterpret_cast<uint4*>(s_bs + (ns / 8) * 2048 + row) = ws;
+                for (int u = 0; u < N; ++u) blk[(u * XH + x) * YH + y] = ok ? v[u] * out_scale : 0.f;
             }
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------------
-        if (tid == 0 && !*s_fail) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + 1536 * s, G::SBO_K2, 128),
-                            tc::desc_noswizzle(bc + 256 * s, 128, 2048), idescx, s > 0 ? 1u : 0u);
-                tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + (kXHP / 8) * 128 + 1536 * s, G::SBO_K2, 128),
-                            tc::desc_noswizzle(bs + 256 * s, 128, 2048), idescx, 1u);
-            }
-            tc::mma_commit(tc::smem_u32(&s_mbar[2]));
-        }
-        ok = wait_cta(2, pa);
-        pa ^= 1u;
-        // ---- dG1 (rows x of lane quarter 0) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) ----------
-        if (ok && q == 0) {
-            float v[16];
-            tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * grp), v);
-            const int x = lane, k = grp >> 1;
-            if (x < kXHP) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int y8 = 16 * (grp & 1) + 8 * h;
-                    if (y8 < YP) {
-                        // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
-                        uint4 w;
-                        w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
-                        w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
-                        w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
-                        w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
-                        *reinterpret_cast<uint4*>(s_at + ((x * YP + y8) / 8) * 256 + k * 16) = w;
-                    }
-                }
-            }
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ------------
-        if (tid == 0 && !*s_fail) {
-            tc::fence_after_sync();
-            const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
-#pragma unroll
-            for (int i = 0; i < G::NB1; ++i)
-                tc::mma_f16(tmem + kColT + 16 * i, tc::desc_noswizzle(at + 4096 * i, 128, 256), btd, idesct,
-                            kt > 0 ? 1u : 0u);
-        }
-        if (kt + 1 < H) {
-            // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
-            ok = wait_cta(0, ph0);
-            ph0 ^= 1u;
-            if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
-            tc::fence_before_sync();
-            __syncthreads();
-        }
-    }
-
-    // ---- the brick's block of gVext (tensor memory) to scratch [u_t][x][y] ----------------------------------
-    if (tid == 0 && !*s_fail) tc::mma_commit(tc::smem_u32(&s_mbar[2]));
-    ok = wait_cta(2, pa);
-    const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    float* blk = blocks + cta * G::BLOCK_FLOATS;
-    const float out_scale = 1.f / (sigma * kDxScale);
-    for (int i = grp; i < G::NB1; i += 4) {
-        float v[16];
-        if (ok) tc::tmem_ld16(tmem + lane_base + kColT + (uint32_t)(16 * i), v);
-        const int pos = 128 * i + m, x = pos / YP, y = pos % YP;
-        if (x < XH && y < YH) {
-#pragma unroll
-            for (int u = 0; u < N; ++u) blk[(u * XH + x) * YH + y] = ok ? v[u] * out_scale : 0.f;
         }
     }
     tc::fence_before_sync();
