@@ -46,8 +46,9 @@ WORKLOADS = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
-K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840}   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
-K5_TRAFFIC = {}
+K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840,   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
+              ("salt128", 16, "bf16"): 8556800}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
+K5_TRAFFIC = {("salt128", 16, "bf16"): 722650000}  # K5 alone: 35.5 MB read + 687.1 MB written (brick blocks)
 
 
 def measured_peaks():
@@ -69,7 +70,7 @@ def bins_per_voxel(n: int) -> int:
     return (n // 2 + 1) * n * n
 
 
-def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic):
+def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt"):
     """Roofline of a spectral kernel.  FP32 form: its contraction flops (the per-voxel figure
     4hn + 8hn^2 + 8hn^3, x2 for the adjoint) on the FP32 FMA pipe.  BF16/FP16 form: the
     contraction runs on the tensor cores (reported as `tensor`), and the binding pipe is the
@@ -81,8 +82,9 @@ def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic):
                 "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
     bins = bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     tpk = measured_peaks().get("bf16_tflops", 1900.0)
-    return {"kernel": kernel, "bound": "alu", "pipe": "MUFU (abs(F) epilogue: one sqrt per bin)", "achieved": bins,
-            "peak": MUFU_PEAK_TOPS, "unit": "Tsqrt/s", "frac": bins / MUFU_PEAK_TOPS, "traffic": traffic,
+    what = "abs(F) epilogue: one sqrt per bin" if mufu_op == "sqrt" else "Gamma epilogue: one rsqrt per bin"
+    return {"kernel": kernel, "bound": "alu", "pipe": f"MUFU ({what})", "achieved": bins,
+            "peak": MUFU_PEAK_TOPS, "unit": f"T{mufu_op}/s", "frac": bins / MUFU_PEAK_TOPS, "traffic": traffic,
             "peak_note": "MUFU 16/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
             "tensor": {"achieved_tflops": flops, "peak_tflops": tpk, "frac": flops / tpk,
                        "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}}
@@ -392,8 +394,9 @@ def main():
     k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1, K1_TRAFFIC.get((args.workload, n, args.prec)))
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
-        rl = roofline(f"k5_spectra_adjoint_{tag} (+ k5_gather_add)", args.prec, n, nvox, k5_ms, 2,
-                      K5_TRAFFIC.get((args.workload, n, args.prec)))
+        # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
+        rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and k5_gather_add)", args.prec, n, nvox, k5_ms,
+                      2, K5_TRAFFIC.get((args.workload, n, args.prec)), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt")
         rl["k1"] = k1_rl
     else:
         rl = k1_rl
