@@ -246,12 +246,19 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 tc::fence_after_sync();
                 return ok;
             };
+            // base descriptors; windows, slots and K steps are the same descriptors moved (desc_add)
+            const uint64_t a2d = tc::desc_noswizzle(tab, 128, G::SBO_K2);
+            const uint64_t b2d = tc::desc_noswizzle(b2base, 128, G::SBO_K2);
+            const uint64_t ared = tc::desc_noswizzle(are, 128, G::SBO_A3);
+            const uint64_t aimd = tc::desc_noswizzle(aim, 128, G::SBO_A3);
+            const uint64_t gd = tc::desc_noswizzle(gbase, 128, G::SBO_G);
+            const uint64_t tred = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE, G::TI_LBO, 128);
+            const uint64_t timd = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM, G::TI_LBO, 128);
             auto issue_s2 = [&](int kt) {
-                const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
+                const uint64_t b2 = tc::desc_add(b2d, (uint32_t)(kt * G::B2_B));
 #pragma unroll
                 for (int s = 0; s < kK2 / 16; ++s)
-                    tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
-                                tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
+                    tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2, s > 0 ? 1u : 0u);
                 commit(0);
             };
             auto issue_s3 = [&](int pass) {
@@ -259,16 +266,14 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
                 for (int j = 0; j < G::OPP; ++j) {
                     const uint32_t y0 = pass * G::OPP + j;
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a,
-                                idesc3, 0);
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b,
-                                idesc3, 1);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
                 }
                 commit(pass & 1);
             };
             // adjoint of stage 3 for the outputs of one pass (Gamma set pass % 2), accumulating into kColY
             auto issue_inv_y = [&](int pass) {
-                const uint32_t set = gbase + (uint32_t)((pass & 1) * G::GSET_B);
+                const uint32_t set = (uint32_t)((pass & 1) * G::GSET_B);
 #pragma unroll
                 for (int j = 0; j < G::OPP; ++j) {
                     const uint32_t y0 = pass * G::OPP + j;
@@ -276,16 +281,10 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                     const uint32_t shift = (15u - y0) * 16u;
 #pragma unroll
                     for (int s = 0; s < G::KG / 16; ++s) {
-                        const uint64_t a = tc::desc_noswizzle(slot + 256 * s, 128, G::SBO_G);
+                        const uint64_t a = tc::desc_add(gd, slot + 256 * s);
                         const uint32_t accum = (y0 > 0 || s > 0) ? 1u : 0u;
-                        tc::mma_f16(tmem + kColY, a,
-                                    tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE + shift + 2 * G::TI_LBO * s,
-                                                       G::TI_LBO, 128),
-                                    idescy, accum);
-                        tc::mma_f16(tmem + kColY + 32, a,
-                                    tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM + shift + 2 * G::TI_LBO * s,
-                                                       G::TI_LBO, 128),
-                                    idescy, accum);
+                        tc::mma_f16(tmem + kColY, a, tc::desc_add(tred, shift + 2 * G::TI_LBO * s), idescy, accum);
+                        tc::mma_f16(tmem + kColY + 32, a, tc::desc_add(timd, shift + 2 * G::TI_LBO * s), idescy, accum);
                     }
                 }
             };
@@ -329,21 +328,23 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 }
                 // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------
                 if (!(alive = pwait(9))) break;
+                const uint64_t a2t = tc::desc_noswizzle(tab, G::SBO_K2, 128);   // A2 read MN-major: A2^T
+                const uint64_t bcd = tc::desc_noswizzle(bc, 128, 2048), bsd = tc::desc_noswizzle(bs, 128, 2048);
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + 1536 * s, G::SBO_K2, 128),
-                                tc::desc_noswizzle(bc + 256 * s, 128, 2048), idescx, s > 0 ? 1u : 0u);
-                    tc::mma_f16(tmem + kColX, tc::desc_noswizzle(tab + (kXHP / 8) * 128 + 1536 * s, G::SBO_K2, 128),
-                                tc::desc_noswizzle(bs + 256 * s, 128, 2048), idescx, 1u);
+                    tc::mma_f16(tmem + kColX, tc::desc_add(a2t, 1536 * s), tc::desc_add(bcd, 256 * s), idescx,
+                                s > 0 ? 1u : 0u);
+                    tc::mma_f16(tmem + kColX, tc::desc_add(a2t, (kXHP / 8) * 128 + 1536 * s), tc::desc_add(bsd, 256 * s),
+                                idescx, 1u);
                 }
                 commit(10);
                 // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
                 if (!(alive = pwait(11))) break;
                 const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
+                const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
 #pragma unroll
                 for (int i = 0; i < G::NB1; ++i)
-                    tc::mma_f16(tmem + kColT + 16 * i, tc::desc_noswizzle(at + 4096 * i, 128, 256), btd, idesct,
-                                kt > 0 ? 1u : 0u);
+                    tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, kt > 0 ? 1u : 0u);
             }
             if (alive) commit(13);
         }

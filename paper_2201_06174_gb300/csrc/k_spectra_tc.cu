@@ -119,12 +119,16 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
                 tc::fence_after_sync();
                 return ok;
             };
+            // base descriptors; windows and K steps are the same descriptors moved (desc_add)
+            const uint64_t a2d = tc::desc_noswizzle(tab, 128, G::SBO_K2);
+            const uint64_t b2d = tc::desc_noswizzle(b2base, 128, G::SBO_K2);
+            const uint64_t ared = tc::desc_noswizzle(are, 128, G::SBO_A3);
+            const uint64_t aimd = tc::desc_noswizzle(aim, 128, G::SBO_A3);
             auto issue_s2 = [&](int kt) {
-                const uint32_t b2 = b2base + (uint32_t)(kt * G::B2_B);
+                const uint64_t b2 = tc::desc_add(b2d, (uint32_t)(kt * G::B2_B));
 #pragma unroll
                 for (int s = 0; s < kK2 / 16; ++s)
-                    tc::mma_f16(tmem, tc::desc_noswizzle(tab + 256 * s, 128, G::SBO_K2),
-                                tc::desc_noswizzle(b2 + 256 * s, 128, G::SBO_K2), idesc2, s > 0 ? 1u : 0u);
+                    tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2, s > 0 ? 1u : 0u);
                 tc::mma_commit(tc::smem_u32(&s_mbar[0]));
             };
             auto issue_s3 = [&](int pass) {
@@ -132,10 +136,8 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
 #pragma unroll
                 for (int j = 0; j < G::OPP; ++j) {
                     const uint32_t y0 = pass * G::OPP + j;
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(are + y0 * 16, 128, G::SBO_A3), b3a,
-                                idesc3, 0);
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_noswizzle(aim + y0 * 16, 128, G::SBO_A3), b3b,
-                                idesc3, 1);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
+                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
                 }
                 tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
             };

@@ -24,6 +24,10 @@ __device__ __forceinline__ uint64_t desc_noswizzle(uint32_t saddr, uint32_t lbo,
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// A descriptor moved by `bytes` (a multiple of 16): the start address is the low 14-bit field in
+// 16-byte units, and shared-memory addresses below 256 KB never carry out of it.
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t bytes) { return desc + (bytes >> 4); }
+
 // Instruction descriptor of kind::f16 with FP32 accumulation.
 // fmt: 0 = F16, 1 = BF16 (both operands); a_mn / b_mn: operand is MN-major.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
