@@ -8,11 +8,14 @@
 //     L = sum gE . E with respect to (Re F, Im F) -- with the zero subgradient where |F| <= 2^-19 of the
 //     window's L1 norm; rounded to FP16 (scaled by sigma = n^3 / (8 max|gE|)) into the operand
 //     [(x0, k_x)][(re | im, k_y)] of one output;
-//   adjoint of stage 3 (y): dG2[(x0,k_x)][(re|im, y)] = sum_y0 Gamma_y0 Tinv(y - y0), one MMA pair per
-//     output into one accumulator -- the overlap-add over the sliding windows happens in the
-//     accumulator.  Tinv is one table of rows y - y0 + 15 (K-major with 16-byte rows), so the window
-//     of output y0 is the same descriptor moved by 16 (15 - y0) bytes:
-//       Tinv_re[(re|im, k_y)][y] = [c | -s](k_y, y - y0),  Tinv_im = [s | c](k_y, y - y0);
+//   adjoint of stage 3 (y): Gamma of bins k and n - k folded into pair coefficients (A = G[k] + G[n-k],
+//     B = G[k] - G[n-k]; the twiddles of n - k are those of k with the sine negated):
+//       dG2r[y] = sum_y0 [A_r | B_i] Tinv_re(y - y0),  Tinv_re = [c_k | -s_k],
+//       dG2i[y] = sum_y0 [A_i | B_r] Tinv_im(y - y0),  Tinv_im = [c_k |  s_k],
+//     one MMA (K = 16) per part and output, all outputs accumulating into one accumulator -- the
+//     overlap-add over the sliding windows happens in the accumulator.  Tinv is one table of rows
+//     y - y0 + 15 (K-major with 16-byte rows), so the window of output y0 is the same descriptor moved
+//     by 16 (15 - y0) bytes;
 //   adjoint of stage 2 (x): the stage-2 twiddle matrix A2 [(x0,k_x)][(cos|sin, x)] read as an MN-major
 //     operand is its transpose; with B_c = [dG2r | dG2i] and B_s = [-dG2i | dG2r] (dG2 rounded to FP16),
 //     D[x][(re|im, y)] = A2_cos^T B_c + A2_sin^T B_s is dG1 = (sum c dG2r - s dG2i, sum c dG2i + s dG2r)
@@ -57,8 +60,10 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr uint32_t SBO_G = KG / 8 * 128;           // 8-row group stride of a Gamma operand
     static constexpr size_t SLOT_B = (size_t)16 * SBO_G;      // one output (128 rows)
     static constexpr size_t GSET_B = (size_t)F::OPP * SLOT_B; // one pass
+    static constexpr int PK = 2 * F::H - 2;                   // pair coefficients per part (n)
     static constexpr uint32_t TI_LBO = kTR * 16;              // K-group stride of a shifted table
-    static constexpr size_t TI_B = (size_t)KG / 8 * TI_LBO;
+    static constexpr size_t TI_B = (size_t)2 * TI_LBO;        // K = 16 per table
+    static constexpr uint32_t IM_OFF = PK == 16 ? 256u : 0u;  // K offset of the imaginary-part operand
     static constexpr size_t TAB_TRE = F::TAB_B;
     static constexpr size_t TAB_TIM = TAB_TRE + TI_B;
     static constexpr size_t TAB_BT = TAB_TIM + TI_B;          // B_t per k_t: [u][(re, im, 0...)], 512 B each
@@ -80,22 +85,32 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// The adjoint's constant operands: the forward tables, then the shifted inverse-y twiddles
-// byte(row, k) = row 16 + (k/8) TI_LBO + (k%8) 2, d = row - 15:
-//   re table: k < n: c(k, d); k >= n: -s(k - n, d).   im table: k < n: s(k, d); k >= n: c(k - n, d).
+// The adjoint's constant operands: the forward tables, then the shifted inverse-y twiddles of the pair
+// coefficients, byte(row, K) = row 16 + (K/8) TI_LBO + (K%8) 2, d = row - 15, K = 16 per table:
+//   re table: kk < H: c(kk, d); H <= kk < 2H-2: -s(kk-H+1, d)   (multiplies [A_r | B_i])
+//   im table: kk < H: c(kk, d); H <= kk < 2H-2:  s(kk-H+1, d)   (multiplies [A_i | B_r])
+// with kk = K for n = 16; for n = 8 the operand holds both parts in one K = 16 row ([re | im], 8 each), so
+// the re table is zero in K 8..15 and the im table holds its entries at K = 8 + kk (zero below).
 template <int N>
 __global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out) {
     using G = BtGeo<N>;
+    constexpr int H = G::H;
     tcs::build_fwd_tables<N, kFmt>(tw, out, threadIdx.x, blockDim.x);
     unsigned char* tre = out + G::TAB_TRE;
     unsigned char* tim = out + G::TAB_TIM;
-    for (int i = threadIdx.x; i < kTR * G::KG; i += blockDim.x) {
-        const int row = i / G::KG, k = i % G::KG, d = row - 15;
-        const int ky = k % N;
-        const float c = tcs::twc<N>(tw, ky, d), s = tcs::tws<N>(tw, ky, d);
-        const size_t off = (size_t)row * 16 + (k / 8) * G::TI_LBO + (k % 8) * 2;
-        *reinterpret_cast<uint16_t*>(tre + off) = Pack<kFmt>::one(k < N ? c : -s);
-        *reinterpret_cast<uint16_t*>(tim + off) = Pack<kFmt>::one(k < N ? s : c);
+    for (int i = threadIdx.x; i < kTR * 16; i += blockDim.x) {
+        const int row = i / 16, K = i % 16, d = row - 15;
+        auto coef = [&](int kk, bool im_part) -> float {
+            if (kk < 0 || kk >= 2 * H - 2) return 0.f;
+            if (kk < H) return tcs::twc<N>(tw, kk, d);
+            const float sv = tcs::tws<N>(tw, kk - H + 1, d);
+            return im_part ? sv : -sv;
+        };
+        const float vre = G::PK == 16 ? coef(K, false) : (K < 8 ? coef(K, false) : 0.f);
+        const float vim = G::PK == 16 ? coef(K, true) : (K >= 8 ? coef(K - 8, true) : 0.f);
+        const size_t off = (size_t)row * 16 + (K / 8) * G::TI_LBO + (K % 8) * 2;
+        *reinterpret_cast<uint16_t*>(tre + off) = Pack<kFmt>::one(vre);
+        *reinterpret_cast<uint16_t*>(tim + off) = Pack<kFmt>::one(vim);
     }
     // B_t(k_t)[u][k] (K-major, N = u): k = 0: c(k_t, u), k = 1: -s(k_t, u), other K rows zero
     unsigned char* bt = out + G::TAB_BT;
@@ -279,13 +294,10 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                     const uint32_t y0 = pass * G::OPP + j;
                     const uint32_t slot = set + (uint32_t)(j * G::SLOT_B);
                     const uint32_t shift = (15u - y0) * 16u;
-#pragma unroll
-                    for (int s = 0; s < G::KG / 16; ++s) {
-                        const uint64_t a = tc::desc_add(gd, slot + 256 * s);
-                        const uint32_t accum = (y0 > 0 || s > 0) ? 1u : 0u;
-                        tc::mma_f16(tmem + kColY, a, tc::desc_add(tred, shift + 2 * G::TI_LBO * s), idescy, accum);
-                        tc::mma_f16(tmem + kColY + 32, a, tc::desc_add(timd, shift + 2 * G::TI_LBO * s), idescy, accum);
-                    }
+                    const uint32_t accum = y0 > 0 ? 1u : 0u;
+                    tc::mma_f16(tmem + kColY, tc::desc_add(gd, slot), tc::desc_add(tred, shift), idescy, accum);
+                    tc::mma_f16(tmem + kColY + 32, tc::desc_add(gd, slot + G::IM_OFF), tc::desc_add(timd, shift),
+                                idescy, accum);
                 }
             };
             bool alive = pwait(12);
@@ -414,21 +426,34 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                             gr[ky] = sc * re;
                             gim[ky] = sc * im;
                         }
+                        // pair coefficients of bins k and n - k (same twiddles up to the sign of the sine):
+                        // re part [A_r | B_i], im part [A_i | B_r], A = G[k] + G[n-k], B = G[k] - G[n-k]
+                        float pr[G::PK], pi[G::PK];
+#pragma unroll
+                        for (int k = 0; k < H; ++k) {
+                            const bool self = k == 0 || 2 * k == N;
+                            pr[k] = self ? gr[k] : gr[k] + gr[N - k];
+                            pi[k] = self ? gim[k] : gim[k] + gim[N - k];
+                            if (!self) {
+                                pr[H - 1 + k] = gim[k] - gim[N - k];
+                                pi[H - 1 + k] = gr[k] - gr[N - k];
+                            }
+                        }
                         // K-major operand: byte(m, k) = (m/8) SBO_G + (k/8) 128 + (m%8) 16 + (k%8) 2, k = [re | im]
                         unsigned char* dst = s_g + b * G::GSET_B + j * G::SLOT_B + (m / 8) * G::SBO_G + (m % 8) * 16;
 #pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {
+                        for (int c = 0; c < G::PK / 8; ++c) {
                             uint4 wr, wi;
-                            wr.x = Pack<kFmt>::two(gr[8 * c + 0], gr[8 * c + 1]);
-                            wr.y = Pack<kFmt>::two(gr[8 * c + 2], gr[8 * c + 3]);
-                            wr.z = Pack<kFmt>::two(gr[8 * c + 4], gr[8 * c + 5]);
-                            wr.w = Pack<kFmt>::two(gr[8 * c + 6], gr[8 * c + 7]);
-                            wi.x = Pack<kFmt>::two(gim[8 * c + 0], gim[8 * c + 1]);
-                            wi.y = Pack<kFmt>::two(gim[8 * c + 2], gim[8 * c + 3]);
-                            wi.z = Pack<kFmt>::two(gim[8 * c + 4], gim[8 * c + 5]);
-                            wi.w = Pack<kFmt>::two(gim[8 * c + 6], gim[8 * c + 7]);
+                            wr.x = Pack<kFmt>::two(pr[8 * c + 0], pr[8 * c + 1]);
+                            wr.y = Pack<kFmt>::two(pr[8 * c + 2], pr[8 * c + 3]);
+                            wr.z = Pack<kFmt>::two(pr[8 * c + 4], pr[8 * c + 5]);
+                            wr.w = Pack<kFmt>::two(pr[8 * c + 6], pr[8 * c + 7]);
+                            wi.x = Pack<kFmt>::two(pi[8 * c + 0], pi[8 * c + 1]);
+                            wi.y = Pack<kFmt>::two(pi[8 * c + 2], pi[8 * c + 3]);
+                            wi.z = Pack<kFmt>::two(pi[8 * c + 4], pi[8 * c + 5]);
+                            wi.w = Pack<kFmt>::two(pi[8 * c + 6], pi[8 * c + 7]);
                             *reinterpret_cast<uint4*>(dst + c * 128) = wr;
-                            *reinterpret_cast<uint4*>(dst + (N / 8 + c) * 128) = wi;
+                            *reinterpret_cast<uint4*>(dst + (G::PK / 8 + c) * 128) = wi;
                         }
                     }
                 }
