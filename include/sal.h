@@ -146,6 +146,31 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
 sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
                                double ls_delta, float* W_out, float* S, void* stream);
 
+/* The paper's adaptive weight update for step 5 (Eq. 4 and the adaptive scheme with LMS, NLMS and
+ * RLS, run as the sequential filters the paper describes; NLMS is its choice for all results).
+ * x_p = (S^_t, S^_x, S^_y)(p) are the min-max normalised maps of S3 (a flat map gives 0), d_p = D[p];
+ * the voxels are visited inline sections (y) outermost, then x, then t; e = d - W.x and
+ *   LMS:  W += mu e x                      (W0 = (1/3, 1/3, 1/3))
+ *   NLMS: W += mu e x / (eps + |x|^2)      (W0 = (1/3, 1/3, 1/3))
+ *   RLS:  k = P x / (lambda + x'P x); W += k e; P = (P - k x'P) / lambda   (W0 = 0, P0 = I / delta)
+ * in FP64.  sections = 0: one recursion over the whole volume; sections = N > 0: the weights are
+ * re-adapted for every block of N inline sections (each block its own recursion from W0), as the
+ * paper allows.  The recursion is sequential by nature: one warp per block.
+ * S3: [3][T][X][Y] raw maps; D: [T][X][Y]; W_out: device [ceil(Y / N)][3] (one row when
+ * sections = 0); err2 (nullable): device [T*X*Y], the squared error e^2 of every step in filter
+ * order.  The weights of a block can be passed to sal_combine as W_in. */
+typedef enum { SAL_ADAPT_LMS = 0, SAL_ADAPT_NLMS = 1, SAL_ADAPT_RLS = 2 } sal_adapt_method;
+typedef struct {
+    sal_adapt_method method;
+    double mu;       /* LMS / NLMS step size (0.5) */
+    double eps;      /* NLMS regulariser (1e-8) */
+    double lambda;   /* RLS forgetting factor (1) */
+    double delta;    /* RLS P0 = I / delta (1e-6) */
+    int sections;    /* inline sections per block; 0 = whole volume */
+} sal_adapt_params;
+sal_status sal_adapt_weights(sal_handle* h, const float* S3, const float* D, const sal_adapt_params* p,
+                             float* W_out, float* err2, void* stream);
+
 /* Stepwise backward calls (adjoints of the three forward steps; the fused call above is
  * their composition).  The paper has no backward pass: these follow from Eq. 1-4.
  *

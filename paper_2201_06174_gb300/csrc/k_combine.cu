@@ -215,6 +215,14 @@ int red_blocks(long long NV) {
     return (int)(b < kRedBlocks ? b : kRedBlocks);
 }
 
+cudaError_t minmax_bounds_launch(const float* S3, long long N, const Reduce& r, cudaStream_t s) {
+    const int nb = red_blocks(N);
+    k3_minmax3<<<nb, kThreads, 0, s>>>(S3, N, r.mm_part);
+    k3_minmax_finalize<<<1, kThreads, 0, s>>>(r.mm_part, nb, 3, r.norm + N_LO, r.norm + N_INV);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t combine_launch(const float* S3, const float* D, const float* W_in, float* W_out, float* S,
                            long long N, double delta, bool s3_partials_ready, const Reduce& r, cudaStream_t s) {
     const int nb = red_blocks(N);

@@ -461,6 +461,26 @@ sal_status sal_center_surround_backward(sal_handle* h, const float* E, const flo
     return SAL_OK;
 }
 
+sal_status sal_adapt_weights(sal_handle* h, const float* S3, const float* D, const sal_adapt_params* p,
+                             float* W_out, float* err2, void* stream) {
+    sal_status s = check_handle(h);
+    if (s != SAL_OK) return s;
+    if (!S3 || !D || !p || !W_out) return fail(h, SAL_ERR_INVALID_ARG, "S3, D, params and W_out must not be NULL");
+    if (p->method != SAL_ADAPT_LMS && p->method != SAL_ADAPT_NLMS && p->method != SAL_ADAPT_RLS)
+        return fail(h, SAL_ERR_INVALID_ARG, "unknown adaptive method");
+    if (p->sections < 0) return fail(h, SAL_ERR_INVALID_ARG, "sections must be >= 0");
+    if (!std::isfinite(p->mu) || !std::isfinite(p->eps) || !(p->eps >= 0.0) || !std::isfinite(p->lambda) ||
+        !(p->lambda > 0.0) || !std::isfinite(p->delta) || !(p->delta > 0.0))
+        return fail(h, SAL_ERR_INVALID_ARG, "mu, eps >= 0, lambda > 0 and delta > 0 must be finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = sal::minmax_bounds_launch(S3, h->N, h->red, st)) != cudaSuccess) return cuda_fail(h, e, "adapt: bounds");
+    if ((e = sal::adapt_launch(S3, D, h->T, h->X, h->Y, (int)p->method, p->mu, p->eps, p->lambda, p->delta,
+                               p->sections, h->red.norm, W_out, err2, st)) != cudaSuccess)
+        return cuda_fail(h, e, "adapt");
+    return SAL_OK;
+}
+
 sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, const float* gS, float* gS3,
                                 float* gW, void* stream) {
     sal_status s = check_handle(h);

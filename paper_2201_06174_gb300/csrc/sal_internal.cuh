@@ -83,6 +83,15 @@ cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, void
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
                               int bnd, int* err, cudaStream_t s);
 
+// ---- K3a: sequential adaptive weights (LMS / NLMS / RLS) over inline-section blocks -------------
+// Per-map bounds of S3 into r.norm (lo at 0..2, 1/(hi-lo) at 3..5; 0 for a flat map).
+cudaError_t minmax_bounds_launch(const float* S3, long long N, const Reduce& r, cudaStream_t s);
+// Normalised maps from S3 and r.norm; one chain per block of `sections` inline sections (0: one chain);
+// W_out [blocks][3]; err2 (nullable) the squared error of every step in filter order.
+cudaError_t adapt_launch(const float* S3, const float* D, int T, int X, int Y, int method, double mu, double eps,
+                         double lambda, double delta, int sections, const float* norm, float* W_out, float* err2,
+                         cudaStream_t s);
+
 // ---- K2: directional center-surround ----------------------------------------------------------
 cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, const Stencil& st,
                        float* mm_part, cudaStream_t s);

@@ -33,7 +33,7 @@ TAPER = {"rect": 0, "hann": 1}
 ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
                 "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
                 "sal_combine_noalloc", "sal_local_spectra_project_backward", "sal_center_surround_backward",
-                "sal_combine_backward", "sal_launch_count")
+                "sal_combine_backward", "sal_launch_count", "sal_adapt_weights")
 
 
 class SalError(RuntimeError):
@@ -50,6 +50,13 @@ class sal_params(ctypes.Structure):
                 ("alpha", ctypes.POINTER(ctypes.c_float)), ("prec", ctypes.c_int),
                 ("ls_delta", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_size_t)]
 
+
+class sal_adapt_params(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("mu", ctypes.c_double), ("eps", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("sections", ctypes.c_int)]
+
+
+ADAPT_METHODS = {"lms": 0, "nlms": 1, "rls": 2}
 
 _lib = None
 
@@ -80,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_center_surround_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.sal_combine_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.sal_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+    L.sal_adapt_weights.argtypes = [vp, vp, vp, ctypes.POINTER(sal_adapt_params), vp, vp, vp]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -210,6 +218,15 @@ def sal_combine_noalloc(S3, D, W_in, W_out, S, ls_delta: float = 1e-6, stream=No
     T, X, Y = (int(v) for v in S3.shape[1:])
     _check(load().sal_combine_noalloc(T, X, Y, _ptr(S3), _ptr(D), _ptr(W_in), float(ls_delta), _ptr(W_out), _ptr(S),
                                       _stream(stream)), None)
+
+
+def sal_adapt_weights(h, S3, D, W_out, method: str = "nlms", sections: int = 0, mu: float = 0.5, eps: float = 1e-8,
+                      lam: float = 1.0, delta: float = 1e-6, err2=None, stream=None):
+    """The paper's sequential LMS / NLMS / RLS weight update on the GPU (one recursion per block of
+    `sections` inline sections; 0 = whole volume).  W_out: device [blocks][3]."""
+    p = sal_adapt_params(ADAPT_METHODS[method], float(mu), float(eps), float(lam), float(delta), int(sections))
+    _check(load().sal_adapt_weights(h, _ptr(S3), _ptr(D), ctypes.byref(p), _ptr(W_out), _ptr(err2), _stream(stream)),
+           h)
 
 
 def sal_launch_count() -> int:

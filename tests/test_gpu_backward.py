@@ -176,6 +176,44 @@ def test_finite_differences_of_gpu_forward(sal):
     assert rel_l2(an, fd) <= 2e-2, rel_l2(an, fd)
 
 
+@pytest.mark.parametrize("n", [8, 16])
+def test_finite_differences_differentiation_workload_128(sal, n):
+    """The differentiation-form workload at full size: the 128^3 single-fault volume, the L2 loss to
+    its fault mask (gS = S - D), central differences (eps = 1e-3) of the FP32 GPU forward at 64 seeded
+    entries with the forward's min-max bounds held fixed, against sal_saliency_backward."""
+    V, D = synth.volume("fault128")
+    W = torch.tensor([0.5, 0.3, 0.2], device="cuda")
+    eng = sal.Saliency(V.shape, sal.Params(n=n))
+    try:
+        Vt = _cuda(V)
+        S3 = eng.center_surround(eng.local_spectra_project(Vt)).double()
+        lo = S3.amin(dim=(1, 2, 3), keepdim=True)
+        hi = S3.amax(dim=(1, 2, 3), keepdim=True)
+        C = (W.double()[:, None, None, None] * (S3 - lo) / (hi - lo)).sum(0)
+        loC, hiC = C.min(), C.max()
+        gS = _cuda(((C - loC) / (hiC - loC)).cpu().numpy() - D)
+
+        def L(Vx):
+            S3x = eng.center_surround(eng.local_spectra_project(Vx)).double()
+            Cx = (W.double()[:, None, None, None] * (S3x - lo) / (hi - lo)).sum(0)
+            return float(((Cx - loC) / (hiC - loC) * gS.double()).sum())
+
+        gV, _, _ = eng.backward(Vt, W, gS)
+        idx = synth.sample_points(V.shape, 64, seed=1234)
+        eps = 1e-3
+        fd = []
+        for p in idx:
+            Vp = Vt.clone(); Vp[tuple(p)] += eps
+            Vm = Vt.clone(); Vm[tuple(p)] -= eps
+            fd.append((L(Vp) - L(Vm)) / (2 * eps))
+        an = gV.cpu().numpy()[idx[:, 0], idx[:, 1], idx[:, 2]]
+    finally:
+        eng.close()
+    fd = np.array(fd)
+    print("n", n, "FD vs analytic rel-L2", f"{rel_l2(an, fd):.2e}")
+    assert rel_l2(an, fd) <= 2e-2, rel_l2(an, fd)
+
+
 def test_autograd_matches_abi_and_descends(sal):
     """The autograd Function returns exactly the C-ABI backward, and a small step of V along
     the negative gradient lowers the L2 distance of S to a fault mask."""

@@ -80,6 +80,31 @@ def test_tensor_core_salt128_n16_sampled(sal, prec):
     assert np.abs(g["S"] - g32["S"]).max() <= 2e-2
 
 
+@pytest.mark.parametrize("n,precs", [(8, ("bf16", "fp16")), (16, ("bf16", "fp16")), (32, ("bf16",))])
+def test_precision_workload_256x384x192_sampled(sal, n, precs):
+    """The precision-form workload at full size (6 faults, 2 salt bodies, SNR 5 dB): raw E_m and S_m of
+    the tensor-core forms at seeded voxels against the FP64 oracle, and the normalised map against the
+    FP32 GPU form (the global min-max couples every voxel, so S is compared whole to FP32)."""
+    V, _ = synth.volume("precision256x384x192")
+    p = sal.Params(n=n)
+    st = oracle.dcs_stencil(p.directions, p.R, p.sigma)
+    pts = synth.sample_points(V.shape, 24 if n < 32 else 8, seed=7)
+    Ec, Sc = oracle.center_surround_at(V, pts, n, st[0], st[3])
+    g32 = _run(sal, V, sal.Params(n=n, prec="fp32"))
+    for prec in precs:
+        g = _run(sal, V, sal.Params(n=n, prec=prec))
+        errs = [rel_l2(g["E"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Ec[:, m]) for m in range(3)]
+        errs += [rel_l2(g["S3"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Sc[:, m]) for m in range(3)]
+        print(prec, n, "E/S_m sampled rel-L2", [f"{e:.2e}" for e in errs], "S vs FP32",
+              f"{rel_l2(g['S'], g32['S']):.2e}", f"max-abs {np.abs(g['S'] - g32['S']).max():.2e}")
+        assert max(errs) <= 1e-2
+        assert rel_l2(g["S"], g32["S"]) <= 1e-2
+        assert np.abs(g["S"] - g32["S"]).max() <= 2e-2
+    # the FP32 form itself at the same voxels
+    errs32 = [rel_l2(g32["E"][m][pts[:, 0], pts[:, 1], pts[:, 2]], Ec[:, m]) for m in range(3)]
+    assert max(errs32) <= 1e-5, errs32
+
+
 # ---- backward on the tensor cores ------------------------------------------------------------------
 
 def _cuda(a):
