@@ -47,8 +47,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
 K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840,   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
-              ("salt128", 16, "bf16"): 8556800}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
-K5_TRAFFIC = {("salt128", 16, "bf16"): 722650000}  # K5 alone: 35.5 MB read + 687.1 MB written (brick blocks)
+              ("salt128", 16, "bf16"): 8625289}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
+K5_TRAFFIC = {("salt128", 16, "bf16"): 718849638}  # K5 alone: 34.8 MB read + 684.1 MB written (brick blocks)
 
 
 def measured_peaks():
