@@ -268,17 +268,21 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
 
 // Overlap-add of the spectral adjoint: gV[q] += sum of every brick block element whose extended
 // position maps to q.  Blocks of the bricks with t0 in [t_begin, t_begin + t_count); brick (xs, ys)
-// covers x_ext in [xs*BX - n/2, xs*BX + BX + n/2 - 1), y_ext likewise with BY.
+// covers x_ext in [xs*BX - n/2, xs*BX + BX + n/2 - 1), y_ext likewise with BY.  Voxels with t in
+// [t_lo, t_hi) are visited (every voxel the slab reaches); the sum runs in a fixed order.
 __global__ void __launch_bounds__(kThreads)
 k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, int X, int Y, int bnd, int n,
-              int BX, int XH, int BY, int YH, int t_begin, int t_count) {
-    const long long NV = (long long)T * X * Y;
+              int BX, int XH, int BY, int YH, int t_begin, int t_count, int t_lo, int t_hi) {
+    const long long q0 = (long long)t_lo * X * Y, q1 = (long long)t_hi * X * Y;
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
     const int nxs = (X + BX - 1) / BX;
     const int t_end = t_begin + t_count;
     const long long bsz = (long long)n * XH * YH;
-    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < NV; q += (long long)gridDim.x * kThreads) {
+    // one step of t0 moves to the next row of bricks and one u_t back
+    const long long tstep = (long long)nxs * nseg * bsz - (long long)XH * YH;
+    for (long long q = q0 + (long long)blockIdx.x * kThreads + threadIdx.x; q < q1;
+         q += (long long)gridDim.x * kThreads) {
         const int y = (int)(q % Y);
         const int x = (int)((q / Y) % X);
         const int t = (int)(q / ((long long)X * Y));
@@ -286,15 +290,20 @@ k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, i
             // interior voxel: its only extended position is itself
             const int t0a = max(t_begin, t - h2 + 1), t0b = min(t_end - 1, t + h2);
             if (t0a > t0b) continue;
+            const int cnt = t0b - t0a + 1;   // <= n <= 16
             const int xa = max(0, ceildiv(x + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(x + h2, BX));
             const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
+            const float* base = blocks + (long long)(t0a - t_begin) * nxs * nseg * bsz +
+                                (long long)(t - t0a + h2) * XH * YH + (y + h2);
             float sum = 0.f;
-            for (int t0 = t0a; t0 <= t0b; ++t0) {
-                const int ut = t - t0 + h2;
-                for (int xs = xa; xs <= xb; ++xs) {
-                    const long long cta_row = ((long long)(t0 - t_begin) * nxs + xs) * nseg;
-                    const long long inner = ((long long)ut * XH + (x - xs * BX + h2)) * YH + y + h2;
-                    for (int sg = sa; sg <= sb; ++sg) sum += __ldg(blocks + (cta_row + sg) * bsz + inner - sg * BY);
+            for (int xs = xa; xs <= xb; ++xs) {
+                for (int sg = sa; sg <= sb; ++sg) {
+                    const float* b = base + (long long)(xs * nseg + sg) * bsz + (x - xs * BX + h2) * YH - sg * BY;
+                    float v[16];   // every t0 of this brick column in flight at once
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = j < cnt ? __ldg(b + j * tstep) : 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum += v[j];
                 }
             }
             gV[q] += sum;
@@ -383,10 +392,20 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
 
 cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
                               SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s) {
-    const long long NV = (long long)T * X * Y;
+    // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_count + n/2 - 1); a slab whose
+    // extension leaves the volume may wrap (periodic) or reflect (symmetric) onto any edge plane
+    const int h2 = n / 2;
+    int t_lo = t_begin - h2, t_hi = t_begin + t_count + h2 - 1;
+    if (t_lo < 0 || t_hi > T) {
+        t_lo = 0;
+        t_hi = T;
+    }
+    const long long NV = (long long)(t_hi - t_lo) * X * Y;
     long long nb = (NV + kThreads - 1) / kThreads;
     if (nb > 152 * 32) nb = 152 * 32;
-    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count);
+    if (nb < 1) nb = 1;
+    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
+                                               t_lo, t_hi);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -72,7 +72,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr int BLOCK_FLOATS = N * F::XH * F::YH;
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + TAB5_B;
-    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets, later B_c | B_s
+    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets; B_c | B_s in set 1
     static constexpr size_t G_B = 2 * GSET_B > 2 * BDG_B ? 2 * GSET_B : 2 * BDG_B;
     static constexpr size_t OFF_AT = OFF_G + G_B;                // t-adjoint A operand [pos][16], MN-major
     static constexpr size_t OFF_GE = OFF_AT + F::A1_B;
@@ -82,6 +82,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static_assert((size_t)(kXHP * F::YP + F::XH * kBY) * 4 <= G_B, "L1 sums fit in the Gamma region");
     static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
     static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
+    static_assert(GSET_B >= 2 * BDG_B, "B_c | B_s fit in Gamma set 1");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -136,8 +137,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     unsigned char* s_are = smem + G::OFF_A3;
     unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;
     unsigned char* s_g = smem + G::OFF_G;                        // Gamma operands, two sets
-    unsigned char* s_bc = smem + G::OFF_G;                       // B_c = [dG2r | dG2i] (after the y adjoint)
-    unsigned char* s_bs = smem + G::OFF_G + G::BDG_B;            // B_s = [-dG2i | dG2r]
+    unsigned char* s_bc = smem + G::OFF_G + G::GSET_B;           // B_c = [dG2r | dG2i] (after the y adjoint)
+    unsigned char* s_bs = s_bc + G::BDG_B;                       // B_s = [-dG2i | dG2r]
     float* s_col = reinterpret_cast<float*>(smem + G::OFF_G);    // L1 column sums (set-up only)
     unsigned char* s_at = smem + G::OFF_AT;                      // t-adjoint A operand
     float* s_ge = reinterpret_cast<float*>(smem + G::OFF_GE);    // [3][P][16]
@@ -145,8 +146,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);
     // mbarriers (arrival counts): [0], [1] forward buffer full (MMA commit); [2], [3] forward buffer read
     // (16 warps); [4] stage-3 A written (16); [5] stage-2 B tiles written (16); [6], [7] Gamma set written
-    // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete (commit); [11] A_t
-    // written (16); [12] constant operands landed (bulk copy); [13] the brick's gV block complete (commit)
+    // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete, B_c | B_s read
+    // (commit); [11] unused; [12] constant operands landed (bulk copy); [13] the brick's gV block complete
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 112);
     int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 116);
@@ -234,8 +235,10 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
 
     if (warp == kConsumers) {
-        // ================================ producer warp: one lane issues every MMA ============================
-        if (lane == 0) {
+        // ====== producer warp: lane 0 issues every MMA; the warp (lane quarter 0 of tensor memory) also moves
+        // dG1 into the t-adjoint operand, so the consumers never wait for the adjoint of stage 2 ======
+        {
+            const bool leader = lane == 0;
             const uint32_t idesc1 = tc::idesc_f16(kFmt, 128, 16, 1, 0);
             const uint32_t idesc2 = tc::idesc_f16(kFmt, 128, G::N2, 0, 0);
             const uint32_t idesc3 = tc::idesc_f16(kFmt, 128, G::N3, 1, 0);
@@ -251,13 +254,15 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             uint32_t ph[14];
 #pragma unroll
             for (int b = 0; b < 14; ++b) ph[b] = 0;
-            auto commit = [&](int b) { tc::mma_commit(tc::smem_u32(&s_mbar[b])); };
-            // bounded wait; a give-up (here or in a consumer) stops all further issue
+            auto commit = [&](int b) {
+                if (leader) tc::mma_commit(tc::smem_u32(&s_mbar[b]));
+            };
+            // warp-uniform bounded wait; a give-up (here or in a consumer) stops all further issue
             auto pwait = [&](int b) -> bool {
-                if (*v_fail) return false;
-                const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
+                bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
                 ph[b] ^= 1u;
-                if (!ok) give_up();
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok && leader && !*v_fail) give_up();
                 tc::fence_after_sync();
                 return ok;
             };
@@ -270,13 +275,15 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             const uint64_t tred = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE, G::TI_LBO, 128);
             const uint64_t timd = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM, G::TI_LBO, 128);
             auto issue_s2 = [&](int kt) {
+                if (!leader) return;
                 const uint64_t b2 = tc::desc_add(b2d, (uint32_t)(kt * G::B2_B));
 #pragma unroll
                 for (int s = 0; s < kK2 / 16; ++s)
                     tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2, s > 0 ? 1u : 0u);
-                commit(0);
+                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
             };
             auto issue_s3 = [&](int pass) {
+                if (!leader) return;
                 const uint32_t col = (uint32_t)(128 * (pass & 1));
 #pragma unroll
                 for (int j = 0; j < G::OPP; ++j) {
@@ -284,10 +291,11 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                     tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
                     tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
                 }
-                commit(pass & 1);
+                tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
             };
             // adjoint of stage 3 for the outputs of one pass (Gamma set pass % 2), accumulating into kColY
             auto issue_inv_y = [&](int pass) {
+                if (!leader) return;
                 const uint32_t set = (uint32_t)((pass & 1) * G::GSET_B);
 #pragma unroll
                 for (int j = 0; j < G::OPP; ++j) {
@@ -301,13 +309,13 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 }
             };
             bool alive = pwait(12);
-            if (alive) {   // stage 1, all k_t at once
+            if (alive && leader) {   // stage 1, all k_t at once
                 const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
 #pragma unroll
                 for (int i = 0; i < G::NB1; ++i)
                     tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1,
                                 idesc1, 0);
-                commit(0);
+                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
             }
             alive = alive && pwait(5);
             if (alive) issue_s2(0);
@@ -340,23 +348,54 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 }
                 // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------
                 if (!(alive = pwait(9))) break;
-                const uint64_t a2t = tc::desc_noswizzle(tab, G::SBO_K2, 128);   // A2 read MN-major: A2^T
-                const uint64_t bcd = tc::desc_noswizzle(bc, 128, 2048), bsd = tc::desc_noswizzle(bs, 128, 2048);
+                if (leader) {
+                    const uint64_t a2t = tc::desc_noswizzle(tab, G::SBO_K2, 128);   // A2 read MN-major: A2^T
+                    const uint64_t bcd = tc::desc_noswizzle(bc, 128, 2048), bsd = tc::desc_noswizzle(bs, 128, 2048);
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    tc::mma_f16(tmem + kColX, tc::desc_add(a2t, 1536 * s), tc::desc_add(bcd, 256 * s), idescx,
-                                s > 0 ? 1u : 0u);
-                    tc::mma_f16(tmem + kColX, tc::desc_add(a2t, (kXHP / 8) * 128 + 1536 * s), tc::desc_add(bsd, 256 * s),
-                                idescx, 1u);
+                    for (int s = 0; s < 8; ++s) {
+                        tc::mma_f16(tmem + kColX, tc::desc_add(a2t, 1536 * s), tc::desc_add(bcd, 256 * s), idescx,
+                                    s > 0 ? 1u : 0u);
+                        tc::mma_f16(tmem + kColX, tc::desc_add(a2t, (kXHP / 8) * 128 + 1536 * s),
+                                    tc::desc_add(bsd, 256 * s), idescx, 1u);
+                    }
                 }
                 commit(10);
-                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
-                if (!(alive = pwait(11))) break;
-                const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
-                const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
+                // ---- dG1 (rows x = lane) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) -------------------
+                // (the t-adjoint MMAs of k_t - 1, issued before, are complete once dG1 of k_t is)
+                if (!(alive = pwait(10))) break;
 #pragma unroll
-                for (int i = 0; i < G::NB1; ++i)
-                    tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, kt > 0 ? 1u : 0u);
+                for (int c = 0; c < 4; ++c) {   // columns 16 c ..: re over y (c = 0, 1), im over y (c = 2, 3)
+                    float v[16];
+                    tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * c), v);
+                    const int k = c >> 1;
+                    if (lane < kXHP) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int y8 = 16 * (c & 1) + 8 * h;
+                            if (y8 < YP) {
+                                // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
+                                uint4 w;
+                                w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
+                                w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
+                                w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
+                                w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
+                                *reinterpret_cast<uint4*>(s_at + ((lane * YP + y8) / 8) * 256 + k * 16) = w;
+                            }
+                        }
+                    }
+                }
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                __syncwarp();
+                tc::fence_after_sync();
+                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
+                if (leader) {
+                    const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
+                    const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
+#pragma unroll
+                    for (int i = 0; i < G::NB1; ++i)
+                        tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, kt > 0 ? 1u : 0u);
+                }
             }
             if (alive) commit(13);
         }
@@ -402,6 +441,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
             for (int pass = 0; pass < G::PASSES; ++pass) {
                 const int b = pass & 1;
+                // Gamma set 1 holds B_c | B_s of k_t - 1 until its adjoint-x MMAs complete
+                if (pass == 1 && kt > 0) cwait(10);
                 if (cwait(b)) {
                     float v[32];
                     tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * grp), v);
@@ -493,29 +534,6 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             }
             tc::fence_async_smem();
             arrive(9);
-            // ---- dG1 (rows x of lane quarter 0) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) --------
-            if (cwait(10) && q == 0) {
-                float v[16];
-                tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * grp), v);
-                const int x = lane, k = grp >> 1;
-                if (x < kXHP) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int y8 = 16 * (grp & 1) + 8 * h;
-                        if (y8 < YP) {
-                            // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
-                            uint4 w;
-                            w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
-                            w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
-                            w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
-                            w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
-                            *reinterpret_cast<uint4*>(s_at + ((x * YP + y8) / 8) * 256 + k * 16) = w;
-                        }
-                    }
-                }
-            }
-            tc::fence_async_smem();
-            arrive(11);
         }
         // ---- the brick's block of gVext (tensor memory) to scratch [u_t][x][y] --------------------------------
         ok = cwait(13);
