@@ -111,124 +111,151 @@ kb_weights_finalize(const double* __restrict__ part, int nparts, const float* __
     }
 }
 
-// K4: gradient of the features through Eq. 3 (gather form).
+// K4: gradient of the features through Eq. 3 (gather form).  One warp per (t, x) row, lanes along y;
+// voxels the stencil halo away from every border read their neighbours q + o and their preimages q - o
+// at linear offsets, the others go through the border extension.
 __global__ void __launch_bounds__(kThreads)
 k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
                float* __restrict__ gE, int T, int X, int Y, int bnd, const __grid_constant__ Stencil st) {
+    constexpr int kWarps = kThreads / 32;
     // gradient of the raw map m at p: coef[m] * gS[m * gms + p]
     const long long NV = (long long)T * X * Y;
     const float c0 = coef[0], c1 = coef[1], c2 = coef[2];
-    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < NV; q += (long long)gridDim.x * kThreads) {
-        const int y = (int)(q % Y);
-        const int x = (int)((q / Y) % X);
-        const int t = (int)(q / ((long long)X * Y));
-        float eq[3], gq[3], acc[3] = {0.f, 0.f, 0.f};
+    __shared__ long long s_lin[kMaxOffsets];
+    __shared__ float s_w[kMaxOffsets];
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        s_lin[o] = ((long long)st.off[o][0] * X + st.off[o][1]) * Y + st.off[o][2];
+        s_w[o] = st.w[o];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int Q = st.Q;
+    const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
+    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+        const int t = (int)(r / X), x = (int)(r - (long long)t * X);
+        const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
+        for (int y = lane; y < Y; y += 32) {
+            const long long q = r * Y + y;
+            float eq[3], gq[3], acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            eq[m] = __ldg(E + m * NV + q);
-            gq[m] = __ldg(gS + m * gms + q);
-        }
-        // interior voxels (at least the stencil halo away from every border): the neighbour is q + o and
-        // the only preimage of q under offset o is q - o
-        const bool inner = t >= st.halo[0] && t < T - st.halo[0] && x >= st.halo[1] && x < X - st.halo[1] &&
-                           y >= st.halo[2] && y < Y - st.halo[2];
-        if (inner) {
-            for (int o = 0; o < st.Q; ++o) {
-                const long long d = ((long long)st.off[o][0] * X + st.off[o][1]) * Y + st.off[o][2];
-                const float w = st.w[o];
+            for (int m = 0; m < 3; ++m) {
+                eq[m] = __ldg(E + m * NV + q);
+                gq[m] = __ldg(gS + m * gms + q);
+            }
+            if (row_inner && y >= hy && y < Y - hy) {
+                // the neighbour is q + o and the only preimage of q under offset o is q - o
+#pragma unroll 2
+                for (int o = 0; o < Q; ++o) {
+                    const long long d = s_lin[o];
+                    const float w = s_w[o];
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const float nb = __ldg(E + m * NV + q + d);
-                    const float pe = __ldg(E + m * NV + q - d), pg = __ldg(gS + m * gms + q - d);
-                    acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
-                    acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
+                    for (int m = 0; m < 3; ++m) {
+                        const float nb = __ldg(E + m * NV + q + d);
+                        const float pe = __ldg(E + m * NV + q - d), pg = __ldg(gS + m * gms + q - d);
+                        acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+                        acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
+                    }
+                }
+            } else {
+                for (int o = 0; o < Q; ++o) {
+                    const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
+                    const float w = s_w[o];
+                    // q as the center of the comparison
+                    const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd),
+                              yy = ext_index(y + dy, Y, bnd);
+                    const bool ok = (tt | xx | yy) >= 0;
+                    const long long nq = ok ? ((long long)tt * X + xx) * Y + yy : 0;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const float nb = ok ? __ldg(E + m * NV + nq) : 0.f;
+                        acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+                    }
+                    // q as the neighbour: p with ext(p + o) = q
+                    int pt[2], px[2], py[2];
+                    const int nt = pre_offset(t, dt, T, bnd, pt);
+                    const int nx = pre_offset(x, dx, X, bnd, px);
+                    const int ny = pre_offset(y, dy, Y, bnd, py);
+                    for (int a = 0; a < nt; ++a)
+                        for (int b = 0; b < nx; ++b)
+                            for (int c = 0; c < ny; ++c) {
+                                const long long p = ((long long)pt[a] * X + px[b]) * Y + py[c];
+#pragma unroll
+                                for (int m = 0; m < 3; ++m)
+                                    acc[m] -= w * sgnf(fmaf(-w, eq[m], __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p);
+                            }
                 }
             }
             gE[q] = acc[0] * c0 * st.invQ;
             gE[NV + q] = acc[1] * c1 * st.invQ;
             gE[2 * NV + q] = acc[2] * c2 * st.invQ;
-            continue;
         }
-        for (int o = 0; o < st.Q; ++o) {
-            const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
-            const float w = st.w[o];
-            // q as the center of the comparison
-            const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd), yy = ext_index(y + dy, Y, bnd);
-            const bool ok = (tt | xx | yy) >= 0;
-            const long long nq = ok ? ((long long)tt * X + xx) * Y + yy : 0;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float nb = ok ? __ldg(E + m * NV + nq) : 0.f;
-                acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
-            }
-            // q as the neighbour: p with ext(p + o) = q
-            int pt[2], px[2], py[2];
-            const int nt = pre_offset(t, dt, T, bnd, pt);
-            const int nx = pre_offset(x, dx, X, bnd, px);
-            const int ny = pre_offset(y, dy, Y, bnd, py);
-            for (int a = 0; a < nt; ++a)
-                for (int b = 0; b < nx; ++b)
-                    for (int c = 0; c < ny; ++c) {
-                        const long long p = ((long long)pt[a] * X + px[b]) * Y + py[c];
-#pragma unroll
-                        for (int m = 0; m < 3; ++m)
-                            acc[m] -= w * sgnf(fmaf(-w, eq[m], __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p);
-                    }
-        }
-        gE[q] = acc[0] * c0 * st.invQ;
-        gE[NV + q] = acc[1] * c1 * st.invQ;
-        gE[2 * NV + q] = acc[2] * c2 * st.invQ;
     }
 }
 
-// FP64 partials of gw_o (before the -1/Q factor): one pass over the block's voxels; for each offset the
-// warp sums its 32 voxels' terms (fixed shuffle tree) into a warp-private FP64 accumulator, and the
-// warps' accumulators are summed in warp order.
+// FP64 partials of gw_o (before the -1/Q factor): one warp per (t, x) row, lanes along y, 4 voxels per
+// lane at a time; for each offset the warp sums its voxels' terms (fixed shuffle tree) into a
+// warp-private FP64 accumulator, and the warps' accumulators are summed in warp order.
 __global__ void __launch_bounds__(kThreads)
 k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
               int T, int X, int Y, int bnd, const __grid_constant__ Stencil st, double* __restrict__ part) {
+    constexpr int kWarps = kThreads / 32, kJ = 4;
     const long long NV = (long long)T * X * Y;
     const float c[3] = {coef[0], coef[1], coef[2]};
-    constexpr int kWarps = kThreads / 32;
     __shared__ double wacc[kWarps][kMaxOffsets];
+    __shared__ long long s_lin[kMaxOffsets];
+    __shared__ float s_w[kMaxOffsets];
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        s_lin[o] = ((long long)st.off[o][0] * X + st.off[o][1]) * Y + st.off[o][2];
+        s_w[o] = st.w[o];
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = lane; o < kMaxOffsets; o += 32) wacc[wid][o] = 0.0;
-    __syncwarp();
-    const long long stride = (long long)gridDim.x * kThreads;
-    const long long first = (long long)blockIdx.x * kThreads + wid * 32;
-    for (long long base = first; base < NV; base += stride) {   // warp-uniform trip count
-        const long long p = base + lane;
-        const bool live = p < NV;
-        int t = 0, x = 0, y = 0;
-        float ep[3] = {0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
-        if (live) {
-            y = (int)(p % Y);
-            x = (int)((p / Y) % X);
-            t = (int)(p / ((long long)X * Y));
+    __syncthreads();
+    const int Q = st.Q;
+    const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
+    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+        const int t = (int)(r / X), x = (int)(r - (long long)t * X);
+        const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
+        for (int y0 = 0; y0 < Y; y0 += 32 * kJ) {   // warp-uniform trip count
+            float ep[kJ][3], gp[kJ][3];
+            bool live[kJ], inner[kJ];
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                ep[m] = __ldg(E + m * NV + p);
-                gp[m] = c[m] * __ldg(gS + m * gms + p);
+            for (int j = 0; j < kJ; ++j) {
+                const int y = y0 + 32 * j + lane;
+                live[j] = y < Y;
+                inner[j] = row_inner && y >= hy && y < Y - hy;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    ep[j][m] = live[j] ? __ldg(E + m * NV + r * Y + y) : 0.f;
+                    gp[j][m] = live[j] ? c[m] * __ldg(gS + m * gms + r * Y + y) : 0.f;
+                }
             }
-        }
-        for (int o = 0; o < st.Q; ++o) {
-            const float w = st.w[o];
-            float s = 0.f;
-            if (live) {
-                const int tt = ext_index(t + st.off[o][0], T, bnd), xx = ext_index(x + st.off[o][1], X, bnd),
-                          yy = ext_index(y + st.off[o][2], Y, bnd);
-                if ((tt | xx | yy) >= 0) {
-                    const long long nq = ((long long)tt * X + xx) * Y + yy;
+            for (int o = 0; o < Q; ++o) {
+                const float w = s_w[o];
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < kJ; ++j) {
+                    if (!live[j]) continue;
+                    const int y = y0 + 32 * j + lane;
+                    long long nq;
+                    if (inner[j]) {
+                        nq = r * Y + y + s_lin[o];
+                    } else {
+                        const int tt = ext_index(t + st.off[o][0], T, bnd), xx = ext_index(x + st.off[o][1], X, bnd),
+                                  yy = ext_index(y + st.off[o][2], Y, bnd);
+                        if ((tt | xx | yy) < 0) continue;
+                        nq = ((long long)tt * X + xx) * Y + yy;
+                    }
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {
                         const float nb = __ldg(E + m * NV + nq);
-                        s = fmaf(sgnf(fmaf(-w, nb, ep[m])) * gp[m], nb, s);
+                        s = fmaf(sgnf(fmaf(-w, nb, ep[j][m])) * gp[j][m], nb, s);
                     }
                 }
-            }
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-            if (lane == 0) wacc[wid][o] += (double)s;
+                for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+                if (lane == 0) wacc[wid][o] += (double)s;
+            }
         }
     }
     __syncthreads();
@@ -239,25 +266,21 @@ k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long lo
     }
 }
 
-// galpha_d = sum_{o in d} g_o gw_o, gw_o = -(1/Q) sum_blocks part[block][o].  One block; each
-// offset's partials are summed by a fixed-order tree.
+// galpha_d = sum_{o in d} g_o gw_o, gw_o = -(1/Q) sum_blocks part[block][o].  One block; one warp per
+// offset sums its partials in a fixed order (strided lanes, then a shuffle tree).
 __global__ void __launch_bounds__(kThreads)
 k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_constant__ Stencil st,
                    float* __restrict__ galpha) {
-    __shared__ double red[kThreads];
     __shared__ double gw[kMaxOffsets];
-    for (int o = 0; o < st.Q; ++o) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = wid; o < st.Q; o += kThreads / 32) {
         double a = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += kThreads) a += part[i * 64 + o];
-        red[threadIdx.x] = a;
-        __syncthreads();
-        for (int s = kThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) gw[o] = -red[0] / st.Q;
-        __syncthreads();
+        for (int i = lane; i < nparts; i += 32) a += part[i * 64 + o];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+        if (lane == 0) gw[o] = -a / st.Q;
     }
+    __syncthreads();
     if (threadIdx.x < st.n_dirs) {
         double a = 0.0;
         for (int o = 0; o < st.Q; ++o)

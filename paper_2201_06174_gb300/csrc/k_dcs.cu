@@ -2,8 +2,9 @@
 //   S_m[p] = (1/Q) sum_o | E_m[p] - w_o * Eext_m[p + o] |,   m in {t, x, y},
 // in compensated FP32: each difference is formed by one FMA (fmaf(-w, e_nb, e_c): the product is
 // not rounded before the subtraction) and the Q distances are summed with Kahan compensation.
-// HBM-bound: 12 B read + 12 B written per voxel; neighbours come from L1/L2.  Fused per-block
-// min/max of each S_m for the normalisation in K3.
+// HBM-bound: 12 B read + 12 B written per voxel; neighbours come from L1/L2.  One warp per (t, x) row;
+// voxels the halo away from every border take the stencil as linear offsets, the others go through the
+// border extension.  Fused per-block min/max of each S_m for the normalisation in K3.
 #include <cfloat>
 
 #include "sal_internal.cuh"
@@ -27,43 +28,72 @@ __device__ __forceinline__ float warp_max(float v) {
 __global__ void __launch_bounds__(kThreads)
 k2_dcs(const float* __restrict__ E, float* __restrict__ S3, int T, int X, int Y, int bnd,
        const __grid_constant__ Stencil st, float* __restrict__ mm_part) {
+    constexpr int kWarps = kThreads / 32;
     const long long NV = (long long)T * X * Y;
+    // linear offset of each neighbour: the whole comparison of a voxel at least the halo away from every
+    // border reads E at p + s_lin[o]
+    __shared__ long long s_lin[kMaxOffsets];
+    __shared__ float s_w[kMaxOffsets];
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        s_lin[o] = ((long long)st.off[o][0] * X + st.off[o][1]) * Y + st.off[o][2];
+        s_w[o] = st.w[o];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int Q = st.Q;
+    const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
     float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < NV;
-         p += (long long)gridDim.x * kThreads) {
-        const int y = (int)(p % Y);
-        const int x = (int)((p / Y) % X);
-        const int t = (int)(p / ((long long)X * Y));
-        float ec[3], acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+    // one warp per (t, x) row, lanes along y
+    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+        const int t = (int)(r / X), x = (int)(r - (long long)t * X);
+        const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
+        for (int y = lane; y < Y; y += 32) {
+            const long long p = r * Y + y;
+            float ec[3], acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int m = 0; m < 3; ++m) ec[m] = __ldg(E + m * NV + p);
-        for (int o = 0; o < st.Q; ++o) {
-            const int tt = ext_index(t + st.off[o][0], T, bnd);
-            const int xx = ext_index(x + st.off[o][1], X, bnd);
-            const int yy = ext_index(y + st.off[o][2], Y, bnd);
-            const bool ok = tt >= 0 && xx >= 0 && yy >= 0;
-            const long long q = ok ? ((long long)tt * X + xx) * Y + yy : 0;
-            const float w = st.w[o];
+            for (int m = 0; m < 3; ++m) ec[m] = __ldg(E + m * NV + p);
+            if (row_inner && y >= hy && y < Y - hy) {
+#pragma unroll 2
+                for (int o = 0; o < Q; ++o) {
+                    const float* e = E + p + s_lin[o];
+                    const float w = s_w[o];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        // Kahan: acc + cmp carries the sum to about twice the FP32 precision
+                        const float yv = fabsf(fmaf(-w, __ldg(e + m * NV), ec[m])) - cmp[m];
+                        const float tv = acc[m] + yv;
+                        cmp[m] = (tv - acc[m]) - yv;
+                        acc[m] = tv;
+                    }
+                }
+            } else {
+                for (int o = 0; o < Q; ++o) {
+                    const int tt = ext_index(t + st.off[o][0], T, bnd);
+                    const int xx = ext_index(x + st.off[o][1], X, bnd);
+                    const int yy = ext_index(y + st.off[o][2], Y, bnd);
+                    const bool ok = tt >= 0 && xx >= 0 && yy >= 0;
+                    const long long q = ok ? ((long long)tt * X + xx) * Y + yy : 0;
+                    const float w = s_w[o];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const float nb = ok ? __ldg(E + m * NV + q) : 0.f;
+                        const float yv = fabsf(fmaf(-w, nb, ec[m])) - cmp[m];
+                        const float tv = acc[m] + yv;
+                        cmp[m] = (tv - acc[m]) - yv;
+                        acc[m] = tv;
+                    }
+                }
+            }
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const float nb = ok ? __ldg(E + m * NV + q) : 0.f;
-                // Kahan: acc + cmp carries the sum to about twice the FP32 precision
-                const float yv = fabsf(fmaf(-w, nb, ec[m])) - cmp[m];
-                const float tv = acc[m] + yv;
-                cmp[m] = (tv - acc[m]) - yv;
-                acc[m] = tv;
+                const float s = acc[m] * st.invQ;
+                S3[m * NV + p] = s;
+                mn[m] = fminf(mn[m], s);
+                mx[m] = fmaxf(mx[m], s);
             }
-        }
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const float s = acc[m] * st.invQ;
-            S3[m * NV + p] = s;
-            mn[m] = fminf(mn[m], s);
-            mx[m] = fmaxf(mx[m], s);
         }
     }
     __shared__ float red[kThreads / 32][6];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         float a = warp_min(mn[m]), b = warp_max(mx[m]);
