@@ -289,21 +289,50 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
     }
 }
 
-// Overlap-add of the spectral adjoint: gV[q] += sum of every brick block element whose extended
-// position maps to q.  Blocks of the bricks with t0 in [t_begin, t_begin + t_count); brick (xs, ys)
-// covers x_ext in [xs*BX - n/2, xs*BX + BX + n/2 - 1), y_ext likewise with BY.  Voxels with t in
-// [t_lo, t_hi) are visited (every voxel the slab reaches); the sum runs in a fixed order.
+// Overlap-add of the spectral adjoint, in two passes.  The bricks of t0 in [t_begin, t_begin + t_count)
+// hold blocks [u_t][x'][y'] (u_t < n, x' < XH, y' < YH); brick (xs, sg) covers x_ext in
+// [xs*BX - n/2, xs*BX - n/2 + XH), y_ext likewise with BY, YH; slice u_t of brick t0 lies at
+// t_ext = t0 - n/2 + u_t.
+//   pass 1 (along t): ext[i][brick][x'][y'] = sum over t0 of the slices at t_ext = t_begin - n/2 + i, for
+//     every extended plane i < t_count + n - 1 -- contiguous slices, read once;
+//   pass 2 (across bricks): gV[q] += sum of ext over the extended positions (t_ext, x_ext, y_ext) that
+//     map to q and the bricks that hold them.
+// Both passes sum in a fixed order, so the result is deterministic.
 __global__ void __launch_bounds__(kThreads)
-k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, int X, int Y, int bnd, int n,
-              int BX, int XH, int BY, int YH, int t_begin, int t_count, int t_lo, int t_hi) {
+k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, int nb, int slice, int t_count) {
+    const long long bsz = (long long)n * slice;
+    const long long total = (long long)(t_count + n - 1) * nb * slice;
+    for (long long idx = (long long)blockIdx.x * kThreads + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * kThreads) {
+        const int e = (int)(idx % slice);
+        const long long rest = idx / slice;
+        const int brick = (int)(rest % nb), i = (int)(rest / nb);
+        // t0 - t_begin = i - n + 1 + j (j < n) covers every brick whose slice u_t = n - 1 - j lands on plane i
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int r = i - n + 1 + j;   // t0 - t_begin
+            v[j] = (j < n && r >= 0 && r < t_count)
+                       ? __ldg(blocks + ((long long)r * nb + brick) * bsz + (long long)(n - 1 - j) * slice + e)
+                       : 0.f;
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sum += v[j];
+        ext[idx] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k5_gather_xy(const float* __restrict__ ext, float* __restrict__ gV, int T, int X, int Y, int bnd, int n, int BX,
+             int XH, int BY, int YH, int t_begin, int t_count, int t_lo, int t_hi) {
     const long long q0 = (long long)t_lo * X * Y, q1 = (long long)t_hi * X * Y;
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
     const int nxs = (X + BX - 1) / BX;
-    const int t_end = t_begin + t_count;
-    const long long bsz = (long long)n * XH * YH;
-    // one step of t0 moves to the next row of bricks and one u_t back
-    const long long tstep = (long long)nxs * nseg * bsz - (long long)XH * YH;
+    const int nb = nxs * nseg;
+    const int slice = XH * YH;
+    const int te_lo = t_begin - h2, te_hi = t_begin + t_count + h2 - 1;   // extended planes of this slab
     for (long long q = q0 + (long long)blockIdx.x * kThreads + threadIdx.x; q < q1;
          q += (long long)gridDim.x * kThreads) {
         const int y = (int)(q % Y);
@@ -311,53 +340,37 @@ k5_gather_add(const float* __restrict__ blocks, float* __restrict__ gV, int T, i
         const int t = (int)(q / ((long long)X * Y));
         if (t >= h2 && t < T - h2 && x >= h2 && x < X - h2 && y >= h2 && y < Y - h2) {
             // interior voxel: its only extended position is itself
-            const int t0a = max(t_begin, t - h2 + 1), t0b = min(t_end - 1, t + h2);
-            if (t0a > t0b) continue;
-            const int cnt = t0b - t0a + 1;   // <= n <= 16
+            if (t < te_lo || t >= te_hi) continue;
             const int xa = max(0, ceildiv(x + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(x + h2, BX));
             const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
-            const float* base = blocks + (long long)(t0a - t_begin) * nxs * nseg * bsz +
-                                (long long)(t - t0a + h2) * XH * YH + (y + h2);
+            const float* plane = ext + (long long)(t - te_lo) * nb * slice;
             float sum = 0.f;
-            for (int xs = xa; xs <= xb; ++xs) {
-                for (int sg = sa; sg <= sb; ++sg) {
-                    const float* b = base + (long long)(xs * nseg + sg) * bsz + (x - xs * BX + h2) * YH - sg * BY;
-                    float v[16];   // every t0 of this brick column in flight at once
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = j < cnt ? __ldg(b + j * tstep) : 0.f;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) sum += v[j];
-                }
-            }
+            for (int xs = xa; xs <= xb; ++xs)
+                for (int sg = sa; sg <= sb; ++sg)
+                    sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
+                                 (y - sg * BY + h2));
             gV[q] += sum;
             continue;
         }
         int et[40], ex[40], ey[40];
-        const int nt = pre_range(t, T, bnd, t_begin - h2, t_end + h2 - 1, et, 40);
+        const int nt = pre_range(t, T, bnd, te_lo, te_hi, et, 40);
         if (nt == 0) continue;
         const int nx = pre_range(x, X, bnd, -h2, X + h2 - 1, ex, 40);
         const int ny = pre_range(y, Y, bnd, -h2, Y + h2 - 1, ey, 40);
         float sum = 0.f;
         for (int a = 0; a < nt; ++a) {
-            const int te = et[a];
-            const int t0a = max(t_begin, te - h2 + 1), t0b = min(t_end - 1, te + h2);
-            for (int t0 = t0a; t0 <= t0b; ++t0) {
-                const int ut = te - t0 + h2;
-                for (int b = 0; b < nx; ++b) {
-                    const int xe = ex[b];
-                    const int xa = max(0, ceildiv(xe + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(xe + h2, BX));
-                    for (int xs = xa; xs <= xb; ++xs) {
-                        const int ux = xe - xs * BX + h2;
-                        const long long cta_row = ((long long)(t0 - t_begin) * nxs + xs) * nseg;
-                        for (int c = 0; c < ny; ++c) {
-                            const int ye = ey[c];
-                            const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
-                            const int sb = min(nseg - 1, floordiv(ye + h2, BY));
-                            for (int sg = sa; sg <= sb; ++sg) {
-                                const int yy = ye - sg * BY + h2;
-                                sum += __ldg(blocks + (cta_row + sg) * bsz + ((long long)ut * XH + ux) * YH + yy);
-                            }
-                        }
+            const float* plane = ext + (long long)(et[a] - te_lo) * nb * slice;
+            for (int b = 0; b < nx; ++b) {
+                const int xe = ex[b];
+                const int xa = max(0, ceildiv(xe + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(xe + h2, BX));
+                for (int xs = xa; xs <= xb; ++xs) {
+                    const int ux = xe - xs * BX + h2;
+                    for (int c = 0; c < ny; ++c) {
+                        const int ye = ey[c];
+                        const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
+                        const int sb = min(nseg - 1, floordiv(ye + h2, BY));
+                        for (int sg = sa; sg <= sb; ++sg)
+                            sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + ux * YH + (ye - sg * BY + h2));
                     }
                 }
             }
@@ -413,8 +426,20 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
     return cudaGetLastError();
 }
 
-cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
+size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count) {
+    const size_t nb = (size_t)((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
+    return (size_t)(t_count + n - 1) * nb * g.XH * g.YH;
+}
+
+cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
                               SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s) {
+    if (n > 16) return cudaErrorInvalidValue;   // pass 1 unrolls up to 16 bricks per plane
+    const int nb = ((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
+    const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count);
+    long long b1 = (e_total + kThreads - 1) / kThreads;
+    if (b1 > 152 * 32) b1 = 152 * 32;
+    if (b1 < 1) b1 = 1;
+    k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count);
     // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_count + n/2 - 1); a slab whose
     // extension leaves the volume may wrap (periodic) or reflect (symmetric) onto any edge plane
     const int h2 = n / 2;
@@ -424,12 +449,12 @@ cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int 
         t_hi = T;
     }
     const long long NV = (long long)(t_hi - t_lo) * X * Y;
-    long long nb = (NV + kThreads - 1) / kThreads;
-    if (nb > 152 * 32) nb = 152 * 32;
-    if (nb < 1) nb = 1;
-    k5_gather_add<<<(int)nb, kThreads, 0, s>>>(blocks, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
-                                               t_lo, t_hi);
-    note_launches(1);
+    long long b2 = (NV + kThreads - 1) / kThreads;
+    if (b2 > 152 * 32) b2 = 152 * 32;
+    if (b2 < 1) b2 = 1;
+    k5_gather_xy<<<(int)b2, kThreads, 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
+                                              t_lo, t_hi);
+    note_launches(2);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ struct sal_handle {
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
     float* blocks = nullptr; // brick blocks of the spectral adjoint for one slab of t0
+    float* gext = nullptr;   // the blocks summed along t, per extended plane of the slab
     int slab_t = 0;
     volatile int* err_host = nullptr;  // mapped host word set by bounded device waits that gave up
     int* err_dev = nullptr;
@@ -64,7 +65,8 @@ void free_scratch(sal_handle* h) {
     if (h->gE) cudaFree(h->gE);
     if (h->bpart) cudaFree(h->bpart);
     if (h->blocks) cudaFree(h->blocks);
-    h->E = h->S3 = h->gE = h->blocks = nullptr;
+    if (h->gext) cudaFree(h->gext);
+    h->E = h->S3 = h->gE = h->blocks = h->gext = nullptr;
     h->small = nullptr;
     h->bpart = nullptr;
 }
@@ -354,28 +356,34 @@ sal_status ensure_backward_scratch(sal_handle* h) {
     const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     const int nseg = (h->Y + g.BY - 1) / g.BY;
     const size_t per_t = (size_t)((h->X + g.BX - 1) / g.BX) * nseg * g.block_floats * sizeof(float);
+    // the overlap-add's scratch: one brick-summed plane per extended plane of the slab (slab + n - 1)
+    const size_t per_ext = sal::gather_ext_floats(h->n, g, h->X, h->Y, 1) / h->n * sizeof(float);
+    const size_t ext_fixed = (size_t)(h->n - 1) * per_ext;
     size_t cap = kBlocksCap;
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
     const size_t bpart = (size_t)sal::kRedBlocks * 64 * sizeof(double);
     if (h->budget) {
-        const size_t used = h->bytes + plane3 + bpart;
-        if (used + per_t > h->budget)
+        const size_t used = h->bytes + plane3 + bpart + ext_fixed;
+        if (used + per_t + per_ext > h->budget)
             return fail(h, SAL_ERR_OOM, "backward scratch exceeds hbm_budget_bytes");
         cap = std::min(cap, h->budget - used);
     }
-    int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->T, cap / per_t));
+    int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->T, cap / (per_t + per_ext)));
+    const size_t ext_bytes = sal::gather_ext_floats(h->n, g, h->X, h->Y, slab) * sizeof(float);
     cudaError_t e;
     if ((e = cudaMalloc(&h->gE, plane3)) != cudaSuccess || (e = cudaMalloc(&h->bpart, bpart)) != cudaSuccess ||
-        (e = cudaMalloc(&h->blocks, per_t * slab)) != cudaSuccess) {
+        (e = cudaMalloc(&h->blocks, per_t * slab)) != cudaSuccess ||
+        (e = cudaMalloc(&h->gext, ext_bytes)) != cudaSuccess) {
         if (h->gE) cudaFree(h->gE);
         if (h->bpart) cudaFree(h->bpart);
-        h->gE = h->blocks = nullptr;
+        if (h->blocks) cudaFree(h->blocks);
+        h->gE = h->blocks = h->gext = nullptr;
         h->bpart = nullptr;
         cudaGetLastError();
         return fail(h, SAL_ERR_OOM, std::string("backward scratch cudaMalloc: ") + cudaGetErrorString(e));
     }
     h->slab_t = slab;
-    h->bytes += plane3 + bpart + per_t * slab;
+    h->bytes += plane3 + bpart + per_t * slab + ext_bytes;
     return SAL_OK;
 }
 
@@ -395,7 +403,8 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,
                                                  h->boundary, t_begin, cnt, h->err_dev, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
-        if ((e = sal::gather_add_launch(h->blocks, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt, st)) !=
+        if ((e = sal::gather_add_launch(h->blocks, h->gext, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt,
+                                        st)) !=
             cudaSuccess)
             return cuda_fail(h, e, "spectral adjoint: overlap-add");
     }

@@ -131,7 +131,10 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
 cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, int T, int X, int Y,
                               int bnd, const Stencil& st, double* part, float* galpha, cudaStream_t s);
 cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s);
-cudaError_t gather_add_launch(const float* blocks, float* gV, int T, int X, int Y, int bnd, int n,
+// Overlap-add of one slab's brick blocks into gV through the scratch `ext` (gather_ext_floats floats):
+// first along t (contiguous slices), then across the bricks that overlap each voxel.
+size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count);
+cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
                               SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s);
 
 // Process-wide count of kernels launched by the library (sal_launch_count).
