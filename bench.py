@@ -47,8 +47,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
 K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840,   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
-              ("salt128", 16, "bf16"): 8625289}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
-K5_TRAFFIC = {("salt128", 16, "bf16"): 718849638}  # K5 alone: 34.8 MB read + 684.1 MB written (brick blocks)
+              ("salt128", 16, "bf16"): 8616380}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
+K5_TRAFFIC = {("salt128", 16, "bf16"): 717473101}  # K5 alone: 34.2 MB read + 683.3 MB written (brick blocks)
 
 
 def measured_peaks():
@@ -395,7 +395,7 @@ def main():
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
-        rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and k5_gather_add)", args.prec, n, nvox, k5_ms,
+        rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
                       2, K5_TRAFFIC.get((args.workload, n, args.prec)), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt")
         rl["k1"] = k1_rl
     else:
