@@ -13,7 +13,8 @@ Pipeline (Sec. 2 of the paper, Fig. 2 block diagram):
 Readings where the paper is silent (each an argument here):
   * stride 1 (a window around every voxel), window offsets [-n/2, n/2-1];
   * rectangular taper (the cube C_n as is); Hann optional;
-  * E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]|;
+  * E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (feature "abs"); the energy reading of the garbled step 3,
+    E_m = (1/n^3) sum_{k != 0} r_m(k)^2 |F[k]|^2, is feature "energy";
   * DCS stencil: direction groups t, x and t-x (Fig. 4), offsets s*d for s in +-1..+-R,
     Gaussian weights w_o = alpha_d exp(-|o|^2 / (2 sigma^2)) multiplying the neighbour
     inside |.| as Eq. 3 is written, Q = number of offsets;
@@ -35,6 +36,7 @@ from . import build as _build
 
 BOUNDARY = {"symmetric": 0, "periodic": 1, "zero": 2}
 TAPER = {"rect": 0, "hann": 1}
+FEATURE = {"abs": 0, "energy": 1}   # step 3: mean of |F_m| (the paper's), or of |F_m|^2
 
 _lib = None
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -51,12 +53,12 @@ def lib():
         i = ctypes.c_int
         L.sal_oracle_local_spectrum.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, L_, L_, L_, _c_dbl_p]
         L.sal_oracle_projected_spectra.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, L_, L_, L_, _c_dbl_p]
-        L.sal_oracle_features.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_dbl_p, i]
-        L.sal_oracle_features_at.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_i64_p, L_, _c_dbl_p, i]
+        L.sal_oracle_features.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, i, _c_dbl_p, i]
+        L.sal_oracle_features_at.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, i, _c_i64_p, L_, _c_dbl_p, i]
         L.sal_oracle_center_surround.argtypes = [_c_dbl_p, L_, L_, L_, i, i, _c_int_p, _c_dbl_p, _c_dbl_p, i]
         L.sal_oracle_center_surround_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, _c_int_p, _c_dbl_p,
                                                          _c_dbl_p, _c_dbl_p, _c_dbl_p]
-        L.sal_oracle_features_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, _c_dbl_p, _c_dbl_p, i]
+        L.sal_oracle_features_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, i, _c_dbl_p, _c_dbl_p, i]
         L.sal_oracle_lms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, _c_dbl_p, _c_dbl_p]
         L.sal_oracle_nlms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, ctypes.c_double, _c_dbl_p,
                                       _c_dbl_p]
@@ -101,23 +103,25 @@ def projected_spectra(V, t: int, x: int, y: int, n: int, boundary="symmetric", t
     return out[..., 0] + 1j * out[..., 1]
 
 
-def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
-    """E [3][T][X][Y] (E_t, E_x, E_y) at every voxel."""
+def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, feature="abs") -> np.ndarray:
+    """E [3][T][X][Y] (E_t, E_x, E_y) at every voxel: the mean over the cube's bins of |F_m|
+    (feature "abs", step 3) or of |F_m|^2 (feature "energy")."""
     V = _f64(V)
     E = np.empty((3,) + V.shape, dtype=np.float64)
-    _check(lib().sal_oracle_features(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], _dp(E),
-                                     threads), "features")
+    _check(lib().sal_oracle_features(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], FEATURE[feature],
+                                     _dp(E), threads), "features")
     return E
 
 
-def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
+def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int = 0,
+                feature="abs") -> np.ndarray:
     """E at listed voxels: pts [count][3] -> [count][3]."""
     V = _f64(V)
     pts = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
     out = np.empty((pts.shape[0], 3), dtype=np.float64)
     if pts.shape[0] == 0:
         return out
-    _check(lib().sal_oracle_features_at(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper],
+    _check(lib().sal_oracle_features_at(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], FEATURE[feature],
                                         pts.ctypes.data_as(_c_i64_p), pts.shape[0], _dp(out), threads),
            "features_at")
     return out
@@ -173,7 +177,7 @@ def ext_index(i, N: int, boundary: str):
 
 
 def center_surround_at(V, pts, n: int, offsets, w, boundary="symmetric", taper="rect",
-                       threads: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+                       threads: int = 0, feature="abs") -> Tuple[np.ndarray, np.ndarray]:
     """(E at pts [count][3], raw S at pts [count][3]) computed from V one voxel at a time."""
     pts = np.asarray(pts, dtype=np.int64).reshape(-1, 3)
     shape = np.asarray(V).shape
@@ -183,7 +187,7 @@ def center_surround_at(V, pts, n: int, offsets, w, boundary="symmetric", taper="
     valid = np.all(idx >= 0, axis=-1)
     allp = np.concatenate([pts, np.where(valid[..., None], idx, 0).reshape(-1, 3)], axis=0)
     uniq, inv = np.unique(allp, axis=0, return_inverse=True)
-    Eu = features_at(V, uniq, n, boundary, taper, threads)
+    Eu = features_at(V, uniq, n, boundary, taper, threads, feature)
     Eall = Eu[inv.reshape(-1)]
     Ec = Eall[: len(pts)]                                      # [count][3]
     Enb = Eall[len(pts):].reshape(len(pts), len(w), 3)
@@ -281,12 +285,12 @@ def combine(S3, weights="equal", D=None, delta: float = 1e-6, bounds=None) -> Di
 
 
 def saliency(V, n: int, boundary="symmetric", taper="rect", stencil=None, weights="equal", D=None,
-             delta: float = 1e-6, threads: int = 0, bounds=None) -> Dict[str, np.ndarray]:
+             delta: float = 1e-6, threads: int = 0, bounds=None, feature="abs") -> Dict[str, np.ndarray]:
     """Whole forward pass: E, raw S_m, weights and the consolidated map S."""
     if stencil is None:
         stencil = dcs_stencil()
     offsets, g, did, w = stencil
-    E = features(V, n, boundary, taper, threads)
+    E = features(V, n, boundary, taper, threads, feature)
     S3 = center_surround(E, offsets, w, boundary, threads)
     out = combine(S3, weights, D, delta, bounds)
     out.update({"E": E, "S3": S3})
@@ -336,18 +340,19 @@ def direction_gradient(gw, g, did):
     return galpha
 
 
-def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads: int = 0) -> np.ndarray:
+def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads: int = 0,
+                     feature="abs") -> np.ndarray:
     """gV = (dE/dV)^T gE through the extension (adjoint of the feature step)."""
     V64 = _f64(V)
     gE = _f64(gE)
     gV = np.empty_like(V64)
     _check(lib().sal_oracle_features_adjoint(_dp(V64), *V64.shape, n, BOUNDARY[boundary], TAPER[taper],
-                                             _dp(gE), _dp(gV), threads), "features_adjoint")
+                                             FEATURE[feature], _dp(gE), _dp(gV), threads), "features_adjoint")
     return gV
 
 
 def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", stencil=None, fwd=None,
-                      threads: int = 0) -> Dict[str, np.ndarray]:
+                      threads: int = 0, feature="abs") -> Dict[str, np.ndarray]:
     """Gradients of sum_p gS_p S_p with respect to V, the 3 weights W and the per-direction
     alpha_d, with the min-max bounds of the forward pass held constant."""
     if stencil is None:
@@ -355,9 +360,9 @@ def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", sten
     offsets, g, did, w = stencil
     W = np.asarray(W, dtype=np.float64)
     if fwd is None:
-        fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads)
+        fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads, feature=feature)
     gS3, gW = combine_backward(fwd, W, gS)
     gE, gw = center_surround_adjoint(fwd["E"], gS3, offsets, w, boundary)
     galpha = direction_gradient(gw, g, did)
-    gV = features_adjoint(V, gE, n, boundary, taper, threads)
+    gV = features_adjoint(V, gE, n, boundary, taper, threads, feature)
     return {"gV": gV, "gW": gW, "galpha": galpha, "gE": gE, "gS3": gS3, "gw": gw}

@@ -11,7 +11,8 @@
  *     Eq. 2 (separable DFT K = D_t (x) D_x (x) D_y applied to the cube C_n);
  *   - spectral projection F_m = F * P_m / sqrt(i^2+j^2+k^2): Eq. 1, with the
  *     zero-frequency bin left out (Sec. 2, text after Eq. 2);
- *   - feature E_m = mean over the cube's bins of |F_m| (Sec. 2 step 3);
+ *   - feature E_m = mean over the cube's bins of |F_m| (Sec. 2 step 3), or, as the alternative
+ *     reading of that garbled step, the mean of |F_m|^2 (the projected spectral energy);
  *   - directional center-surround S_m (Eq. 3);
  *   - sequential LMS / NLMS / RLS weight adaptation (Sec. 2, text around Eq. 4);
  *   - the analytic adjoints of the feature and center-surround steps (used to
@@ -20,7 +21,8 @@
  * Readings of points the paper leaves open (all configurable by argument):
  *   window offsets u in [-n/2, n/2-1] per axis around the voxel (stride 1);
  *   signed bin index i = k for k < n/2, else k - n;  i <-> f_t, j <-> f_x, k <-> f_y;
- *   E_m = (1/n^3) * sum over bins k != 0 of r_m(k) |F[k]|;
+ *   E_m = (1/n^3) * sum over bins k != 0 of r_m(k) |F[k]|  (feature 0), or
+ *   E_m = (1/n^3) * sum over bins k != 0 of r_m(k)^2 |F[k]|^2  (feature 1, energy);
  *   borders: symmetric (edge sample repeated), periodic or zero extension.
  */
 #include <math.h>
@@ -175,8 +177,9 @@ static void local_spectrum(const double* V, long T, long X, long Y, int n, int m
             }
 }
 
-/* Step 2 + 3: E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]|  (Eq. 1, DC excluded). */
-static void features_from_spectrum(const work_t* W, double E[3]) {
+/* Step 2 + 3: E_m = (1/n^3) sum_{k != 0} |F_m[k]| with F_m = r_m F (Eq. 1, DC excluded); with
+   feature 1 the squared magnitude |F_m[k]|^2 = r_m(k)^2 |F[k]|^2 is averaged instead. */
+static void features_from_spectrum(const work_t* W, int feature, double E[3]) {
     const int n = W->n;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int kt = 0; kt < n; ++kt)
@@ -185,8 +188,11 @@ static void features_from_spectrum(const work_t* W, double E[3]) {
                 if (kt == 0 && kx == 0 && ky == 0) continue;
                 int i = signed_bin(kt, n), j = signed_bin(kx, n), k = signed_bin(ky, n);
                 size_t b = IDX3(kt, kx, ky, n);
-                double mag = sqrt(W->fre[b] * W->fre[b] + W->fim[b] * W->fim[b]);
-                for (int m = 0; m < 3; ++m) acc[m] += proj_ratio(m, i, j, k) * mag;
+                double mag2 = W->fre[b] * W->fre[b] + W->fim[b] * W->fim[b];
+                for (int m = 0; m < 3; ++m) {
+                    double r = proj_ratio(m, i, j, k);
+                    acc[m] += feature == 1 ? r * r * mag2 : r * sqrt(mag2);
+                }
             }
     double inv = 1.0 / ((double)n * n * n);
     for (int m = 0; m < 3; ++m) E[m] = acc[m] * inv;
@@ -237,10 +243,11 @@ int sal_oracle_projected_spectra(const double* V, long T, long X, long Y, int n,
 }
 
 /* Features E [3][T][X][Y] of every voxel. */
-int sal_oracle_features(const double* V, long T, long X, long Y, int n, int mode, int taper,
+int sal_oracle_features(const double* V, long T, long X, long Y, int n, int mode, int taper, int feature,
                         double* E, int nthreads) {
     int rc = check_common(T, X, Y, n, mode);
     if (rc) return rc;
+    if (feature < 0 || feature > 1) return -5;
     const long N = T * X * Y;
     int fail = 0;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
@@ -257,7 +264,7 @@ int sal_oracle_features(const double* V, long T, long X, long Y, int n, int mode
             long t = p / (X * Y), x = (p / Y) % X, y = p % Y;
             double e[3];
             local_spectrum(V, T, X, Y, n, mode, taper, t, x, y, &W);
-            features_from_spectrum(&W, e);
+            features_from_spectrum(&W, feature, e);
             for (int m = 0; m < 3; ++m) E[m * N + p] = e[m];
         }
         work_free(&W);
@@ -266,10 +273,11 @@ int sal_oracle_features(const double* V, long T, long X, long Y, int n, int mode
 }
 
 /* Features at listed voxels: pts [count][3] (t,x,y) -> Eout [count][3]. */
-int sal_oracle_features_at(const double* V, long T, long X, long Y, int n, int mode, int taper,
+int sal_oracle_features_at(const double* V, long T, long X, long Y, int n, int mode, int taper, int feature,
                            const int64_t* pts, long count, double* Eout, int nthreads) {
     int rc = check_common(T, X, Y, n, mode);
     if (rc) return rc;
+    if (feature < 0 || feature > 1) return -5;
     int fail = 0;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
     {
@@ -283,7 +291,7 @@ int sal_oracle_features_at(const double* V, long T, long X, long Y, int n, int m
         for (long s = 0; s < count; ++s) {
             if (!ok) continue;
             local_spectrum(V, T, X, Y, n, mode, taper, pts[3 * s], pts[3 * s + 1], pts[3 * s + 2], &W);
-            features_from_spectrum(&W, &Eout[3 * s]);
+            features_from_spectrum(&W, feature, &Eout[3 * s]);
         }
         work_free(&W);
     }
@@ -351,16 +359,18 @@ int sal_oracle_center_surround_adjoint(const double* E, long T, long X, long Y, 
 
 /*
  * Adjoint of the feature step.  For each voxel p, with F_p recomputed,
- *   U[k] = (1/n^3) (sum_m gE_m[p] r_m(k)) F_p[k] / |F_p[k]|
+ *   U[k] = (1/n^3) (sum_m gE_m[p] r_m(k)) F_p[k] / |F_p[k]|       (feature 0), or
+ *   U[k] = (2/n^3) (sum_m gE_m[p] r_m(k)^2) F_p[k]                 (feature 1, energy)
  *   (0 at DC and where |F| <= 2^-19 sum_u |h(u) Vext[p+u-n/2]|, the zero subgradient of |F|),
  *   gVext[p + u - n/2] += h(u) Re sum_k U[k] exp(+2 pi i k.u / n),
  * then the extension is folded back onto V (zero extension drops).  gV [T][X][Y] is
  * overwritten.  Per-thread accumulators are summed in thread order.
  */
-int sal_oracle_features_adjoint(const double* V, long T, long X, long Y, int n, int mode, int taper,
+int sal_oracle_features_adjoint(const double* V, long T, long X, long Y, int n, int mode, int taper, int feature,
                                 const double* gE, double* gV, int nthreads) {
     int rc = check_common(T, X, Y, n, mode);
     if (rc) return rc;
+    if (feature < 0 || feature > 1) return -5;
     const long N = T * X * Y;
     const int h2 = n / 2;
     const size_t n3 = (size_t)n * n * n;
@@ -401,11 +411,21 @@ int sal_oracle_features_adjoint(const double* V, long T, long X, long Y, int n, 
                         size_t b = IDX3(kt, kx, ky, n);
                         double mag = sqrt(W.fre[b] * W.fre[b] + W.fim[b] * W.fim[b]);
                         ure[b] = uim[b] = 0.0;
-                        if ((kt == 0 && kx == 0 && ky == 0) || mag <= thr) continue;
+                        if (kt == 0 && kx == 0 && ky == 0) continue;
                         int i = signed_bin(kt, n), j = signed_bin(kx, n), k = signed_bin(ky, n);
                         double c = 0.0;
-                        for (int m = 0; m < 3; ++m) c += ge[m] * proj_ratio(m, i, j, k);
-                        c /= (double)n3 * mag;
+                        if (feature == 1) {
+                            /* d |F|^2 / d(Re F, Im F) = 2 (Re F, Im F): smooth, no kink */
+                            for (int m = 0; m < 3; ++m) {
+                                double r = proj_ratio(m, i, j, k);
+                                c += ge[m] * r * r;
+                            }
+                            c *= 2.0 / (double)n3;
+                        } else {
+                            if (mag <= thr) continue;
+                            for (int m = 0; m < 3; ++m) c += ge[m] * proj_ratio(m, i, j, k);
+                            c /= (double)n3 * mag;
+                        }
                         ure[b] = c * W.fre[b];
                         uim[b] = c * W.fim[b];
                     }
