@@ -44,6 +44,7 @@ WORKLOADS = {
 }
 # Peak of the binding pipe of K1 (FP32 SIMT form): 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FMA_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12   # FMA-pipe operations per second (an FFMA counts once)
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
 K1_TRAFFIC = {("salt128", 16, "fp32"): 8451840,   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
@@ -70,11 +71,13 @@ def bins_per_voxel(n: int) -> int:
     return (n // 2 + 1) * n * n
 
 
-def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt"):
+def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt", feature="abs"):
     """Roofline of a spectral kernel.  FP32 form: its contraction flops (the per-voxel figure
     4hn + 8hn^2 + 8hn^3, x2 for the adjoint) on the FP32 FMA pipe.  BF16/FP16 form: the
     contraction runs on the tensor cores (reported as `tensor`), and the binding pipe is the
-    abs(F) epilogue, h n^2 square roots per voxel on the MUFU pipe."""
+    abs(F) epilogue, h n^2 square roots per voxel on the MUFU pipe; with the energy reading of the
+    feature there is no root, and the epilogue's FP32 arithmetic (about 4 FMA-pipe operations per
+    bin: |F|^2 and its share of the weighted sums) on the FMA pipe binds."""
     flops = flops_mult * k1_flops_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     if prec == "fp32":
         return {"kernel": kernel, "bound": "alu", "pipe": "fp32 fma", "achieved": flops, "peak": FP32_PEAK_TFLOPS,
@@ -82,12 +85,19 @@ def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt"):
                 "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
     bins = bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     tpk = measured_peaks().get("bf16_tflops", 1900.0)
+    tensor = {"achieved_tflops": flops, "peak_tflops": tpk, "frac": flops / tpk,
+              "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}
+    if feature == "energy":
+        ops = 4.0 * bins
+        return {"kernel": kernel, "bound": "alu", "pipe": "FP32 FMA (energy epilogue: ~4 operations per bin)",
+                "achieved": ops, "peak": FMA_OPS_PEAK, "unit": "Tops/s", "frac": ops / FMA_OPS_PEAK,
+                "traffic": traffic, "peak_note": "FMA pipe 128 ops/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
+                "tensor": tensor}
     what = "abs(F) epilogue: one sqrt per bin" if mufu_op == "sqrt" else "Gamma epilogue: one rsqrt per bin"
     return {"kernel": kernel, "bound": "alu", "pipe": f"MUFU ({what})", "achieved": bins,
             "peak": MUFU_PEAK_TOPS, "unit": f"T{mufu_op}/s", "frac": bins / MUFU_PEAK_TOPS, "traffic": traffic,
             "peak_note": "MUFU 16/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
-            "tensor": {"achieved_tflops": flops, "peak_tflops": tpk, "frac": flops / tpk,
-                       "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}}
+            "tensor": tensor}
 
 
 def max_over_ranks(values, dist=None, device="cpu"):
@@ -156,7 +166,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(V, n, sample, backward=True):  # noqa: C901
+def cpu_oracle_rate(V, n, sample, backward=True, feature="abs"):  # noqa: C901
     """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host
     cores): forward, and the backward with the same fixed upstream gradient as the GPU step."""
     import numpy as np
@@ -165,9 +175,9 @@ def cpu_oracle_rate(V, n, sample, backward=True):  # noqa: C901
     sub = np.ascontiguousarray(V[:sample, :sample, :sample])
     gS = _upstream(sub.shape)
     t0 = time.perf_counter()
-    fwd = oracle.saliency(sub, n)
+    fwd = oracle.saliency(sub, n, feature=feature)
     if backward:
-        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd)
+        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd, feature=feature)
     dt = time.perf_counter() - t0
     return sub.size / dt / 1e6, dt, sub.shape
 
@@ -181,7 +191,7 @@ def sampled_error(V, n, params, E, S3, count=48, seed=7):
     import synth
     st = oracle.dcs_stencil(params.directions, params.R, params.sigma)
     pts = synth.sample_points(V.shape, count, seed=seed)
-    Ec, Sc = oracle.center_surround_at(V, pts, n, st[0], st[3])
+    Ec, Sc = oracle.center_surround_at(V, pts, n, st[0], st[3], feature=params.feature)
     Eg = E.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
     Sg = S3.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -205,10 +215,10 @@ def run_reference(args, wl):
     s = wl["ref_sample"]
     bwd = getattr(args, "form", "fwdbwd") == "fwdbwd"
     for _ in range(args.warmup):
-        cpu_oracle_rate(V, wl["n"], s, backward=bwd)
+        cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature)
     times = []
     for _ in range(args.steps):
-        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd)
+        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature)
         times.append(dt)
     vox = s ** 3
     value = vox * args.steps / sum(times) / 1e6
@@ -217,7 +227,7 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": wl["n"], "shape": list(V.shape), "precision": "fp64 oracle",
-                       "form": "forward+backward"},
+                       "form": "forward+backward" if bwd else "forward", "feature": args.feature},
             "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": cores, "kind": "oracle",
                              "sample": f"{s}^3 corner sub-volume of the workload per step, FP64 forward+backward"},
             "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -237,6 +247,8 @@ def main():
     ap.add_argument("--form", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwdbwd: forward + backward step (default); fwd: forward only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--feature", default="abs", choices=["abs", "energy"],
+                    help="E_m: mean of |F_m| (the paper's step 3) or of |F_m|^2 (energy reading)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:
@@ -270,7 +282,7 @@ def main():
 
     V, _ = synth.volume(wl["spec"], with_mask=False)
     nvox = V.size
-    params = sal.Params(n=wl["n"], prec=args.prec)
+    params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature)
     eng = sal.Saliency(V.shape, params)
     dev = torch.device("cuda", local_rank)
     Vd = torch.from_numpy(V).to(dev)
@@ -368,7 +380,7 @@ def main():
     # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
     k1_fp32_ms = None
     if args.prec != "fp32":
-        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32"))
+        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature))
         E32 = torch.empty_like(E)
         for _ in range(3):
             sal.sal_local_spectra_project(eng32.h, Vd, E32)
@@ -391,12 +403,13 @@ def main():
     # K1 in the forward-only form
     k1_ms = per_call[names.index("k1_local_spectra_project")] / args.steps
     tag = "tc" if args.prec != "fp32" else "f32"
-    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1, K1_TRAFFIC.get((args.workload, n, args.prec)))
+    trk = (args.workload, n, args.prec) if args.feature == "abs" else None
+    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature)
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
         rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
-                      2, K5_TRAFFIC.get((args.workload, n, args.prec)), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt")
+                      2, K5_TRAFFIC.get(trk), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt", feature=args.feature)
         rl["k1"] = k1_rl
     else:
         rl = k1_rl
@@ -409,6 +422,7 @@ def main():
                                              "tensor-core operands are FP16" if args.prec != "fp32" else " SIMT"),
                    "form": "forward+backward (upstream gradient fixed, seeded)" if args.form == "fwdbwd"
                    else "forward",
+                   "feature": "mean of |F_m| (step 3)" if args.feature == "abs" else "mean of |F_m|^2 (energy reading)",
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "forward": {"value": world * nvox * args.steps / (fwd_ms / 1e3) / 1e6, "unit": "Mvoxel/s",
@@ -427,7 +441,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = wl["cpu_sample"]
-        rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd")
+        rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd", feature=args.feature)
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{s}^3 corner sub-volume of the workload, FP64 "
                                           f"{'forward+backward' if args.form == 'fwdbwd' else 'forward'}, {dt:.1f} s",

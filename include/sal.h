@@ -63,7 +63,10 @@ typedef struct {
     int stride;             /* window stride; must be 1 (a cube around every voxel)   */
     int taper;              /* 0 = rectangular (the cube as is), 1 = periodic Hann    */
     int boundary;           /* sal_boundary                                           */
-    int feature;            /* 0 = E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (step 3)  */
+    int feature;            /* 0 = E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (step 3: the mean
+                               of |F_m| over the cube's bins); 1 = E_m = (1/n^3) sum_{k != 0}
+                               r_m(k)^2 |F[k]|^2 (the mean of |F_m|^2, the energy reading of
+                               that garbled step); both forward and backward, all precisions */
     /* Directional center-surround window (Eq. 3, Fig. 4): Q = n_offsets neighbours
        o = (dt,dx,dy), |dt|,|dx|,|dy| <= 8, with weight w_o = alpha[dir_id[o]] * gauss_w[o].
        Host pointers; copied by sal_create. */

@@ -24,7 +24,6 @@
 namespace sal {
 namespace {
 
-using f32::fast_rsqrt;
 using f32::Tw;
 
 constexpr float kKinkTau = 1.0f / 524288.0f;  // zero-subgradient level of |F| relative to the window L1 norm
@@ -54,7 +53,8 @@ template <int N> struct BGeo {
     static_assert(BY % YC == 0 && NT <= 1024, "geometry");
 };
 
-template <int N>
+// EN: the energy reading of the feature (Gamma = 2 rho F, no kink band)
+template <int N, bool EN>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                        int T, int X, int Y, int bnd, int t_begin, const __grid_constant__ Tw<N> tw) {
@@ -104,7 +104,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const int row = tid % ROWS;
     const int ych = tid / ROWS;
     float wt[3][H];
-    B::row_weights(row, wt);
+    B::template row_weights<EN>(row, wt);
 #pragma unroll
     for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
     const float2* grow = s_g2 + (size_t)row * YH;
@@ -136,7 +136,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             const float rho = fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
             if (k == 0 || 2 * k == N) {
                 const float m2 = fmaf(pr[k], pr[k], pi[k] * pi[k]);
-                const float sc = m2 > thr2 ? rho * fast_rsqrt(m2) : 0.f;
+                const float sc = f32::bin_adjoint_scale<EN>(rho, m2, thr2);
                 ar[k] = sc * pr[k];
                 ai[k] = sc * pi[k];
                 br[k] = bi[k] = 0.f;
@@ -144,8 +144,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
                 const float fr = pr[k] + qi[k], fi = pi[k] - qr[k];   // F[k]
                 const float hr = pr[k] - qi[k], hi = pi[k] + qr[k];   // F[n-k]
                 const float m2a = fmaf(fr, fr, fi * fi), m2b = fmaf(hr, hr, hi * hi);
-                const float sa = m2a > thr2 ? rho * fast_rsqrt(m2a) : 0.f;
-                const float sb = m2b > thr2 ? rho * fast_rsqrt(m2b) : 0.f;
+                const float sa = f32::bin_adjoint_scale<EN>(rho, m2a, thr2);
+                const float sb = f32::bin_adjoint_scale<EN>(rho, m2b, thr2);
                 const float gar = sa * fr, gai = sa * fi, gbr = sb * hr, gbi = sb * hi;
                 ar[k] = gar + gbr;
                 ai[k] = gai + gbi;
@@ -248,16 +248,24 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
 
 template <int N>
 cudaError_t prepare_n() {
-    return cudaFuncSetAttribute(k5_spectra_adjoint_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BGeo<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)BGeo<N>::SMEM);
 }
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const float* V, const float* gE, float* blocks, int T, int X, int Y,
-                     int bnd, int t_begin, int t_count, cudaStream_t s) {
+                     int bnd, int feat, int t_begin, int t_count, cudaStream_t s) {
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
-    k5_spectra_adjoint_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, f32::make_tw<N>(t));
+    if (feat == 1)
+        k5_spectra_adjoint_f32<N, true><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
+                                                                    f32::make_tw<N>(t));
+    else
+        k5_spectra_adjoint_f32<N, false><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
+                                                                     f32::make_tw<N>(t));
     note_launches(1);
     return cudaGetLastError();
 }
@@ -285,12 +293,13 @@ SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
 }
 
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
-                                       int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s) {
+                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_count,
+                                       cudaStream_t s) {
     switch (n) {
-        case 2: return launch_n<2>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
-        case 4: return launch_n<4>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
-        case 8: return launch_n<8>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
-        case 16: return launch_n<16>(tw, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, s);
+        case 2: return launch_n<2>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, s);
+        case 4: return launch_n<4>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, s);
+        case 8: return launch_n<8>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, s);
+        case 16: return launch_n<16>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -6,8 +6,9 @@
 //     brick by brick, never stored;
 //   Gamma (epilogue from tensor memory): Gamma[k] = (sum_m gE_m wt_m(k)) F[k]/|F[k]| -- the gradient of
 //     L = sum gE . E with respect to (Re F, Im F) -- with the zero subgradient where |F| <= 2^-19 of the
-//     window's L1 norm; rounded to FP16 (scaled by sigma = n^3 / (8 max|gE|)) into the operand
-//     [(x0, k_x)][(re | im, k_y)] of one output;
+//     window's L1 norm (the energy reading: Gamma[k] = 2 (sum_m gE_m wt_m(k)) F[k], wt holding r_m^2);
+//     rounded to FP16 (scaled by sigma = n^3 / (8 max|gE|)) into the operand [(x0, k_x)][(re | im, k_y)]
+//     of one output;
 //   adjoint of stage 3 (y): Gamma of bins k and n - k folded into pair coefficients (A = G[k] + G[n-k],
 //     B = G[k] - G[n-k]; the twiddles of n - k are those of k with the sine negated):
 //       dG2r[y] = sum_y0 [A_r | B_i] Tinv_re(y - y0),  Tinv_re = [c_k | -s_k],
@@ -93,10 +94,10 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
 // with kk = K for n = 16; for n = 8 the operand holds both parts in one K = 16 row ([re | im], 8 each), so
 // the re table is zero in K 8..15 and the im table holds its entries at K = 8 + kk (zero below).
 template <int N>
-__global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out) {
+__global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out, int feat) {
     using G = BtGeo<N>;
     constexpr int H = G::H;
-    tcs::build_fwd_tables<N, kFmt>(tw, out, threadIdx.x, blockDim.x);
+    tcs::build_fwd_tables<N, kFmt>(tw, out, threadIdx.x, blockDim.x, feat);
     unsigned char* tre = out + G::TAB_TRE;
     unsigned char* tim = out + G::TAB_TIM;
     for (int i = threadIdx.x; i < kTR * 16; i += blockDim.x) {
@@ -123,7 +124,10 @@ __global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __
     }
 }
 
-template <int N>
+// EN: the energy reading of the feature: Gamma = 2 rho F (no kink band).  The operand holds
+// sigma (2 / n^3) rho F of the staged brick (whose |F| is at most n^3, so the FP16 operand stays in the
+// range of the feature's unit directions) and the block is scaled back by n^3 max|V| / sigma.
+template <int N, bool EN>
 __global__ void __launch_bounds__(kThreads, 1)
 k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                       int T, int X, int Y, int bnd, int t_begin, const unsigned char* __restrict__ tables,
@@ -186,11 +190,14 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     if (lane == 0) s_red[32 + warp] = gmax;
     const float scale = tcs::stage_brick<N, kFmt, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid);
-    (void)scale;   // the direction F/|F| and the adjoint stages do not depend on the brick scale
+    // the direction F/|F| does not depend on the brick scale; the energy's Gamma = 2 rho F does (F of the
+    // unscaled brick = scale x F of the staged one): that factor is applied to the block at the end
     float bgmax = 0.f;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) bgmax = fmaxf(bgmax, s_red[32 + w]);
     const float sigma = bgmax > 0.f ? (float)(N * N * N) / (8.f * bgmax) : 1.f;   // Gamma operand scale
+    // per-bin factor of the operand: sigma rho / |F| (feature), sigma (2 / n^3) rho (energy)
+    const float sigma_op = EN ? sigma * (2.f / (float)(N * N * N)) : sigma;
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -457,13 +464,14 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                         float rho[H];
 #pragma unroll
                         for (int k = 0; k < H; ++k)
-                            rho[k] = sigma * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
+                            rho[k] = sigma_op * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
                         float gr[N], gim[N];
 #pragma unroll
                         for (int ky = 0; ky < N; ++ky) {
                             const float re = v[o * G::N3 + ky], im = v[o * G::N3 + N + ky];
                             const float m2 = fmaf(re, re, im * im);
-                            const float sc = m2 > thr2 ? rho[ky <= N / 2 ? ky : N - ky] * fast_rsqrt(m2) : 0.f;
+                            const float r = rho[ky <= N / 2 ? ky : N - ky];
+                            const float sc = EN ? r : (m2 > thr2 ? r * fast_rsqrt(m2) : 0.f);
                             gr[ky] = sc * re;
                             gim[ky] = sc * im;
                         }
@@ -539,7 +547,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         ok = cwait(13);
         const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         float* blk = blocks + cta * G::BLOCK_FLOATS;
-        const float out_scale = 1.f / (sigma * kDxScale);
+        const float out_scale = EN ? (float)(N * N * N) * scale / (sigma * kDxScale) : 1.f / (sigma * kDxScale);
         for (int i = grp; i < G::NB1; i += 4) {
             float v[16];
             if (ok) tc::tmem_ld16(tmem + lane_base + kColT + (uint32_t)(16 * i), v);
@@ -557,25 +565,32 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 
 template <int N>
 cudaError_t prepare_n() {
-    return cudaFuncSetAttribute(k5_spectra_adjoint_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k5_spectra_adjoint_tc<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BtGeo<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k5_spectra_adjoint_tc<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)BtGeo<N>::SMEM);
 }
 
 template <int N>
-cudaError_t tables_n(const TwiddleTable& t, void* dst, cudaStream_t s) {
-    k5_tc_tables<N><<<1, 256, 0, s>>>(f32::make_tw<N>(t), static_cast<unsigned char*>(dst));
+cudaError_t tables_n(const TwiddleTable& t, int feat, void* dst, cudaStream_t s) {
+    k5_tc_tables<N><<<1, 256, 0, s>>>(f32::make_tw<N>(t), static_cast<unsigned char*>(dst), feat);
     note_launches(1);
     return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const void* tables, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int t_begin, int t_count, int* err, cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_count, int* err, cudaStream_t s) {
     using G = BtGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, t_count);
-    k5_spectra_adjoint_tc<N><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                             static_cast<const unsigned char*>(tables),
-                                                             f32::make_tw<N>(t), err);
+    const unsigned char* tab = static_cast<const unsigned char*>(tables);
+    if (feat == 1)
+        k5_spectra_adjoint_tc<N, true><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, tab,
+                                                                       f32::make_tw<N>(t), err);
+    else
+        k5_spectra_adjoint_tc<N, false><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, tab,
+                                                                        f32::make_tw<N>(t), err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -595,9 +610,9 @@ size_t spectra_adjoint_tc_tables_bytes(int n) {
     return 0;
 }
 
-cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, void* dst, cudaStream_t s) {
-    if (n == 8) return tables_n<8>(tw, dst, s);
-    if (n == 16) return tables_n<16>(tw, dst, s);
+cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, int feat, void* dst, cudaStream_t s) {
+    if (n == 8) return tables_n<8>(tw, feat, dst, s);
+    if (n == 16) return tables_n<16>(tw, feat, dst, s);
     return cudaErrorInvalidValue;
 }
 
@@ -608,11 +623,11 @@ SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n) {
 }
 
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
-                                      const float* gE, float* blocks, int T, int X, int Y, int bnd, int t_begin,
-                                      int t_count, int* err, cudaStream_t s) {
+                                      const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
+                                      int t_begin, int t_count, int* err, cudaStream_t s) {
     if (fmt != 0) return cudaErrorInvalidValue;
-    if (n == 8) return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, err, s);
-    if (n == 16) return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, t_begin, t_count, err, s);
+    if (n == 8) return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, err, s);
+    if (n == 16) return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, err, s);
     return cudaErrorInvalidValue;
 }
 

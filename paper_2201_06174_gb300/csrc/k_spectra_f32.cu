@@ -10,15 +10,15 @@
 // Hermitian symmetry of a real cube keeps only k_t in [0, n/2] (multiplicity 2 for
 // 0 < k_t < n/2).  Each one-axis DFT pairs bins k and n-k: with P = sum g cos, Q = sum g sin,
 // F[k] = P - iQ and F[n-k] = P + iQ, which halves the multiplies.
-// Stage 3 is fused with the feature epilogue: |F| per bin, weighted by the projection ratios
-// r_m(k) of Eq. 1 (zero at DC), summed over k_y in registers and over (k_t,k_x) rows through
+// Stage 3 is fused with the feature epilogue: |F| per bin (|F|^2 for the energy reading), weighted by
+// the projection ratios r_m(k) of Eq. 1 (r_m^2 for the energy; zero at DC), summed over k_y in registers and over (k_t,k_x) rows through
 // shared memory in a fixed order.  Per-voxel spectra never leave the SM.
 #include "spectra_f32_common.cuh"
 
 namespace sal {
 namespace {
 
-using f32::fast_sqrt;
+using f32::bin_mag;
 using f32::Tw;
 
 template <int N> struct Cfg;
@@ -43,7 +43,7 @@ template <int N> struct Geo {
     static_assert(NT <= 1024, "threads");
 };
 
-template <int N>
+template <int N, bool EN>
 __global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
 k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
                const __grid_constant__ Tw<N> tw) {
@@ -71,8 +71,8 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     // ---- stage 3 + projection/feature epilogue ----------------------------------------------
     const int row = tid % ROWS;           // (k_t, k_x)
     const int ych = tid / ROWS;           // chunk of YC outputs
-    float wt[3][H];                       // r_m(k_t,k_x,+-k_y) * multiplicity / n^3
-    B::row_weights(row, wt);
+    float wt[3][H];                       // r_m(k_t,k_x,+-k_y) (r_m^2: energy) * multiplicity / n^3
+    B::template row_weights<EN>(row, wt);
     const float2* grow = s_g2 + (size_t)row * YH;
     for (int yl = ych * YC; yl < ych * YC + YC; ++yl) {
         float pr[H], pi[H], qr[H], qi[H];
@@ -96,11 +96,11 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
         for (int k = 0; k < H; ++k) {
             float a;
             if (k == 0 || 2 * k == N) {
-                a = fast_sqrt(fmaf(pr[k], pr[k], pi[k] * pi[k]));
+                a = bin_mag<EN>(fmaf(pr[k], pr[k], pi[k] * pi[k]));
             } else {
                 const float ar = pr[k] + qi[k], ai = pi[k] - qr[k];   // F[k]   = P - iQ
                 const float br = pr[k] - qi[k], bi = pi[k] + qr[k];   // F[n-k] = P + iQ
-                a = fast_sqrt(fmaf(ar, ar, ai * ai)) + fast_sqrt(fmaf(br, br, bi * bi));
+                a = bin_mag<EN>(fmaf(ar, ar, ai * ai)) + bin_mag<EN>(fmaf(br, br, bi * bi));
             }
             e0 = fmaf(wt[0][k], a, e0);
             e1 = fmaf(wt[1][k], a, e1);
@@ -129,16 +129,22 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
 
 template <int N>
 cudaError_t prepare() {
-    return cudaFuncSetAttribute(k1_spectra_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k1_spectra_f32<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k1_spectra_f32<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo<N>::SMEM);
 }
 
 template <int N>
-cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd,
+cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
                    cudaStream_t s) {
     using G = Geo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, T);
-    k1_spectra_f32<N><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    if (feat == 1)
+        k1_spectra_f32<N, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    else
+        k1_spectra_f32<N, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
     note_launches(1);
     return cudaGetLastError();
 }
@@ -158,13 +164,13 @@ cudaError_t spectra_f32_prepare(int n) {
 }
 
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, cudaStream_t s) {
+                               int Y, int bnd, int feat, cudaStream_t s) {
     if (T > 65535 || X > 65535) return cudaErrorInvalidConfiguration;
     switch (n) {
-        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, s);
-        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, s);
-        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, s);
-        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, s);
+        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, s);
+        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, s);
+        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, s);
+        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, s);
         default: return cudaErrorInvalidValue;
     }
 }

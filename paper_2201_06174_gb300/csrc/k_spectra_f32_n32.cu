@@ -13,7 +13,7 @@
 namespace sal {
 namespace {
 
-using f32::fast_sqrt;
+using f32::bin_mag;
 using f32::Tw;
 
 constexpr int N = 32, H = N / 2 + 1, BY = 8, YH = BY + N - 1, NT = 256;
@@ -22,6 +22,7 @@ constexpr size_t G_B = (size_t)N * YH * 8;
 constexpr size_t WT_B = (size_t)N * H * 3 * 4;
 constexpr size_t SMEM = IN_B + 2 * G_B + WT_B;
 
+template <bool EN>
 __global__ void __launch_bounds__(NT, 1)
 k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
                    const __grid_constant__ Tw<N> tw) {
@@ -59,14 +60,8 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
             const int k = i % H, x = i / H;
             const int ii = kt, j = x < N / 2 ? x : x - N;
             const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-            const float r2 = (float)(ii * ii + j * j + k * k);
-            float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-            if (r2 > 0.f) {
-                const float inv = mult / (float)(N * N * N) / sqrtf(r2);
-                w0 = sqrtf((float)(j * j + k * k)) * inv;
-                w1 = sqrtf((float)(ii * ii + k * k)) * inv;
-                w2 = sqrtf((float)(ii * ii + j * j)) * inv;
-            }
+            float w0, w1, w2;
+            f32::bin_weights<EN>(ii, j, k, mult / (float)(N * N * N), w0, w1, w2);
             s_wt[i * 3 + 0] = w0;
             s_wt[i * 3 + 1] = w1;
             s_wt[i * 3 + 2] = w2;
@@ -131,11 +126,11 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
             for (int k = 0; k < H; ++k) {
                 float a;
                 if (k == 0 || 2 * k == N) {
-                    a = fast_sqrt(fmaf(pr[k], pr[k], pi[k] * pi[k]));
+                    a = bin_mag<EN>(fmaf(pr[k], pr[k], pi[k] * pi[k]));
                 } else {
                     const float ar = pr[k] + qi[k], ai = pi[k] - qr[k];
                     const float br = pr[k] - qi[k], bi = pi[k] + qr[k];
-                    a = fast_sqrt(fmaf(ar, ar, ai * ai)) + fast_sqrt(fmaf(br, br, bi * bi));
+                    a = bin_mag<EN>(fmaf(ar, ar, ai * ai)) + bin_mag<EN>(fmaf(br, br, bi * bi));
                 }
                 e0 = fmaf(w[k * 3 + 0], a, e0);
                 e1 = fmaf(w[k * 3 + 1], a, e1);
@@ -161,13 +156,19 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
 }  // namespace
 
 cudaError_t spectra_f32_n32_prepare() {
-    return cudaFuncSetAttribute(k1_spectra_f32_n32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k1_spectra_f32_n32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k1_spectra_f32_n32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
 }
 
 cudaError_t spectra_f32_n32_launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd,
-                                   cudaStream_t s) {
+                                   int feat, cudaStream_t s) {
     dim3 grid((Y + BY - 1) / BY, X, T);
-    k1_spectra_f32_n32<<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    if (feat == 1)
+        k1_spectra_f32_n32<true><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    else
+        k1_spectra_f32_n32<false><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
     note_launches(1);
     return cudaGetLastError();
 }

@@ -15,7 +15,7 @@
 namespace sal {
 namespace {
 
-using f32::fast_sqrt;
+using f32::bin_mag;
 using f32::Tw;
 using tcs::kBY;
 using tcs::kK2;
@@ -38,11 +38,12 @@ template <int N> struct TcGeo : tcs::FwdGeo<N> {
 };
 
 template <int N, int FMT>
-__global__ void k1_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out) {
-    tcs::build_fwd_tables<N, FMT>(tw, out, threadIdx.x, blockDim.x);
+__global__ void k1_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __restrict__ out, int feat) {
+    tcs::build_fwd_tables<N, FMT>(tw, out, threadIdx.x, blockDim.x, feat);
 }
 
-template <int N, int FMT>
+// EN: the energy reading of the feature (|F|^2 per bin; the weight table then holds r_m^2)
+template <int N, int FMT, bool EN>
 __global__ void __launch_bounds__(kThreads, 2)
 k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
               const unsigned char* __restrict__ tables, int* __restrict__ err) {
@@ -238,10 +239,10 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
 #pragma unroll
                             for (int k = 0; k < H; ++k) {
                                 const float re = v[o * G::N3 + k], im = v[o * G::N3 + N + k];
-                                float sm = fast_sqrt(fmaf(re, re, im * im));
+                                float sm = bin_mag<EN>(fmaf(re, re, im * im));
                                 if (k != 0 && 2 * k != N) {
                                     const float re2 = v[o * G::N3 + N - k], im2 = v[o * G::N3 + 2 * N - k];
-                                    sm += fast_sqrt(fmaf(re2, re2, im2 * im2));
+                                    sm += bin_mag<EN>(fmaf(re2, re2, im2 * im2));
                                 }
                                 e0 = fmaf(wt[0][k], sm, e0);
                                 e1 = fmaf(wt[1][k], sm, e1);
@@ -271,6 +272,7 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     const size_t NV = (size_t)T * X * Y;
     const int x = xb + x0l;
     const bool good = *s_fail == 0 && warp < kConsumers;   // the producer warp holds no results
+    const float out_scale = EN ? scale * scale : scale;     // the features of the unscaled brick
 #pragma unroll
     for (int pass = 0; pass < G::PASSES; ++pass)
 #pragma unroll
@@ -285,7 +287,7 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
 #pragma unroll
                     for (int w = 1; w < N; w <<= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
                     const int y = yb + y0;
-                    if (kx == 0 && x < X && y < Y && good) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * scale;
+                    if (kx == 0 && x < X && y < Y && good) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
                 }
             }
     tc::fence_before_sync();
@@ -295,24 +297,30 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
 
 template <int N, int FMT>
 cudaError_t prepare_nf() {
-    return cudaFuncSetAttribute(k1_spectra_tc<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k1_spectra_tc<N, FMT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcGeo<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k1_spectra_tc<N, FMT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TcGeo<N>::SMEM);
 }
 
 template <int N, int FMT>
-cudaError_t tables_nf(const TwiddleTable& t, void* dst, cudaStream_t s) {
-    k1_tc_tables<N, FMT><<<1, 256, 0, s>>>(f32::make_tw<N>(t), static_cast<unsigned char*>(dst));
+cudaError_t tables_nf(const TwiddleTable& t, int feat, void* dst, cudaStream_t s) {
+    k1_tc_tables<N, FMT><<<1, 256, 0, s>>>(f32::make_tw<N>(t), static_cast<unsigned char*>(dst), feat);
     note_launches(1);
     return cudaGetLastError();
 }
 
 template <int N, int FMT>
-cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int* err,
+cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int feat, int* err,
                       cudaStream_t s) {
     using G = TcGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, T);
-    k1_spectra_tc<N, FMT><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd,
-                                                          static_cast<const unsigned char*>(tables), err);
+    const unsigned char* tab = static_cast<const unsigned char*>(tables);
+    if (feat == 1)
+        k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, tab, err);
+    else
+        k1_spectra_tc<N, FMT, false><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, tab, err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -333,18 +341,18 @@ cudaError_t spectra_tc_prepare(int n, int fmt) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, void* dst, cudaStream_t s) {
-    if (n == 8) return fmt == 1 ? tables_nf<8, 1>(tw, dst, s) : tables_nf<8, 0>(tw, dst, s);
-    if (n == 16) return fmt == 1 ? tables_nf<16, 1>(tw, dst, s) : tables_nf<16, 0>(tw, dst, s);
+cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int feat, void* dst, cudaStream_t s) {
+    if (n == 8) return fmt == 1 ? tables_nf<8, 1>(tw, feat, dst, s) : tables_nf<8, 0>(tw, feat, dst, s);
+    if (n == 16) return fmt == 1 ? tables_nf<16, 1>(tw, feat, dst, s) : tables_nf<16, 0>(tw, feat, dst, s);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int* err, cudaStream_t s) {
-    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, err, s)
-                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, err, s);
-    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, err, s)
-                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, err, s);
+                              int bnd, int feat, int* err, cudaStream_t s) {
+    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, feat, err, s)
+                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, feat, err, s);
+    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, feat, err, s)
+                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, feat, err, s);
     return cudaErrorInvalidValue;
 }
 

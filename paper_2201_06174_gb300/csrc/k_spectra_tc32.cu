@@ -14,7 +14,7 @@
 namespace sal {
 namespace {
 
-using f32::fast_sqrt;
+using f32::bin_mag;
 using f32::Tw;
 
 constexpr int N = 32, H = N / 2 + 1, P = 128 / N, BY = 16;
@@ -52,7 +52,7 @@ template <> struct Pack<0> {
     }
 };
 
-template <int FMT>
+template <int FMT, bool EN>
 __global__ void __launch_bounds__(kThreads, 1)
 k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
                 const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
@@ -139,14 +139,8 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             const int k = i % H, x = i / H;
             const int ii = kt, j = x < N / 2 ? x : x - N;
             const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-            const float r2 = (float)(ii * ii + j * j + k * k);
-            float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-            if (r2 > 0.f) {
-                const float inv = mult / (float)(N * N * N) / sqrtf(r2);
-                w0 = sqrtf((float)(j * j + k * k)) * inv;
-                w1 = sqrtf((float)(ii * ii + k * k)) * inv;
-                w2 = sqrtf((float)(ii * ii + j * j)) * inv;
-            }
+            float w0, w1, w2;
+            f32::bin_weights<EN>(ii, j, k, mult / (float)(N * N * N), w0, w1, w2);
             s_wt[i * 3 + 0] = w0;
             s_wt[i * 3 + 1] = w1;
             s_wt[i * 3 + 2] = w2;
@@ -242,11 +236,11 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
                         const float pr = vr[k], pi = vi[k];
                         float a;
                         if (k == 0 || 2 * k == N) {
-                            a = fast_sqrt(fmaf(pr, pr, pi * pi));
+                            a = bin_mag<EN>(fmaf(pr, pr, pi * pi));
                         } else {
                             const float qr = vr[H + k - 1], qi = vi[H + k - 1];
                             const float ar = pr + qi, ai = pi - qr, br = pr - qi, bi = pi + qr;
-                            a = fast_sqrt(fmaf(ar, ar, ai * ai)) + fast_sqrt(fmaf(br, br, bi * bi));
+                            a = bin_mag<EN>(fmaf(ar, ar, ai * ai)) + bin_mag<EN>(fmaf(br, br, bi * bi));
                         }
                         e0 = fmaf(wt[0][k], a, e0);
                         e1 = fmaf(wt[1][k], a, e1);
@@ -264,6 +258,7 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
 
     const size_t NV = (size_t)T * X * Y;
     const int x = xb + x0l;
+    const float out_scale = EN ? scale * scale : scale;   // the features of the unscaled brick
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int y0 = (i / 4) * 8 + half + 2 * (i % 4);
@@ -273,7 +268,7 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
 #pragma unroll
             for (int o = 1; o < N; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             const int y = yb + y0;
-            if (kx == 0 && x < X && y < Y && !*s_fail) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * scale;
+            if (kx == 0 && x < X && y < Y && !*s_fail) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
         }
     }
     tc::fence_before_sync();
@@ -281,20 +276,27 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+template <int FMT, bool EN>
+cudaError_t prepare32() {
+    return cudaFuncSetAttribute(k1_spectra_tc32<FMT, EN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+}
+
 }  // namespace
 
 cudaError_t spectra_tc32_prepare(int fmt) {
-    return fmt == 1 ? cudaFuncSetAttribute(k1_spectra_tc32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM)
-                    : cudaFuncSetAttribute(k1_spectra_tc32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e = fmt == 1 ? prepare32<1, false>() : prepare32<0, false>();
+    if (e != cudaSuccess) return e;
+    return fmt == 1 ? prepare32<1, true>() : prepare32<0, true>();
 }
 
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& t, const float* V, float* E, int T, int X, int Y,
-                                int bnd, int* err, cudaStream_t s) {
+                                int bnd, int feat, int* err, cudaStream_t s) {
     dim3 grid((Y + BY - 1) / BY, (X + P - 1) / P, T);
-    if (fmt == 1)
-        k1_spectra_tc32<1><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t), err);
-    else
-        k1_spectra_tc32<0><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t), err);
+    const Tw<N> tw = f32::make_tw<N>(t);
+    if (fmt == 1 && feat == 1) k1_spectra_tc32<1, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
+    else if (fmt == 1) k1_spectra_tc32<1, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
+    else if (feat == 1) k1_spectra_tc32<0, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
+    else k1_spectra_tc32<0, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
     note_launches(1);
     return cudaGetLastError();
 }

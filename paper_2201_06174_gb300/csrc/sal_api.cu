@@ -102,13 +102,15 @@ sal_status check_handle(sal_handle* h) {
 // K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.
 cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) {
     if (h->n == 32) {
-        if (h->prec == SAL_FP32) return sal::spectra_f32_n32_launch(h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+        if (h->prec == SAL_FP32)
+            return sal::spectra_f32_n32_launch(h->tw, V, E, h->T, h->X, h->Y, h->boundary, h->feature, st);
         return sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
-                                        h->err_dev, st);
+                                        h->feature, h->err_dev, st);
     }
-    if (h->prec == SAL_FP32) return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, st);
+    if (h->prec == SAL_FP32)
+        return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, h->feature, st);
     return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, E, h->T, h->X, h->Y,
-                                  h->boundary, h->err_dev, st);
+                                  h->boundary, h->feature, h->err_dev, st);
 }
 
 }  // namespace
@@ -132,7 +134,8 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     if (p->stride != 1) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only stride 1 is built");
     if (p->taper != 0 && p->taper != 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "taper must be 0 or 1");
     if (p->boundary < 0 || p->boundary > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad boundary");
-    if (p->feature != 0) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only feature 0 is built");
+    if (p->feature != 0 && p->feature != 1)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "feature must be 0 (mean of |F_m|) or 1 (mean of |F_m|^2)");
     if (p->prec < 0 || p->prec > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad precision");
     if (!sal::spectra_f32_supported(p->n) && p->n != 32)
         return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16,32}");
@@ -259,9 +262,9 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
             cudaGetLastError();
             return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
-        if ((e = sal::spectra_tc_tables_build(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, h->tc_tables, 0)) !=
-                cudaSuccess ||
-            (e = sal::spectra_adjoint_tc_tables_build(h->n, h->tw, h->adj_tables, 0)) != cudaSuccess ||
+        if ((e = sal::spectra_tc_tables_build(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tw, h->feature, h->tc_tables,
+                                              0)) != cudaSuccess ||
+            (e = sal::spectra_adjoint_tc_tables_build(h->n, h->tw, h->feature, h->adj_tables, 0)) != cudaSuccess ||
             (e = cudaStreamSynchronize(0)) != cudaSuccess) {
             free_scratch(h);
             delete h;
@@ -397,11 +400,11 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
         const int cnt = std::min(h->slab_t, h->T - t_begin);
         e = h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
-                                                  t_begin, cnt, st)
+                                                  h->feature, t_begin, cnt, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,
-                                                 h->boundary, t_begin, cnt, h->err_dev, st);
+                                                 h->boundary, h->feature, t_begin, cnt, h->err_dev, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
         if ((e = sal::gather_add_launch(h->blocks, h->gext, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt,
                                         st)) !=

@@ -61,27 +61,28 @@ struct Reduce {
 };
 
 // ---- K1: local spectra + projection + features ----------------------------------------------
+// feat: 0 = the mean of |F_m| (step 3), 1 = the mean of |F_m|^2 (energy reading)
 bool spectra_f32_supported(int n);
 cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, cudaStream_t s);
+                               int Y, int bnd, int feat, cudaStream_t s);
 
 // K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
 cudaError_t spectra_f32_n32_prepare();
 cudaError_t spectra_f32_n32_launch(const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y, int bnd,
-                                   cudaStream_t s);
+                                   int feat, cudaStream_t s);
 cudaError_t spectra_tc32_prepare(int fmt);
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
-                                int bnd, int* err, cudaStream_t s);
+                                int bnd, int feat, int* err, cudaStream_t s);
 
 // K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word.  The constant
 // operands (twiddles in the operand layouts, Eq. 1 weights) are built once per handle into `tables`.
 bool spectra_tc_supported(int n);
 size_t spectra_tc_tables_bytes(int n);
 cudaError_t spectra_tc_prepare(int n, int fmt);
-cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, void* tables, cudaStream_t s);
+cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int feat, void* tables, cudaStream_t s);
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int* err, cudaStream_t s);
+                              int bnd, int feat, int* err, cudaStream_t s);
 
 // ---- K3a: sequential adaptive weights (LMS / NLMS / RLS) over inline-section blocks -------------
 // Per-map bounds of S3 into r.norm (lo at 0..2, 1/(hi-lo) at 3..5; 0 for a flat map).
@@ -114,15 +115,16 @@ struct SpectraAdjointGeometry {
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
-                                       int T, int X, int Y, int bnd, int t_begin, int t_count, cudaStream_t s);
+                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_count,
+                                       cudaStream_t s);
 // K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
 size_t spectra_adjoint_tc_tables_bytes(int n);
-cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, void* tables, cudaStream_t s);
+cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, int feat, void* tables, cudaStream_t s);
 SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
-                                      const float* gE, float* blocks, int T, int X, int Y, int bnd, int t_begin,
-                                      int t_count, int* err, cudaStream_t s);
+                                      const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
+                                      int t_begin, int t_count, int* err, cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]

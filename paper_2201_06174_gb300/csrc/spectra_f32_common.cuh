@@ -28,6 +28,46 @@ __device__ __forceinline__ float fast_rsqrt(float x) {
     return r;
 }
 
+// Eq. 1 weights of one bin (signed indices i, j, k; only their squares enter) with the multiplicity of
+// its k_t and the 1/n^3 of the mean folded in (mult_over_n3): r_m = P_m / |k| for the feature of step 3
+// (the mean of |F_m| = r_m |F|), or r_m^2 for the energy reading (the mean of |F_m|^2 = r_m^2 |F|^2);
+// zero at DC.
+template <bool EN>
+__host__ __device__ __forceinline__ void bin_weights(int i, int j, int k, float mult_over_n3, float& w0, float& w1,
+                                                     float& w2) {
+    const float r2 = (float)(i * i + j * j + k * k);
+    w0 = w1 = w2 = 0.f;
+    if (r2 > 0.f) {
+        const float p0 = (float)(j * j + k * k), p1 = (float)(i * i + k * k), p2 = (float)(i * i + j * j);
+        if (EN) {
+            const float inv = mult_over_n3 / r2;
+            w0 = p0 * inv;
+            w1 = p1 * inv;
+            w2 = p2 * inv;
+        } else {
+            const float inv = mult_over_n3 / sqrtf(r2);
+            w0 = sqrtf(p0) * inv;
+            w1 = sqrtf(p1) * inv;
+            w2 = sqrtf(p2) * inv;
+        }
+    }
+}
+
+// The per-bin quantity the feature averages, from |F|^2: |F| (step 3) or |F|^2 (energy).
+template <bool EN>
+__device__ __forceinline__ float bin_mag(float m2) {
+    if (EN) return m2;
+    return fast_sqrt(m2);
+}
+
+// Adjoint of the per-bin quantity: the factor sc with Gamma = sc F for the bin weight rho = sum_m gE_m w_m:
+// d|F| = F / |F| (zero subgradient where |F|^2 <= thr2, the kink band), d|F|^2 = 2 F (smooth).
+template <bool EN>
+__device__ __forceinline__ float bin_adjoint_scale(float rho, float m2, float thr2) {
+    if (EN) return 2.f * rho;
+    return m2 > thr2 ? rho * fast_rsqrt(m2) : 0.f;
+}
+
 // Twiddles with the taper folded in: c[k][u] = h(u) cos(2 pi k u / n), s[k][u] = h(u) sin(...).
 template <int N> struct Tw {
     float c[N / 2 + 1][N];
@@ -120,7 +160,8 @@ template <int N_, int BY_, int NT_> struct Brick {
     }
 
     // Projection weights of one stage-3 row (k_t, k_x) for |k_y| = k in [0, n/2]:
-    // wt[m][k] = r_m(k_t, k_x, k) * multiplicity(k_t) / n^3, zero at DC (Eq. 1).
+    // wt[m][k] = r_m(k_t, k_x, k) (or r_m^2, energy) * multiplicity(k_t) / n^3, zero at DC (Eq. 1).
+    template <bool EN>
     __device__ static void row_weights(int row, float (&wt)[3][H]) {
         const int kt = row / N, kx = row % N;
         const int i = kt;
@@ -128,17 +169,7 @@ template <int N_, int BY_, int NT_> struct Brick {
         const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
         const float scale = mult / (float)(N * N * N);
 #pragma unroll
-        for (int k = 0; k < H; ++k) {
-            const float r2 = (float)(i * i + j * j + k * k);
-            if (r2 == 0.f) {
-                wt[0][k] = wt[1][k] = wt[2][k] = 0.f;
-            } else {
-                const float inv = scale / sqrtf(r2);
-                wt[0][k] = sqrtf((float)(j * j + k * k)) * inv;
-                wt[1][k] = sqrtf((float)(i * i + k * k)) * inv;
-                wt[2][k] = sqrtf((float)(i * i + j * j)) * inv;
-            }
-        }
+        for (int k = 0; k < H; ++k) bin_weights<EN>(i, j, k, scale, wt[0][k], wt[1][k], wt[2][k]);
     }
 };
 

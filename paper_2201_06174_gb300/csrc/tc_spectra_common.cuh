@@ -107,9 +107,10 @@ template <int N> __device__ __forceinline__ float tws(const Tw<N>& tw, int k, in
 
 // The forward constant operands of one (n, operand type) into `out` (TAB_B bytes): A2 (Toeplitz
 // stage-2 twiddles, K-major), B1 (stage-1 twiddles), B3a / B3b (stage-3 twiddles), the Eq. 1 weight
-// table [k_t][|k_x|][|k_y|][3] (r_m / |k| with the k_t multiplicity folded in).
+// table [k_t][|k_x|][|k_y|][3] (r_m, or r_m^2 for the energy reading feat = 1, with the k_t multiplicity
+// and the 1/n^3 of the mean folded in).
 template <int N, int FMT>
-__device__ void build_fwd_tables(const Tw<N>& tw, unsigned char* out, int tid, int nt) {
+__device__ void build_fwd_tables(const Tw<N>& tw, unsigned char* out, int tid, int nt, int feat) {
     using G = FwdGeo<N>;
     constexpr int H = G::H;
     unsigned char* a2 = out;
@@ -146,14 +147,9 @@ __device__ void build_fwd_tables(const Tw<N>& tw, unsigned char* out, int tid, i
     for (int i = tid; i < H * H * H; i += nt) {
         const int k = i % H, aj = (i / H) % H, kt = i / (H * H);
         const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-        const float r2 = (float)(kt * kt + aj * aj + k * k);
-        float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-        if (r2 > 0.f) {
-            const float inv = mult / (float)(N * N * N) / sqrtf(r2);
-            w0 = sqrtf((float)(aj * aj + k * k)) * inv;
-            w1 = sqrtf((float)(kt * kt + k * k)) * inv;
-            w2 = sqrtf((float)(kt * kt + aj * aj)) * inv;
-        }
+        float w0, w1, w2;
+        if (feat == 1) f32::bin_weights<true>(kt, aj, k, mult / (float)(N * N * N), w0, w1, w2);
+        else f32::bin_weights<false>(kt, aj, k, mult / (float)(N * N * N), w0, w1, w2);
         wt[i * 3 + 0] = w0;
         wt[i * 3 + 1] = w1;
         wt[i * 3 + 2] = w2;

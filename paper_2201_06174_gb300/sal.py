@@ -26,6 +26,7 @@ SAL_OK, SAL_ERR_INVALID_ARG, SAL_ERR_UNSUPPORTED, SAL_ERR_OOM, SAL_ERR_CUDA, SAL
 STATUS_NAMES = ["SAL_OK", "SAL_ERR_INVALID_ARG", "SAL_ERR_UNSUPPORTED", "SAL_ERR_OOM", "SAL_ERR_CUDA",
                 "SAL_ERR_TIMEOUT", "SAL_ERR_DEVICE_CHECK"]
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
+FEATURE = {"abs": 0, "energy": 1}   # E_m: mean over the cube's bins of |F_m| (step 3), or of |F_m|^2
 BOUNDARY = {"symmetric": 0, "periodic": 1, "zero": 2}
 TAPER = {"rect": 0, "hann": 1}
 
@@ -133,6 +134,7 @@ class Params:
     sigma: float = 1.5
     alpha: Optional[Sequence[float]] = None
     prec: str = "fp32"
+    feature: str = "abs"
     ls_delta: float = 1e-6
     hbm_budget_bytes: int = 0
     offsets: Optional[np.ndarray] = None   # explicit window overrides directions/R/sigma
@@ -152,7 +154,8 @@ def sal_create(params: Params, shape: Sequence[int]):
     offs, g, did = params.window()
     ndirs = int(did.max()) + 1 if len(did) else 0
     alpha = np.ones(ndirs, np.float32) if params.alpha is None else np.ascontiguousarray(params.alpha, np.float32)
-    p = sal_params(n=params.n, stride=1, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary], feature=0,
+    p = sal_params(n=params.n, stride=1, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary],
+                   feature=FEATURE[params.feature],
                    n_offsets=len(g), offsets=offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                    gauss_w=g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                    dir_id=did.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n_dirs=len(alpha),
