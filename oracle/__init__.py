@@ -11,7 +11,9 @@ Pipeline (Sec. 2 of the paper, Fig. 2 block diagram):
     --weighted sum (Eq. 4; equal, given, LS fit to a desired map D, or LMS/NLMS/RLS)--> S.
 
 Readings where the paper is silent (each an argument here):
-  * stride 1 (a window around every voxel), window offsets [-n/2, n/2-1];
+  * stride 1 (a window around every voxel), window offsets [-n/2, n/2-1]; stride s < n/2 (windows
+    overlapping by more than half) as an option, with E interpolated (trilinear) between the lattice
+    voxels and held constant past the last lattice point of an axis;
   * rectangular taper (the cube C_n as is); Hann optional;
   * E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (feature "abs"); the energy reading of the garbled step 3,
     E_m = (1/n^3) sum_{k != 0} r_m(k)^2 |F[k]|^2, is feature "energy";
@@ -103,14 +105,48 @@ def projected_spectra(V, t: int, x: int, y: int, n: int, boundary="symmetric", t
     return out[..., 0] + 1j * out[..., 1]
 
 
-def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, feature="abs") -> np.ndarray:
+def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, feature="abs",
+             stride: int = 1) -> np.ndarray:
     """E [3][T][X][Y] (E_t, E_x, E_y) at every voxel: the mean over the cube's bins of |F_m|
-    (feature "abs", step 3) or of |F_m|^2 (feature "energy")."""
+    (feature "abs", step 3) or of |F_m|^2 (feature "energy").  stride s > 1: the cubes sit only on
+    the lattice of voxels whose indices are all multiples of s (windows overlapping by n - s of n,
+    the paper's ">50% overlap" for s < n/2), and E elsewhere is interpolated from them (upsample)."""
     V = _f64(V)
+    if stride > 1:
+        T, X, Y = V.shape
+        lat = [np.arange(0, d, stride) for d in (T, X, Y)]
+        pts = np.stack(np.meshgrid(*lat, indexing="ij"), -1).reshape(-1, 3)
+        Ec = features_at(V, pts, n, boundary, taper, threads, feature).T.reshape((3,) + tuple(len(a) for a in lat))
+        return upsample(Ec, stride, V.shape)
     E = np.empty((3,) + V.shape, dtype=np.float64)
     _check(lib().sal_oracle_features(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], FEATURE[feature],
                                      _dp(E), threads), "features")
     return E
+
+
+def upsample(Ec, stride: int, shape) -> np.ndarray:
+    """Lattice values Ec [3][Tc][Xc][Yc] (at indices multiples of s) to every voxel of `shape`:
+    along each axis, a voxel between lattice points a = s floor(i/s) and a + s takes the linear
+    interpolation (1 - f) E(a) + f E(a + s), f = (i - a)/s; past the last lattice point of the axis
+    it takes that point's value.  Applied axis by axis (trilinear)."""
+    out = _f64(Ec)
+    for ax, N in enumerate(shape):
+        L = out.shape[ax + 1]
+        res = np.empty(out.shape[:ax + 1] + (N,) + out.shape[ax + 2:])
+        for i in range(N):
+            a = i // stride
+            f = (i - a * stride) / stride
+            lo = np.take(out, a, axis=ax + 1)
+            if a + 1 < L:
+                hi = np.take(out, a + 1, axis=ax + 1)
+                val = (1.0 - f) * lo + f * hi
+            else:
+                val = lo
+            idx = [slice(None)] * res.ndim
+            idx[ax + 1] = i
+            res[tuple(idx)] = val
+        out = res
+    return out
 
 
 def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int = 0,
@@ -285,12 +321,12 @@ def combine(S3, weights="equal", D=None, delta: float = 1e-6, bounds=None) -> Di
 
 
 def saliency(V, n: int, boundary="symmetric", taper="rect", stencil=None, weights="equal", D=None,
-             delta: float = 1e-6, threads: int = 0, bounds=None, feature="abs") -> Dict[str, np.ndarray]:
+             delta: float = 1e-6, threads: int = 0, bounds=None, feature="abs", stride: int = 1) -> Dict[str, np.ndarray]:
     """Whole forward pass: E, raw S_m, weights and the consolidated map S."""
     if stencil is None:
         stencil = dcs_stencil()
     offsets, g, did, w = stencil
-    E = features(V, n, boundary, taper, threads, feature)
+    E = features(V, n, boundary, taper, threads, feature, stride)
     S3 = center_surround(E, offsets, w, boundary, threads)
     out = combine(S3, weights, D, delta, bounds)
     out.update({"E": E, "S3": S3})
