@@ -166,7 +166,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(V, n, sample, backward=True, feature="abs"):  # noqa: C901
+def cpu_oracle_rate(V, n, sample, backward=True, feature="abs", stride=1):  # noqa: C901
     """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host
     cores): forward, and the backward with the same fixed upstream gradient as the GPU step."""
     import numpy as np
@@ -175,7 +175,7 @@ def cpu_oracle_rate(V, n, sample, backward=True, feature="abs"):  # noqa: C901
     sub = np.ascontiguousarray(V[:sample, :sample, :sample])
     gS = _upstream(sub.shape)
     t0 = time.perf_counter()
-    fwd = oracle.saliency(sub, n, feature=feature)
+    fwd = oracle.saliency(sub, n, feature=feature, stride=stride)
     if backward:
         oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd, feature=feature)
     dt = time.perf_counter() - t0
@@ -191,10 +191,16 @@ def sampled_error(V, n, params, E, S3, count=48, seed=7):
     import synth
     st = oracle.dcs_stencil(params.directions, params.R, params.sigma)
     pts = synth.sample_points(V.shape, count, seed=seed)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    if params.stride > 1:
+        # stride s: the sampled voxels moved to the lattice, where E is the cube's own feature
+        pts = (pts // params.stride) * params.stride
+        Ec = oracle.features_at(V, pts, n, feature=params.feature)
+        Eg = E.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
+        return {"voxels": count, "lattice": True, "E_rel_l2": [rel(Eg[:, m], Ec[:, m]) for m in range(3)]}
     Ec, Sc = oracle.center_surround_at(V, pts, n, st[0], st[3], feature=params.feature)
     Eg = E.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
     Sg = S3.cpu().numpy()[:, pts[:, 0], pts[:, 1], pts[:, 2]].T.astype(np.float64)
-    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     return {"voxels": count, "E_rel_l2": [rel(Eg[:, m], Ec[:, m]) for m in range(3)],
             "S_m_rel_l2": [rel(Sg[:, m], Sc[:, m]) for m in range(3)]}
 
@@ -215,10 +221,10 @@ def run_reference(args, wl):
     s = wl["ref_sample"]
     bwd = getattr(args, "form", "fwdbwd") == "fwdbwd"
     for _ in range(args.warmup):
-        cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature)
+        cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride)
     times = []
     for _ in range(args.steps):
-        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature)
+        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride)
         times.append(dt)
     vox = s ** 3
     value = vox * args.steps / sum(times) / 1e6
@@ -227,7 +233,8 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": wl["n"], "shape": list(V.shape), "precision": "fp64 oracle",
-                       "form": "forward+backward" if bwd else "forward", "feature": args.feature},
+                       "form": "forward+backward" if bwd else "forward", "feature": args.feature,
+                       "stride": args.stride},
             "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": cores, "kind": "oracle",
                              "sample": f"{s}^3 corner sub-volume of the workload per step, FP64 forward+backward"},
             "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -249,6 +256,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--feature", default="abs", choices=["abs", "energy"],
                     help="E_m: mean of |F_m| (the paper's step 3) or of |F_m|^2 (energy reading)")
+    ap.add_argument("--stride", type=int, default=1,
+                    help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2; forward only)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:
@@ -282,7 +291,9 @@ def main():
 
     V, _ = synth.volume(wl["spec"], with_mask=False)
     nvox = V.size
-    params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature)
+    if args.stride > 1 and args.form != "fwd":
+        raise SystemExit("--stride > 1 is a forward-only form: pass --form fwd")
+    params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature, stride=args.stride)
     eng = sal.Saliency(V.shape, params)
     dev = torch.device("cuda", local_rank)
     Vd = torch.from_numpy(V).to(dev)
@@ -380,7 +391,7 @@ def main():
     # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
     k1_fp32_ms = None
     if args.prec != "fp32":
-        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature))
+        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature, stride=args.stride))
         E32 = torch.empty_like(E)
         for _ in range(3):
             sal.sal_local_spectra_project(eng32.h, Vd, E32)
@@ -403,8 +414,16 @@ def main():
     # K1 in the forward-only form
     k1_ms = per_call[names.index("k1_local_spectra_project")] / args.steps
     tag = "tc" if args.prec != "fp32" else "f32"
-    trk = (args.workload, n, args.prec) if args.feature == "abs" else None
-    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, nvox, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature)
+    trk = (args.workload, n, args.prec) if args.feature == "abs" and args.stride == 1 else None
+    # cubes the K1 launch computes: every voxel at stride 1; with stride s the tensor-core form computes
+    # the whole lattice planes t = k s, the FP32 form only the lattice
+    sc = args.stride
+    T_, X_, Y_ = V.shape
+    ncubes = nvox if sc == 1 else (-(-T_ // sc) * X_ * Y_ if args.prec != "fp32" else
+                                   -(-T_ // sc) * -(-X_ // sc) * -(-Y_ // sc))
+    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, ncubes, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature)
+    if sc > 1:
+        k1_rl["cubes_per_launch"] = ncubes
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
@@ -423,6 +442,7 @@ def main():
                    "form": "forward+backward (upstream gradient fixed, seeded)" if args.form == "fwdbwd"
                    else "forward",
                    "feature": "mean of |F_m| (step 3)" if args.feature == "abs" else "mean of |F_m|^2 (energy reading)",
+                   "stride": args.stride,
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "forward": {"value": world * nvox * args.steps / (fwd_ms / 1e3) / 1e6, "unit": "Mvoxel/s",
@@ -441,7 +461,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = wl["cpu_sample"]
-        rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd", feature=args.feature)
+        rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd", feature=args.feature,
+                                          stride=args.stride)
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{s}^3 corner sub-volume of the workload, FP64 "
                                           f"{'forward+backward' if args.form == 'fwdbwd' else 'forward'}, {dt:.1f} s",

@@ -60,7 +60,12 @@ typedef struct {
     int n;                  /* cube side of the local DFT (Sec. 2 step 1, Eq. 2): n in
                                {2,4,8,16,32} for SAL_FP32, {8,16,32} for BF16/FP16; the
                                backward calls are built for n <= 16                      */
-    int stride;             /* window stride; must be 1 (a cube around every voxel)   */
+    int stride;             /* window stride s: 1 = a cube around every voxel; s > 1 with
+                               s < n/2 (windows overlapping by more than half, Sec. 2
+                               step 1) = cubes only at voxels whose indices are all
+                               multiples of s, E interpolated trilinearly in between
+                               (held past the last lattice point of an axis).  Forward
+                               only: the spectral backward calls need s = 1          */
     int taper;              /* 0 = rectangular (the cube as is), 1 = periodic Hann    */
     int boundary;           /* sal_boundary                                           */
     int feature;            /* 0 = E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (step 3: the mean

@@ -43,9 +43,10 @@ template <int N> struct Geo {
     static_assert(NT <= 1024, "threads");
 };
 
-template <int N, bool EN>
+// EN: the energy reading of the feature; STR: stride > 1 (cubes on the lattice of multiples of `stride`)
+template <int N, bool EN, bool STR>
 __global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
-k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
+k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
                const __grid_constant__ Tw<N> tw) {
     using G = Geo<N>;
     using B = typename G::B;
@@ -58,8 +59,8 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
 
     const int tid = threadIdx.x;
     const int y_start = blockIdx.x * BY;
-    const int x0 = blockIdx.y;
-    const int t0 = blockIdx.z;
+    const int x0 = blockIdx.y * stride;   // stride s: cubes only at indices that are multiples of s
+    const int t0 = blockIdx.z * stride;
 
     B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
     __syncthreads();
@@ -75,6 +76,7 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     B::template row_weights<EN>(row, wt);
     const float2* grow = s_g2 + (size_t)row * YH;
     for (int yl = ych * YC; yl < ych * YC + YC; ++yl) {
+        if (STR && (y_start + yl) % stride != 0) continue;
         float pr[H], pi[H], qr[H], qi[H];
 #pragma unroll
         for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
@@ -113,38 +115,51 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     __syncthreads();
 
     // ---- fixed-order reduction over the (k_t, k_x) rows ---------------------------------------
-    const size_t NV = (size_t)T * X * Y;
+    // E: [3][T][X][Y], or the lattice [3][Tc][Xc][Yc] (ceil(T / s) ...) for stride s > 1
+    const int Xc = (X + stride - 1) / stride, Yc = (Y + stride - 1) / stride;
+    const size_t NVc = (size_t)((T + stride - 1) / stride) * Xc * Yc;
     const int lane = tid & 31, warp = tid >> 5;
     for (int it = warp; it < BY * 3; it += NT / 32) {
         const int yl = it / 3, m = it % 3;
+        const int y = y_start + yl;
+        if (STR && y % stride != 0) continue;
         const float* p = s_part + (size_t)(yl * 3 + m) * ROWS;
         float acc = 0.f;
         for (int r = lane; r < ROWS; r += 32) acc += p[r];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const int y = y_start + yl;
-        if (lane == 0 && y < Y) E[m * NV + ((size_t)t0 * X + x0) * Y + y] = acc;
+        if (lane == 0 && y < Y) {
+            if (STR) E[m * NVc + ((size_t)(t0 / stride) * Xc + x0 / stride) * Yc + y / stride] = acc;
+            else E[m * NVc + ((size_t)t0 * X + x0) * Y + y] = acc;
+        }
     }
 }
 
-template <int N>
-cudaError_t prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k1_spectra_f32<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<N>::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_spectra_f32<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int N, bool EN, bool STR>
+cudaError_t prepare_one() {
+    return cudaFuncSetAttribute(k1_spectra_f32<N, EN, STR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo<N>::SMEM);
 }
 
 template <int N>
+cudaError_t prepare() {
+    cudaError_t e = prepare_one<N, false, false>();
+    if (e == cudaSuccess) e = prepare_one<N, true, false>();
+    if (e == cudaSuccess) e = prepare_one<N, false, true>();
+    if (e == cudaSuccess) e = prepare_one<N, true, true>();
+    return e;
+}
+
+template <int N>
 cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
-                   cudaStream_t s) {
+                   int stride, cudaStream_t s) {
     using G = Geo<N>;
-    dim3 grid((Y + G::BY - 1) / G::BY, X, T);
-    if (feat == 1)
-        k1_spectra_f32<N, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
-    else
-        k1_spectra_f32<N, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+    dim3 grid((Y + G::BY - 1) / G::BY, (X + stride - 1) / stride, (T + stride - 1) / stride);
+    const Tw<N> tw = f32::make_tw<N>(t);
+    if (feat == 1 && stride > 1) k1_spectra_f32<N, true, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
+    else if (feat == 1) k1_spectra_f32<N, true, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, 1, tw);
+    else if (stride > 1) k1_spectra_f32<N, false, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
+    else k1_spectra_f32<N, false, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, 1, tw);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -164,13 +179,13 @@ cudaError_t spectra_f32_prepare(int n) {
 }
 
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, cudaStream_t s) {
-    if (T > 65535 || X > 65535) return cudaErrorInvalidConfiguration;
+                               int Y, int bnd, int feat, int stride, cudaStream_t s) {
+    if (T > 65535 || X > 65535 || stride < 1) return cudaErrorInvalidConfiguration;
     switch (n) {
-        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, s);
-        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, s);
-        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, s);
-        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, s);
+        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, stride, s);
+        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, stride, s);
+        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, stride, s);
+        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, stride, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -24,7 +24,7 @@ constexpr size_t SMEM = IN_B + 2 * G_B + WT_B;
 
 template <bool EN>
 __global__ void __launch_bounds__(NT, 1)
-k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
+k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
                    const __grid_constant__ Tw<N> tw) {
     extern __shared__ __align__(16) unsigned char smem[];
     float* s_in = reinterpret_cast<float*>(smem);                         // [N][N][YH]
@@ -33,7 +33,8 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
     float* s_wt = reinterpret_cast<float*>(smem + IN_B + 2 * G_B);        // [k_x][k][3] of this tile
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int yb = blockIdx.x * BY, x0 = blockIdx.y, t0 = blockIdx.z;
+    // stride s: cubes only at indices that are multiples of s
+    const int yb = blockIdx.x * BY, x0 = blockIdx.y * stride, t0 = blockIdx.z * stride;
 
     for (int r = tid; r < N * N * YH; r += NT) {
         const int yy = r % YH, ux = (r / YH) % N, ut = r / (YH * N);
@@ -103,7 +104,7 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
         }
         __syncthreads();
         // stage 3 (y) + projection/feature epilogue: warp = y0, lane = k_x
-        {
+        if (stride == 1 || (yb + y0) % stride == 0) {
             float pr[H], pi[H], qr[H], qi[H];
 #pragma unroll
             for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
@@ -144,9 +145,12 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
         e1 += __shfl_xor_sync(0xffffffffu, e1, o);
         e2 += __shfl_xor_sync(0xffffffffu, e2, o);
     }
+    // E: [3][T][X][Y], or the lattice [3][Tc][Xc][Yc] (ceil(T / s) ...) for stride s > 1
     const int y = yb + y0;
-    if (lane == 0 && y < Y) {
-        const size_t NV = (size_t)T * X * Y, p = ((size_t)t0 * X + x0) * Y + y;
+    if (lane == 0 && y < Y && (stride == 1 || y % stride == 0)) {
+        const int Xc = (X + stride - 1) / stride, Yc = (Y + stride - 1) / stride;
+        const size_t NV = (size_t)((T + stride - 1) / stride) * Xc * Yc;
+        const size_t p = ((size_t)(t0 / stride) * Xc + x0 / stride) * Yc + y / stride;
         E[p] = e0;
         E[NV + p] = e1;
         E[2 * NV + p] = e2;
@@ -163,12 +167,13 @@ cudaError_t spectra_f32_n32_prepare() {
 }
 
 cudaError_t spectra_f32_n32_launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd,
-                                   int feat, cudaStream_t s) {
-    dim3 grid((Y + BY - 1) / BY, X, T);
+                                   int feat, int stride, cudaStream_t s) {
+    if (stride < 1) return cudaErrorInvalidConfiguration;
+    dim3 grid((Y + BY - 1) / BY, (X + stride - 1) / stride, (T + stride - 1) / stride);
     if (feat == 1)
-        k1_spectra_f32_n32<true><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+        k1_spectra_f32_n32<true><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, stride, f32::make_tw<N>(t));
     else
-        k1_spectra_f32_n32<false><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, f32::make_tw<N>(t));
+        k1_spectra_f32_n32<false><<<grid, NT, SMEM, s>>>(V, E, T, X, Y, bnd, stride, f32::make_tw<N>(t));
     note_launches(1);
     return cudaGetLastError();
 }

@@ -45,7 +45,7 @@ __global__ void k1_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __
 // EN: the energy reading of the feature (|F|^2 per bin; the weight table then holds r_m^2)
 template <int N, int FMT, bool EN>
 __global__ void __launch_bounds__(kThreads, 2)
-k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
+k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
               const unsigned char* __restrict__ tables, int* __restrict__ err) {
     using G = TcGeo<N>;
     constexpr int H = G::H, P = G::P;
@@ -66,7 +66,7 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int yb = blockIdx.x * kBY;
     const int xb = blockIdx.y * P;
-    const int t0 = blockIdx.z;
+    const int t0 = blockIdx.z * stride;   // stride s: only the planes t0 = multiple of s
 
     // ---- set-up: tensor memory, mbarriers, constant operands (bulk copy), stage-3 A zero rows --------
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
@@ -269,7 +269,9 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     __syncthreads();
 
     // ---- sum over the n lanes of each x0 (k_x), write E -------------------------------------------
-    const size_t NV = (size_t)T * X * Y;
+    // E: [3][T][X][Y], or the lattice [3][Tc][Xc][Yc] (ceil(T / s) ...) for stride s > 1
+    const int Xc = (X + stride - 1) / stride, Yc = (Y + stride - 1) / stride;
+    const size_t NV = (size_t)((T + stride - 1) / stride) * Xc * Yc;
     const int x = xb + x0l;
     const bool good = *s_fail == 0 && warp < kConsumers;   // the producer warp holds no results
     const float out_scale = EN ? scale * scale : scale;     // the features of the unscaled brick
@@ -287,7 +289,12 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
 #pragma unroll
                     for (int w = 1; w < N; w <<= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
                     const int y = yb + y0;
-                    if (kx == 0 && x < X && y < Y && good) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
+                    if (kx == 0 && x < X && y < Y && good) {
+                        if (stride == 1)
+                            E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
+                        else if (x % stride == 0 && y % stride == 0)   // the lattice (a rare path)
+                            E[c * NV + ((size_t)(t0 / stride) * Xc + x / stride) * Yc + y / stride] = s * out_scale;
+                    }
                 }
             }
     tc::fence_before_sync();
@@ -312,15 +319,15 @@ cudaError_t tables_nf(const TwiddleTable& t, int feat, void* dst, cudaStream_t s
 }
 
 template <int N, int FMT>
-cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int feat, int* err,
-                      cudaStream_t s) {
+cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int feat, int stride,
+                      int* err, cudaStream_t s) {
     using G = TcGeo<N>;
-    dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, T);
+    dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, (T + stride - 1) / stride);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
     if (feat == 1)
-        k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, tab, err);
+        k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err);
     else
-        k1_spectra_tc<N, FMT, false><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, tab, err);
+        k1_spectra_tc<N, FMT, false><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -348,11 +355,12 @@ cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int 
 }
 
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int feat, int* err, cudaStream_t s) {
-    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, feat, err, s)
-                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, feat, err, s);
-    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, feat, err, s)
-                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, feat, err, s);
+                              int bnd, int feat, int stride, int* err, cudaStream_t s) {
+    if (stride < 1) return cudaErrorInvalidConfiguration;
+    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, feat, stride, err, s)
+                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, feat, stride, err, s);
+    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, feat, stride, err, s)
+                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, feat, stride, err, s);
     return cudaErrorInvalidValue;
 }
 

@@ -54,7 +54,7 @@ template <> struct Pack<0> {
 
 template <int FMT, bool EN>
 __global__ void __launch_bounds__(kThreads, 1)
-k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd,
+k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
                 const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __half* s_in = reinterpret_cast<__half*>(smem);                     // [N][XH][YH], scaled
@@ -69,7 +69,7 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     float* s_red = reinterpret_cast<float*>(smem + OFF_MISC + 64);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int yb = blockIdx.x * BY, xb = blockIdx.y * P, t0 = blockIdx.z;
+    const int yb = blockIdx.x * BY, xb = blockIdx.y * P, t0 = blockIdx.z * stride;   // stride s: planes t0 = k s
 
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
     if (tid == 0) {
@@ -256,7 +256,9 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
         }
     }
 
-    const size_t NV = (size_t)T * X * Y;
+    // E: [3][T][X][Y], or the lattice [3][Tc][Xc][Yc] (ceil(T / s) ...) for stride s > 1
+    const int Xc = (X + stride - 1) / stride, Yc = (Y + stride - 1) / stride;
+    const size_t NV = (size_t)((T + stride - 1) / stride) * Xc * Yc;
     const int x = xb + x0l;
     const float out_scale = EN ? scale * scale : scale;   // the features of the unscaled brick
 #pragma unroll
@@ -268,7 +270,12 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
 #pragma unroll
             for (int o = 1; o < N; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             const int y = yb + y0;
-            if (kx == 0 && x < X && y < Y && !*s_fail) E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
+            if (kx == 0 && x < X && y < Y && !*s_fail) {
+                if (stride == 1)
+                    E[c * NV + ((size_t)t0 * X + x) * Y + y] = s * out_scale;
+                else if (x % stride == 0 && y % stride == 0)   // the lattice (a rare path)
+                    E[c * NV + ((size_t)(t0 / stride) * Xc + x / stride) * Yc + y / stride] = s * out_scale;
+            }
         }
     }
     tc::fence_before_sync();
@@ -290,13 +297,15 @@ cudaError_t spectra_tc32_prepare(int fmt) {
 }
 
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& t, const float* V, float* E, int T, int X, int Y,
-                                int bnd, int feat, int* err, cudaStream_t s) {
-    dim3 grid((Y + BY - 1) / BY, (X + P - 1) / P, T);
+                                int bnd, int feat, int stride, int* err, cudaStream_t s) {
+    if (stride < 1) return cudaErrorInvalidConfiguration;
+    dim3 grid((Y + BY - 1) / BY, (X + P - 1) / P, (T + stride - 1) / stride);
     const Tw<N> tw = f32::make_tw<N>(t);
-    if (fmt == 1 && feat == 1) k1_spectra_tc32<1, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
-    else if (fmt == 1) k1_spectra_tc32<1, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
-    else if (feat == 1) k1_spectra_tc32<0, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
-    else k1_spectra_tc32<0, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, tw, err);
+    const int st = stride;
+    if (fmt == 1 && feat == 1) k1_spectra_tc32<1, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, st, tw, err);
+    else if (fmt == 1) k1_spectra_tc32<1, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, st, tw, err);
+    else if (feat == 1) k1_spectra_tc32<0, true><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, st, tw, err);
+    else k1_spectra_tc32<0, false><<<grid, kThreads, SMEM, s>>>(V, E, T, X, Y, bnd, st, tw, err);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -15,13 +15,14 @@ struct sal_handle {
     int device = 0;
     int T = 0, X = 0, Y = 0;
     long long N = 0;
-    int n = 0, taper = 0, boundary = 0, feature = 0, prec = 0;
+    int n = 0, taper = 0, boundary = 0, feature = 0, prec = 0, stride = 1;
     double ls_delta = 1e-6;
     size_t budget = 0;
     sal::Stencil st{};
     std::vector<float> alpha;
     sal::TwiddleTable tw{};
     float* E = nullptr;      // [3][N] feature scratch
+    float* Ec = nullptr;     // [3][Tc][Xc][Yc] lattice features of stride > 1
     float* S3 = nullptr;     // [3][N] raw center-surround scratch
     sal::Reduce red{};
     void* small = nullptr;   // one allocation holding the reduction scratch
@@ -55,6 +56,8 @@ sal_status cuda_fail(sal_handle* h, cudaError_t e, const char* where) {
 void free_scratch(sal_handle* h) {
     if (h->E) cudaFree(h->E);
     if (h->S3) cudaFree(h->S3);
+    if (h->Ec) cudaFree(h->Ec);
+    h->Ec = nullptr;
     if (h->small) cudaFree(h->small);
     if (h->tc_tables) cudaFree(h->tc_tables);
     if (h->adj_tables) cudaFree(h->adj_tables);
@@ -99,18 +102,26 @@ sal_status check_handle(sal_handle* h) {
     return SAL_OK;
 }
 
-// K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.
+// K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.  With stride
+// s > 1 the cubes sit on the lattice of multiples of s (into the handle's lattice scratch) and E is
+// interpolated from them.
 cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) {
+    const int s = h->stride;
+    float* out = s > 1 ? h->Ec : E;
+    cudaError_t e;
     if (h->n == 32) {
-        if (h->prec == SAL_FP32)
-            return sal::spectra_f32_n32_launch(h->tw, V, E, h->T, h->X, h->Y, h->boundary, h->feature, st);
-        return sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, E, h->T, h->X, h->Y, h->boundary,
-                                        h->feature, h->err_dev, st);
+        e = h->prec == SAL_FP32
+                ? sal::spectra_f32_n32_launch(h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, st)
+                : sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, out, h->T, h->X, h->Y, h->boundary,
+                                           h->feature, s, h->err_dev, st);
+    } else if (h->prec == SAL_FP32) {
+        e = sal::spectra_f32_launch(h->n, h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, st);
+    } else {
+        e = sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, out, h->T, h->X, h->Y,
+                                   h->boundary, h->feature, s, h->err_dev, st);
     }
-    if (h->prec == SAL_FP32)
-        return sal::spectra_f32_launch(h->n, h->tw, V, E, h->T, h->X, h->Y, h->boundary, h->feature, st);
-    return sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, E, h->T, h->X, h->Y,
-                                  h->boundary, h->feature, h->err_dev, st);
+    if (e != cudaSuccess || s == 1) return e;
+    return sal::upsample_launch(h->Ec, E, h->T, h->X, h->Y, s, st);
 }
 
 }  // namespace
@@ -131,7 +142,8 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     if (T > 65535 || X > 65535) return fail(nullptr, SAL_ERR_UNSUPPORTED, "T and X must be <= 65535");
     if (p->n < 2 || (p->n & 1) || p->n > sal::kMaxN)
         return fail(nullptr, SAL_ERR_INVALID_ARG, "n must be even, 2 <= n <= 32");
-    if (p->stride != 1) return fail(nullptr, SAL_ERR_UNSUPPORTED, "only stride 1 is built");
+    if (p->stride < 1 || (p->stride > 1 && 2 * p->stride >= p->n))
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "stride must be 1 or satisfy 1 < stride < n/2 (overlap > 50%)");
     if (p->taper != 0 && p->taper != 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "taper must be 0 or 1");
     if (p->boundary < 0 || p->boundary > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad boundary");
     if (p->feature != 0 && p->feature != 1)
@@ -153,7 +165,7 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     sal_handle* h = new sal_handle();
     h->T = T; h->X = X; h->Y = Y;
     h->N = (long long)T * X * Y;
-    h->n = p->n; h->taper = p->taper; h->boundary = p->boundary; h->feature = p->feature;
+    h->n = p->n; h->taper = p->taper; h->boundary = p->boundary; h->feature = p->feature; h->stride = p->stride;
     h->prec = p->prec; h->ls_delta = p->ls_delta; h->budget = p->hbm_budget_bytes;
     h->st.Q = p->n_offsets;
     h->st.n_dirs = p->n_dirs;
@@ -207,13 +219,18 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     const bool tc_fwd = h->prec != SAL_FP32 && sal::spectra_tc_supported(h->n);
     const size_t tab_bytes = tc_fwd ? sal::spectra_tc_tables_bytes(h->n) : 0;
     const size_t adj_bytes = tc_fwd ? sal::spectra_adjoint_tc_tables_bytes(h->n) : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes;
+    const int sc = p->stride;
+    const size_t ec_bytes = sc > 1 ? (size_t)3 * ((T + sc - 1) / sc) * ((X + sc - 1) / sc) * ((Y + sc - 1) / sc) *
+                                         sizeof(float)
+                                   : 0;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
     }
     if ((e = cudaMalloc(&h->E, plane3)) != cudaSuccess || (e = cudaMalloc(&h->S3, plane3)) != cudaSuccess ||
-        (e = cudaMalloc(&h->small, small)) != cudaSuccess) {
+        (e = cudaMalloc(&h->small, small)) != cudaSuccess ||
+        (ec_bytes && (e = cudaMalloc(&h->Ec, ec_bytes)) != cudaSuccess)) {
         free_scratch(h);
         delete h;
         cudaGetLastError();
@@ -421,6 +438,7 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !W || !gS) return fail(h, SAL_ERR_INVALID_ARG, "V, W and gS must not be NULL");
+    if (h->stride != 1) return fail(h, SAL_ERR_UNSUPPORTED, "the spectral adjoint is built for stride 1");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
@@ -451,6 +469,7 @@ sal_status sal_local_spectra_project_backward(sal_handle* h, const float* V, con
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !gE || !gV) return fail(h, SAL_ERR_INVALID_ARG, "V, gE and gV must not be NULL");
+    if (h->stride != 1) return fail(h, SAL_ERR_UNSUPPORTED, "the spectral adjoint is built for stride 1");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     return spectral_adjoint(h, V, gE, gV, static_cast<cudaStream_t>(stream));
 }

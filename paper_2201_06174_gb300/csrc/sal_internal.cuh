@@ -61,19 +61,22 @@ struct Reduce {
 };
 
 // ---- K1: local spectra + projection + features ----------------------------------------------
-// feat: 0 = the mean of |F_m| (step 3), 1 = the mean of |F_m|^2 (energy reading)
+// feat: 0 = the mean of |F_m| (step 3), 1 = the mean of |F_m|^2 (energy reading).  stride s: cubes only
+// at voxels whose indices are multiples of s; E is then the lattice [3][ceil(T/s)][ceil(X/s)][ceil(Y/s)].
 bool spectra_f32_supported(int n);
 cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, cudaStream_t s);
+                               int Y, int bnd, int feat, int stride, cudaStream_t s);
+// The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point).
+cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s);
 
 // K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
 cudaError_t spectra_f32_n32_prepare();
 cudaError_t spectra_f32_n32_launch(const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y, int bnd,
-                                   int feat, cudaStream_t s);
+                                   int feat, int stride, cudaStream_t s);
 cudaError_t spectra_tc32_prepare(int fmt);
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
-                                int bnd, int feat, int* err, cudaStream_t s);
+                                int bnd, int feat, int stride, int* err, cudaStream_t s);
 
 // K1 on the tensor cores (BF16 fmt = 1, FP16 fmt = 0); err: device-visible error word.  The constant
 // operands (twiddles in the operand layouts, Eq. 1 weights) are built once per handle into `tables`.
@@ -82,7 +85,7 @@ size_t spectra_tc_tables_bytes(int n);
 cudaError_t spectra_tc_prepare(int n, int fmt);
 cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int feat, void* tables, cudaStream_t s);
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int feat, int* err, cudaStream_t s);
+                              int bnd, int feat, int stride, int* err, cudaStream_t s);
 
 // ---- K3a: sequential adaptive weights (LMS / NLMS / RLS) over inline-section blocks -------------
 // Per-map bounds of S3 into r.norm (lo at 0..2, 1/(hi-lo) at 3..5; 0 for a flat map).

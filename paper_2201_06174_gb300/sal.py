@@ -135,6 +135,7 @@ class Params:
     alpha: Optional[Sequence[float]] = None
     prec: str = "fp32"
     feature: str = "abs"
+    stride: int = 1          # cubes at voxels whose indices are multiples of stride (1 < stride < n/2)
     ls_delta: float = 1e-6
     hbm_budget_bytes: int = 0
     offsets: Optional[np.ndarray] = None   # explicit window overrides directions/R/sigma
@@ -154,7 +155,7 @@ def sal_create(params: Params, shape: Sequence[int]):
     offs, g, did = params.window()
     ndirs = int(did.max()) + 1 if len(did) else 0
     alpha = np.ones(ndirs, np.float32) if params.alpha is None else np.ascontiguousarray(params.alpha, np.float32)
-    p = sal_params(n=params.n, stride=1, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary],
+    p = sal_params(n=params.n, stride=params.stride, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary],
                    feature=FEATURE[params.feature],
                    n_offsets=len(g), offsets=offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                    gauss_w=g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

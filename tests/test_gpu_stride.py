@@ -1,0 +1,95 @@
+"""GPU parity of the stride-s windows (cubes only at voxels whose indices are multiples of s, windows
+overlapping by n - s of n, more than half for s < n/2; the features interpolated trilinearly in
+between) against the FP64 oracle, through the C ABI, in every precision.
+
+Tolerances as for stride 1: FP32 relative L2 <= 1e-5 per map; the 16-bit tensor-core forms relative
+L2 <= 1e-2 per map and max-abs <= 2e-2 on the normalised map S.  Volumes are not multiples of s, so
+the held values past the last lattice point are covered.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def sal():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_06174_gb300 as s
+    s.load()
+    return s
+
+
+@pytest.mark.parametrize("n,s,shape,boundary,prec,feature,tol", [
+    (8, 2, (11, 9, 37), "symmetric", "fp32", "abs", 1e-5),
+    (8, 3, (10, 8, 35), "periodic", "fp32", "energy", 1e-5),
+    (16, 4, (9, 10, 21), "zero", "fp32", "abs", 1e-5),
+    (32, 5, (7, 9, 21), "symmetric", "fp32", "abs", 1e-5),
+    (8, 2, (9, 21, 37), "symmetric", "bf16", "abs", 1e-2),
+    (16, 3, (8, 11, 35), "symmetric", "fp16", "abs", 1e-2),
+    (16, 2, (7, 10, 20), "periodic", "bf16", "energy", 1e-2),
+    (32, 4, (7, 9, 21), "symmetric", "bf16", "abs", 1e-2),
+])
+def test_stride_forward_matches_oracle(sal, n, s, shape, boundary, prec, feature, tol):
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + s + shape[2], faults=2))
+    p = sal.Params(n=n, boundary=boundary, prec=prec, feature=feature, stride=s)
+    eng = sal.Saliency(shape, p)
+    try:
+        out = eng.saliency(torch.from_numpy(V).cuda(), None, intermediates=True)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        eng.close()
+    ref = oracle.saliency(V, n, boundary=boundary, stencil=oracle.dcs_stencil(p.directions, p.R, p.sigma),
+                          feature=feature, stride=s)
+    errs = {f"E{m}": rel_l2(g["E"][m], ref["E"][m]) for m in range(3)}
+    errs.update({f"S{m}": rel_l2(g["S3"][m], ref["S3"][m]) for m in range(3)})
+    errs["S"] = rel_l2(g["S"], ref["S"])
+    print(prec, n, s, shape, boundary, feature, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= tol, (k, v)
+    if prec != "fp32":
+        assert np.abs(g["S"] - ref["S"]).max() <= 2e-2
+
+
+def test_stride_lattice_matches_stride_one(sal):
+    """On the lattice the stride-3 features are the per-voxel features (FP32, bit for bit apart from the
+    order of the interpolation's terms, which is exact there: weights 0 and 1)."""
+    shape = (10, 9, 40)
+    V, _ = synth.volume(synth.small_spec(shape, seed=3, faults=1))
+    Es = []
+    for s in (1, 3):
+        eng = sal.Saliency(shape, sal.Params(n=8, stride=s))
+        try:
+            out = eng.saliency(torch.from_numpy(V).cuda(), None, intermediates=True)
+            torch.cuda.synchronize()
+            Es.append(out["E"].cpu().numpy())
+        finally:
+            eng.close()
+    lat = np.ix_(range(3), range(0, 10, 3), range(0, 9, 3), range(0, 40, 3))
+    assert np.array_equal(Es[0][lat], Es[1][lat])
+
+
+def test_stride_arguments(sal):
+    V = torch.zeros((8, 8, 8), device="cuda")
+    for n, s in ((8, 4), (4, 2), (16, 0)):   # s must be 1 or 1 < s < n/2
+        with pytest.raises(sal.SalError):
+            sal.Saliency((8, 8, 8), sal.Params(n=n, stride=s))
+    eng = sal.Saliency((8, 8, 8), sal.Params(n=8, stride=2))
+    try:
+        with pytest.raises(sal.SalError):
+            sal.sal_local_spectra_project_backward(eng.h, V, torch.zeros((3, 8, 8, 8), device="cuda"),
+                                                   torch.empty_like(V))
+    finally:
+        eng.close()
