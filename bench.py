@@ -38,6 +38,11 @@ WORKLOADS = {
     "precision256x384x192": dict(spec="precision256x384x192", n=16, desc="256x384x192 synthetic seismic volume "
                                  "(6 faults, 2 salt bodies, SNR 5 dB, folds), window 16^3", cpu_sample=40,
                                  ref_sample=20),
+    "section462x951": dict(spec="section462x951", n=16, section=True, weights=(0.0, 0.5, 0.5),
+                           directions=((0, 1, 0), (0, 0, 1), (0, 1, 1)),
+                           desc="2-D vertical section 462 (t) x 951 (x) of a synthetic seismic slab (6 faults, 1 salt "
+                           "body, folds, noise 0.1 rms), passed as a volume [1][462][951] (one plane), window 16^2, "
+                           "the in-plane t, x, t-x window, weights (0, 1/2, 1/2)", cpu_sample=40, ref_sample=24),
     "full462x951x651": dict(spec="full462x951x651", n=16, desc="462x951x651 synthetic seismic volume (20 faults, "
                             "3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3", cpu_sample=40,
                             ref_sample=20),
@@ -205,6 +210,18 @@ def sampled_error(V, n, params, E, S3, count=48, seed=7):
             "S_m_rel_l2": [rel(Sg[:, m], Sc[:, m]) for m in range(3)]}
 
 
+def _workload_volume(wl):
+    """The workload's volume; a section workload is the middle plane along y of its slab (t x x), passed
+    as one plane [1][T][X] (its bricks and rows then run along the section's x)."""
+    import numpy as np
+
+    import synth
+    V, _ = synth.volume(wl["spec"], with_mask=False)
+    if wl.get("section"):
+        V = np.ascontiguousarray(V[:, :, V.shape[2] // 2])[None]
+    return V
+
+
 def _upstream(shape):
     """Fixed seeded upstream gradient dL/dS of the backward half of a step."""
     import numpy as np
@@ -217,7 +234,7 @@ def run_reference(args, wl):
     if rank != 0:
         return
     import synth
-    V, _ = synth.volume(wl["spec"], with_mask=False)
+    V = _workload_volume(wl)
     s = wl["ref_sample"]
     bwd = getattr(args, "form", "fwdbwd") == "fwdbwd"
     for _ in range(args.warmup):
@@ -289,16 +306,17 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    V, _ = synth.volume(wl["spec"], with_mask=False)
+    V = _workload_volume(wl)
     nvox = V.size
     if args.stride > 1 and args.form != "fwd":
         raise SystemExit("--stride > 1 is a forward-only form: pass --form fwd")
-    params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature, stride=args.stride)
+    params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature, stride=args.stride,
+                        **({"directions": wl["directions"]} if "directions" in wl else {}))
     eng = sal.Saliency(V.shape, params)
     dev = torch.device("cuda", local_rank)
     Vd = torch.from_numpy(V).to(dev)
     gSd = torch.from_numpy(_upstream(V.shape)).to(dev)
-    Wd = torch.full((3,), 1.0 / 3.0, dtype=torch.float32, device=dev)
+    Wd = torch.tensor(wl.get("weights", (1.0 / 3.0,) * 3), dtype=torch.float32, device=dev)
     E = torch.empty((3,) + V.shape, dtype=torch.float32, device=dev)
     S3 = torch.empty_like(E)
     gS3 = torch.empty_like(E)

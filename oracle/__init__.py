@@ -164,6 +164,48 @@ def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int
 
 
 # ----------------------------------------------------------------------------------------------
+# 2-D sections (one inline or crossline section A [X][Y]: the method with square n x n windows)
+# ----------------------------------------------------------------------------------------------
+
+def section_features(A, n: int, boundary="symmetric") -> np.ndarray:
+    """Per-pixel features of a 2-D section A [X][Y] with n x n windows (offsets -n/2 .. n/2-1, border
+    extension as for volumes): F = 2-D DFT of the window, signed bins (j, k); Eq. 1 in two dimensions
+    keeps, for each axis, the frequency component of the other axis: r_x = |k| / |(j, k)|,
+    r_y = |j| / |(j, k)|; E_x, E_y = (1/n^2) sum over bins != 0 of r |F|.  Returned with the
+    unprojected mean (1/n^2) sum |F| in front: [E_0, E_x, E_y] [3][X][Y]."""
+    A = _f64(A)
+    X, Y = A.shape
+    mode = {"symmetric": "symmetric", "periodic": "wrap", "zero": "constant"}[boundary]
+    P = np.pad(A, n, mode=mode)
+    sb = np.where(np.arange(n) < n // 2, np.arange(n), np.arange(n) - n).astype(np.float64)
+    j, k = np.meshgrid(sb, sb, indexing="ij")
+    rad = np.sqrt(j * j + k * k)
+    rad[0, 0] = 1.0
+    r = np.stack([np.ones((n, n)), np.abs(k) / rad, np.abs(j) / rad])
+    r[:, 0, 0] = 0.0
+    E = np.empty((3, X, Y))
+    for x in range(X):
+        for y in range(Y):
+            w = P[x + n - n // 2: x + n - n // 2 + n, y + n - n // 2: y + n - n // 2 + n]
+            mag = np.abs(np.fft.fft2(w))
+            for m in range(3):
+                E[m, x, y] = np.sum(r[m] * mag) / (n * n)
+    return E
+
+
+def section_saliency(A, n: int, boundary="symmetric", directions=((0, 1, 0), (0, 0, 1), (0, 1, 1)), R: int = 3,
+                     sigma: float = 1.5, weights=(0.0, 0.5, 0.5)) -> Dict[str, np.ndarray]:
+    """The method on a 2-D section: section features, an in-plane directional center-surround (Eq. 3)
+    and the combination of the two projected maps (Eq. 4; the unprojected map gets weight 0)."""
+    E2 = section_features(A, n, boundary)[:, None]          # [3][1][X][Y]
+    offs, g, did, w = dcs_stencil(directions, R, sigma)
+    S3 = center_surround(E2, offs, w, boundary)
+    out = combine(S3, np.asarray(weights, float))
+    out.update({"E": E2, "S3": S3})
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
 # Step 4: directional center-surround (Eq. 3, Fig. 4)
 # ----------------------------------------------------------------------------------------------
 

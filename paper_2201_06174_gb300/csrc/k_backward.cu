@@ -17,6 +17,7 @@ namespace sal {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kYChunk = 128;   // voxels of a row per warp work item of the stencil kernels
 enum : int { N_LO = 0, N_INV = 3, N_W = 6, N_LOC = 9, N_INVC = 10 };
 
 __device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
@@ -111,7 +112,7 @@ kb_weights_finalize(const double* __restrict__ part, int nparts, const float* __
     }
 }
 
-// K4: gradient of the features through Eq. 3 (gather form).  One warp per (t, x) row, lanes along y;
+// K4: gradient of the features through Eq. 3 (gather form).  One warp per 128 voxels of a (t, x) row;
 // voxels the stencil halo away from every border read their neighbours q + o and their preimages q - o
 // at linear offsets, the others go through the border extension.
 __global__ void __launch_bounds__(kThreads)
@@ -131,10 +132,14 @@ k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long l
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int Q = st.Q;
     const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
-    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+    const int nyc = (Y + kYChunk - 1) / kYChunk;
+    for (long long it = (long long)blockIdx.x * kWarps + wid; it < (long long)T * X * nyc;
+         it += (long long)gridDim.x * kWarps) {
+        const long long r = it / nyc;
+        const int yc = (int)(it - r * nyc) * kYChunk, ye = min(Y, yc + kYChunk);
         const int t = (int)(r / X), x = (int)(r - (long long)t * X);
         const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
-        for (int y = lane; y < Y; y += 32) {
+        for (int y = yc + lane; y < ye; y += 32) {
             const long long q = r * Y + y;
             float eq[3], gq[3], acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -192,8 +197,7 @@ k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long l
     }
 }
 
-// FP64 partials of gw_o (before the -1/Q factor): one warp per (t, x) row, lanes along y, 4 voxels per
-// lane at a time; for each offset the warp sums its voxels' terms (fixed shuffle tree) into a
+// FP64 partials of gw_o (before the -1/Q factor): one warp per 128 voxels of a (t, x) row, 4 per lane; for each offset the warp sums its voxels' terms (fixed shuffle tree) into a
 // warp-private FP64 accumulator, and the warps' accumulators are summed in warp order.
 __global__ void __launch_bounds__(kThreads)
 k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long long gms, const float* __restrict__ coef,
@@ -213,10 +217,15 @@ k4_gw_partial(const float* __restrict__ E, const float* __restrict__ gS, long lo
     __syncthreads();
     const int Q = st.Q;
     const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
-    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+    static_assert(32 * kJ == kYChunk, "one chunk per work item");
+    const int nyc = (Y + kYChunk - 1) / kYChunk;
+    for (long long it = (long long)blockIdx.x * kWarps + wid; it < (long long)T * X * nyc;
+         it += (long long)gridDim.x * kWarps) {
+        const long long r = it / nyc;
         const int t = (int)(r / X), x = (int)(r - (long long)t * X);
         const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
-        for (int y0 = 0; y0 < Y; y0 += 32 * kJ) {   // warp-uniform trip count
+        {
+            const int y0 = (int)(it - r * nyc) * kYChunk;   // warp-uniform
             float ep[kJ][3], gp[kJ][3];
             bool live[kJ], inner[kJ];
 #pragma unroll

@@ -2,7 +2,8 @@
 //   S_m[p] = (1/Q) sum_o | E_m[p] - w_o * Eext_m[p + o] |,   m in {t, x, y},
 // in compensated FP32: each difference is formed by one FMA (fmaf(-w, e_nb, e_c): the product is
 // not rounded before the subtraction) and the Q distances are summed with Kahan compensation.
-// HBM-bound: 12 B read + 12 B written per voxel; neighbours come from L1/L2.  One warp per (t, x) row;
+// HBM-bound: 12 B read + 12 B written per voxel; neighbours come from L1/L2.  One warp per 128 voxels of
+// a (t, x) row;
 // voxels the halo away from every border take the stencil as linear offsets, the others go through the
 // border extension.  Fused per-block min/max of each S_m for the normalisation in K3.
 #include <cfloat>
@@ -13,6 +14,7 @@ namespace sal {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kYChunk = 128;   // voxels of a row per warp work item
 
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
@@ -43,11 +45,15 @@ k2_dcs(const float* __restrict__ E, float* __restrict__ S3, int T, int X, int Y,
     const int Q = st.Q;
     const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
     float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    // one warp per (t, x) row, lanes along y
-    for (long long r = (long long)blockIdx.x * kWarps + wid; r < (long long)T * X; r += (long long)gridDim.x * kWarps) {
+    // one warp per 128-voxel chunk of a (t, x) row, lanes along y
+    const int nyc = (Y + kYChunk - 1) / kYChunk;
+    for (long long it = (long long)blockIdx.x * kWarps + wid; it < (long long)T * X * nyc;
+         it += (long long)gridDim.x * kWarps) {
+        const long long r = it / nyc;
+        const int yc = (int)(it - r * nyc) * kYChunk, ye = min(Y, yc + kYChunk);
         const int t = (int)(r / X), x = (int)(r - (long long)t * X);
         const bool row_inner = t >= ht && t < T - ht && x >= hx && x < X - hx;
-        for (int y = lane; y < Y; y += 32) {
+        for (int y = yc + lane; y < ye; y += 32) {
             const long long p = r * Y + y;
             float ec[3], acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
 #pragma unroll

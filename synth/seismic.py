@@ -142,6 +142,12 @@ def spec_for(name: str) -> VolumeSpec:
         return VolumeSpec(shape, seed=2, faults=_random_faults(rng, shape, 6),
                           salts=_random_salts(rng, shape, 2), fold_amp=5.0,
                           noise_rel=None, snr_db=5.0)
+    if name == "section462x951":
+        # a slab 8 samples thick along y; the 2-D section workload is its middle inline section (t x x)
+        shape = (462, 951, 8)
+        rng = np.random.default_rng(1004)
+        return VolumeSpec(shape, seed=4, faults=_random_faults(rng, shape, 6),
+                          salts=_random_salts(rng, shape, 1), fold_amp=5.0, noise_rel=0.1)
     if name in ("full462x951x651", "cfg5"):
         shape = (462, 951, 651)
         rng = np.random.default_rng(1003)
