@@ -124,6 +124,31 @@ def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, fe
     return E
 
 
+def upsample_adjoint(gE, stride: int) -> np.ndarray:
+    """Transpose of `upsample`: every voxel's gradient goes back to the two lattice points of each axis
+    it was interpolated from, with the same weights (1 - f, f; 1 past the last lattice point)."""
+    out = _f64(gE)
+    for ax in range(3):
+        N = out.shape[ax + 1]
+        L = -(-N // stride)
+        res = np.zeros(out.shape[:ax + 1] + (L,) + out.shape[ax + 2:])
+        for i in range(N):
+            a = i // stride
+            f = (i - a * stride) / stride
+            val = np.take(out, i, axis=ax + 1)
+            lo = [slice(None)] * res.ndim
+            lo[ax + 1] = a
+            if a + 1 < L:
+                hi = list(lo)
+                hi[ax + 1] = a + 1
+                res[tuple(lo)] += (1.0 - f) * val
+                res[tuple(hi)] += f * val
+            else:
+                res[tuple(lo)] += val
+        out = res
+    return out
+
+
 def upsample(Ec, stride: int, shape) -> np.ndarray:
     """Lattice values Ec [3][Tc][Xc][Yc] (at indices multiples of s) to every voxel of `shape`:
     along each axis, a voxel between lattice points a = s floor(i/s) and a + s takes the linear
@@ -419,10 +444,17 @@ def direction_gradient(gw, g, did):
 
 
 def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads: int = 0,
-                     feature="abs") -> np.ndarray:
-    """gV = (dE/dV)^T gE through the extension (adjoint of the feature step)."""
+                     feature="abs", stride: int = 1) -> np.ndarray:
+    """gV = (dE/dV)^T gE through the extension (adjoint of the feature step).  stride s > 1: the
+    gradient of the interpolated features goes back to the lattice (upsample_adjoint) and from there
+    through the cubes of the lattice voxels."""
     V64 = _f64(V)
     gE = _f64(gE)
+    if stride > 1:
+        gEc = upsample_adjoint(gE, stride)
+        lat = np.zeros_like(gE)
+        lat[:, ::stride, ::stride, ::stride] = gEc
+        gE = lat
     gV = np.empty_like(V64)
     _check(lib().sal_oracle_features_adjoint(_dp(V64), *V64.shape, n, BOUNDARY[boundary], TAPER[taper],
                                              FEATURE[feature], _dp(gE), _dp(gV), threads), "features_adjoint")
@@ -430,7 +462,7 @@ def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads:
 
 
 def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", stencil=None, fwd=None,
-                      threads: int = 0, feature="abs") -> Dict[str, np.ndarray]:
+                      threads: int = 0, feature="abs", stride: int = 1) -> Dict[str, np.ndarray]:
     """Gradients of sum_p gS_p S_p with respect to V, the 3 weights W and the per-direction
     alpha_d, with the min-max bounds of the forward pass held constant."""
     if stencil is None:
@@ -438,9 +470,9 @@ def saliency_backward(V, n: int, W, gS, boundary="symmetric", taper="rect", sten
     offsets, g, did, w = stencil
     W = np.asarray(W, dtype=np.float64)
     if fwd is None:
-        fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads, feature=feature)
+        fwd = saliency(V, n, boundary, taper, stencil, weights=W, threads=threads, feature=feature, stride=stride)
     gS3, gW = combine_backward(fwd, W, gS)
     gE, gw = center_surround_adjoint(fwd["E"], gS3, offsets, w, boundary)
     galpha = direction_gradient(gw, g, did)
-    gV = features_adjoint(V, gE, n, boundary, taper, threads, feature)
+    gV = features_adjoint(V, gE, n, boundary, taper, threads, feature, stride)
     return {"gV": gV, "gW": gW, "galpha": galpha, "gE": gE, "gS3": gS3, "gw": gw}

@@ -5,7 +5,10 @@ features interpolated in between) against facts fixed by the definition:
   * the interpolation reproduces an affine field exactly up to the last lattice point of each axis
     and holds that point's value beyond it;
   * one unit lattice value spreads as the separable tent (1 - |d_t|/s)(1 - |d_x|/s)(1 - |d_y|/s);
-  * stride 1 is the per-voxel definition itself.
+  * stride 1 is the per-voxel definition itself;
+  * the interpolation's adjoint satisfies <upsample(a), b> = <a, upsample_adjoint(b)>, and the
+    stride-s feature adjoint matches central differences of the stride-s features (the energy
+    feature: a quadratic form, so the differences are exact up to rounding).
 """
 import numpy as np
 import pytest
@@ -49,3 +52,30 @@ def test_upsample_of_one_lattice_value_is_the_tent():
     hat = [np.maximum(0.0, 1.0 - np.abs(np.arange(d) - s * c) / s) for d, c in zip(shape, a)]
     ref = hat[0][:, None, None] * hat[1][None, :, None] * hat[2][None, None, :]
     assert np.allclose(E[1], ref, atol=1e-15) and not E[0].any() and not E[2].any()
+
+
+@pytest.mark.parametrize("s,shape", [(2, (9, 7, 10)), (3, (10, 8, 13))])
+def test_upsample_adjoint_dot_product(s, shape):
+    rng = np.random.default_rng(s)
+    Tc, Xc, Yc = (-(-d // s) for d in shape)
+    a = rng.standard_normal((3, Tc, Xc, Yc))
+    b = rng.standard_normal((3,) + shape)
+    lhs = np.sum(oracle.upsample(a, s, shape) * b)
+    rhs = np.sum(a * oracle.upsample_adjoint(b, s))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("boundary", ["symmetric", "periodic"])
+def test_stride_feature_adjoint_matches_exact_differences(boundary):
+    n, s = 8, 3
+    V = synth.random_volume((8, 7, 10), seed=31).astype(np.float64)
+    gE = synth.random_volume((3,) + V.shape, seed=32).astype(np.float64)
+    gV = oracle.features_adjoint(V, gE, n, boundary=boundary, feature="energy", stride=s)
+    eps = 1e-3
+    for p in synth.sample_points(V.shape, 10, seed=4).tolist() + [[0, 0, 0], [7, 6, 9]]:
+        Vp = V.copy(); Vp[tuple(p)] += eps
+        Vm = V.copy(); Vm[tuple(p)] -= eps
+        fd = (np.sum(gE * oracle.features(Vp, n, boundary=boundary, feature="energy", stride=s))
+              - np.sum(gE * oracle.features(Vm, n, boundary=boundary, feature="energy", stride=s))) / (2 * eps)
+        # exact for a quadratic form; the bound is the rounding of the two O(1e3) sums differenced
+        assert abs(fd - gV[tuple(p)]) <= 1e-7 * max(1.0, abs(fd)), (p, fd, gV[tuple(p)])
