@@ -182,7 +182,7 @@ def cpu_oracle_rate(V, n, sample, backward=True, feature="abs", stride=1):  # no
     t0 = time.perf_counter()
     fwd = oracle.saliency(sub, n, feature=feature, stride=stride)
     if backward:
-        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd, feature=feature)
+        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd, feature=feature, stride=stride)
     dt = time.perf_counter() - t0
     return sub.size / dt / 1e6, dt, sub.shape
 
@@ -274,7 +274,7 @@ def main():
     ap.add_argument("--feature", default="abs", choices=["abs", "energy"],
                     help="E_m: mean of |F_m| (the paper's step 3) or of |F_m|^2 (energy reading)")
     ap.add_argument("--stride", type=int, default=1,
-                    help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2; forward only)")
+                    help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:
@@ -308,8 +308,6 @@ def main():
 
     V = _workload_volume(wl)
     nvox = V.size
-    if args.stride > 1 and args.form != "fwd":
-        raise SystemExit("--stride > 1 is a forward-only form: pass --form fwd")
     params = sal.Params(n=wl["n"], prec=args.prec, feature=args.feature, stride=args.stride,
                         **({"directions": wl["directions"]} if "directions" in wl else {}))
     eng = sal.Saliency(V.shape, params)

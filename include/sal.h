@@ -64,8 +64,9 @@ typedef struct {
                                s < n/2 (windows overlapping by more than half, Sec. 2
                                step 1) = cubes only at voxels whose indices are all
                                multiples of s, E interpolated trilinearly in between
-                               (held past the last lattice point of an axis).  Forward
-                               only: the spectral backward calls need s = 1          */
+                               (held past the last lattice point of an axis); the
+                               backward goes through the interpolation's adjoint and the
+                               cubes of the lattice voxels                           */
     int taper;              /* 0 = rectangular (the cube as is), 1 = periodic Hann    */
     int boundary;           /* sal_boundary                                           */
     int feature;            /* 0 = E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (step 3: the mean

@@ -298,32 +298,34 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
     }
 }
 
-// Overlap-add of the spectral adjoint, in two passes.  The bricks of t0 in [t_begin, t_begin + t_count)
-// hold blocks [u_t][x'][y'] (u_t < n, x' < XH, y' < YH); brick (xs, sg) covers x_ext in
-// [xs*BX - n/2, xs*BX - n/2 + XH), y_ext likewise with BY, YH; slice u_t of brick t0 lies at
-// t_ext = t0 - n/2 + u_t.
+// Overlap-add of the spectral adjoint, in two passes.  The bricks of t0 = t_begin + r t_step, r < t_count
+// (t_step > 1: the lattice planes of stride-s windows), hold blocks [u_t][x'][y'] (u_t < n, x' < XH,
+// y' < YH); brick (xs, sg) covers x_ext in [xs*BX - n/2, xs*BX - n/2 + XH), y_ext likewise with BY, YH;
+// slice u_t of brick t0 lies at t_ext = t0 - n/2 + u_t.
 //   pass 1 (along t): ext[i][brick][x'][y'] = sum over t0 of the slices at t_ext = t_begin - n/2 + i, for
-//     every extended plane i < t_count + n - 1 -- contiguous slices, read once;
+//     every extended plane i < t_step (t_count - 1) + n -- contiguous slices, read once;
 //   pass 2 (across bricks): gV[q] += sum of ext over the extended positions (t_ext, x_ext, y_ext) that
 //     map to q and the bricks that hold them.
 // Both passes sum in a fixed order, so the result is deterministic.
 __global__ void __launch_bounds__(kThreads)
-k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, int nb, int slice, int t_count) {
+k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, int nb, int slice, int t_count,
+            int t_step) {
     const long long bsz = (long long)n * slice;
-    const long long total = (long long)(t_count + n - 1) * nb * slice;
+    const long long total = (long long)(t_step * (t_count - 1) + n) * nb * slice;
     for (long long idx = (long long)blockIdx.x * kThreads + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * kThreads) {
         const int e = (int)(idx % slice);
         const long long rest = idx / slice;
         const int brick = (int)(rest % nb), i = (int)(rest / nb);
-        // t0 - t_begin = i - n + 1 + j (j < n) covers every brick whose slice u_t = n - 1 - j lands on plane i
+        // the bricks r whose slice u_t = i - t_step r (< n) lands on plane i, in increasing r
+        const int r_lo = i >= n ? (i - n + t_step) / t_step : 0;
+        const int r_hi = min(t_count - 1, i / t_step);
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int r = i - n + 1 + j;   // t0 - t_begin
-            v[j] = (j < n && r >= 0 && r < t_count)
-                       ? __ldg(blocks + ((long long)r * nb + brick) * bsz + (long long)(n - 1 - j) * slice + e)
-                       : 0.f;
+            const int r = r_lo + j;
+            v[j] = r <= r_hi ? __ldg(blocks + ((long long)r * nb + brick) * bsz + (long long)(i - t_step * r) * slice + e)
+                             : 0.f;
         }
         float sum = 0.f;
 #pragma unroll
@@ -334,14 +336,14 @@ k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, in
 
 __global__ void __launch_bounds__(kThreads)
 k5_gather_xy(const float* __restrict__ ext, float* __restrict__ gV, int T, int X, int Y, int bnd, int n, int BX,
-             int XH, int BY, int YH, int t_begin, int t_count, int t_lo, int t_hi) {
+             int XH, int BY, int YH, int t_begin, int t_count, int t_step, int t_lo, int t_hi) {
     const long long q0 = (long long)t_lo * X * Y, q1 = (long long)t_hi * X * Y;
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
     const int nxs = (X + BX - 1) / BX;
     const int nb = nxs * nseg;
     const int slice = XH * YH;
-    const int te_lo = t_begin - h2, te_hi = t_begin + t_count + h2 - 1;   // extended planes of this slab
+    const int te_lo = t_begin - h2, te_hi = t_begin + t_step * (t_count - 1) + h2;   // extended planes of this slab
     for (long long q = q0 + (long long)blockIdx.x * kThreads + threadIdx.x; q < q1;
          q += (long long)gridDim.x * kThreads) {
         const int y = (int)(q % Y);
@@ -435,24 +437,24 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
     return cudaGetLastError();
 }
 
-size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count) {
+size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count, int t_step) {
     const size_t nb = (size_t)((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
-    return (size_t)(t_count + n - 1) * nb * g.XH * g.YH;
+    return (size_t)(t_step * (t_count - 1) + n) * nb * g.XH * g.YH;
 }
 
 cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
-                              SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s) {
-    if (n > 16) return cudaErrorInvalidValue;   // pass 1 unrolls up to 16 bricks per plane
+                              SpectraAdjointGeometry g, int t_begin, int t_count, int t_step, cudaStream_t s) {
+    if (n > 16 || t_step < 1) return cudaErrorInvalidValue;   // pass 1 unrolls up to 16 bricks per plane
     const int nb = ((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
-    const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count);
+    const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count, t_step);
     long long b1 = (e_total + kThreads - 1) / kThreads;
     if (b1 > 152 * 32) b1 = 152 * 32;
     if (b1 < 1) b1 = 1;
-    k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count);
-    // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_count + n/2 - 1); a slab whose
-    // extension leaves the volume may wrap (periodic) or reflect (symmetric) onto any edge plane
+    k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count, t_step);
+    // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_step (t_count - 1) + n/2); a slab
+    // whose extension leaves the volume may wrap (periodic) or reflect (symmetric) onto any edge plane
     const int h2 = n / 2;
-    int t_lo = t_begin - h2, t_hi = t_begin + t_count + h2 - 1;
+    int t_lo = t_begin - h2, t_hi = t_begin + t_step * (t_count - 1) + h2;
     if (t_lo < 0 || t_hi > T) {
         t_lo = 0;
         t_hi = T;
@@ -462,7 +464,7 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
     if (b2 > 152 * 32) b2 = 152 * 32;
     if (b2 < 1) b2 = 1;
     k5_gather_xy<<<(int)b2, kThreads, 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
-                                              t_lo, t_hi);
+                                              t_step, t_lo, t_hi);
     note_launches(2);
     return cudaGetLastError();
 }

@@ -130,7 +130,8 @@ __global__ void k5_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __
 template <int N, bool EN>
 __global__ void __launch_bounds__(kThreads, 1)
 k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
-                      int T, int X, int Y, int bnd, int t_begin, const unsigned char* __restrict__ tables,
+                      int T, int X, int Y, int bnd, int t_begin, int t_step,
+                      const unsigned char* __restrict__ tables,
                       const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
     using G = BtGeo<N>;
     constexpr int H = G::H, P = G::P, XH = G::XH, YH = G::YH, YP = G::YP;
@@ -161,7 +162,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const int q = warp & 3, grp = (warp >> 2) & 3;
     const int yb = blockIdx.x * kBY;
     const int xb = blockIdx.y * P;
-    const int t0 = t_begin + blockIdx.z;
+    const int t0 = t_begin + blockIdx.z * t_step;   // t_step s > 1: the lattice planes of stride-s windows
     const size_t NV = (size_t)T * X * Y;
 
     // ---- set-up ------------------------------------------------------------------------------------
@@ -581,16 +582,17 @@ cudaError_t tables_n(const TwiddleTable& t, int feat, void* dst, cudaStream_t s)
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const void* tables, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int feat, int t_begin, int t_count, int* err, cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, int* err,
+                     cudaStream_t s) {
     using G = BtGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, t_count);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
     if (feat == 1)
-        k5_spectra_adjoint_tc<N, true><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, tab,
-                                                                       f32::make_tw<N>(t), err);
+        k5_spectra_adjoint_tc<N, true><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, t_step,
+                                                                       tab, f32::make_tw<N>(t), err);
     else
-        k5_spectra_adjoint_tc<N, false><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, tab,
-                                                                        f32::make_tw<N>(t), err);
+        k5_spectra_adjoint_tc<N, false><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, t_step,
+                                                                        tab, f32::make_tw<N>(t), err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -624,10 +626,10 @@ SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n) {
 
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                      int t_begin, int t_count, int* err, cudaStream_t s) {
-    if (fmt != 0) return cudaErrorInvalidValue;
-    if (n == 8) return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, err, s);
-    if (n == 16) return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_count, err, s);
+                                      int t_begin, int t_step, int t_count, int* err, cudaStream_t s) {
+    if (fmt != 0 || t_step < 1) return cudaErrorInvalidValue;
+    if (n == 8) return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, err, s);
+    if (n == 16) return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, err, s);
     return cudaErrorInvalidValue;
 }
 

@@ -33,6 +33,7 @@ struct sal_handle {
     double* bpart = nullptr; // [kRedBlocks][64]
     float* blocks = nullptr; // brick blocks of the spectral adjoint for one slab of t0
     float* gext = nullptr;   // the blocks summed along t, per extended plane of the slab
+    float* gEl = nullptr;    // stride > 1: the feature gradient gathered onto the lattice voxels (zero elsewhere)
     int slab_t = 0;
     volatile int* err_host = nullptr;  // mapped host word set by bounded device waits that gave up
     int* err_dev = nullptr;
@@ -69,7 +70,8 @@ void free_scratch(sal_handle* h) {
     if (h->bpart) cudaFree(h->bpart);
     if (h->blocks) cudaFree(h->blocks);
     if (h->gext) cudaFree(h->gext);
-    h->E = h->S3 = h->gE = h->blocks = h->gext = nullptr;
+    if (h->gEl) cudaFree(h->gEl);
+    h->E = h->S3 = h->gE = h->blocks = h->gext = h->gEl = nullptr;
     h->small = nullptr;
     h->bpart = nullptr;
 }
@@ -376,34 +378,40 @@ sal_status ensure_backward_scratch(sal_handle* h) {
     const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     const int nseg = (h->Y + g.BY - 1) / g.BY;
     const size_t per_t = (size_t)((h->X + g.BX - 1) / g.BX) * nseg * g.block_floats * sizeof(float);
-    // the overlap-add's scratch: one brick-summed plane per extended plane of the slab (slab + n - 1)
-    const size_t per_ext = sal::gather_ext_floats(h->n, g, h->X, h->Y, 1) / h->n * sizeof(float);
-    const size_t ext_fixed = (size_t)(h->n - 1) * per_ext;
+    // the overlap-add's scratch: one brick-summed plane per extended plane of the slab (s (slab - 1) + n,
+    // s the stride: the bricks of a slab sit on the lattice planes)
+    const int sc = h->stride;
+    const size_t per_ext = sal::gather_ext_floats(h->n, g, h->X, h->Y, 1, 1) / h->n * sizeof(float);
+    const size_t ext_fixed = (size_t)(h->n - sc) * per_ext;
+    const int planes = (h->T + sc - 1) / sc;   // lattice planes (every plane at stride 1)
     size_t cap = kBlocksCap;
     const size_t plane3 = (size_t)3 * h->N * sizeof(float);
+    const size_t lat3 = sc > 1 ? plane3 : 0;
     const size_t bpart = (size_t)sal::kRedBlocks * 64 * sizeof(double);
     if (h->budget) {
-        const size_t used = h->bytes + plane3 + bpart + ext_fixed;
-        if (used + per_t + per_ext > h->budget)
+        const size_t used = h->bytes + plane3 + lat3 + bpart + ext_fixed;
+        if (used + per_t + sc * per_ext > h->budget)
             return fail(h, SAL_ERR_OOM, "backward scratch exceeds hbm_budget_bytes");
         cap = std::min(cap, h->budget - used);
     }
-    int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->T, cap / (per_t + per_ext)));
-    const size_t ext_bytes = sal::gather_ext_floats(h->n, g, h->X, h->Y, slab) * sizeof(float);
+    int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)planes, cap / (per_t + sc * per_ext)));
+    const size_t ext_bytes = sal::gather_ext_floats(h->n, g, h->X, h->Y, slab, sc) * sizeof(float);
     cudaError_t e;
     if ((e = cudaMalloc(&h->gE, plane3)) != cudaSuccess || (e = cudaMalloc(&h->bpart, bpart)) != cudaSuccess ||
         (e = cudaMalloc(&h->blocks, per_t * slab)) != cudaSuccess ||
-        (e = cudaMalloc(&h->gext, ext_bytes)) != cudaSuccess) {
+        (e = cudaMalloc(&h->gext, ext_bytes)) != cudaSuccess ||
+        (lat3 && (e = cudaMalloc(&h->gEl, lat3)) != cudaSuccess)) {
         if (h->gE) cudaFree(h->gE);
         if (h->bpart) cudaFree(h->bpart);
         if (h->blocks) cudaFree(h->blocks);
+        if (h->gext) cudaFree(h->gext);
         h->gE = h->blocks = h->gext = nullptr;
         h->bpart = nullptr;
         cudaGetLastError();
         return fail(h, SAL_ERR_OOM, std::string("backward scratch cudaMalloc: ") + cudaGetErrorString(e));
     }
-    h->slab_t = slab;
-    h->bytes += plane3 + bpart + per_t * slab + ext_bytes;
+    h->slab_t = slab;   // lattice planes per slab
+    h->bytes += plane3 + lat3 + bpart + per_t * slab + ext_bytes;
     return SAL_OK;
 }
 
@@ -412,20 +420,29 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     cudaError_t e;
     if ((e = cudaMemsetAsync(gV, 0, (size_t)h->N * sizeof(float), st)) != cudaSuccess)
         return cuda_fail(h, e, "spectral adjoint: memset");
+    const int sc = h->stride;
+    if (sc > 1) {
+        // stride s: the gradient of the interpolated features back onto the lattice voxels; the cubes of
+        // the other voxels were never taken, so only the bricks of the lattice planes run
+        if ((e = cudaMemsetAsync(h->gEl, 0, (size_t)3 * h->N * sizeof(float), st)) != cudaSuccess ||
+            (e = sal::upsample_adjoint_launch(gE, h->gEl, h->T, h->X, h->Y, sc, st)) != cudaSuccess)
+            return cuda_fail(h, e, "spectral adjoint: interpolation adjoint");
+        gE = h->gEl;
+    }
     const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
-    for (int t_begin = 0; t_begin < h->T; t_begin += h->slab_t) {
-        const int cnt = std::min(h->slab_t, h->T - t_begin);
+    const int planes = (h->T + sc - 1) / sc;
+    for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
+        const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
-                                                  h->feature, t_begin, cnt, st)
+                                                  h->feature, t_begin, sc, cnt, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,
-                                                 h->boundary, h->feature, t_begin, cnt, h->err_dev, st);
+                                                 h->boundary, h->feature, t_begin, sc, cnt, h->err_dev, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
         if ((e = sal::gather_add_launch(h->blocks, h->gext, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt,
-                                        st)) !=
-            cudaSuccess)
+                                        sc, st)) != cudaSuccess)
             return cuda_fail(h, e, "spectral adjoint: overlap-add");
     }
     return SAL_OK;
@@ -438,7 +455,6 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !W || !gS) return fail(h, SAL_ERR_INVALID_ARG, "V, W and gS must not be NULL");
-    if (h->stride != 1) return fail(h, SAL_ERR_UNSUPPORTED, "the spectral adjoint is built for stride 1");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
@@ -469,7 +485,6 @@ sal_status sal_local_spectra_project_backward(sal_handle* h, const float* V, con
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !gE || !gV) return fail(h, SAL_ERR_INVALID_ARG, "V, gE and gV must not be NULL");
-    if (h->stride != 1) return fail(h, SAL_ERR_UNSUPPORTED, "the spectral adjoint is built for stride 1");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     return spectral_adjoint(h, V, gE, gV, static_cast<cudaStream_t>(stream));
 }

@@ -67,8 +67,10 @@ bool spectra_f32_supported(int n);
 cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
                                int Y, int bnd, int feat, int stride, cudaStream_t s);
-// The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point).
+// The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point),
+// and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.
 cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s);
+cudaError_t upsample_adjoint_launch(const float* gE, float* gEl, int T, int X, int Y, int stride, cudaStream_t s);
 
 // K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
 cudaError_t spectra_f32_n32_prepare();
@@ -117,8 +119,9 @@ struct SpectraAdjointGeometry {
 };
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
+// bricks of t0 = t_begin + r t_step, r < t_count (t_step s > 1: the lattice planes of stride-s windows)
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
-                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_count,
+                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count,
                                        cudaStream_t s);
 // K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
@@ -127,7 +130,7 @@ cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, int f
 SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                      int t_begin, int t_count, int* err, cudaStream_t s);
+                                      int t_begin, int t_step, int t_count, int* err, cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]
@@ -138,9 +141,9 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
 cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s);
 // Overlap-add of one slab's brick blocks into gV through the scratch `ext` (gather_ext_floats floats):
 // first along t (contiguous slices), then across the bricks that overlap each voxel.
-size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count);
+size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count, int t_step);
 cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
-                              SpectraAdjointGeometry g, int t_begin, int t_count, cudaStream_t s);
+                              SpectraAdjointGeometry g, int t_begin, int t_count, int t_step, cudaStream_t s);
 
 // Process-wide count of kernels launched by the library (sal_launch_count).
 void note_launches(int k);

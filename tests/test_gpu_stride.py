@@ -1,6 +1,6 @@
 """GPU parity of the stride-s windows (cubes only at voxels whose indices are multiples of s, windows
 overlapping by n - s of n, more than half for s < n/2; the features interpolated trilinearly in
-between) against the FP64 oracle, through the C ABI, in every precision.
+between) against the FP64 oracle, through the C ABI, in every precision, forward and backward.
 
 Tolerances as for stride 1: FP32 relative L2 <= 1e-5 per map; the 16-bit tensor-core forms relative
 L2 <= 1e-2 per map and max-abs <= 2e-2 on the normalised map S.  Volumes are not multiples of s, so
@@ -82,14 +82,81 @@ def test_stride_lattice_matches_stride_one(sal):
 
 
 def test_stride_arguments(sal):
-    V = torch.zeros((8, 8, 8), device="cuda")
     for n, s in ((8, 4), (4, 2), (16, 0)):   # s must be 1 or 1 < s < n/2
         with pytest.raises(sal.SalError):
             sal.Saliency((8, 8, 8), sal.Params(n=n, stride=s))
-    eng = sal.Saliency((8, 8, 8), sal.Params(n=8, stride=2))
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.mark.parametrize("n,s,shape,boundary,prec,feature,tol", [
+    (8, 2, (9, 7, 37), "symmetric", "fp32", "abs", 1e-5),
+    (8, 3, (10, 8, 35), "periodic", "fp32", "energy", 1e-5),
+    (16, 4, (9, 6, 21), "zero", "fp32", "abs", 1e-5),
+    (8, 2, (9, 21, 37), "symmetric", "bf16", "abs", 1e-2),
+    (16, 3, (8, 11, 35), "symmetric", "fp16", "energy", 1e-2),
+])
+def test_stride_spectral_adjoint_matches_oracle(sal, n, s, shape, boundary, prec, feature, tol):
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 3 * s, faults=1))
+    gE = synth.random_volume((3,) + shape, seed=n + s)
+    eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, prec=prec, feature=feature, stride=s))
     try:
-        with pytest.raises(sal.SalError):
-            sal.sal_local_spectra_project_backward(eng.h, V, torch.zeros((3, 8, 8, 8), device="cuda"),
-                                                   torch.empty_like(V))
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
     finally:
         eng.close()
+    ref = oracle.features_adjoint(V, gE, n, boundary=boundary, feature=feature, stride=s)
+    err = rel_l2(got, ref)
+    print(prec, n, s, shape, boundary, feature, "gV rel-L2", f"{err:.2e}")
+    assert err <= tol
+
+
+def test_stride_spectral_adjoint_in_slabs(sal):
+    """A budget that leaves room for one lattice plane of bricks at a time."""
+    n, s, shape = 8, 2, (11, 9, 40)
+    V, _ = synth.volume(synth.small_spec(shape, seed=9, faults=1))
+    gE = synth.random_volume((3,) + shape, seed=10)
+    base = sal.Saliency(shape, sal.Params(n=n, stride=s))
+    created = sal.sal_workspace_size(base.h)
+    base.close()
+    N = int(np.prod(shape))
+    nseg = -(-shape[2] // 32)
+    per_t = shape[1] * nseg * n * n * (32 + n - 1) * 4
+    per_ext = per_t // n
+    budget = created + 2 * 3 * N * 4 + 1216 * 64 * 8 + per_t + (n - s) * per_ext + s * per_ext
+    eng = sal.Saliency(shape, sal.Params(n=n, stride=s, hbm_budget_bytes=budget))
+    try:
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
+    finally:
+        eng.close()
+    ref = oracle.features_adjoint(V, gE, n, stride=s)
+    assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("n,s,shape,prec,tol", [(8, 2, (10, 12, 33), "fp32", 1e-5), (16, 3, (7, 10, 20), "bf16", 1e-2)])
+def test_stride_fused_backward(sal, n, s, shape, prec, tol):
+    V, D = synth.volume(synth.small_spec(shape, seed=n + s, faults=2))
+    W = np.array([0.45, 0.35, 0.2])
+    alpha = [1.0, 0.8, 1.2]
+    params = sal.Params(n=n, alpha=alpha, prec=prec, stride=s)
+    st = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
+    fwd = oracle.saliency(V, n, stencil=st, weights=W, stride=s)
+    gS = (fwd["S"] - D).astype(np.float32)
+    ref = oracle.saliency_backward(V, n, W, gS, stencil=st, fwd=fwd, stride=s)
+    eng = sal.Saliency(shape, params)
+    try:
+        gV, gW, ga = eng.backward(_cuda(V), _cuda(W), _cuda(gS))
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    errs = (rel_l2(gV.cpu().numpy(), ref["gV"]), rel_l2(gW.cpu().numpy(), ref["gW"]),
+            rel_l2(ga.cpu().numpy(), ref["galpha"]))
+    print(prec, n, s, shape, "gV gW galpha rel-L2", [f"{e:.2e}" for e in errs])
+    assert max(errs) <= tol
