@@ -381,28 +381,40 @@ def main():
     Sh = torch.empty(V.shape, dtype=torch.float32).pin_memory()
     gVh = torch.empty(V.shape, dtype=torch.float32).pin_memory()
 
-    def e2e_step():
+    # (a) the forward as one call that also returns its intermediates, the backward through the
+    # per-step adjoint calls that take them (each step computed once); (b) the fused backward call,
+    # which recomputes the forward from V by itself
+    def e2e_step(fused_backward=False):
         Vd.copy_(Vh, non_blocking=True)
         if args.form == "fwdbwd":
             gSd.copy_(gSh, non_blocking=True)
-        sal.sal_saliency(eng.h, Vd, None, Wd, S, None, None, W)
+        sal.sal_saliency(eng.h, Vd, None, Wd, S, S3, E, W)
         if args.form == "fwdbwd":
-            sal.sal_saliency_backward(eng.h, Vd, Wd, gSd, gV, gW, galpha)
+            if fused_backward:
+                sal.sal_saliency_backward(eng.h, Vd, Wd, gSd, gV, gW, galpha)
+            else:
+                sal.sal_combine_backward(eng.h, S3, Wd, gSd, gS3, gW)
+                sal.sal_center_surround_backward(eng.h, E, gS3, gE, galpha)
+                sal.sal_local_spectra_project_backward(eng.h, Vd, gE, gV)
         Sh.copy_(S, non_blocking=True)
         if args.form == "fwdbwd":
             gVh.copy_(gV, non_blocking=True)
 
-    for _ in range(max(args.warmup, 3)):
-        e2e_step()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record()
-    barrier()
-    e2e_ms = max_over_ranks([e0.elapsed_time(e1)], dist, dev)[0]
-    e2e_value = job_throughput(world, nvox, args.steps, e2e_ms)
+    def e2e_rate(fused_backward):
+        for _ in range(max(args.warmup, 3)):
+            e2e_step(fused_backward)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step(fused_backward)
+        e1.record()
+        barrier()
+        ms = max_over_ranks([e0.elapsed_time(e1)], dist, dev)[0]
+        return job_throughput(world, nvox, args.steps, ms)
+
+    e2e_value = e2e_rate(False)
+    e2e_fused_value = e2e_rate(True) if args.form == "fwdbwd" else None
 
     # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
     k1_fp32_ms = None
@@ -470,7 +482,11 @@ def main():
         "roofline": rl,
         "e2e": {"value": e2e_value, "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes,
-                "d2h_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes},
+                "d2h_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes,
+                "calls": "sal_saliency (with E, S3 out)" + (" + sal_combine_backward + sal_center_surround_backward + "
+                                                            "sal_local_spectra_project_backward"
+                                                            if args.form == "fwdbwd" else ""),
+                "fused_backward_value": e2e_fused_value},
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": wall,

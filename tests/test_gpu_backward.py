@@ -215,8 +215,10 @@ def test_finite_differences_differentiation_workload_128(sal, n):
 
 
 def test_autograd_matches_abi_and_descends(sal):
-    """The autograd Function returns exactly the C-ABI backward, and a small step of V along
-    the negative gradient lowers the L2 distance of S to a fault mask."""
+    """The autograd Function returns exactly the C-ABI per-step adjoint calls on the forward's E and
+    S3 (and the fused backward call to rounding: it applies the combination coefficients at another
+    point), and a small step of V along the negative gradient lowers the L2 distance of S to a
+    fault mask."""
     from paper_2201_06174_gb300.autograd import saliency
     V, D = synth.volume(synth.small_spec((20, 18, 36), seed=2, faults=2))
     eng = sal.Saliency(V.shape, sal.Params(n=8))
@@ -231,8 +233,20 @@ def test_autograd_matches_abi_and_descends(sal):
         loss0.backward()
         gS = (S.detach() - Dt).contiguous()
         eng.set_alpha(ar.detach().cpu().numpy())
+        # the per-step calls on the forward's intermediates
+        E = torch.empty((3,) + V.shape, device="cuda")
+        S3 = torch.empty_like(E)
+        Sx = torch.empty(V.shape, device="cuda")
+        sal.sal_saliency(eng.h, Vt, None, Wr.detach(), Sx, S3, E)
+        gS3, gE = torch.empty_like(E), torch.empty_like(E)
+        gW1, ga1, gV1 = torch.empty(3, device="cuda"), torch.empty(3, device="cuda"), torch.empty_like(Vt)
+        sal.sal_combine_backward(eng.h, S3, Wr.detach(), gS, gS3, gW1)
+        sal.sal_center_surround_backward(eng.h, E, gS3, gE, ga1)
+        sal.sal_local_spectra_project_backward(eng.h, Vt, gE, gV1)
+        assert torch.equal(Vr.grad, gV1) and torch.equal(Wr.grad, gW1) and torch.equal(ar.grad, ga1)
         gV, gW, ga = eng.backward(Vt, Wr.detach(), gS)
-        assert torch.equal(Vr.grad, gV) and torch.equal(Wr.grad, gW) and torch.equal(ar.grad, ga)
+        for a, b in ((Vr.grad, gV), (Wr.grad, gW), (ar.grad, ga)):
+            assert float((a - b).norm()) <= 1e-6 * float(b.norm())
         eta = 1e-3 * float(Vt.norm()) / float(gV.norm())
         with torch.no_grad():
             S1 = saliency(Vt - eta * gV, Wr.detach(), ar.detach(), eng)
