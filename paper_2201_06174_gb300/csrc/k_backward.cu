@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kYChunk = 128;   // voxels of a row per warp work item of the stencil kernels
+constexpr size_t kTileSmemMax = 96 * 1024;   // plane ring of the tiled center-surround adjoint
 enum : int { N_LO = 0, N_INV = 3, N_W = 6, N_LOC = 9, N_INVC = 10 };
 
 __device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
@@ -43,6 +44,26 @@ __device__ __forceinline__ int pre_offset(int q, int o, int N, int mode, int* ou
         for (int i = q + P * ceildiv(lo - q, P); i < hi; i += P) out[c++] = i - o;
         const int r = P - 1 - q;
         for (int i = r + P * ceildiv(lo - r, P); i < hi; i += P) out[c++] = i - o;
+    }
+    return c;
+}
+
+// pre_offset without divisions when N >= abs(o) (the general form otherwise); same positions, same order:
+// the direct preimage q - o, then the reflections below and above the volume (symmetric); the one
+// wrapped position (periodic).
+__device__ __forceinline__ int pre_offset_near(int q, int o, int N, int mode, int* out) {
+    if (N < (o < 0 ? -o : o)) return pre_offset(q, o, N, mode, out);
+    int c = 0;
+    const int p = q - o;
+    if (mode == BND_ZERO) {
+        if ((unsigned)p < (unsigned)N) out[c++] = p;
+    } else if (mode == BND_PERIODIC) {
+        out[c++] = p < 0 ? p + N : (p >= N ? p - N : p);   // p in [-N, 2N): exactly one wrap lands
+    } else {
+        const int lo = -1 - q - o, hi = 2 * N - 1 - q - o;
+        if ((unsigned)p < (unsigned)N) out[c++] = p;
+        if ((unsigned)lo < (unsigned)N) out[c++] = lo;
+        if ((unsigned)hi < (unsigned)N) out[c++] = hi;
     }
     return c;
 }
@@ -112,6 +133,41 @@ kb_weights_finalize(const double* __restrict__ part, int nparts, const float* __
     }
 }
 
+// One voxel q = (t, x, y) of the center-surround adjoint through the border extension: q as the center of
+// each comparison (neighbour ext(q + o)) and as the neighbour (every p with ext(p + o) = q).
+__device__ __forceinline__ void dcs_adjoint_border(const float* __restrict__ E, const float* __restrict__ gS,
+                                                   long long gms, int T, int X, int Y, int bnd, const Stencil& st,
+                                                   const float* s_w, int t, int x, int y, const float (&eq)[3],
+                                                   const float (&gq)[3], float (&acc)[3]) {
+    const long long NV = (long long)T * X * Y;
+    for (int o = 0; o < st.Q; ++o) {
+        const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
+        const float w = s_w[o];
+        // q as the center of the comparison
+        const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd), yy = ext_index(y + dy, Y, bnd);
+        const bool ok = (tt | xx | yy) >= 0;
+        const long long nq = ok ? ((long long)tt * X + xx) * Y + yy : 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float nb = ok ? __ldg(E + m * NV + nq) : 0.f;
+            acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+        }
+        // q as the neighbour: p with ext(p + o) = q
+        int pt[2], px[2], py[2];
+        const int nt = pre_offset_near(t, dt, T, bnd, pt);
+        const int nx = pre_offset_near(x, dx, X, bnd, px);
+        const int ny = pre_offset_near(y, dy, Y, bnd, py);
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nx; ++b)
+                for (int c = 0; c < ny; ++c) {
+                    const long long p = ((long long)pt[a] * X + px[b]) * Y + py[c];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        acc[m] -= w * sgnf(fmaf(-w, eq[m], __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p);
+                }
+    }
+}
+
 // K4: gradient of the features through Eq. 3 (gather form).  One warp per 128 voxels of a (t, x) row;
 // voxels the stencil halo away from every border read their neighbours q + o and their preimages q - o
 // at linear offsets, the others go through the border extension.
@@ -162,38 +218,208 @@ k4_dcs_adjoint(const float* __restrict__ E, const float* __restrict__ gS, long l
                     }
                 }
             } else {
-                for (int o = 0; o < Q; ++o) {
-                    const int dt = st.off[o][0], dx = st.off[o][1], dy = st.off[o][2];
-                    const float w = s_w[o];
-                    // q as the center of the comparison
-                    const int tt = ext_index(t + dt, T, bnd), xx = ext_index(x + dx, X, bnd),
-                              yy = ext_index(y + dy, Y, bnd);
-                    const bool ok = (tt | xx | yy) >= 0;
-                    const long long nq = ok ? ((long long)tt * X + xx) * Y + yy : 0;
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        const float nb = ok ? __ldg(E + m * NV + nq) : 0.f;
-                        acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
-                    }
-                    // q as the neighbour: p with ext(p + o) = q
-                    int pt[2], px[2], py[2];
-                    const int nt = pre_offset(t, dt, T, bnd, pt);
-                    const int nx = pre_offset(x, dx, X, bnd, px);
-                    const int ny = pre_offset(y, dy, Y, bnd, py);
-                    for (int a = 0; a < nt; ++a)
-                        for (int b = 0; b < nx; ++b)
-                            for (int c = 0; c < ny; ++c) {
-                                const long long p = ((long long)pt[a] * X + px[b]) * Y + py[c];
-#pragma unroll
-                                for (int m = 0; m < 3; ++m)
-                                    acc[m] -= w * sgnf(fmaf(-w, eq[m], __ldg(E + m * NV + p))) * __ldg(gS + m * gms + p);
-                            }
-                }
+                dcs_adjoint_border(E, gS, gms, T, X, Y, bnd, st, s_w, t, x, y, eq, gq, acc);
             }
             gE[q] = acc[0] * c0 * st.invQ;
             gE[NV + q] = acc[1] * c1 * st.invQ;
             gE[2 * NV + q] = acc[2] * c2 * st.invQ;
         }
+    }
+}
+
+// K4, tiled: one block per tile of 16 x 16 (x, y) columns and up to 8 planes along t (a thread per
+// column).  E and gS of the tile and its halo stream through a ring of 2 h_t + 1 planes in shared memory
+// (border extension applied at load), so each value is read from global memory once per tile instead of
+// once per neighbour; the next plane is fetched into registers while the current one is computed.  Voxels
+// the stencil halo away from every border do exactly the arithmetic of the row kernel on the staged
+// values; the others (several preimages, or none) take the border path, also on the staged values.
+constexpr int kTX = 16, kTY = 16, kTileT = 8;
+constexpr int kPre = 2;   // plane elements per thread prefetched into registers (the rest loaded at store)
+static_assert(kTX * kTY == kThreads, "one column per thread");
+
+__host__ __device__ inline size_t dcs_tile_smem_bytes(int ht, int hx, int hy) {
+    return (size_t)(2 * ht + 1) * 6 * (kTX + 2 * hx) * (kTY + 2 * hy) * sizeof(float);
+}
+
+// Geometry of the staged planes of one tile: ring slot b of plane t, planes t - h_t .. t + h_t, columns
+// [x0 - h_x, x0 + kTX + h_x) x [y0 - h_y, y0 + kTY + h_y).
+struct TileRing {
+    const float* ring;
+    int R, PL, PE, TXH, TYH, ht, hx, hy, x0, y0;
+    __device__ __forceinline__ int slot(int b, int dt) const {   // |dt| <= h_t: one wrap at most
+        int sl = b + dt;
+        sl += sl < 0 ? R : 0;
+        sl -= sl >= R ? R : 0;
+        return sl;
+    }
+};
+
+// The per-voxel border path of the tiled kernel, in the order of dcs_adjoint_border (same sums, same
+// result): the neighbour ext(q + o) is staged for every voxel of the tile; each preimage p comes from the
+// ring when it lies in the staged region (always, for symmetric and zero extension: a reflected preimage
+// is within the halo of q) and from global memory otherwise (periodic wrap across the volume).
+__device__ __forceinline__ void dcs_adjoint_border_tile(const float* __restrict__ E, const float* __restrict__ gS,
+                                                        long long gms, int T, int X, int Y, int bnd,
+                                                        const TileRing& tr, const int (*s_d)[3], const float* s_w,
+                                                        int Q, int b, int t, int x, int y, const float (&eq)[3],
+                                                        const float (&gq)[3], float (&acc)[3]) {
+    const long long NV = (long long)T * X * Y;
+    for (int o = 0; o < Q; ++o) {
+        const int dt = s_d[o][0], dx = s_d[o][1], dy = s_d[o][2];
+        const float w = s_w[o];
+        const float* nb_p = tr.ring + (size_t)tr.slot(b, dt) * tr.PL + (x - tr.x0 + tr.hx + dx) * tr.TYH +
+                            (y - tr.y0 + tr.hy + dy);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[m] += sgnf(fmaf(-w, nb_p[m * tr.PE], eq[m])) * gq[m];
+        int pt[2], px[2], py[2];
+        const int nt = pre_offset_near(t, dt, T, bnd, pt);
+        const int nx = pre_offset_near(x, dx, X, bnd, px);
+        const int ny = pre_offset_near(y, dy, Y, bnd, py);
+        for (int a = 0; a < nt; ++a)
+            for (int c = 0; c < nx; ++c)
+                for (int e = 0; e < ny; ++e) {
+                    const int rt = pt[a] - t, rx = px[c] - tr.x0 + tr.hx, ry = py[e] - tr.y0 + tr.hy;
+                    float pe[3], pg[3];
+                    if (rt >= -tr.ht && rt <= tr.ht && rx >= 0 && rx < tr.TXH && ry >= 0 && ry < tr.TYH) {
+                        const float* pp = tr.ring + (size_t)tr.slot(b, rt) * tr.PL + rx * tr.TYH + ry;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            pe[m] = pp[m * tr.PE];
+                            pg[m] = pp[(3 + m) * tr.PE];
+                        }
+                    } else {
+                        const long long g = ((long long)pt[a] * X + px[c]) * Y + py[e];
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            pe[m] = __ldg(E + m * NV + g);
+                            pg[m] = __ldg(gS + m * gms + g);
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) acc[m] -= w * sgnf(fmaf(-w, eq[m], pe[m])) * pg[m];
+                }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 3)   // 3 blocks per SM: 59 KB of ring each for the default window
+k4_dcs_adjoint_tiled(const float* __restrict__ E, const float* __restrict__ gS, long long gms,
+                     const float* __restrict__ coef, float* __restrict__ gE, int T, int X, int Y, int bnd,
+                     const __grid_constant__ Stencil st) {
+    extern __shared__ float s_ring[];   // [2 h_t + 1][6][TXH][TYH]: E_t, E_x, E_y, gS_t, gS_x, gS_y
+    __shared__ float s_w[kMaxOffsets];
+    __shared__ int s_d[kMaxOffsets][3];
+    const long long NV = (long long)T * X * Y;
+    const int ht = st.halo[0], hx = st.halo[1], hy = st.halo[2];
+    const int R = 2 * ht + 1, TXH = kTX + 2 * hx, TYH = kTY + 2 * hy, PE = TXH * TYH, PL = 6 * PE;
+    for (int o = threadIdx.x; o < st.Q; o += kThreads) {
+        s_w[o] = st.w[o];
+        s_d[o][0] = st.off[o][0];
+        s_d[o][1] = st.off[o][1];
+        s_d[o][2] = st.off[o][2];
+    }
+    const int ntx = (X + kTX - 1) / kTX, nty = (Y + kTY - 1) / kTY;
+    const int tyi = blockIdx.x % nty, txi = (blockIdx.x / nty) % ntx, tti = blockIdx.x / (nty * ntx);
+    const int x0 = txi * kTX, y0 = tyi * kTY, ta = tti * kTileT, tb = min(T, ta + kTileT);
+    const int lx = threadIdx.x / kTY, ly = threadIdx.x % kTY;
+    const int x = x0 + lx, y = y0 + ly;
+    const float c0 = coef[0], c1 = coef[1], c2 = coef[2];
+    const int Q = st.Q;
+    const bool col_ok = x < X && y < Y;
+    const bool col_inner = x >= hx && x < X - hx && y >= hy && y < Y - hy;
+    // global index of element i (< PE) of extended plane gt, or -1 outside a zero-extended volume
+    auto src = [&](int gt, int i) -> long long {
+        const int ix = i / TYH, iy = i - ix * TYH;
+        const int gx = ext_index(x0 - hx + ix, X, bnd), gy = ext_index(y0 - hy + iy, Y, bnd);
+        return (gt | gx | gy) >= 0 ? ((long long)gt * X + gx) * Y + gy : -1;
+    };
+    float pre[kPre][6];
+    auto fetch = [&](int tp) {   // the first kPre * kThreads elements of plane tp into registers
+        const int gt = ext_index(tp, T, bnd);
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            const long long g = i < PE ? src(gt, i) : -1;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                pre[k][m] = g >= 0 ? __ldg(E + m * NV + g) : 0.f;
+                pre[k][3 + m] = g >= 0 ? __ldg(gS + m * gms + g) : 0.f;
+            }
+        }
+    };
+    auto store = [&](int tp) {   // registers into the ring slot of plane tp; the rest of the plane directly
+        int sl = tp % R;
+        sl += sl < 0 ? R : 0;
+        float* dst = s_ring + (size_t)sl * PL;
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            if (i < PE) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) dst[c * PE + i] = pre[k][c];
+            }
+        }
+        const int gt = ext_index(tp, T, bnd);
+        for (int i = threadIdx.x + kPre * kThreads; i < PE; i += kThreads) {
+            const long long g = src(gt, i);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                dst[m * PE + i] = g >= 0 ? __ldg(E + m * NV + g) : 0.f;
+                dst[(3 + m) * PE + i] = g >= 0 ? __ldg(gS + m * gms + g) : 0.f;
+            }
+        }
+    };
+    for (int tp = ta - ht; tp <= ta + ht; ++tp) {   // planes ta - h_t .. ta + h_t
+        fetch(tp);
+        store(tp);
+    }
+    __syncthreads();
+    int b = ta % R;   // ring slot of plane t, advanced step by step
+    for (int t = ta; t < tb; ++t, b = b + 1 == R ? 0 : b + 1) {
+        const bool more = t + 1 < tb;   // block-uniform
+        if (more) fetch(t + 1 + ht);
+        // every thread reaches the same two barriers of each step; only columns inside the volume compute
+        if (col_ok) {
+            const long long q = ((long long)t * X + x) * Y + y;
+            float eq[3], gq[3], acc[3] = {0.f, 0.f, 0.f};
+            const float* here = s_ring + (size_t)b * PL + (lx + hx) * TYH + (ly + hy);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                eq[m] = here[m * PE];
+                gq[m] = here[(3 + m) * PE];
+            }
+            if (col_inner && t >= ht && t < T - ht) {
+                // the neighbour is q + o and the only preimage of q under offset o is q - o
+#pragma unroll 2
+                for (int o = 0; o < Q; ++o) {
+                    const int dt = s_d[o][0], dx = s_d[o][1], dy = s_d[o][2];
+                    const float w = s_w[o];
+                    // slots of planes t + dt and t - dt (|dt| <= h_t < R: one wrap at most)
+                    int sn = b + dt, sp = b - dt;
+                    sn += sn < 0 ? R : 0;
+                    sn -= sn >= R ? R : 0;
+                    sp += sp < 0 ? R : 0;
+                    sp -= sp >= R ? R : 0;
+                    const float* nb_p = s_ring + (size_t)sn * PL + (lx + hx + dx) * TYH + (ly + hy + dy);
+                    const float* pr_p = s_ring + (size_t)sp * PL + (lx + hx - dx) * TYH + (ly + hy - dy);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const float nb = nb_p[m * PE];
+                        const float pe = pr_p[m * PE], pg = pr_p[(3 + m) * PE];
+                        acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+                        acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
+                    }
+                }
+            } else {
+                const TileRing tr{s_ring, R, PL, PE, TXH, TYH, ht, hx, hy, x0, y0};
+                dcs_adjoint_border_tile(E, gS, gms, T, X, Y, bnd, tr, s_d, s_w, Q, b, t, x, y, eq, gq, acc);
+            }
+            gE[q] = acc[0] * c0 * st.invQ;
+            gE[NV + q] = acc[1] * c1 * st.invQ;
+            gE[2 * NV + q] = acc[2] * c2 * st.invQ;
+        }
+        __syncthreads();   // plane t - h_t is no longer read: its slot takes plane t + 1 + h_t
+        if (more) store(t + 1 + ht);
+        __syncthreads();
     }
 }
 
@@ -419,9 +645,21 @@ cudaError_t backward_weights_launch(const float* S3, const float* gS, long long 
     return cudaGetLastError();
 }
 
+cudaError_t dcs_adjoint_prepare() {
+    return cudaFuncSetAttribute(k4_dcs_adjoint_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+}
+
 cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,
                                int X, int Y, int bnd, const Stencil& st, cudaStream_t s) {
     const long long NV = (long long)T * X * Y;
+    const size_t smem = dcs_tile_smem_bytes(st.halo[0], st.halo[1], st.halo[2]);
+    if (smem <= kTileSmemMax) {   // the tiled kernel when its plane ring fits (dcs_adjoint_prepare)
+        const long long nblk = (long long)((T + kTileT - 1) / kTileT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
+        if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        k4_dcs_adjoint_tiled<<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
+        note_launches(1);
+        return cudaGetLastError();
+    }
     k4_dcs_adjoint<<<red_blocks(NV), kThreads, 0, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
     note_launches(1);
     return cudaGetLastError();

@@ -133,6 +133,9 @@ cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, co
                                       int t_begin, int t_step, int t_count, int* err, cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
+// gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p].  Windows whose
+// plane ring fits shared memory run tiled (dcs_adjoint_prepare sets its size limit; once per device).
+cudaError_t dcs_adjoint_prepare();
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]
 cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,
                                int X, int Y, int bnd, const Stencil& st, cudaStream_t s);

@@ -43,7 +43,7 @@ def _cuda(a):
 
 
 @pytest.mark.parametrize("shape,boundary", [((10, 9, 140), "symmetric"), ((8, 7, 133), "periodic"),
-                                            ((7, 10, 150), "zero")])
+                                            ((7, 10, 150), "zero"), ((12, 26, 140), "symmetric")])
 def test_13_direction_template_forward_and_adjoint(sal, shape, boundary):
     V, _ = synth.volume(synth.small_spec(shape, seed=sum(shape), faults=1))
     E32 = oracle.features(V, 4, boundary=boundary).astype(np.float32)
