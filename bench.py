@@ -52,7 +52,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FMA_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12   # FMA-pipe operations per second (an FFMA counts once)
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
-K1_TRAFFIC = {("salt128", 16, "fp32"): 8843674,   # profiles/salt128_n16_fp32_fwd_bwd.md (per launch)
+K1_TRAFFIC = {("salt128", 16, "fp32"): None,   # the sliding form: not yet captured
               ("salt128", 16, "bf16"): 8597163}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
 K5_TRAFFIC = {("salt128", 16, "bf16"): 717391437}  # K5 alone: 34.2 MB read + 683.2 MB written (brick blocks)
 
@@ -76,14 +76,16 @@ def bins_per_voxel(n: int) -> int:
     return (n // 2 + 1) * n * n
 
 
-def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt", feature="abs"):
+def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt", feature="abs", flops_per_voxel=None):
     """Roofline of a spectral kernel.  FP32 form: its contraction flops (the per-voxel figure
-    4hn + 8hn^2 + 8hn^3, x2 for the adjoint) on the FP32 FMA pipe.  BF16/FP16 form: the
+    4hn + 8hn^2 + 8hn^3, x2 for the adjoint; the sliding form's own count where it runs) on the FP32
+    FMA pipe.  BF16/FP16 form: the
     contraction runs on the tensor cores (reported as `tensor`), and the binding pipe is the
     abs(F) epilogue, h n^2 square roots per voxel on the MUFU pipe; with the energy reading of the
     feature there is no root, and the epilogue's FP32 arithmetic (about 4 FMA-pipe operations per
     bin: |F|^2 and its share of the weighted sums) on the FMA pipe binds."""
-    flops = flops_mult * k1_flops_per_voxel(n) * nvox / (ms / 1e3) / 1e12
+    fpv = k1_flops_per_voxel(n) if flops_per_voxel is None else flops_per_voxel
+    flops = flops_mult * fpv * nvox / (ms / 1e3) / 1e12
     if prec == "fp32":
         return {"kernel": kernel, "bound": "alu", "pipe": "fp32 fma", "achieved": flops, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": flops / FP32_PEAK_TFLOPS, "traffic": traffic,
@@ -124,6 +126,19 @@ def k1_flops_per_voxel(n: int) -> int:
     h = n/2+1 retained t-bins): 4hn + 8hn^2 + 8hn^3."""
     h = n // 2 + 1
     return 4 * h * n + 8 * h * n * n + 8 * h * n ** 3
+
+
+# Outputs per thread of the FP32 K1's sliding form (rect taper, stride 1): the first of each run by the
+# direct stage-3 sum, the others by the recursion.
+K1_F32_SLIDING_RUN = {8: 4, 16: 8}
+
+
+def k1_flops_per_voxel_sliding(n: int) -> int:
+    """Algorithmic flops per voxel of the FP32 K1's sliding form: stages along t and x as in the direct
+    form (4hn + 8hn^2); along y one complex add and one complex rotation per bin and output (8hn^2),
+    and the direct sum (8hn^3) for one output of each run."""
+    h = n // 2 + 1
+    return 4 * h * n + 8 * h * n * n + 8 * h * n * n + 8 * h * n ** 3 // K1_F32_SLIDING_RUN[n]
 
 
 class ClockSampler:
@@ -449,7 +464,11 @@ def main():
     T_, X_, Y_ = V.shape
     ncubes = nvox if sc == 1 else (-(-T_ // sc) * X_ * Y_ if args.prec != "fp32" else
                                    -(-T_ // sc) * -(-X_ // sc) * -(-Y_ // sc))
-    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, ncubes, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature)
+    sliding = args.prec == "fp32" and sc == 1 and n in K1_F32_SLIDING_RUN
+    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, ncubes, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature,
+                     flops_per_voxel=k1_flops_per_voxel_sliding(n) if sliding else None)
+    if sliding:
+        k1_rl["form"] = "sliding DFT along y (flops of that form)"
     if sc > 1:
         k1_rl["cubes_per_launch"] = ncubes
     if args.form == "fwdbwd":

@@ -10,6 +10,12 @@
 // Hermitian symmetry of a real cube keeps only k_t in [0, n/2] (multiplicity 2 for
 // 0 < k_t < n/2).  Each one-axis DFT pairs bins k and n-k: with P = sum g cos, Q = sum g sin,
 // F[k] = P - iQ and F[n-k] = P + iQ, which halves the multiplies.
+// Sliding form of stage 3 (rect taper, n >= 8, one cube per voxel; the brick is staged minus one of its
+// voxels): each thread takes the first output of its chunk by the direct sum and every later one by the
+// recursion of the sliding DFT,
+//   F_{y0+1}[k_y] = e^{2 pi i k_y / n} (F_{y0}[k_y] - G2[y0 - n/2] + G2[y0 + n/2])
+// (the window drops its first sample, gains the next, and its phase origin moves by one), which
+// costs O(1) per bin and output instead of O(n).
 // Stage 3 is fused with the feature epilogue: |F| per bin (|F|^2 for the energy reading), weighted by
 // the projection ratios r_m(k) of Eq. 1 (r_m^2 for the energy; zero at DC), summed over k_y in registers and over (k_t,k_x) rows through
 // shared memory in a fixed order.  Per-voxel spectra never leave the SM.
@@ -43,11 +49,17 @@ template <int N> struct Geo {
     static_assert(NT <= 1024, "threads");
 };
 
-// EN: the energy reading of the feature; STR: stride > 1 (cubes on the lattice of multiples of `stride`)
-template <int N, bool EN, bool STR>
+// Stage-3 forms: direct sum per output; direct on the lattice of multiples of `stride` (stride > 1);
+// sliding recursion along y (rect taper, stride 1).
+enum : int { kDirect = 0, kLattice = 1, kSliding = 2 };
+
+// EN: the energy reading of the feature
+template <int N, bool EN, int MODE>
 __global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
 k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
                const __grid_constant__ Tw<N> tw) {
+    constexpr bool STR = MODE == kLattice;
+    static_assert(MODE != kSliding || N >= 8, "the sliding form pays from n = 8");
     using G = Geo<N>;
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT;
@@ -62,7 +74,11 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     const int x0 = blockIdx.y * stride;   // stride s: cubes only at indices that are multiples of s
     const int t0 = blockIdx.z * stride;
 
-    B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
+    // Sliding form: the brick minus one of its voxels.  Every non-DC bin is unchanged (rect taper), and a
+    // constant region stages exact zeros, whose spectra the recursion keeps at zero; without the shift the
+    // rounding residues of its non-DC bins would be rotated differently at each output.
+    const float vshift = MODE == kSliding ? __ldg(V + ((size_t)t0 * X + x0) * Y + y_start) : 0.f;
+    B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start, vshift);
     __syncthreads();
     B::stage1(s_in, s_g1, tw);
     __syncthreads();
@@ -75,7 +91,69 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     float wt[3][H];                       // r_m(k_t,k_x,+-k_y) (r_m^2: energy) * multiplicity / n^3
     B::template row_weights<EN>(row, wt);
     const float2* grow = s_g2 + (size_t)row * YH;
-    for (int yl = ych * YC; yl < ych * YC + YC; ++yl) {
+    if (MODE == kSliding) {
+        float fr[N], fi[N];   // F[k_y] of the current output, all n bins
+        {
+            const float2* g0 = grow + ych * YC;
+            float pr[H], pi[H], qr[H], qi[H];
+#pragma unroll
+            for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+                const float2 g = g0[u];
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    pr[k] = fmaf(g.x, tw.c[k][u], pr[k]);
+                    pi[k] = fmaf(g.y, tw.c[k][u], pi[k]);
+                    if (k != 0 && 2 * k != N) {
+                        qr[k] = fmaf(g.x, tw.s[k][u], qr[k]);
+                        qi[k] = fmaf(g.y, tw.s[k][u], qi[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                if (k == 0 || 2 * k == N) {
+                    fr[k] = pr[k];
+                    fi[k] = pi[k];
+                } else {
+                    fr[k] = pr[k] + qi[k];       // F[k]   = P - iQ
+                    fi[k] = pi[k] - qr[k];
+                    fr[N - k] = pr[k] - qi[k];   // F[n-k] = P + iQ
+                    fi[N - k] = pi[k] + qr[k];
+                }
+            }
+        }
+        for (int j = 0; j < YC; ++j) {
+            const int yl = ych * YC + j;
+            if (j > 0) {
+                const float2 a = grow[yl - 1], b = grow[yl - 1 + N];   // sample leaving, sample entering
+                const float dr = b.x - a.x, di = b.y - a.y;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    // e^{2 pi i k / n}: the twiddles at u = 1 (rect taper), sine negated above n/2
+                    const float c = k <= N / 2 ? tw.c[k][1] : tw.c[N - k][1];
+                    const float sn = k <= N / 2 ? tw.s[k][1] : -tw.s[N - k][1];
+                    const float xr = fr[k] + dr, xi = fi[k] + di;
+                    fr[k] = fmaf(c, xr, -sn * xi);
+                    fi[k] = fmaf(sn, xr, c * xi);
+                }
+            }
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                float a = bin_mag<EN>(fmaf(fr[k], fr[k], fi[k] * fi[k]));
+                if (k != 0 && 2 * k != N) a += bin_mag<EN>(fmaf(fr[N - k], fr[N - k], fi[N - k] * fi[N - k]));
+                e0 = fmaf(wt[0][k], a, e0);
+                e1 = fmaf(wt[1][k], a, e1);
+                e2 = fmaf(wt[2][k], a, e2);
+            }
+            s_part[(yl * 3 + 0) * ROWS + row] = e0;
+            s_part[(yl * 3 + 1) * ROWS + row] = e1;
+            s_part[(yl * 3 + 2) * ROWS + row] = e2;
+        }
+    }
+    for (int yl = ych * YC; MODE != kSliding && yl < ych * YC + YC; ++yl) {
         if (STR && (y_start + yl) % stride != 0) continue;
         float pr[H], pi[H], qr[H], qi[H];
 #pragma unroll
@@ -135,31 +213,49 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     }
 }
 
-template <int N, bool EN, bool STR>
+template <int N, bool EN, int MODE>
 cudaError_t prepare_one() {
-    return cudaFuncSetAttribute(k1_spectra_f32<N, EN, STR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k1_spectra_f32<N, EN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo<N>::SMEM);
 }
 
+template <int N> constexpr bool kHasSliding = N >= 8;
+
 template <int N>
 cudaError_t prepare() {
-    cudaError_t e = prepare_one<N, false, false>();
-    if (e == cudaSuccess) e = prepare_one<N, true, false>();
-    if (e == cudaSuccess) e = prepare_one<N, false, true>();
-    if (e == cudaSuccess) e = prepare_one<N, true, true>();
+    cudaError_t e = prepare_one<N, false, kDirect>();
+    if (e == cudaSuccess) e = prepare_one<N, true, kDirect>();
+    if (e == cudaSuccess) e = prepare_one<N, false, kLattice>();
+    if (e == cudaSuccess) e = prepare_one<N, true, kLattice>();
+    if constexpr (kHasSliding<N>) {
+        if (e == cudaSuccess) e = prepare_one<N, false, kSliding>();
+        if (e == cudaSuccess) e = prepare_one<N, true, kSliding>();
+    }
     return e;
+}
+
+template <int N, int MODE>
+void launch_mode(const Tw<N>& tw, dim3 grid, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
+                 int stride, cudaStream_t s) {
+    using G = Geo<N>;
+    if (feat == 1) k1_spectra_f32<N, true, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
+    else k1_spectra_f32<N, false, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
 }
 
 template <int N>
 cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
-                   int stride, cudaStream_t s) {
+                   int stride, bool rect, cudaStream_t s) {
     using G = Geo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, (X + stride - 1) / stride, (T + stride - 1) / stride);
     const Tw<N> tw = f32::make_tw<N>(t);
-    if (feat == 1 && stride > 1) k1_spectra_f32<N, true, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
-    else if (feat == 1) k1_spectra_f32<N, true, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, 1, tw);
-    else if (stride > 1) k1_spectra_f32<N, false, true><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
-    else k1_spectra_f32<N, false, false><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, 1, tw);
+    if (stride > 1) {
+        launch_mode<N, kLattice>(tw, grid, V, E, T, X, Y, bnd, feat, stride, s);
+    } else if constexpr (kHasSliding<N>) {
+        if (rect) launch_mode<N, kSliding>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
+        else launch_mode<N, kDirect>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
+    } else {
+        launch_mode<N, kDirect>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
+    }
     note_launches(1);
     return cudaGetLastError();
 }
@@ -179,13 +275,14 @@ cudaError_t spectra_f32_prepare(int n) {
 }
 
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, int stride, cudaStream_t s) {
+                               int Y, int bnd, int feat, int stride, int taper, cudaStream_t s) {
     if (T > 65535 || X > 65535 || stride < 1) return cudaErrorInvalidConfiguration;
+    const bool rect = taper == 0;
     switch (n) {
-        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, stride, s);
-        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, stride, s);
-        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, stride, s);
-        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, stride, s);
+        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
         default: return cudaErrorInvalidValue;
     }
 }

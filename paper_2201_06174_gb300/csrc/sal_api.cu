@@ -117,7 +117,7 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
                 : sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, out, h->T, h->X, h->Y, h->boundary,
                                            h->feature, s, h->err_dev, st);
     } else if (h->prec == SAL_FP32) {
-        e = sal::spectra_f32_launch(h->n, h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, st);
+        e = sal::spectra_f32_launch(h->n, h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, h->taper, st);
     } else {
         e = sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, out, h->T, h->X, h->Y,
                                    h->boundary, h->feature, s, h->err_dev, st);

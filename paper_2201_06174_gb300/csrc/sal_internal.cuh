@@ -65,8 +65,9 @@ struct Reduce {
 // at voxels whose indices are multiples of s; E is then the lattice [3][ceil(T/s)][ceil(X/s)][ceil(Y/s)].
 bool spectra_f32_supported(int n);
 cudaError_t spectra_f32_prepare(int n);
+// taper 0 (rect) at stride 1 takes the sliding form of stage 3 for n >= 8
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, int stride, cudaStream_t s);
+                               int Y, int bnd, int feat, int stride, int taper, cudaStream_t s);
 // The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point),
 // and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.
 cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s);

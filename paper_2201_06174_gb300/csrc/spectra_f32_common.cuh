@@ -94,22 +94,33 @@ template <int N_, int BY_, int NT_> struct Brick {
     static constexpr int G_FLOAT2 = H * N * YH;
     static_assert(NT % 32 == 0 && NT >= YH, "staging maps one y position per thread");
 
-    // Halo brick of V into s_in [N][N][YH], border extension applied per axis.
+    // Halo brick of V into s_in [N][N][YH], border extension applied per axis, minus vshift (a constant
+    // over the brick moves only the DC bin of a rect-tapered cube).
     __device__ static void stage_brick(const float* __restrict__ V, float* s_in, int T, int X, int Y, int bnd,
-                                       int t0, int x0, int y_start) {
+                                       int t0, int x0, int y_start, float vshift = 0.f) {
         constexpr int RSTEP = NT / YH;
+        constexpr int ITERS = (N * N + RSTEP - 1) / RSTEP;   // rows per thread: all loads issued, then stored
         const int tid = threadIdx.x;
         const int yy = tid % YH;
         const int r0 = tid / YH;
         const int gy = ext_index(y_start - N / 2 + yy, Y, bnd);
         if (r0 < RSTEP) {
-            for (int r = r0; r < N * N; r += RSTEP) {
-                const int ut = r / N, ux = r % N;
-                const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-                const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
-                float v = 0.f;
-                if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-                s_in[r * YH + yy] = v;
+            float v[ITERS];
+#pragma unroll
+            for (int i = 0; i < ITERS; ++i) {
+                const int r = r0 + i * RSTEP;
+                v[i] = 0.f;
+                if (r < N * N) {
+                    const int ut = r / N, ux = r % N;
+                    const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
+                    const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
+                    if ((gt | gx | gy) >= 0) v[i] = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < ITERS; ++i) {
+                const int r = r0 + i * RSTEP;
+                if (r < N * N) s_in[r * YH + yy] = v[i] - vshift;
             }
         }
     }

@@ -78,6 +78,30 @@ def test_features_match_oracle(sal, n, shape, boundary):
     assert rel_l2(g["S"], ref["S"]) <= RTOL_F32
 
 
+@pytest.mark.parametrize("n,prec,tol", [(8, "fp32", RTOL_F32), (16, "fp32", RTOL_F32), (8, "bf16", 1e-2),
+                                         (16, "fp16", 1e-2)])
+def test_hann_taper_features_match_oracle(sal, n, prec, tol):
+    """The periodic Hann taper on every axis of the cube.  In the FP32 form it keeps the direct stage-3
+    sum (the sliding recursion along y holds for the rect cube only), so both forms are covered."""
+    shape = (7, 9, 37)
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 7, faults=1))
+    g = _run(sal, V, sal.Params(n=n, taper="hann", prec=prec))
+    E = oracle.features(V, n, taper="hann")
+    for m in range(3):
+        assert rel_l2(g["E"][m], E[m]) <= tol, (m, rel_l2(g["E"][m], E[m]))
+
+
+@pytest.mark.parametrize("n,shape", [(8, (4, 5, 200)), (16, (3, 4, 150))])
+def test_sliding_form_long_rows(sal, n, shape):
+    """Rows long enough for many y bricks (ragged last brick): every chunk of the sliding recursion
+    restarts from a direct sum, so the error stays at the level of the direct form."""
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 11, faults=2))
+    g = _run(sal, V, sal.Params(n=n))
+    E = oracle.features(V, n)
+    for m in range(3):
+        assert rel_l2(g["E"][m], E[m]) <= RTOL_F32, (m, rel_l2(g["E"][m], E[m]))
+
+
 def test_fault48_n8_whole_volume(sal):
     """The 48^3 fault volume, window 8, every map element by element."""
     V, D = synth.volume("fault48")
