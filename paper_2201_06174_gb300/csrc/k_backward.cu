@@ -645,7 +645,16 @@ cudaError_t backward_weights_launch(const float* S3, const float* gS, long long 
     return cudaGetLastError();
 }
 
+// The tiled kernel holds one block per tile for all its planes; with fewer tiles than two waves of
+// resident blocks (3 per SM) it leaves SMs idle, and the row kernel, whose warps cover every row, is faster.
+static int g_tiled_min_blocks = 2 * 152 * 3;
+
 cudaError_t dcs_adjoint_prepare() {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_tiled_min_blocks = 2 * 3 * sms;
     return cudaFuncSetAttribute(k4_dcs_adjoint_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
 }
 
@@ -653,8 +662,9 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
                                int X, int Y, int bnd, const Stencil& st, cudaStream_t s) {
     const long long NV = (long long)T * X * Y;
     const size_t smem = dcs_tile_smem_bytes(st.halo[0], st.halo[1], st.halo[2]);
-    if (smem <= kTileSmemMax) {   // the tiled kernel when its plane ring fits (dcs_adjoint_prepare)
-        const long long nblk = (long long)((T + kTileT - 1) / kTileT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
+    const long long nblk = (long long)((T + kTileT - 1) / kTileT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
+    // the tiled kernel when its plane ring fits (dcs_adjoint_prepare) and its tiles fill the GPU
+    if (smem <= kTileSmemMax && nblk >= g_tiled_min_blocks) {
         if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         k4_dcs_adjoint_tiled<<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
         note_launches(1);

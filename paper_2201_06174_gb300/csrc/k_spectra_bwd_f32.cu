@@ -57,7 +57,8 @@ template <int N> struct BGeo {
 template <int N, bool EN>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
-                       int T, int X, int Y, int bnd, int t_begin, int t_step, const __grid_constant__ Tw<N> tw) {
+                       int T, int X, int Y, int bnd, int t_begin, int t_step, const float* __restrict__ wtab,
+                       const __grid_constant__ Tw<N> tw) {
     using G = BGeo<N>;
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT, WIN = G::WIN;
@@ -104,7 +105,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const int row = tid % ROWS;
     const int ych = tid / ROWS;
     float wt[3][H];
-    B::template row_weights<EN>(row, wt);
+    B::row_weights(wtab, row, wt);
 #pragma unroll
     for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
     const float2* grow = s_g2 + (size_t)row * YH;
@@ -256,16 +257,16 @@ cudaError_t prepare_n() {
 }
 
 template <int N>
-cudaError_t launch_n(const TwiddleTable& t, const float* V, const float* gE, float* blocks, int T, int X, int Y,
-                     int bnd, int feat, int t_begin, int t_step, int t_count, cudaStream_t s) {
+cudaError_t launch_n(const TwiddleTable& t, const float* wtab, const float* V, const float* gE, float* blocks, int T,
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, cudaStream_t s) {
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
     if (feat == 1)
         k5_spectra_adjoint_f32<N, true><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                    t_step, f32::make_tw<N>(t));
+                                                                    t_step, wtab, f32::make_tw<N>(t));
     else
         k5_spectra_adjoint_f32<N, false><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                     t_step, f32::make_tw<N>(t));
+                                                                     t_step, wtab, f32::make_tw<N>(t));
     note_launches(1);
     return cudaGetLastError();
 }
@@ -292,15 +293,16 @@ SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
     }
 }
 
-cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
+cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
+                                       const float* gE, float* blocks,
                                        int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count,
                                        cudaStream_t s) {
     if (t_step < 1) return cudaErrorInvalidValue;
     switch (n) {
-        case 2: return launch_n<2>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 4: return launch_n<4>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 8: return launch_n<8>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 16: return launch_n<16>(tw, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
+        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
+        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
+        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
+        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
         default: return cudaErrorInvalidValue;
     }
 }

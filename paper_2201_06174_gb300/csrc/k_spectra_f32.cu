@@ -57,7 +57,7 @@ enum : int { kDirect = 0, kLattice = 1, kSliding = 2 };
 template <int N, bool EN, int MODE>
 __global__ void __launch_bounds__(Geo<N>::NT, Cfg<N>::MINB)
 k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
-               const __grid_constant__ Tw<N> tw) {
+               const float* __restrict__ wtab, const __grid_constant__ Tw<N> tw) {
     constexpr bool STR = MODE == kLattice;
     static_assert(MODE != kSliding || N >= 8, "the sliding form pays from n = 8");
     using G = Geo<N>;
@@ -89,7 +89,7 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     const int row = tid % ROWS;           // (k_t, k_x)
     const int ych = tid / ROWS;           // chunk of YC outputs
     float wt[3][H];                       // r_m(k_t,k_x,+-k_y) (r_m^2: energy) * multiplicity / n^3
-    B::template row_weights<EN>(row, wt);
+    B::row_weights(wtab, row, wt);
     const float2* grow = s_g2 + (size_t)row * YH;
     if (MODE == kSliding) {
         float fr[N], fi[N];   // F[k_y] of the current output, all n bins
@@ -235,26 +235,26 @@ cudaError_t prepare() {
 }
 
 template <int N, int MODE>
-void launch_mode(const Tw<N>& tw, dim3 grid, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
-                 int stride, cudaStream_t s) {
+void launch_mode(const Tw<N>& tw, const float* wtab, dim3 grid, const float* V, float* E, int T, int X, int Y,
+                 int bnd, int feat, int stride, cudaStream_t s) {
     using G = Geo<N>;
-    if (feat == 1) k1_spectra_f32<N, true, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
-    else k1_spectra_f32<N, false, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tw);
+    if (feat == 1) k1_spectra_f32<N, true, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, wtab, tw);
+    else k1_spectra_f32<N, false, MODE><<<grid, G::NT, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, wtab, tw);
 }
 
 template <int N>
-cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X, int Y, int bnd, int feat,
-                   int stride, bool rect, cudaStream_t s) {
+cudaError_t launch(const TwiddleTable& t, const float* wtab, const float* V, float* E, int T, int X, int Y,
+                   int bnd, int feat, int stride, bool rect, cudaStream_t s) {
     using G = Geo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, (X + stride - 1) / stride, (T + stride - 1) / stride);
     const Tw<N> tw = f32::make_tw<N>(t);
     if (stride > 1) {
-        launch_mode<N, kLattice>(tw, grid, V, E, T, X, Y, bnd, feat, stride, s);
+        launch_mode<N, kLattice>(tw, wtab, grid, V, E, T, X, Y, bnd, feat, stride, s);
     } else if constexpr (kHasSliding<N>) {
-        if (rect) launch_mode<N, kSliding>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
-        else launch_mode<N, kDirect>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
+        if (rect) launch_mode<N, kSliding>(tw, wtab, grid, V, E, T, X, Y, bnd, feat, 1, s);
+        else launch_mode<N, kDirect>(tw, wtab, grid, V, E, T, X, Y, bnd, feat, 1, s);
     } else {
-        launch_mode<N, kDirect>(tw, grid, V, E, T, X, Y, bnd, feat, 1, s);
+        launch_mode<N, kDirect>(tw, wtab, grid, V, E, T, X, Y, bnd, feat, 1, s);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -263,6 +263,16 @@ cudaError_t launch(const TwiddleTable& t, const float* V, float* E, int T, int X
 }  // namespace
 
 bool spectra_f32_supported(int n) { return n == 2 || n == 4 || n == 8 || n == 16; }
+
+size_t f32_weight_table_floats(int n) {
+    const int h = n / 2 + 1;
+    return (size_t)3 * h * h * n;
+}
+
+void f32_weight_table_fill(int n, int feat, float* out) {
+    if (feat == 1) f32::f32_weight_table<true>(n, out);
+    else f32::f32_weight_table<false>(n, out);
+}
 
 cudaError_t spectra_f32_prepare(int n) {
     switch (n) {
@@ -274,15 +284,15 @@ cudaError_t spectra_f32_prepare(int n) {
     }
 }
 
-cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, int stride, int taper, cudaStream_t s) {
+cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V, float* E, int T,
+                               int X, int Y, int bnd, int feat, int stride, int taper, cudaStream_t s) {
     if (T > 65535 || X > 65535 || stride < 1) return cudaErrorInvalidConfiguration;
     const bool rect = taper == 0;
     switch (n) {
-        case 2: return launch<2>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
-        case 4: return launch<4>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
-        case 8: return launch<8>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
-        case 16: return launch<16>(tw, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 2: return launch<2>(tw, wtab, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 4: return launch<4>(tw, wtab, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 8: return launch<8>(tw, wtab, V, E, T, X, Y, bnd, feat, stride, rect, s);
+        case 16: return launch<16>(tw, wtab, V, E, T, X, Y, bnd, feat, stride, rect, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -28,6 +28,7 @@ struct sal_handle {
     void* small = nullptr;   // one allocation holding the reduction scratch
     void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
     void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
+    float* f32_wt = nullptr;    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
     // backward scratch, allocated by the first sal_saliency_backward call
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
@@ -63,6 +64,8 @@ void free_scratch(sal_handle* h) {
     if (h->tc_tables) cudaFree(h->tc_tables);
     if (h->adj_tables) cudaFree(h->adj_tables);
     h->tc_tables = h->adj_tables = nullptr;
+    if (h->f32_wt) cudaFree(h->f32_wt);
+    h->f32_wt = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
     h->err_host = nullptr;
     h->err_dev = nullptr;
@@ -117,7 +120,8 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
                 : sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, out, h->T, h->X, h->Y, h->boundary,
                                            h->feature, s, h->err_dev, st);
     } else if (h->prec == SAL_FP32) {
-        e = sal::spectra_f32_launch(h->n, h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, h->taper, st);
+        e = sal::spectra_f32_launch(h->n, h->tw, h->f32_wt, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s,
+                                    h->taper, st);
     } else {
         e = sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, out, h->T, h->X, h->Y,
                                    h->boundary, h->feature, s, h->err_dev, st);
@@ -222,11 +226,13 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
     const bool tc_fwd = h->prec != SAL_FP32 && sal::spectra_tc_supported(h->n);
     const size_t tab_bytes = tc_fwd ? sal::spectra_tc_tables_bytes(h->n) : 0;
     const size_t adj_bytes = tc_fwd ? sal::spectra_adjoint_tc_tables_bytes(h->n) : 0;
+    const bool f32_tab = h->prec == SAL_FP32 && sal::spectra_f32_supported(h->n);
+    const size_t wt_bytes = f32_tab ? sal::f32_weight_table_floats(h->n) * sizeof(float) : 0;
     const int sc = p->stride;
     const size_t ec_bytes = sc > 1 ? (size_t)3 * ((T + sc - 1) / sc) * ((X + sc - 1) / sc) * ((Y + sc - 1) / sc) *
                                          sizeof(float)
                                    : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
@@ -289,6 +295,21 @@ sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out
             free_scratch(h);
             delete h;
             return cuda_fail(nullptr, e, "tensor-core tables");
+        }
+    }
+    if (f32_tab) {
+        std::vector<float> wt(sal::f32_weight_table_floats(h->n));
+        sal::f32_weight_table_fill(h->n, h->feature, wt.data());
+        if ((e = cudaMalloc(&h->f32_wt, wt_bytes)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            cudaGetLastError();
+            return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        if ((e = cudaMemcpy(h->f32_wt, wt.data(), wt_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            return cuda_fail(nullptr, e, "cudaMemcpy");
         }
     }
     h->bytes = need;
@@ -435,8 +456,8 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->prec == SAL_FP32
-                ? sal::spectra_adjoint_f32_launch(h->n, h->tw, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary,
-                                                  h->feature, t_begin, sc, cnt, st)
+                ? sal::spectra_adjoint_f32_launch(h->n, h->tw, h->f32_wt, V, gE, h->blocks, h->T, h->X, h->Y,
+                                                  h->boundary, h->feature, t_begin, sc, cnt, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,

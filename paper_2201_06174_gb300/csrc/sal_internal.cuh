@@ -66,8 +66,11 @@ struct Reduce {
 bool spectra_f32_supported(int n);
 cudaError_t spectra_f32_prepare(int n);
 // taper 0 (rect) at stride 1 takes the sliding form of stage 3 for n >= 8
-cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* V, float* E, int T, int X,
-                               int Y, int bnd, int feat, int stride, int taper, cudaStream_t s);
+// wtab: the Eq. 1 weight table of the FP32 kernels (f32_weight_table_fill), device memory
+cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V, float* E, int T,
+                               int X, int Y, int bnd, int feat, int stride, int taper, cudaStream_t s);
+size_t f32_weight_table_floats(int n);
+void f32_weight_table_fill(int n, int feat, float* out);   // host
 // The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point),
 // and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.
 cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s);
@@ -121,9 +124,9 @@ struct SpectraAdjointGeometry {
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 // bricks of t0 = t_begin + r t_step, r < t_count (t_step s > 1: the lattice planes of stride-s windows)
-cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* V, const float* gE, float* blocks,
-                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count,
-                                       cudaStream_t s);
+cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
+                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
+                                       int t_begin, int t_step, int t_count, cudaStream_t s);
 // K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
 size_t spectra_adjoint_tc_tables_bytes(int n);
@@ -135,7 +138,8 @@ cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, co
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p].  Windows whose
-// plane ring fits shared memory run tiled (dcs_adjoint_prepare sets its size limit; once per device).
+// plane ring fits shared memory run tiled when the tiles fill two waves of the GPU (dcs_adjoint_prepare
+// sets the size limit and reads the SM count; once per device).
 cudaError_t dcs_adjoint_prepare();
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p]
 cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,

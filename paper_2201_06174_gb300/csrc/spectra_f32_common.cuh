@@ -170,19 +170,35 @@ template <int N_, int BY_, int NT_> struct Brick {
         }
     }
 
-    // Projection weights of one stage-3 row (k_t, k_x) for |k_y| = k in [0, n/2]:
-    // wt[m][k] = r_m(k_t, k_x, k) (or r_m^2, energy) * multiplicity(k_t) / n^3, zero at DC (Eq. 1).
-    template <bool EN>
-    __device__ static void row_weights(int row, float (&wt)[3][H]) {
-        const int kt = row / N, kx = row % N;
-        const int i = kt;
-        const int j = kx < N / 2 ? kx : kx - N;
-        const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
-        const float scale = mult / (float)(N * N * N);
+    // Projection weights of one stage-3 row (k_t, k_x) for |k_y| = k in [0, n/2], from the handle's table
+    // [3][H][ROWS] (f32_weight_table): wt[m][k] = r_m(k_t, k_x, k) (or r_m^2, energy) * multiplicity(k_t)
+    // / n^3, zero at DC (Eq. 1).
+    __device__ static void row_weights(const float* __restrict__ wtab, int row, float (&wt)[3][H]) {
 #pragma unroll
-        for (int k = 0; k < H; ++k) bin_weights<EN>(i, j, k, scale, wt[0][k], wt[1][k], wt[2][k]);
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int k = 0; k < H; ++k) wt[m][k] = __ldg(wtab + (m * H + k) * ROWS + row);
     }
 };
+
+// The table row_weights reads, [3][h][h n] (rows k_t n + k_x), for window n and the feature reading
+// (EN: energy), computed on the host with bin_weights (correctly rounded square roots and division, as on
+// the device).
+template <bool EN>
+inline void f32_weight_table(int n, float* out) {
+    const int h = n / 2 + 1, rows = h * n;
+    for (int row = 0; row < rows; ++row) {
+        const int kt = row / n, kx = row % n;
+        const int j = kx < n / 2 ? kx : kx - n;
+        const float mult = (kt == 0 || 2 * kt == n) ? 1.f : 2.f;
+        const float scale = mult / (float)(n * n * n);
+        for (int k = 0; k < h; ++k) {
+            float w[3];
+            bin_weights<EN>(kt, j, k, scale, w[0], w[1], w[2]);
+            for (int m = 0; m < 3; ++m) out[(m * h + k) * rows + row] = w[m];
+        }
+    }
+}
 
 }  // namespace f32
 }  // namespace sal

@@ -76,23 +76,50 @@ def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
                                             ("symmetric", (20, 24, 70)), ("periodic", (20, 24, 70)),
                                             ("zero", (19, 27, 66))])
 def test_center_surround_adjoint_matches_oracle(sal, boundary, shape):
-    """Thin volumes go through the per-voxel border path only; the wider ones also through the tiled
-    path (16 x 16 column tiles, voxels the stencil halo away from every border)."""
+    """Volumes too small to fill the GPU with tiles: the row kernel, interior and border voxels."""
     _check_center_surround_adjoint(sal, boundary, shape, sal.Params(n=4, boundary=boundary, alpha=[1.0, 0.7, 1.3]))
+
+
+@pytest.mark.parametrize("boundary", ["symmetric", "periodic"])
+def test_center_surround_adjoint_tiled_kernel(sal, boundary):
+    """A volume whose 16 x 16 x 8 tiles fill two waves of the GPU (smaller ones take the row kernel), with
+    ragged tiles on every axis; E and gS random (the adjoint takes any E)."""
+    shape = (100, 130, 150)
+    E32 = np.abs(synth.random_volume((3,) + shape, seed=21)).astype(np.float32)
+    gS3 = synth.random_volume((3,) + shape, seed=22)
+    alpha = [1.0, 0.7, 1.3]
+    params = sal.Params(n=4, boundary=boundary, alpha=alpha)
+    offs, g, did, _ = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
+    w32 = (np.asarray(alpha, np.float32)[did] * g.astype(np.float32)).astype(np.float64)
+    eng = sal.Saliency(shape, params)
+    try:
+        gE = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+        ga = torch.empty(3, dtype=torch.float32, device="cuda")
+        sal.sal_center_surround_backward(eng.h, _cuda(E32), _cuda(gS3), gE, ga)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    refE, gw = oracle.center_surround_adjoint(E32, gS3, offs, w32, boundary)
+    ref_ga = oracle.direction_gradient(gw, g.astype(np.float32), did)
+    assert rel_l2(gE.cpu().numpy(), refE) <= RTOL
+    assert rel_l2(ga.cpu().numpy(), ref_ga) <= RTOL
 
 
 @pytest.mark.parametrize("boundary", ["symmetric", "zero"])
 def test_center_surround_adjoint_wide_in_plane_window(sal, boundary):
-    """An in-plane window of 8 steps each way (the largest offset the library takes): the tiled kernel's
-    planes (32 x 32 with the halo) are larger than what it prefetches into registers, so the rest of each
-    plane is loaded at store time."""
+    """An in-plane window of 8 steps each way (the largest offset the library takes) on a volume the tiled
+    kernel takes: its planes (32 x 32 with the halo) are larger than what it prefetches into registers, so
+    the rest of each plane is loaded at store time."""
     params = sal.Params(n=4, boundary=boundary, directions=((0, 1, 0), (0, 0, 1)), R=8, alpha=[1.1, 0.9])
-    _check_center_surround_adjoint(sal, boundary, (3, 40, 41), params)
+    _check_center_surround_adjoint(sal, boundary, (8, 520, 440), params, random_e=True)
 
 
-def _check_center_surround_adjoint(sal, boundary, shape, params):
-    V, _ = synth.volume(synth.small_spec(shape, seed=5, faults=1))
-    E32 = oracle.features(V, 4, boundary=boundary).astype(np.float32)
+def _check_center_surround_adjoint(sal, boundary, shape, params, random_e=False):
+    if random_e:
+        E32 = np.abs(synth.random_volume((3,) + shape, seed=5)).astype(np.float32)
+    else:
+        V, _ = synth.volume(synth.small_spec(shape, seed=5, faults=1))
+        E32 = oracle.features(V, 4, boundary=boundary).astype(np.float32)
     gS3 = synth.random_volume((3,) + shape, seed=11)
     alpha = params.alpha
     offs, g, did, w = oracle.dcs_stencil(params.directions, params.R, params.sigma, alpha)
