@@ -474,8 +474,15 @@ def main():
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
+        # the FP32 adjoint at n = 16 recomputes the forward stage 3 by the sliding recursion: its flops are
+        # the sliding forward's plus the direct adjoint's; otherwise twice the direct forward's
+        k5_sliding = args.prec == "fp32" and n == 16
         rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
-                      2, K5_TRAFFIC.get(trk), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt", feature=args.feature)
+                      1 if k5_sliding else 2, K5_TRAFFIC.get(trk), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt",
+                      feature=args.feature,
+                      flops_per_voxel=k1_flops_per_voxel_sliding(n) + k1_flops_per_voxel(n) if k5_sliding else None)
+        if k5_sliding:
+            rl["form"] = "forward recompute by the sliding DFT along y (flops of that form)"
         rl["k1"] = k1_rl
     else:
         rl = k1_rl

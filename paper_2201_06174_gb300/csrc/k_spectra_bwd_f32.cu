@@ -53,8 +53,12 @@ template <int N> struct BGeo {
     static_assert(BY % YC == 0 && NT <= 1024, "geometry");
 };
 
-// EN: the energy reading of the feature (Gamma = 2 rho F, no kink band)
-template <int N, bool EN>
+// EN: the energy reading of the feature (Gamma = 2 rho F, no kink band); SL: the forward stage 3 by the
+// sliding recursion along y (rect taper, n = 16; at n = 8 the direct sum is as fast, with 30 fewer
+// registers): the first output of each thread's run by the direct sum,
+// then F_{y0+1}[k] = e^{2 pi i k/n} (F_{y0}[k] - G2[y0 - n/2] + G2[y0 + n/2]) (the forward kernel's form).
+// The brick is staged as is: the kink band below is relative to the raw window's L1 norm.
+template <int N, bool EN, bool SL>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                        int T, int X, int Y, int bnd, int t_begin, int t_step, const float* __restrict__ wtab,
@@ -109,22 +113,48 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
 #pragma unroll
     for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
     const float2* grow = s_g2 + (size_t)row * YH;
+    float fr[N], fi[N];   // F[k_y] of the current output, all n bins
     for (int yi = 0; yi < YC; ++yi) {
         const int yl = ych * YC + yi;
-        float pr[H], pi[H], qr[H], qi[H];
+        if (!SL || yi == 0) {
+            float pr[H], pi[H], qr[H], qi[H];
 #pragma unroll
-        for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
+            for (int k = 0; k < H; ++k) pr[k] = pi[k] = qr[k] = qi[k] = 0.f;
 #pragma unroll
-        for (int u = 0; u < N; ++u) {
-            const float2 g = grow[yl + u];
+            for (int u = 0; u < N; ++u) {
+                const float2 g = grow[yl + u];
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    pr[k] = fmaf(g.x, tw.c[k][u], pr[k]);
+                    pi[k] = fmaf(g.y, tw.c[k][u], pi[k]);
+                    if (k != 0 && 2 * k != N) {
+                        qr[k] = fmaf(g.x, tw.s[k][u], qr[k]);
+                        qi[k] = fmaf(g.y, tw.s[k][u], qi[k]);
+                    }
+                }
+            }
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                pr[k] = fmaf(g.x, tw.c[k][u], pr[k]);
-                pi[k] = fmaf(g.y, tw.c[k][u], pi[k]);
-                if (k != 0 && 2 * k != N) {
-                    qr[k] = fmaf(g.x, tw.s[k][u], qr[k]);
-                    qi[k] = fmaf(g.y, tw.s[k][u], qi[k]);
+                if (k == 0 || 2 * k == N) {
+                    fr[k] = pr[k];
+                    fi[k] = pi[k];
+                } else {
+                    fr[k] = pr[k] + qi[k];       // F[k]   = P - iQ
+                    fi[k] = pi[k] - qr[k];
+                    fr[N - k] = pr[k] - qi[k];   // F[n-k] = P + iQ
+                    fi[N - k] = pi[k] + qr[k];
                 }
+            }
+        } else {
+            const float2 a = grow[yl - 1], b = grow[yl - 1 + N];   // sample leaving, sample entering
+            const float dr = b.x - a.x, di = b.y - a.y;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const float c = k <= N / 2 ? tw.c[k][1] : tw.c[N - k][1];
+                const float sn = k <= N / 2 ? tw.s[k][1] : -tw.s[N - k][1];
+                const float xr = fr[k] + dr, xi = fi[k] + di;
+                fr[k] = fmaf(c, xr, -sn * xi);
+                fi[k] = fmaf(sn, xr, c * xi);
             }
         }
         const float g0 = s_ge[yl], g1 = s_ge[BY + yl], g2 = s_ge[2 * BY + yl];
@@ -136,18 +166,18 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
         for (int k = 0; k < H; ++k) {
             const float rho = fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
             if (k == 0 || 2 * k == N) {
-                const float m2 = fmaf(pr[k], pr[k], pi[k] * pi[k]);
+                const float m2 = fmaf(fr[k], fr[k], fi[k] * fi[k]);
                 const float sc = f32::bin_adjoint_scale<EN>(rho, m2, thr2);
-                ar[k] = sc * pr[k];
-                ai[k] = sc * pi[k];
+                ar[k] = sc * fr[k];
+                ai[k] = sc * fi[k];
                 br[k] = bi[k] = 0.f;
             } else {
-                const float fr = pr[k] + qi[k], fi = pi[k] - qr[k];   // F[k]
-                const float hr = pr[k] - qi[k], hi = pi[k] + qr[k];   // F[n-k]
-                const float m2a = fmaf(fr, fr, fi * fi), m2b = fmaf(hr, hr, hi * hi);
+                const float far = fr[k], fai = fi[k];            // F[k]
+                const float hr = fr[N - k], hi = fi[N - k];      // F[n-k]
+                const float m2a = fmaf(far, far, fai * fai), m2b = fmaf(hr, hr, hi * hi);
                 const float sa = f32::bin_adjoint_scale<EN>(rho, m2a, thr2);
                 const float sb = f32::bin_adjoint_scale<EN>(rho, m2b, thr2);
-                const float gar = sa * fr, gai = sa * fi, gbr = sb * hr, gbi = sb * hi;
+                const float gar = sa * far, gai = sa * fai, gbr = sb * hr, gbi = sb * hi;
                 ar[k] = gar + gbr;
                 ai[k] = gai + gbi;
                 br[k] = gbi - gai;        // i * (Gamma_a - Gamma_b)
@@ -247,26 +277,49 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     }
 }
 
+template <int N> constexpr bool kAdjointSliding = N >= 16;
+
 template <int N>
 cudaError_t prepare_n() {
-    cudaError_t e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)BGeo<N>::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)BGeo<N>::SMEM);
+    constexpr int smem = (int)BGeo<N>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (kAdjointSliding<N>) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k5_spectra_adjoint_f32<N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+    }
+    return e;
+}
+
+template <int N, bool SL>
+void launch_sl(const TwiddleTable& t, const float* wtab, dim3 grid, const float* V, const float* gE, float* blocks,
+               int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, cudaStream_t s) {
+    using G = BGeo<N>;
+    if (feat == 1)
+        k5_spectra_adjoint_f32<N, true, SL><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
+                                                                        t_step, wtab, f32::make_tw<N>(t));
+    else
+        k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
+                                                                         t_step, wtab, f32::make_tw<N>(t));
 }
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const float* wtab, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, bool rect, cudaStream_t s) {
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
-    if (feat == 1)
-        k5_spectra_adjoint_f32<N, true><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                    t_step, wtab, f32::make_tw<N>(t));
-    else
-        k5_spectra_adjoint_f32<N, false><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                     t_step, wtab, f32::make_tw<N>(t));
+    if constexpr (kAdjointSliding<N>) {
+        if (rect) launch_sl<N, true>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
+        else launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
+    } else {
+        launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
+    }
     note_launches(1);
     return cudaGetLastError();
 }
@@ -294,15 +347,15 @@ SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
 }
 
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
-                                       const float* gE, float* blocks,
-                                       int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count,
-                                       cudaStream_t s) {
+                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
+                                       int t_begin, int t_step, int t_count, int taper, cudaStream_t s) {
+    const bool rect = taper == 0;
     if (t_step < 1) return cudaErrorInvalidValue;
     switch (n) {
-        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
-        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, s);
+        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
+        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
+        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
+        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
         default: return cudaErrorInvalidValue;
     }
 }

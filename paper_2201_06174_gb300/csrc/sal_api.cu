@@ -457,7 +457,7 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, h->f32_wt, V, gE, h->blocks, h->T, h->X, h->Y,
-                                                  h->boundary, h->feature, t_begin, sc, cnt, st)
+                                                  h->boundary, h->feature, t_begin, sc, cnt, h->taper, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,

@@ -124,9 +124,10 @@ struct SpectraAdjointGeometry {
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 // bricks of t0 = t_begin + r t_step, r < t_count (t_step s > 1: the lattice planes of stride-s windows)
+// taper 0 (rect) recomputes the forward stage 3 by the sliding recursion for n = 16
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
                                        const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                       int t_begin, int t_step, int t_count, cudaStream_t s);
+                                       int t_begin, int t_step, int t_count, int taper, cudaStream_t s);
 // K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
 size_t spectra_adjoint_tc_tables_bytes(int n);

@@ -72,6 +72,30 @@ def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
     assert rel_l2(got, ref) <= RTOL, rel_l2(got, ref)
 
 
+@pytest.mark.parametrize("n,shape,taper,prec,tol", [
+    (8, (6, 7, 70), "hann", "fp32", RTOL),
+    (16, (5, 6, 40), "hann", "fp32", RTOL),
+    (16, (5, 6, 40), "hann", "bf16", 1e-2),
+    (8, (4, 5, 150), "rect", "fp32", RTOL),
+    (16, (3, 4, 100), "rect", "fp32", RTOL),
+])
+def test_spectral_adjoint_taper_and_long_rows(sal, n, shape, taper, prec, tol):
+    """The Hann taper (the FP32 adjoint recomputes the forward stage 3 by the direct sum there) and rows of
+    many y bricks (the sliding recomputation restarts from a direct sum for every run of outputs)."""
+    V, _ = synth.volume(synth.small_spec(shape, seed=n + 31, faults=2))
+    gE = synth.random_volume((3,) + shape, seed=n + 32)
+    eng = sal.Saliency(shape, sal.Params(n=n, taper=taper, prec=prec))
+    try:
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
+    finally:
+        eng.close()
+    ref = oracle.features_adjoint(V, gE, n, taper=taper)
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+
+
 @pytest.mark.parametrize("boundary,shape", [("symmetric", (9, 8, 35)), ("periodic", (9, 8, 35)), ("zero", (9, 8, 35)),
                                             ("symmetric", (20, 24, 70)), ("periodic", (20, 24, 70)),
                                             ("zero", (19, 27, 66))])
