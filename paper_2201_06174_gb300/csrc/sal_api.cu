@@ -116,7 +116,7 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
     cudaError_t e;
     if (h->n == 32) {
         e = h->prec == SAL_FP32
-                ? sal::spectra_f32_n32_launch(h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, st)
+                ? sal::spectra_f32_n32_launch(h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, h->taper, st)
                 : sal::spectra_tc32_launch(h->prec == SAL_BF16 ? 1 : 0, h->tw, V, out, h->T, h->X, h->Y, h->boundary,
                                            h->feature, s, h->err_dev, st);
     } else if (h->prec == SAL_FP32) {

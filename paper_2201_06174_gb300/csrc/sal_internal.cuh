@@ -78,8 +78,9 @@ cudaError_t upsample_adjoint_launch(const float* gE, float* gEl, int T, int X, i
 
 // K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
 cudaError_t spectra_f32_n32_prepare();
+// taper 0 (rect) at stride 1 takes the sliding form of stage 3
 cudaError_t spectra_f32_n32_launch(const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y, int bnd,
-                                   int feat, int stride, cudaStream_t s);
+                                   int feat, int stride, int taper, cudaStream_t s);
 cudaError_t spectra_tc32_prepare(int fmt);
 cudaError_t spectra_tc32_launch(int fmt, const TwiddleTable& tw, const float* V, float* E, int T, int X, int Y,
                                 int bnd, int feat, int stride, int* err, cudaStream_t s);

@@ -187,6 +187,24 @@ def test_window32_forward_matches_oracle(sal, prec, tol):
         assert np.abs(g["S"] - ref["S"]).max() <= 2e-2
 
 
+@pytest.mark.parametrize("shape,taper", [((3, 4, 40), "rect"), ((3, 5, 19), "hann")])
+def test_window32_fp32_sliding_and_taper(sal, shape, taper):
+    """FP32, 32^3 window: rows of several y bricks (ragged last one) through the sliding form, and the Hann
+    taper through the direct stage-3 sum."""
+    V, _ = synth.volume(synth.small_spec(shape, seed=33, faults=2))
+    g = _run(sal, V, sal.Params(n=32, taper=taper))
+    E = oracle.features(V, 32, taper=taper)
+    for m in range(3):
+        assert rel_l2(g["E"][m], E[m]) <= 1e-5, (m, rel_l2(g["E"][m], E[m]))
+
+
+def test_window32_constant_volume_gives_zero(sal):
+    V = np.full((4, 5, 20), 1.75, np.float32)
+    g = _run(sal, V, sal.Params(n=32))
+    assert np.max(np.abs(g["E"])) <= 1e-5 * 1.75
+    assert np.all(g["S"] == 0.0)
+
+
 def test_window32_backward_is_not_built(sal):
     eng = sal.Saliency((4, 4, 8), sal.Params(n=32))
     try:
