@@ -31,7 +31,7 @@ template <int N> struct Cfg;
 template <> struct Cfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
 template <> struct Cfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
 template <> struct Cfg<8>  { static constexpr int BY = 32, YC = 4, MINB = 2; };
-template <> struct Cfg<16> { static constexpr int BY = 16, YC = 8, MINB = 2; };
+template <> struct Cfg<16> { static constexpr int BY = 32, YC = 16, MINB = 2; };
 
 template <int N> struct Geo {
     static constexpr int H = N / 2 + 1;
@@ -42,9 +42,12 @@ template <int N> struct Geo {
     using B = f32::Brick<N, BY, NT>;
     static constexpr int YH = B::YH;
     static constexpr int PART_FLOATS = BY * 3 * ROWS;
-    static constexpr size_t A_BYTES_IN = (size_t)B::IN_FLOATS * 4 + (size_t)B::G_FLOAT2 * 8;
-    static constexpr size_t A_BYTES = A_BYTES_IN > (size_t)PART_FLOATS * 4 ? A_BYTES_IN : (size_t)PART_FLOATS * 4;
-    static constexpr size_t SMEM = A_BYTES + (size_t)B::G_FLOAT2 * 8;
+    // region 1: G1 (stages 1-2), then the partial sums (stage 3, reduction); region 2: the halo brick
+    // (staging, stage 1), then G2 (stages 2-3).  Each stage reads one region and writes the other.
+    static constexpr size_t G_BYTES = (size_t)B::G_FLOAT2 * 8, IN_BYTES = (size_t)B::IN_FLOATS * 4;
+    static constexpr size_t R1 = G_BYTES > (size_t)PART_FLOATS * 4 ? G_BYTES : (size_t)PART_FLOATS * 4;
+    static constexpr size_t R2 = IN_BYTES > G_BYTES ? IN_BYTES : G_BYTES;
+    static constexpr size_t SMEM = R1 + R2;
     static_assert(BY % YC == 0, "BY/YC");
     static_assert(NT <= 1024, "threads");
 };
@@ -64,10 +67,10 @@ k1_spectra_f32(const float* __restrict__ V, float* __restrict__ E, int T, int X,
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* s_in = reinterpret_cast<float*>(smem_raw);                                // [N][N][YH]
-    float2* s_g1 = reinterpret_cast<float2*>(smem_raw + (size_t)B::IN_FLOATS * 4);   // [H][N][YH]
-    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::A_BYTES);                 // [H][N][YH]
-    float* s_part = reinterpret_cast<float*>(smem_raw);                              // [BY][3][ROWS] (aliases A)
+    float2* s_g1 = reinterpret_cast<float2*>(smem_raw);                              // [H][N][YH]    region 1
+    float* s_part = reinterpret_cast<float*>(smem_raw);                              // [BY][3][ROWS] region 1
+    float* s_in = reinterpret_cast<float*>(smem_raw + G::R1);                        // [N][N][YH]    region 2
+    float2* s_g2 = reinterpret_cast<float2*>(smem_raw + G::R1);                      // [H][N][YH]    region 2
 
     const int tid = threadIdx.x;
     const int y_start = blockIdx.x * BY;
