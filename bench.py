@@ -52,7 +52,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FMA_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12   # FMA-pipe operations per second (an FFMA counts once)
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
-K1_TRAFFIC = {("salt128", 16, "fp32"): None,   # 32-output form: not yet captured
+K1_TRAFFIC = {("salt128", 16, "fp32"): 8711168,   # sliding, 32-output form; profiles/salt128_n16_fp32_fwd_bwd.md
               ("salt128", 16, "bf16"): 8597163}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
 K5_TRAFFIC = {("salt128", 16, "bf16"): 717391437}  # K5 alone: 34.2 MB read + 683.2 MB written (brick blocks)
 
