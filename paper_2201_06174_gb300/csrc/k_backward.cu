@@ -533,87 +533,87 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
 //   pass 2 (across bricks): gV[q] += sum of ext over the extended positions (t_ext, x_ext, y_ext) that
 //     map to q and the bricks that hold them.
 // Both passes sum in a fixed order, so the result is deterministic.
+// Pass 1: one warp per (plane i, brick) row of `slice` contiguous floats, lanes along the row.
 __global__ void __launch_bounds__(kThreads)
 k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, int nb, int slice, int t_count,
             int t_step) {
+    constexpr int kWarps = kThreads / 32;
+    const int lane = threadIdx.x & 31;
     const long long bsz = (long long)n * slice;
-    const long long total = (long long)(t_step * (t_count - 1) + n) * nb * slice;
-    for (long long idx = (long long)blockIdx.x * kThreads + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * kThreads) {
-        const int e = (int)(idx % slice);
-        const long long rest = idx / slice;
-        const int brick = (int)(rest % nb), i = (int)(rest / nb);
+    const long long rows = (long long)(t_step * (t_count - 1) + n) * nb;
+    // from the slice of brick r to that of brick r + 1 on the same plane: the next t0's block, u_t - t_step
+    const long long rstep = (long long)nb * bsz - (long long)t_step * slice;
+    for (long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); w < rows;
+         w += (long long)gridDim.x * kWarps) {
+        const int brick = (int)(w % nb), i = (int)(w / nb);
         // the bricks r whose slice u_t = i - t_step r (< n) lands on plane i, in increasing r
         const int r_lo = i >= n ? (i - n + t_step) / t_step : 0;
-        const int r_hi = min(t_count - 1, i / t_step);
-        float v[16];
+        const int nr = min(t_count - 1, i / t_step) - r_lo + 1;   // at most 16 (n <= 16)
+        const float* src = blocks + ((long long)r_lo * nb + brick) * bsz + (long long)(i - t_step * r_lo) * slice;
+        float* dst = ext + w * slice;
+        for (int e = lane; e < slice; e += 32) {
+            float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int r = r_lo + j;
-            v[j] = r <= r_hi ? __ldg(blocks + ((long long)r * nb + brick) * bsz + (long long)(i - t_step * r) * slice + e)
-                             : 0.f;
+            for (int j = 0; j < 16; ++j) v[j] = j < nr ? __ldg(src + j * rstep + e) : 0.f;
+            float sum = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum += v[j];
+            dst[e] = sum;
         }
-        float sum = 0.f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) sum += v[j];
-        ext[idx] = sum;
     }
 }
 
+// Pass 2: one thread per voxel; block (32 y, 8 x) of plane t = t_lo + blockIdx.z.
 __global__ void __launch_bounds__(kThreads)
 k5_gather_xy(const float* __restrict__ ext, float* __restrict__ gV, int T, int X, int Y, int bnd, int n, int BX,
-             int XH, int BY, int YH, int t_begin, int t_count, int t_step, int t_lo, int t_hi) {
-    const long long q0 = (long long)t_lo * X * Y, q1 = (long long)t_hi * X * Y;
+             int XH, int BY, int YH, int t_begin, int t_count, int t_step, int t_lo) {
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
     const int nxs = (X + BX - 1) / BX;
     const int nb = nxs * nseg;
     const int slice = XH * YH;
     const int te_lo = t_begin - h2, te_hi = t_begin + t_step * (t_count - 1) + h2;   // extended planes of this slab
-    for (long long q = q0 + (long long)blockIdx.x * kThreads + threadIdx.x; q < q1;
-         q += (long long)gridDim.x * kThreads) {
-        const int y = (int)(q % Y);
-        const int x = (int)((q / Y) % X);
-        const int t = (int)(q / ((long long)X * Y));
-        if (t >= h2 && t < T - h2 && x >= h2 && x < X - h2 && y >= h2 && y < Y - h2) {
-            // interior voxel: its only extended position is itself
-            if (t < te_lo || t >= te_hi) continue;
-            const int xa = max(0, ceildiv(x + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(x + h2, BX));
-            const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
-            const float* plane = ext + (long long)(t - te_lo) * nb * slice;
-            float sum = 0.f;
-            for (int xs = xa; xs <= xb; ++xs)
-                for (int sg = sa; sg <= sb; ++sg)
-                    sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
-                                 (y - sg * BY + h2));
-            gV[q] += sum;
-            continue;
-        }
-        int et[40], ex[40], ey[40];
-        const int nt = pre_range(t, T, bnd, te_lo, te_hi, et, 40);
-        if (nt == 0) continue;
-        const int nx = pre_range(x, X, bnd, -h2, X + h2 - 1, ex, 40);
-        const int ny = pre_range(y, Y, bnd, -h2, Y + h2 - 1, ey, 40);
+    const int t = t_lo + blockIdx.z, x = blockIdx.y * 8 + threadIdx.y, y = blockIdx.x * 32 + threadIdx.x;
+    if (x >= X || y >= Y) return;
+    const long long q = ((long long)t * X + x) * Y + y;
+    if (t >= h2 && t < T - h2 && x >= h2 && x < X - h2 && y >= h2 && y < Y - h2) {
+        // interior voxel: its only extended position is itself
+        if (t < te_lo || t >= te_hi) return;
+        const int xa = max(0, ceildiv(x + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(x + h2, BX));
+        const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
+        const float* plane = ext + (long long)(t - te_lo) * nb * slice;
         float sum = 0.f;
-        for (int a = 0; a < nt; ++a) {
-            const float* plane = ext + (long long)(et[a] - te_lo) * nb * slice;
-            for (int b = 0; b < nx; ++b) {
-                const int xe = ex[b];
-                const int xa = max(0, ceildiv(xe + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(xe + h2, BX));
-                for (int xs = xa; xs <= xb; ++xs) {
-                    const int ux = xe - xs * BX + h2;
-                    for (int c = 0; c < ny; ++c) {
-                        const int ye = ey[c];
-                        const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
-                        const int sb = min(nseg - 1, floordiv(ye + h2, BY));
-                        for (int sg = sa; sg <= sb; ++sg)
-                            sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + ux * YH + (ye - sg * BY + h2));
-                    }
+        for (int xs = xa; xs <= xb; ++xs)
+            for (int sg = sa; sg <= sb; ++sg)
+                sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
+                             (y - sg * BY + h2));
+        gV[q] += sum;
+        return;
+    }
+    int et[40], ex[40], ey[40];
+    const int nt = pre_range(t, T, bnd, te_lo, te_hi, et, 40);
+    if (nt == 0) return;
+    const int nx = pre_range(x, X, bnd, -h2, X + h2 - 1, ex, 40);
+    const int ny = pre_range(y, Y, bnd, -h2, Y + h2 - 1, ey, 40);
+    float sum = 0.f;
+    for (int a = 0; a < nt; ++a) {
+        const float* plane = ext + (long long)(et[a] - te_lo) * nb * slice;
+        for (int b = 0; b < nx; ++b) {
+            const int xe = ex[b];
+            const int xa = max(0, ceildiv(xe + h2 - XH + 1, BX)), xb = min(nxs - 1, floordiv(xe + h2, BX));
+            for (int xs = xa; xs <= xb; ++xs) {
+                const int ux = xe - xs * BX + h2;
+                for (int c = 0; c < ny; ++c) {
+                    const int ye = ey[c];
+                    const int sa = max(0, ceildiv(ye + h2 - YH + 1, BY));
+                    const int sb = min(nseg - 1, floordiv(ye + h2, BY));
+                    for (int sg = sa; sg <= sb; ++sg)
+                        sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + ux * YH + (ye - sg * BY + h2));
                 }
             }
         }
-        gV[q] += sum;
     }
+    gV[q] += sum;
 }
 
 // gS3[m][p] = coef[m] * gS[p]
@@ -695,8 +695,9 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
     if (n > 16 || t_step < 1) return cudaErrorInvalidValue;   // pass 1 unrolls up to 16 bricks per plane
     const int nb = ((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
     const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count, t_step);
-    long long b1 = (e_total + kThreads - 1) / kThreads;
-    if (b1 > 152 * 32) b1 = 152 * 32;
+    const long long rows1 = e_total / (g.XH * g.YH);   // (plane, brick) rows, a warp each
+    long long b1 = (rows1 + kThreads / 32 - 1) / (kThreads / 32);
+    if (b1 > 152 * 8) b1 = 152 * 8;
     if (b1 < 1) b1 = 1;
     k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count, t_step);
     // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_step (t_count - 1) + n/2); a slab
@@ -707,12 +708,10 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
         t_lo = 0;
         t_hi = T;
     }
-    const long long NV = (long long)(t_hi - t_lo) * X * Y;
-    long long b2 = (NV + kThreads - 1) / kThreads;
-    if (b2 > 152 * 32) b2 = 152 * 32;
-    if (b2 < 1) b2 = 1;
-    k5_gather_xy<<<(int)b2, kThreads, 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
-                                              t_step, t_lo, t_hi);
+    static_assert(kThreads == 32 * 8, "pass 2 blocks are 32 y x 8 x");
+    const dim3 grid2((Y + 31) / 32, (X + 7) / 8, t_hi - t_lo);   // T, X <= 65535 (checked at create)
+    k5_gather_xy<<<grid2, dim3(32, 8), 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
+                                              t_step, t_lo);
     note_launches(2);
     return cudaGetLastError();
 }
