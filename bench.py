@@ -130,7 +130,7 @@ def k1_flops_per_voxel(n: int) -> int:
 
 # Outputs per thread of the FP32 K1's sliding form (rect taper, stride 1): the first of each run by the
 # direct stage-3 sum, the others by the recursion.
-K1_F32_SLIDING_RUN = {8: 4, 16: 16, 32: 8}
+K1_F32_SLIDING_RUN = {8: 8, 16: 16, 32: 8}
 
 
 def k1_flops_per_voxel_sliding(n: int) -> int:

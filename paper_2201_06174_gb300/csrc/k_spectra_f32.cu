@@ -30,7 +30,7 @@ using f32::Tw;
 template <int N> struct Cfg;
 template <> struct Cfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
 template <> struct Cfg<4>  { static constexpr int BY = 32, YC = 2, MINB = 4; };
-template <> struct Cfg<8>  { static constexpr int BY = 32, YC = 4, MINB = 2; };
+template <> struct Cfg<8>  { static constexpr int BY = 64, YC = 8, MINB = 2; };
 template <> struct Cfg<16> { static constexpr int BY = 32, YC = 16, MINB = 2; };
 
 template <int N> struct Geo {
