@@ -1,8 +1,8 @@
 """Precision form: the local-DFT contraction on the tensor cores in BF16 / FP16 with FP32
 accumulation, against the FP64 oracle.
 
-Tolerance (the benchmark spec, BF16/FP16 form): relative L2 <= 1e-2 per map and max-abs <= 2e-2 on the
-normalised [0, 1] map S.
+Tolerance of the 16-bit forms: relative L2 <= 1e-2 per map and max-abs <= 2e-2 on the normalised
+[0, 1] map S.
 """
 import numpy as np
 import pytest
