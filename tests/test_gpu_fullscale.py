@@ -70,3 +70,48 @@ def test_full_volume_forward_sampled(sal, volume, prec, tol):
     assert max(errs) <= tol, errs
     assert s_min == 0.0 and abs(s_max - 1.0) <= 1e-6
     assert s_err <= 1e-5
+
+
+def test_full_volume_spectral_adjoint(sal, volume):
+    """The backward at full size.  FP32: the spectral adjoint of a seeded random gE at 6 interior voxels q
+    against the oracle, exactly: the windows that contain q are those centred at q - 7 .. q + 8 on each
+    axis, all inside the 31^3 sub-volume around q, so the oracle's adjoint of that sub-volume with gE kept
+    on those windows (zero elsewhere) gives gV[q].  BF16 (the form the benchmark times): the whole gV
+    against the FP32 one for the gradient gE = E (a structured upstream gradient), relative L2 <= 1e-2."""
+    V, _ = volume
+    T, X, Y = SHAPE
+    gen = torch.Generator(device="cuda").manual_seed(651)
+    Vd = torch.from_numpy(V).cuda()
+    gE = torch.randn((3,) + SHAPE, device="cuda", generator=gen)
+    q = 15 + synth.sample_points((T - 31, X - 31, Y - 31), 6, seed=951)
+    eng = sal.Saliency(SHAPE, sal.Params(n=16, prec="fp32"))
+    try:
+        gV = torch.empty(SHAPE, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, Vd, gE, gV)
+        qd = torch.from_numpy(q).cuda()
+        got = gV[qd[:, 0], qd[:, 1], qd[:, 2]].cpu().numpy()
+        gEq = [gE[:, a - 7:a + 9, b - 7:b + 9, c - 7:c + 9].cpu().numpy() for a, b, c in q]
+        E = torch.empty((3,) + SHAPE, device="cuda")
+        sal.sal_local_spectra_project(eng.h, Vd, E)
+        del gE
+        gV32 = torch.empty(SHAPE, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, Vd, E, gV32)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    ref = []
+    for (a, b, c), g in zip(q, gEq):
+        gsub = np.zeros((3, 31, 31, 31))
+        gsub[:, 8:24, 8:24, 8:24] = g
+        ref.append(oracle.features_adjoint(V[a - 15:a + 16, b - 15:b + 16, c - 15:c + 16], gsub, 16)[15, 15, 15])
+    err32 = rel_l2(got, ref)
+    eng = sal.Saliency(SHAPE, sal.Params(n=16, prec="bf16"))
+    try:
+        gV16 = torch.empty(SHAPE, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, Vd, E, gV16)
+        torch.cuda.synchronize()
+        err16 = float((gV16.double() - gV32.double()).norm() / gV32.double().norm())
+    finally:
+        eng.close()
+    print("spectral adjoint: FP32 at 6 voxels vs oracle", f"{err32:.2e}", "BF16 vs FP32 whole volume", f"{err16:.2e}")
+    assert err32 <= 1e-5 and err16 <= 1e-2
