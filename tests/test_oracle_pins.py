@@ -69,6 +69,19 @@ def test_dft_matches_numpy_fftn(n):
 
 
 @pytest.mark.parametrize("n", [4, 8, 16])
+def test_hann_taper_spectrum_matches_numpy_fftn(n):
+    """The optional taper: the cube times the periodic Hann window 1/2 - 1/2 cos(2 pi u / n) on every axis,
+    built here independently, then numpy's FFT."""
+    V = synth.random_volume((19, 17, 21), seed=n + 40)
+    h = 0.5 - 0.5 * np.cos(2 * np.pi * np.arange(n) / n)
+    h3 = h[:, None, None] * h[None, :, None] * h[None, None, :]
+    for p in synth.sample_points(V.shape, 4, seed=n + 41).tolist() + [[0, 0, 0]]:
+        F = oracle.local_spectrum(V, *p, n=n, taper="hann")
+        ref = np.fft.fftn(_window(V.astype(np.float64), p, n, "symmetric") * h3)
+        assert np.max(np.abs(F - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
 def test_parseval_per_window(n):
     V, _ = synth.volume(synth.small_spec((24, 20, 22), seed=2, faults=1))
     for p in synth.sample_points(V.shape, 5, seed=11).tolist():
