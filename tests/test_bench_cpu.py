@@ -1,0 +1,55 @@
+"""Host arithmetic of the benchmark's roofline: the algorithmic work per voxel of each form of the local
+DFT and the fractions reported against the peaks (no GPU)."""
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("n,flops", [(8, 23_200), (16, 313_920), (32, 4_597_888)])
+def test_direct_dft_flops_per_voxel(n, flops):
+    """4hn + 8hn^2 + 8hn^3 (h = n/2 + 1 retained t-bins): real input along t, complex along x and y."""
+    assert bench.k1_flops_per_voxel(n) == flops
+
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+def test_sliding_form_flops_per_voxel(n):
+    """Stages along t and x as in the direct form, 8 flops per bin and output along y, and the direct
+    stage-3 sum once per run of outputs: below the direct count, above the stages along t and x."""
+    h = n // 2 + 1
+    run = bench.K1_F32_SLIDING_RUN[n]
+    tx = 4 * h * n + 8 * h * n * n
+    assert bench.k1_flops_per_voxel_sliding(n) == tx + 8 * h * n * n + 8 * h * n ** 3 // run
+    assert tx < bench.k1_flops_per_voxel_sliding(n) < bench.k1_flops_per_voxel(n)
+
+
+def test_bins_per_voxel():
+    assert [bench.bins_per_voxel(n) for n in (8, 16, 32)] == [320, 2304, 17408]
+
+
+def test_fp32_roofline_fraction():
+    n, nvox, ms = 16, 128 ** 3, 8.0
+    rl = bench.roofline("k", "fp32", n, nvox, ms, 1, 123)
+    achieved = bench.k1_flops_per_voxel(n) * nvox / (ms / 1e3) / 1e12
+    assert rl["achieved"] == pytest.approx(achieved)
+    assert rl["frac"] == pytest.approx(achieved / bench.FP32_PEAK_TFLOPS)
+    assert rl["unit"] == "TFLOP/s" and rl["traffic"] == 123 and rl["bound"] == "alu"
+    sl = bench.roofline("k", "fp32", n, nvox, ms, 1, None, flops_per_voxel=bench.k1_flops_per_voxel_sliding(n))
+    assert sl["achieved"] == pytest.approx(achieved * bench.k1_flops_per_voxel_sliding(n) / bench.k1_flops_per_voxel(n))
+
+
+def test_tensor_form_roofline_is_the_mufu_epilogue():
+    n, nvox, ms = 16, 128 ** 3, 2.7
+    rl = bench.roofline("k", "bf16", n, nvox, ms, 1, None)
+    bins = bench.bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
+    assert rl["achieved"] == pytest.approx(bins) and rl["peak"] == bench.MUFU_PEAK_TOPS
+    assert rl["frac"] == pytest.approx(bins / bench.MUFU_PEAK_TOPS)
+    assert "tensor" in rl and rl["tensor"]["frac"] == pytest.approx(rl["tensor"]["achieved_tflops"] /
+                                                                     rl["tensor"]["peak_tflops"])
+    en = bench.roofline("k", "bf16", n, nvox, ms, 1, None, feature="energy")
+    assert en["peak"] == bench.FMA_OPS_PEAK and en["achieved"] == pytest.approx(4 * bins)
+
+
+def test_peaks_derived_from_unit_counts():
+    assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
+    assert bench.MUFU_PEAK_TOPS == pytest.approx(16 * 152 * 2.070e9 / 1e12)
+    assert bench.FMA_OPS_PEAK == pytest.approx(bench.FP32_PEAK_TFLOPS / 2)
