@@ -663,9 +663,9 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
     const long long NV = (long long)T * X * Y;
     const size_t smem = dcs_tile_smem_bytes(st.halo[0], st.halo[1], st.halo[2]);
     const long long nblk = (long long)((T + kTileT - 1) / kTileT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
-    // the tiled kernel when its plane ring fits (dcs_adjoint_prepare) and its tiles fill the GPU
-    if (smem <= kTileSmemMax && nblk >= g_tiled_min_blocks) {
-        if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    // the tiled kernel when its plane ring fits (dcs_adjoint_prepare), its tiles fill the GPU and their
+    // count fits a one-dimensional grid; the row kernel otherwise
+    if (smem <= kTileSmemMax && nblk >= g_tiled_min_blocks && nblk <= 0x7fffffffLL) {
         k4_dcs_adjoint_tiled<<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
         note_launches(1);
         return cudaGetLastError();
