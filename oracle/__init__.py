@@ -16,7 +16,8 @@ Readings where the paper is silent (each an argument here):
     voxels and held constant past the last lattice point of an axis;
   * rectangular taper (the cube C_n as is); Hann optional;
   * E_m = (1/n^3) sum_{k != 0} r_m(k) |F[k]| (feature "abs"); the energy reading of the garbled step 3,
-    E_m = (1/n^3) sum_{k != 0} r_m(k)^2 |F[k]|^2, is feature "energy";
+    E_m = (1/n^3) sum_{k != 0} r_m(k)^2 |F[k]|^2, is feature "energy"; its spatial-domain reading,
+    the mean over the cube of |IDFT(F_m)|, is `spatial_features`;
   * DCS stencil: direction groups t, x and t-x (Fig. 4), offsets s*d for s in +-1..+-R,
     Gaussian weights w_o = alpha_d exp(-|o|^2 / (2 sigma^2)) multiplying the neighbour
     inside |.| as Eq. 3 is written, Q = number of offsets;
@@ -122,6 +123,27 @@ def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, fe
     _check(lib().sal_oracle_features(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], FEATURE[feature],
                                      _dp(E), threads), "features")
     return E
+
+
+def spatial_features_at(V, pts, n: int, boundary="symmetric", taper="rect") -> np.ndarray:
+    """The spatial-domain reading of the feature step at listed voxels, pts [count][3] -> [count][3]:
+    E_m = (1/n^3) sum_u |f_m[u]|, f_m the inverse DFT over the cube of the projected spectrum F_m of Eq. 1
+    (DC = 0).  f_m is real up to rounding: F is Hermitian for a real cube and the ratio P_m / |k| depends
+    on squared signed indices only.  Projected spectra from `projected_spectra`, then numpy's inverse FFT
+    (a library step); one voxel at a time, for small cases."""
+    pts = np.asarray(pts, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((pts.shape[0], 3), dtype=np.float64)
+    for i, (t, x, y) in enumerate(pts.tolist()):
+        f = np.fft.ifftn(projected_spectra(V, t, x, y, n, boundary, taper), axes=(1, 2, 3))
+        out[i] = np.abs(f).mean(axis=(1, 2, 3))
+    return out
+
+
+def spatial_features(V, n: int, boundary="symmetric", taper="rect") -> np.ndarray:
+    """E [3][T][X][Y] of the spatial-domain reading at every voxel (spatial_features_at over the volume)."""
+    shape = np.asarray(V).shape
+    pts = np.stack(np.meshgrid(*[np.arange(d) for d in shape], indexing="ij"), -1).reshape(-1, 3)
+    return spatial_features_at(V, pts, n, boundary, taper).T.reshape((3,) + shape)
 
 
 def upsample_adjoint(gE, stride: int) -> np.ndarray:
