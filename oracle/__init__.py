@@ -146,6 +146,50 @@ def spatial_features(V, n: int, boundary="symmetric", taper="rect") -> np.ndarra
     return spatial_features_at(V, pts, n, boundary, taper).T.reshape((3,) + shape)
 
 
+def _eq1_ratios(n: int) -> np.ndarray:
+    """r_m(k) = P_m(k) / |k| of Eq. 1 over the n^3 bins (signed indices; zero at DC): [3][n][n][n]."""
+    s = np.array([k if k < n // 2 else k - n for k in range(n)], dtype=np.float64)
+    i, j, k = np.meshgrid(s, s, s, indexing="ij")
+    r = np.sqrt(i * i + j * j + k * k)
+    P = np.stack([np.sqrt(j * j + k * k), np.sqrt(i * i + k * k), np.sqrt(i * i + j * j)])
+    return np.where(r > 0, P / np.where(r > 0, r, 1.0), 0.0)
+
+
+def _taper3(n: int, taper: str) -> np.ndarray:
+    u = np.arange(n)
+    h = np.ones(n) if taper == "rect" else 0.5 - 0.5 * np.cos(2.0 * np.pi * u / n)
+    return h[:, None, None] * h[None, :, None] * h[None, None, :]
+
+
+def spatial_features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect") -> np.ndarray:
+    """gV = (dE/dV)^T gE for the spatial-domain reading.  Per voxel p, with w the tapered window and
+    A_m = IDFT diag(r_m) DFT (a real circulant, symmetric since r_m is even in k): f_m = A_m w and
+    E_m = (1/n^3) sum_u |f_m[u]|, so dE_m/dw = (1/n^3) A_m sign(f_m) (sign(0) = 0); each window's
+    gradient, times the taper, goes back to the voxels its samples came from through the border
+    extension.  numpy's FFTs as library steps; small cases only."""
+    V = _f64(V)
+    gE = _f64(gE)
+    T, X, Y = V.shape
+    R = _eq1_ratios(n)
+    h3 = _taper3(n, taper)
+    gV = np.zeros_like(V)
+    off = np.arange(n) - n // 2
+    for t in range(T):
+        for x in range(X):
+            for y in range(Y):
+                it, ix, iy = (ext_index(c + off, N, boundary) for c, N in ((t, T), (x, X), (y, Y)))
+                ok = (it[:, None, None] >= 0) & (ix[None, :, None] >= 0) & (iy[None, None, :] >= 0)
+                w = np.where(ok, V[np.ix_(np.maximum(it, 0), np.maximum(ix, 0), np.maximum(iy, 0))], 0.0) * h3
+                F = np.fft.fftn(w)
+                gw = np.zeros((n, n, n))
+                for m in range(3):
+                    f = np.real(np.fft.ifftn(R[m] * F))
+                    gw += gE[m, t, x, y] * np.real(np.fft.ifftn(R[m] * np.fft.fftn(np.sign(f))))
+                gw *= h3 / n ** 3
+                np.add.at(gV, np.ix_(np.maximum(it, 0), np.maximum(ix, 0), np.maximum(iy, 0)), np.where(ok, gw, 0.0))
+    return gV
+
+
 def upsample_adjoint(gE, stride: int) -> np.ndarray:
     """Transpose of `upsample`: every voxel's gradient goes back to the two lattice points of each axis
     it was interpolated from, with the same weights (1 - f, f; 1 past the last lattice point)."""

@@ -93,3 +93,24 @@ def test_bounded_by_the_energy_reading(n):
     Ee = oracle.features_at(V, pts, n, feature="energy")
     assert np.all(Es <= np.sqrt(Ee / n ** 3) * (1 + 1e-12))
     assert np.all(Es > 0.2 * np.sqrt(Ee / n ** 3))   # and not degenerate
+
+
+@pytest.mark.parametrize("n,boundary,taper", [(4, "symmetric", "rect"), (4, "periodic", "hann"), (4, "zero", "rect"),
+                                              (2, "symmetric", "rect")])
+def test_spatial_adjoint_matches_exact_differences(n, boundary, taper):
+    """gV[q] = d/dV[q] sum_m,p gE_m[p] E_m[p], against central differences of the forward in FP64 (no
+    sample of any window's f_m crosses zero within the step: the reading is linear there up to the step's
+    second order, which central differences cancel)."""
+    shape = (5, 4, 6)
+    V = synth.random_volume(shape, seed=70 + n).astype(np.float64)
+    gE = synth.random_volume((3,) + shape, seed=71 + n).astype(np.float64)
+    gV = oracle.spatial_features_adjoint(V, gE, n, boundary, taper)
+    d = 1e-6
+    for q in synth.sample_points(shape, 5, seed=72).tolist() + [[0, 0, 0]]:
+        Vp, Vm = V.copy(), V.copy()
+        Vp[tuple(q)] += d
+        Vm[tuple(q)] -= d
+        Lp = np.sum(gE * oracle.spatial_features(Vp, n, boundary, taper))
+        Lm = np.sum(gE * oracle.spatial_features(Vm, n, boundary, taper))
+        fd = (Lp - Lm) / (2 * d)
+        assert abs(fd - gV[tuple(q)]) <= 1e-6 * max(1.0, abs(gV[tuple(q)])), (q, fd, gV[tuple(q)])
