@@ -42,7 +42,8 @@ WORKLOADS = {
                            directions=((0, 1, 0), (0, 0, 1), (0, 1, 1)),
                            desc="2-D vertical section 462 (t) x 951 (x) of a synthetic seismic slab (6 faults, 1 salt "
                            "body, folds, noise 0.1 rms), passed as a volume [1][462][951] (one plane), window 16^2, "
-                           "the in-plane t, x, t-x window, weights (0, 1/2, 1/2)", cpu_sample=40, ref_sample=24),
+                           "the in-plane t, x, t-x window, weights (0, 1/2, 1/2)",
+                           cpu_sample=256, ref_sample=80),   # one plane: sample x sample voxels
     "full462x951x651": dict(spec="full462x951x651", n=16, desc="462x951x651 synthetic seismic volume (20 faults, "
                             "3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3", cpu_sample=40,
                             ref_sample=20),
@@ -186,18 +187,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(V, n, sample, backward=True, feature="abs", stride=1):  # noqa: C901
-    """The FP64 oracle, as it stands, on a sample^3 corner sub-volume of the workload (all host
-    cores): forward, and the backward with the same fixed upstream gradient as the GPU step."""
+def cpu_oracle_rate(V, n, sample, backward=True, feature="abs", stride=1, wl=None):  # noqa: C901
+    """The FP64 oracle, as it stands, on a corner sub-volume of the workload, sample voxels per axis (a
+    one-plane section: sample x sample), all host cores: forward, and the backward with the same fixed
+    upstream gradient as the GPU step, with the workload's window and weights."""
     import numpy as np
 
     import oracle
     sub = np.ascontiguousarray(V[:sample, :sample, :sample])
     gS = _upstream(sub.shape)
+    wl = wl or {}
+    st = oracle.dcs_stencil(wl["directions"]) if "directions" in wl else None
+    W = np.asarray(wl["weights"], np.float64) if "weights" in wl else np.full(3, 1.0 / 3.0)
     t0 = time.perf_counter()
-    fwd = oracle.saliency(sub, n, feature=feature, stride=stride)
+    fwd = oracle.saliency(sub, n, stencil=st, weights=W if "weights" in wl else "equal", feature=feature,
+                          stride=stride)
     if backward:
-        oracle.saliency_backward(sub, n, np.full(3, 1.0 / 3.0), gS, fwd=fwd, feature=feature, stride=stride)
+        oracle.saliency_backward(sub, n, W, gS, stencil=st, fwd=fwd, feature=feature, stride=stride)
     dt = time.perf_counter() - t0
     return sub.size / dt / 1e6, dt, sub.shape
 
@@ -248,17 +254,18 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import synth
+    import numpy as np
     V = _workload_volume(wl)
     s = wl["ref_sample"]
     bwd = getattr(args, "form", "fwdbwd") == "fwdbwd"
     for _ in range(args.warmup):
-        cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride)
+        cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride, wl=wl)
     times = []
     for _ in range(args.steps):
-        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride)
+        _, dt, shape = cpu_oracle_rate(V, wl["n"], s, backward=bwd, feature=args.feature, stride=args.stride,
+                                       wl=wl)
         times.append(dt)
-    vox = s ** 3
+    vox = int(np.prod(shape))
     value = vox * args.steps / sum(times) / 1e6
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": args.gpus,
@@ -268,7 +275,8 @@ def run_reference(args, wl):
                        "form": "forward+backward" if bwd else "forward", "feature": args.feature,
                        "stride": args.stride},
             "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{s}^3 corner sub-volume of the workload per step, FP64 forward+backward"},
+                             "sample": f"{'x'.join(map(str, shape))} corner sub-volume of the workload per step, "
+                                       f"FP64 {'forward+backward' if bwd else 'forward'}"},
             "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -520,9 +528,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = wl["cpu_sample"]
         rate, dt, shape = cpu_oracle_rate(V, n, s, backward=args.form == "fwdbwd", feature=args.feature,
-                                          stride=args.stride)
+                                          stride=args.stride, wl=wl)
         line["cpu_baseline"] = {"value": rate, "unit": "Mvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{s}^3 corner sub-volume of the workload, FP64 "
+                                "sample": f"{'x'.join(map(str, shape))} corner sub-volume of the workload, FP64 "
                                           f"{'forward+backward' if args.form == 'fwdbwd' else 'forward'}, {dt:.1f} s",
                                 "sampled_error_vs_fp64": sampled_error(V, n, params, E, S3)}
     if rank == 0:
