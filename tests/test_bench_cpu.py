@@ -53,3 +53,42 @@ def test_peaks_derived_from_unit_counts():
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
     assert bench.MUFU_PEAK_TOPS == pytest.approx(16 * 152 * 2.070e9 / 1e12)
     assert bench.FMA_OPS_PEAK == pytest.approx(bench.FP32_PEAK_TFLOPS / 2)
+
+
+def test_reference_arm_on_a_section_counts_its_plane_and_uses_its_window(monkeypatch, capsys):
+    """The oracle is timed on the workload's own configuration: a one-plane section sample has
+    sample^2 voxels, and runs with the section's in-plane window and weights."""
+    import json
+
+    import numpy as np
+
+    import oracle
+    calls = []
+    real_saliency, real_backward = oracle.saliency, oracle.saliency_backward
+
+    def saliency(V, n, **kw):
+        calls.append(("fwd", V.shape, kw.get("stencil"), kw.get("weights")))
+        return real_saliency(V, n, **kw)
+
+    def saliency_backward(V, n, W, gS, **kw):
+        calls.append(("bwd", V.shape, kw.get("stencil"), W))
+        return real_backward(V, n, W, gS, **kw)
+    monkeypatch.setattr(oracle, "saliency", saliency)
+    monkeypatch.setattr(oracle, "saliency_backward", saliency_backward)
+    monkeypatch.setenv("RANK", "0")
+    wl = dict(bench.WORKLOADS["section462x951"], ref_sample=20)
+    monkeypatch.setattr(bench, "_workload_volume", lambda w: np.random.default_rng(0).standard_normal(
+        (1, 40, 50)).astype(np.float32))
+
+    class A:
+        steps, warmup, gpus, feature, stride, form = 1, 0, 1, "abs", 1, "fwdbwd"
+    bench.run_reference(A(), wl)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["cpu_baseline"]["sample"].startswith("1x20x20 ")
+    assert line["value"] * line["ms_per_step"] / 1e3 * 1e6 == pytest.approx(400)
+    expect = oracle.dcs_stencil(wl["directions"])
+    for kind, shape, st, W in calls:
+        assert shape == (1, 20, 20)
+        assert np.array_equal(st[0], expect[0]) and np.allclose(st[3], expect[3])
+        assert np.allclose(W, [0.0, 0.5, 0.5])
+    assert [c[0] for c in calls] == ["fwd", "bwd"]
