@@ -70,6 +70,13 @@ cudaError_t spectra_f32_prepare(int n);
 cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V, float* E, int T,
                                int X, int Y, int bnd, int feat, int stride, int taper, cudaStream_t s);
 size_t f32_weight_table_floats(int n);
+// The spatial-domain reading of the feature step (FP32, n in {2, 4, 8}, stride 1, forward only): the
+// table holds the kernels h_m = IDFT(r_m) [3][n^3] and the taper [n^3] (spatial_table_fill, host).
+bool spatial_f32_supported(int n);
+size_t spatial_table_floats(int n);
+void spatial_table_fill(int n, int taper, float* out);
+cudaError_t spatial_f32_launch(int n, const float* tab, const float* V, float* E, int T, int X, int Y, int bnd,
+                               int taper, cudaStream_t s);
 void f32_weight_table_fill(int n, int feat, float* out);   // host
 // The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point),
 // and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.

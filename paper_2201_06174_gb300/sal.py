@@ -26,7 +26,8 @@ SAL_OK, SAL_ERR_INVALID_ARG, SAL_ERR_UNSUPPORTED, SAL_ERR_OOM, SAL_ERR_CUDA, SAL
 STATUS_NAMES = ["SAL_OK", "SAL_ERR_INVALID_ARG", "SAL_ERR_UNSUPPORTED", "SAL_ERR_OOM", "SAL_ERR_CUDA",
                 "SAL_ERR_TIMEOUT", "SAL_ERR_DEVICE_CHECK"]
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
-FEATURE = {"abs": 0, "energy": 1}   # E_m: mean over the cube's bins of |F_m| (step 3), or of |F_m|^2
+FEATURE = {"abs": 0, "energy": 1, "spatial": 2}   # E_m: mean over the cube's bins of |F_m| (step 3), of |F_m|^2,
+#                                                   or over the cube's voxels of |IDFT(F_m)|
 BOUNDARY = {"symmetric": 0, "periodic": 1, "zero": 2}
 TAPER = {"rect": 0, "hann": 1}
 
