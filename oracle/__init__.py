@@ -111,8 +111,13 @@ def features(V, n: int, boundary="symmetric", taper="rect", threads: int = 0, fe
     """E [3][T][X][Y] (E_t, E_x, E_y) at every voxel: the mean over the cube's bins of |F_m|
     (feature "abs", step 3) or of |F_m|^2 (feature "energy").  stride s > 1: the cubes sit only on
     the lattice of voxels whose indices are all multiples of s (windows overlapping by n - s of n,
-    the paper's ">50% overlap" for s < n/2), and E elsewhere is interpolated from them (upsample)."""
+    the paper's ">50% overlap" for s < n/2), and E elsewhere is interpolated from them (upsample).
+    Feature "spatial": the mean over the cube of |IDFT(F_m)| (spatial_features; stride 1)."""
     V = _f64(V)
+    if feature == "spatial":
+        if stride != 1:
+            raise ValueError("the spatial-domain reading is defined here for stride 1")
+        return spatial_features(V, n, boundary, taper)
     if stride > 1:
         T, X, Y = V.shape
         lat = [np.arange(0, d, stride) for d in (T, X, Y)]
@@ -243,6 +248,8 @@ def upsample(Ec, stride: int, shape) -> np.ndarray:
 def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int = 0,
                 feature="abs") -> np.ndarray:
     """E at listed voxels: pts [count][3] -> [count][3]."""
+    if feature == "spatial":
+        return spatial_features_at(V, pts, n, boundary, taper)
     V = _f64(V)
     pts = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
     out = np.empty((pts.shape[0], 3), dtype=np.float64)

@@ -114,3 +114,20 @@ def test_spatial_adjoint_matches_exact_differences(n, boundary, taper):
         Lm = np.sum(gE * oracle.spatial_features(Vm, n, boundary, taper))
         fd = (Lp - Lm) / (2 * d)
         assert abs(fd - gV[tuple(q)]) <= 1e-6 * max(1.0, abs(gV[tuple(q)])), (q, fd, gV[tuple(q)])
+
+
+def test_spatial_reading_through_the_pipeline_entry_points():
+    """features / features_at / center_surround_at / saliency take feature="spatial" and agree."""
+    V, _ = synth.volume(synth.small_spec((6, 7, 9), seed=80, faults=1))
+    E = oracle.features(V, 4, feature="spatial")
+    assert np.allclose(E, oracle.spatial_features(V, 4), rtol=0, atol=0)
+    pts = synth.sample_points(V.shape, 5, seed=81)
+    assert np.allclose(oracle.features_at(V, pts, 4, feature="spatial"), E[:, pts[:, 0], pts[:, 1], pts[:, 2]].T)
+    st = oracle.dcs_stencil()
+    Ec, Sc = oracle.center_surround_at(V, pts, 4, st[0], st[3], feature="spatial")
+    S3 = oracle.center_surround(E, st[0], st[3])
+    assert np.allclose(Sc, S3[:, pts[:, 0], pts[:, 1], pts[:, 2]].T, rtol=1e-12, atol=1e-14)
+    out = oracle.saliency(V, 4, feature="spatial")
+    assert np.allclose(out["E"], E) and np.allclose(out["S3"], S3)
+    with pytest.raises(ValueError):
+        oracle.features(V, 4, feature="spatial", stride=2)
