@@ -129,6 +129,12 @@ def k1_flops_per_voxel(n: int) -> int:
     return 4 * h * n + 8 * h * n * n + 8 * h * n ** 3
 
 
+def k1_flops_per_voxel_spatial(n: int) -> int:
+    """Flops per voxel of the spatial reading's kernel: for each of the 3 maps and n^3 outputs, an n^3-term
+    circular convolution (one FMA, 2 flops, per term)."""
+    return 3 * 2 * n ** 6
+
+
 # Outputs per thread of the FP32 K1's sliding form (rect taper, stride 1): the first of each run by the
 # direct stage-3 sum, the others by the recursion.
 K1_F32_SLIDING_RUN = {8: 8, 16: 16, 32: 8}
@@ -294,8 +300,9 @@ def main():
     ap.add_argument("--form", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwdbwd: forward + backward step (default); fwd: forward only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--feature", default="abs", choices=["abs", "energy"],
-                    help="E_m: mean of |F_m| (the paper's step 3) or of |F_m|^2 (energy reading)")
+    ap.add_argument("--feature", default="abs", choices=["abs", "energy", "spatial"],
+                    help="E_m: mean of |F_m| (the paper's step 3), of |F_m|^2 (energy reading), or over the "
+                         "cube of |IDFT(F_m)| (spatial reading: FP32, n <= 8, --form fwd)")
     ap.add_argument("--stride", type=int, default=1,
                     help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2)")
     args = ap.parse_args()
@@ -305,6 +312,11 @@ def main():
         wl["desc"] = re.sub(r"window \d+\^3", f"window {args.n}^3", wl["desc"])
     if wl["n"] >= 32:  # the FP64 oracle costs 12 n^4 flop per voxel: keep its sample to ~30 s
         wl["cpu_sample"], wl["ref_sample"] = 16, 12
+    if args.feature == "spatial":
+        if args.prec != "fp32" or wl["n"] > 8 or args.stride != 1 or args.form != "fwd":
+            ap.error("--feature spatial runs in FP32 with n <= 8, stride 1 and --form fwd")
+        # the oracle's spatial reading goes one voxel at a time through numpy's FFTs
+        wl["cpu_sample"], wl["ref_sample"] = min(wl["cpu_sample"], 16), min(wl["ref_sample"], 12)
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -472,11 +484,16 @@ def main():
     T_, X_, Y_ = V.shape
     ncubes = nvox if sc == 1 else (-(-T_ // sc) * X_ * Y_ if args.prec != "fp32" else
                                    -(-T_ // sc) * -(-X_ // sc) * -(-Y_ // sc))
-    sliding = args.prec == "fp32" and sc == 1 and n in K1_F32_SLIDING_RUN
-    k1_rl = roofline(f"k1_spectra_{tag}", args.prec, n, ncubes, k1_ms, 1, K1_TRAFFIC.get(trk), feature=args.feature,
-                     flops_per_voxel=k1_flops_per_voxel_sliding(n) if sliding else None)
+    spatial = args.feature == "spatial"
+    sliding = args.prec == "fp32" and sc == 1 and n in K1_F32_SLIDING_RUN and not spatial
+    k1_rl = roofline("k1_spatial_f32" if spatial else f"k1_spectra_{tag}", args.prec, n, ncubes, k1_ms, 1,
+                     K1_TRAFFIC.get(trk), feature=args.feature,
+                     flops_per_voxel=(k1_flops_per_voxel_spatial(n) if spatial else
+                                      k1_flops_per_voxel_sliding(n) if sliding else None))
     if sliding:
         k1_rl["form"] = "sliding DFT along y (flops of that form)"
+    if spatial:
+        k1_rl["form"] = "spatial reading: the circulant of h_m = IDFT(r_m) applied directly (flops of that form)"
     if sc > 1:
         k1_rl["cubes_per_launch"] = ncubes
     if args.form == "fwdbwd":
@@ -503,7 +520,8 @@ def main():
                                              "tensor-core operands are FP16" if args.prec != "fp32" else " SIMT"),
                    "form": "forward+backward (upstream gradient fixed, seeded)" if args.form == "fwdbwd"
                    else "forward",
-                   "feature": "mean of |F_m| (step 3)" if args.feature == "abs" else "mean of |F_m|^2 (energy reading)",
+                   "feature": {"abs": "mean of |F_m| (step 3)", "energy": "mean of |F_m|^2 (energy reading)",
+                               "spatial": "mean over the cube of |IDFT(F_m)| (spatial reading)"}[args.feature],
                    "stride": args.stride,
                    "l2": "flushed between steps (256 MiB device write outside the events)",
                    "parallelism": f"replicas x{world}"},

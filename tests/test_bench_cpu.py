@@ -92,3 +92,14 @@ def test_reference_arm_on_a_section_counts_its_plane_and_uses_its_window(monkeyp
         assert np.array_equal(st[0], expect[0]) and np.allclose(st[3], expect[3])
         assert np.allclose(W, [0.0, 0.5, 0.5])
     assert [c[0] for c in calls] == ["fwd", "bwd"]
+
+
+def test_spatial_reading_flops_and_guard():
+    """The spatial reading's kernel applies the n^3 x n^3 circulant per map: 6 n^6 flop per voxel; the bench
+    runs it only in the form the library provides."""
+    import subprocess
+    import sys
+    assert [bench.k1_flops_per_voxel_spatial(n) for n in (2, 4, 8)] == [384, 24576, 1572864]
+    r = subprocess.run([sys.executable, bench.__file__, "--feature", "spatial", "--prec", "bf16", "--form", "fwd",
+                        "--workload", "fault48"], capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "--feature spatial runs in FP32" in r.stderr
