@@ -62,6 +62,8 @@ def lib():
         L.sal_oracle_center_surround_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, _c_int_p, _c_dbl_p,
                                                          _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.sal_oracle_features_adjoint.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, i, _c_dbl_p, _c_dbl_p, i]
+        L.sal_oracle_band_count.argtypes = [_c_dbl_p, L_, L_, L_, i, i, i, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int32), i]
         L.sal_oracle_lms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, _c_dbl_p, _c_dbl_p]
         L.sal_oracle_nlms.argtypes = [_c_dbl_p, _c_dbl_p, L_, ctypes.c_double, ctypes.c_double, _c_dbl_p,
                                       _c_dbl_p]
@@ -258,6 +260,42 @@ def features_at(V, pts, n: int, boundary="symmetric", taper="rect", threads: int
     _check(lib().sal_oracle_features_at(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], FEATURE[feature],
                                         pts.ctypes.data_as(_c_i64_p), pts.shape[0], _dp(out), threads),
            "features_at")
+    return out
+
+
+# Kink band of the |F| adjoint: a bin counts as F = 0 when |F| <= ZERO_BIN * ||window||_1.  The
+# level is set by FP64 arithmetic (an exactly zero bin comes out of the FP64 DFT below 2^-45 of the
+# window L1 norm for n <= 32).
+ZERO_BIN = 2.0 ** -40
+# Windows holding a bin with ZERO_BIN < |F| / L1 <= ILL_BIN are ill-conditioned for the adjoint of
+# step 3: its direction F / |F| is known to FP32 arithmetic only to about 2^-24 L1 / |F| (and the
+# FP32 forms zero bins below 2^-19 L1), so a few such bins move the gradient of a small volume by
+# more than 1e-5.  4 x 2^-19 = 2^-17.
+ILL_BIN = 2.0 ** -17
+
+
+def band_count(V, n: int, boundary="symmetric", taper="rect", lo: float = ZERO_BIN, hi: float = ILL_BIN,
+               threads: int = 0) -> np.ndarray:
+    """Per voxel [T][X][Y]: the number of non-DC bins of its cube with lo < |F| / L1 <= hi, L1 the
+    window's L1 norm (test helper for the conditioning of the feature adjoint)."""
+    V = _f64(V)
+    out = np.empty(V.shape, dtype=np.int32)
+    _check(lib().sal_oracle_band_count(_dp(V), *V.shape, n, BOUNDARY[boundary], TAPER[taper], lo, hi,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), threads),
+           "band_count")
+    return out
+
+
+def adjoint_footprint(flags, n: int, boundary="symmetric") -> np.ndarray:
+    """Voxels whose feature-adjoint gradient receives a term from a flagged window: the cube
+    p + u - n/2 (u in [0, n)^3) of every flagged p, folded back through the border extension."""
+    flags = np.asarray(flags, bool)
+    T, X, Y = flags.shape
+    out = np.zeros(flags.shape, bool)
+    for t, x, y in zip(*np.nonzero(flags)):
+        a, b, c = (ext_index(np.arange(n) + p - n // 2, N, boundary) for p, N in ((t, T), (x, X), (y, Y)))
+        a, b, c = a[a >= 0], b[b >= 0], c[c >= 0]
+        out[np.ix_(a, b, c)] = True
     return out
 
 

@@ -39,10 +39,14 @@
 
 enum { BND_SYMMETRIC = 0, BND_PERIODIC = 1, BND_ZERO = 2 };
 
-/* Relative magnitude (to the window L1 norm) below which a bin is treated as F = 0 in the
-   adjoint: 2^-19, above the rounding level of an FP32 DFT of the window, below the bins of
-   real data. */
-#define KINK_TAU (1.0 / 524288.0)
+/* Relative magnitude (to the window L1 norm) at or below which a bin is treated as F = 0 in the
+   adjoint: 2^-40.  The reason is FP64 arithmetic alone: a bin that is exactly zero (a mirror-
+   symmetric or aliased window under the border extension) comes out of the FP64 DFT of this file
+   at no more than about 3n 2^-53 times the L1 norm (three one-axis sums of n terms each, twiddles
+   rounded to 2^-53), below 2^-45 for n <= 32, while |F| / L1 of a bin that is not zero is whatever
+   the data make it.  So the band only catches zeros of the
+   mathematics, where the subgradient of |F| is taken as 0. */
+#define KINK_TAU (1.0 / 1099511627776.0)
 
 /* Boundary extension of one axis.  Returns -1 where the zero extension applies. */
 static long ext_index(long i, long N, int mode) {
@@ -299,6 +303,48 @@ int sal_oracle_features_at(const double* V, long T, long X, long Y, int n, int m
 }
 
 /*
+ * Conditioning of the |F| adjoint (test helper, no step of the method): for every voxel p, the
+ * number of non-DC bins of its cube whose magnitude lies in (lo * L1, hi * L1], L1 = sum_u
+ * |h(u) Vext[p+u-n/2]|.  The direction F / |F| that the adjoint of step 3 needs is ill-conditioned
+ * for small |F|: an arithmetic with unit rounding e computes it with an error of about
+ * e L1 / |F|, so windows holding such bins bound the agreement any lower precision can reach.
+ * counts [T][X][Y] is overwritten.
+ */
+int sal_oracle_band_count(const double* V, long T, long X, long Y, int n, int mode, int taper,
+                          double lo, double hi, int32_t* counts, int nthreads) {
+    int rc = check_common(T, X, Y, n, mode);
+    if (rc) return rc;
+    const long N = T * X * Y;
+    const size_t n3 = (size_t)n * n * n;
+    int fail = 0;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    {
+        work_t W;
+        int ok = work_init(&W, n) == 0;
+        if (!ok) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(static)
+        for (long p = 0; p < N; ++p) {
+            if (!ok) continue;
+            long t = p / (X * Y), x = (p / Y) % X, y = p % Y;
+            local_spectrum(V, T, X, Y, n, mode, taper, t, x, y, &W);
+            double l1 = 0.0;
+            for (size_t b = 0; b < n3; ++b) l1 += fabs(W.w[b]);
+            int c = 0;
+            for (size_t b = 1; b < n3; ++b) {
+                double mag = sqrt(W.fre[b] * W.fre[b] + W.fim[b] * W.fim[b]);
+                if (mag > lo * l1 && mag <= hi * l1) ++c;
+            }
+            counts[p] = c;
+        }
+        work_free(&W);
+    }
+    return fail ? -4 : 0;
+}
+
+/*
  * Directional center-surround, Eq. 3:
  *   S_m[p] = (1/Q) sum_{o} | E_m[p] - w_o * Eext_m[p + o] |,   Q = number of offsets.
  * E, S: [3][T][X][Y]; off [Q][3] (dt,dx,dy); w [Q].
@@ -361,7 +407,8 @@ int sal_oracle_center_surround_adjoint(const double* E, long T, long X, long Y, 
  * Adjoint of the feature step.  For each voxel p, with F_p recomputed,
  *   U[k] = (1/n^3) (sum_m gE_m[p] r_m(k)) F_p[k] / |F_p[k]|       (feature 0), or
  *   U[k] = (2/n^3) (sum_m gE_m[p] r_m(k)^2) F_p[k]                 (feature 1, energy)
- *   (0 at DC and where |F| <= 2^-19 sum_u |h(u) Vext[p+u-n/2]|, the zero subgradient of |F|),
+ *   (0 at DC and where |F| <= 2^-40 sum_u |h(u) Vext[p+u-n/2]|, i.e. F = 0 up to FP64 rounding:
+ *   the zero subgradient of |F|),
  *   gVext[p + u - n/2] += h(u) Re sum_k U[k] exp(+2 pi i k.u / n),
  * then the extension is folded back onto V (zero extension drops).  gV [T][X][Y] is
  * overwritten.  Per-thread accumulators are summed in thread order.
@@ -400,8 +447,8 @@ int sal_oracle_features_adjoint(const double* V, long T, long X, long Y, int n, 
             long t = p / (X * Y), x = (p / Y) % X, y = p % Y;
             local_spectrum(V, T, X, Y, n, mode, taper, t, x, y, &W);
             /* |F| has no direction at F = 0 (a kink): bins whose magnitude is at or below
-               KINK_TAU times the window's L1 norm (the rounding level of the DFT) take the
-               zero subgradient. */
+               KINK_TAU times the window's L1 norm (zero up to the FP64 rounding of the DFT)
+               take the zero subgradient. */
             double l1 = 0.0;
             for (size_t b = 0; b < n3; ++b) l1 += fabs(W.w[b]);
             const double thr = KINK_TAU * l1;
