@@ -5,10 +5,20 @@
 // (extended) input is
 //   gVext[p + u - n/2] += Re sum_{k in half} h(u) exp(+2 pi i k.u / n) Gamma_p[k],
 //   Gamma_p[k] = (sum_m gE_m[p] wt_m(k)) F_p[k] / |F_p[k]|,
-// with Gamma = 0 at DC and wherever |F| <= 2^-19 A_p, A_p = sum_u |h(u) Vext[p + u - n/2]| (the
-// window's L1 norm bounds every |F_p[k]|): |F| has no direction at F = 0, and below that level
-// F is rounding noise, so those bins take the zero subgradient.
-// i.e. the transposes of the three sliding DFT stages applied to Gamma in reverse order.
+// with Gamma = 0 at DC and where F_p[k] = 0 (|F| has no direction there: the zero subgradient), i.e. the
+// transposes of the three sliding DFT stages applied to Gamma in reverse order.
+//
+// The direction F / |F| is ill-conditioned for small |F|: FP32 computes F to about 2^-26 of the window's
+// L1 norm A_p = sum_u |h(u) Vext[p + u - n/2]| (which bounds every |F_p[k]|), so a bin with |F| near that
+// level has no usable FP32 direction.  Such bins are resolved exactly:
+//   - bins that are zero for every input, because the border extension makes the coefficient of every
+//     source sample of one axis vanish (a mirror-symmetric window along an axis zeroes its Nyquist bin,
+//     a window folded onto few samples zeroes more), are found by integer arithmetic on the window's
+//     index map (axis_bin_vanishes) and take Gamma = 0;
+//   - every other bin with FP32 |F| <= 2^-16 A_p and a non-zero weight is recomputed as a direct FP64
+//     sum over its cube by one warp (resolve_small_bins), and takes Gamma = 0 only if |F| <= 2^-40 A_p
+//     (zero up to FP64 rounding), else its FP64 direction.
+// Bins above 2^-16 A_p carry an FP32 direction error of at most about 2^-10.
 // Spectra are recomputed brick by brick (the forward stages of K1), never stored.
 //
 // One CTA = one brick (t0, x0, y_start .. y_start+BY-1), same mapping as K1:
@@ -26,7 +36,50 @@ namespace {
 
 using f32::Tw;
 
-constexpr float kKinkTau = 1.0f / 524288.0f;  // zero-subgradient level of |F| relative to the window L1 norm
+constexpr float kSmallBin = 1.0f / 65536.0f;     // FP32 |F| / A_p at or below which a bin is resolved in FP64
+constexpr double kZeroBin = 1.0 / 1099511627776.0;  // FP64 |F| / A_p at or below which F = 0 (2^-40)
+
+// FP64 constants of the exact recompute: cos, sin of 2 pi m / n and the taper h(u).
+template <int N> struct Exact64 {
+    double c[N], s[N], h[N];
+};
+
+// Does bin k of the one-axis cube at position p (samples p - n/2 .. p + n/2 - 1 of an axis of length L,
+// through the border extension) vanish for every input?  The bin is sum_m h(m) w^(k m) x[src(m)]
+// (w = exp(-2 pi i / n)), so it vanishes for all x iff, for each source sample j, the coefficient
+// sum_{m: src(m) = j} h(m) w^(k m) is 0.  With n a power of two, w has minimal polynomial w^(n/2) + 1, so
+// the coefficient is zero iff its coordinates on w^0 .. w^(n/2-1) (w^(e + n/2) = -w^e) are; they are
+// integers for the rect taper (h = 1) and, scaled by 4, for the periodic Hann taper
+// (4 h(m) w^(km) = 2 w^(km) - w^(km+m) - w^(km-m)).  Exact: no rounding enters.
+template <int N>
+__device__ bool axis_bin_vanishes(int p, int L, int bnd, int taper, int k) {
+    if (p - N / 2 >= 0 && p + N / 2 - 1 < L) return false;   // distinct in-volume samples: never
+    int src[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) src[m] = ext_index(p - N / 2 + m, L, bnd);
+    for (int m = 0; m < N; ++m) {
+        if (src[m] < 0) continue;
+        bool first = true;
+        for (int q = 0; q < m; ++q) first = first && src[q] != src[m];
+        if (!first) continue;
+        int a[N / 2];
+#pragma unroll
+        for (int e = 0; e < N / 2; ++e) a[e] = 0;
+        for (int q = m; q < N; ++q) {
+            if (src[q] != src[m]) continue;
+            const int e0 = (k * q) % N;
+            const int es[3] = {e0, (e0 + q) % N, (e0 - q % N + N) % N};
+            const int vs[3] = {taper ? 2 : 1, taper ? -1 : 0, taper ? -1 : 0};
+            for (int r = 0; r < 3; ++r) {
+                if (es[r] < N / 2) a[es[r]] += vs[r];
+                else a[es[r] - N / 2] -= vs[r];
+            }
+        }
+        for (int e = 0; e < N / 2; ++e)
+            if (a[e] != 0) return false;
+    }
+    return true;
+}
 
 template <int N> struct BCfg;
 template <> struct BCfg<2>  { static constexpr int BY = 32, YC = 1, MINB = 4; };
@@ -48,21 +101,87 @@ template <int N> struct BGeo {
     static constexpr size_t WIN_BYTES = (size_t)NT * WIN * 8;
     static constexpr size_t A0 = IN_BYTES + G_BYTES;
     static constexpr size_t A_BYTES = A0 > WIN_BYTES ? A0 : WIN_BYTES;   // s_in+s_g1 | windows | Gamma_G1
-    static constexpr size_t SMEM = A_BYTES + G_BYTES + (size_t)4 * BY * 4 + (size_t)YH * 4;
+    static constexpr size_t SMALL_OFF = A_BYTES + G_BYTES + (size_t)4 * BY * 4 + (size_t)YH * 4;
+    // [2 + BY] uint32 masks of bins that vanish for every input (k_t, k_x, then k_y per output), then
+    // [YC][NT] uint16 masks of the small bins each thread leaves to the FP64 recompute
+    static constexpr size_t SMEM = SMALL_OFF + (size_t)(2 + BY) * 4 + (size_t)YC * NT * 2;
+    static_assert(H + N + BY * N <= NT, "one thread per (axis position, bin) of the vanishing masks");
+    static_assert(N <= 16, "16-bit masks of small bins");
     static constexpr int BLOCK_FLOATS = N * N * YH;              // scratch block per CTA
     static_assert(BY % YC == 0 && NT <= 1024, "geometry");
 };
+
+// The small bins left by step 2 (s_small[yi][owner] bit k_y: output yi of the owner's run, bin k_y of its
+// (k_t, k_x) row), one warp at a time per owner: the lanes split the n^3 terms of the direct FP64 sum
+// F = sum_u h(u) Vext[p + u - n/2] w^(k.u) and reduce it; Gamma = rho F / |F| (0 if |F| <= 2^-40 A_p)
+// and its inverse DFT along y, h(u) Gamma exp(+2 pi i k_y u / n), go into the owner's private window.
+template <int N, int NT, int YC, int BY, int H, int ROWS>
+__device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int T, int X, int Y, int bnd, int t0,
+                                                int x0, int y_start, const uint16_t* s_small, float2* s_win,
+                                                const float* s_ge, const float* s_l1, const float* __restrict__ wtab,
+                                                const Tw<N>& tw, const Exact64<N>& ex) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    bool mine = false;
+    for (int yi = 0; yi < YC; ++yi) mine = mine || s_small[yi * NT + tid] != 0;
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    while (todo) {
+        const int o = (tid & ~31) + __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
+        for (int yi = 0; yi < YC; ++yi) {
+            unsigned msk = s_small[yi * NT + o];
+            const int yl = ych * YC + yi, y = y_start + yl;
+            while (msk) {
+                const int ky = __ffs(msk) - 1;
+                msk &= msk - 1;
+                double re = 0.0, im = 0.0;
+                for (int e = lane; e < N * N * N; e += 32) {
+                    const int ut = e / (N * N), ux = (e / N) % N, uy = e % N;
+                    const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
+                    const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
+                    const int gy = ext_index(y - N / 2 + uy, Y, bnd);
+                    if ((gt | gx | gy) < 0) continue;
+                    const double v = (double)__ldg(V + ((size_t)gt * X + gx) * Y + gy) * ex.h[ut] * ex.h[ux] * ex.h[uy];
+                    const int ph = (kt * ut + kx * ux + ky * uy) % N;
+                    re = fma(v, ex.c[ph], re);
+                    im = fma(-v, ex.s[ph], im);
+                }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, d);
+                    im += __shfl_xor_sync(0xffffffffu, im, d);
+                }
+                const double mag = sqrt(re * re + im * im);
+                if (mag > kZeroBin * (double)s_l1[yl] && lane < N) {
+                    const int k = ky <= N / 2 ? ky : N - ky;
+                    const float rho = fmaf(s_ge[yl], __ldg(wtab + k * ROWS + row),
+                                           fmaf(s_ge[BY + yl], __ldg(wtab + (H + k) * ROWS + row),
+                                                s_ge[2 * BY + yl] * __ldg(wtab + (2 * H + k) * ROWS + row)));
+                    const float gr = (float)(rho * re / mag), gi = (float)(rho * im / mag);
+                    const int u = lane;
+                    const float c = tw.c[k][u], sn = ky <= N / 2 ? tw.s[k][u] : -tw.s[k][u];
+                    float2* w = s_win + (yi + u) * NT + o;
+                    float2 acc = *w;
+                    acc.x += gr * c - gi * sn;
+                    acc.y += gr * sn + gi * c;
+                    *w = acc;
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
 
 // EN: the energy reading of the feature (Gamma = 2 rho F, no kink band); SL: the forward stage 3 by the
 // sliding recursion along y (rect taper, n = 16; at n = 8 the direct sum is as fast, with 30 fewer
 // registers): the first output of each thread's run by the direct sum,
 // then F_{y0+1}[k] = e^{2 pi i k/n} (F_{y0}[k] - G2[y0 - n/2] + G2[y0 + n/2]) (the forward kernel's form).
-// The brick is staged as is: the kink band below is relative to the raw window's L1 norm.
+// The brick is staged as is: the small-bin level below is relative to the raw window's L1 norm.
 template <int N, bool EN, bool SL>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                        int T, int X, int Y, int bnd, int t_begin, int t_step, const float* __restrict__ wtab,
-                       const __grid_constant__ Tw<N> tw) {
+                       int taper, const __grid_constant__ Tw<N> tw, const __grid_constant__ Exact64<N> ex) {
     using G = BGeo<N>;
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT, WIN = G::WIN;
@@ -75,6 +194,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     float* s_ge = reinterpret_cast<float*>(smem_raw + G::A_BYTES + G::G_BYTES);  // [3][BY]
     float* s_l1 = s_ge + 3 * BY;                                                 // [BY] window L1 norms
     float* s_col = s_l1 + BY;                                                    // [YH] column sums
+    unsigned* s_vanish = reinterpret_cast<unsigned*>(smem_raw + G::SMALL_OFF);   // [2 + BY] (k_t, k_x, k_y)
+    uint16_t* s_small = reinterpret_cast<uint16_t*>(s_vanish + 2 + BY);          // [YC][NT]
 
     const int tid = threadIdx.x;
     const int y_start = blockIdx.x * BY;
@@ -82,6 +203,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const int t0 = t_begin + blockIdx.z * t_step;   // t_step s > 1: the lattice planes of stride-s windows
     const size_t NV = (size_t)T * X * Y;
 
+    if (!EN)
+        for (int i = tid; i < 2 + BY; i += NT) s_vanish[i] = 0u;
     B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
     for (int i = tid; i < 3 * BY; i += NT) {
         const int m = i / BY, yl = i % BY, y = y_start + yl;
@@ -93,6 +216,23 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
         float a = 0.f;
         for (int r = 0; r < N * N; ++r) a = fmaf(tw.c[0][r / N] * tw.c[0][r % N], fabsf(s_in[r * YH + yy]), a);
         s_col[yy] = a;
+    }
+    if (!EN) {
+        // bins that vanish for every input under the border extension: one thread per (axis position, bin)
+        int word = -1, k = 0;
+        bool z = false;
+        if (tid < H) {
+            word = 0; k = tid;
+            z = axis_bin_vanishes<N>(t0, T, bnd, taper, k);
+        } else if (tid < H + N) {
+            word = 1; k = tid - H;
+            z = axis_bin_vanishes<N>(x0, X, bnd, taper, k);
+        } else if (tid < H + N + BY * N) {
+            const int i = tid - H - N;
+            word = 2 + i / N; k = i % N;
+            z = axis_bin_vanishes<N>(y_start + i / N, Y, bnd, taper, k);
+        }
+        if (z) atomicOr(s_vanish + word, 1u << k);
     }
     B::stage1(s_in, s_g1, tw);
     __syncthreads();
@@ -114,6 +254,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
     const float2* grow = s_g2 + (size_t)row * YH;
     float fr[N], fi[N];   // F[k_y] of the current output, all n bins
+    // the whole row vanishes when its k_t or its k_x does
+    const bool row_vanishes = !EN && (((s_vanish[0] >> (row / N)) | (s_vanish[1] >> (row % N))) & 1u);
     for (int yi = 0; yi < YC; ++yi) {
         const int yl = ych * YC + yi;
         if (!SL || yi == 0) {
@@ -158,8 +300,9 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             }
         }
         const float g0 = s_ge[yl], g1 = s_ge[BY + yl], g2 = s_ge[2 * BY + yl];
-        const float thr = kKinkTau * s_l1[yl];
+        const float thr = kSmallBin * s_l1[yl];
         const float thr2 = fmaxf(thr * thr, 1e-30f);   // also keeps subnormal |F|^2 away from rsqrt
+        unsigned small = 0u;                            // bins at or below thr: Gamma left to the FP64 recompute
         // A_k = Gamma[k] + Gamma[n-k], B_k = i (Gamma[k] - Gamma[n-k]); self-paired bins: A_k = Gamma[k]
         float ar[H], ai[H], br[H], bi[H];
 #pragma unroll
@@ -168,6 +311,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             if (k == 0 || 2 * k == N) {
                 const float m2 = fmaf(fr[k], fr[k], fi[k] * fi[k]);
                 const float sc = f32::bin_adjoint_scale<EN>(rho, m2, thr2);
+                if (!EN && m2 <= thr2 && rho != 0.f) small |= 1u << k;
                 ar[k] = sc * fr[k];
                 ai[k] = sc * fi[k];
                 br[k] = bi[k] = 0.f;
@@ -177,12 +321,22 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
                 const float m2a = fmaf(far, far, fai * fai), m2b = fmaf(hr, hr, hi * hi);
                 const float sa = f32::bin_adjoint_scale<EN>(rho, m2a, thr2);
                 const float sb = f32::bin_adjoint_scale<EN>(rho, m2b, thr2);
+                if (!EN && rho != 0.f) {
+                    if (m2a <= thr2) small |= 1u << k;
+                    if (m2b <= thr2) small |= 1u << (N - k);
+                }
                 const float gar = sa * far, gai = sa * fai, gbr = sb * hr, gbi = sb * hi;
                 ar[k] = gar + gbr;
                 ai[k] = gai + gbi;
                 br[k] = gbi - gai;        // i * (Gamma_a - Gamma_b)
                 bi[k] = gar - gbr;
             }
+        }
+        if (!EN) {
+            // bins that vanish for every input keep Gamma = 0; so does an all-zero cube (A_p = 0)
+            if (small != 0u && (row_vanishes || !(s_l1[yl] > 0.f))) small = 0u;
+            if (small != 0u) small &= ~s_vanish[2 + yl];
+            s_small[yi * NT + tid] = (uint16_t)small;
         }
 #pragma unroll
         for (int u = 0; u < N; ++u) {
@@ -203,6 +357,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             *w = acc;
         }
     }
+    if (!EN) resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, T, X, Y, bnd, t0, x0, y_start, s_small, s_win, s_ge, s_l1,
+                                                        wtab, tw, ex);
     __syncthreads();
 
     // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
@@ -297,28 +453,42 @@ cudaError_t prepare_n() {
     return e;
 }
 
+// The FP64 constants of the exact recompute of small bins: cos, sin (2 pi m / n) and the taper (rect, or
+// the periodic Hann window 1/2 - cos(2 pi u / n) / 2), from the host's double-precision libm.
+template <int N>
+Exact64<N> make_exact64(int taper) {
+    Exact64<N> e;
+    for (int m = 0; m < N; ++m) {
+        const double a = 2.0 * 3.14159265358979323846 * m / N;
+        e.c[m] = cos(a);
+        e.s[m] = sin(a);
+        e.h[m] = taper ? 0.5 - 0.5 * cos(a) : 1.0;
+    }
+    return e;
+}
+
 template <int N, bool SL>
 void launch_sl(const TwiddleTable& t, const float* wtab, dim3 grid, const float* V, const float* gE, float* blocks,
-               int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, cudaStream_t s) {
+               int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int taper, cudaStream_t s) {
     using G = BGeo<N>;
     if (feat == 1)
-        k5_spectra_adjoint_f32<N, true, SL><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                        t_step, wtab, f32::make_tw<N>(t));
+        k5_spectra_adjoint_f32<N, true, SL><<<grid, G::NT, G::SMEM, s>>>(
+            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact64<N>(taper));
     else
-        k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin,
-                                                                         t_step, wtab, f32::make_tw<N>(t));
+        k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(
+            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact64<N>(taper));
 }
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const float* wtab, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, bool rect, cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, int taper, cudaStream_t s) {
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
     if constexpr (kAdjointSliding<N>) {
-        if (rect) launch_sl<N, true>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
-        else launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
+        if (taper == 0) launch_sl<N, true>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
+        else launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
     } else {
-        launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, s);
+        launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -349,13 +519,12 @@ SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
                                        const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
                                        int t_begin, int t_step, int t_count, int taper, cudaStream_t s) {
-    const bool rect = taper == 0;
-    if (t_step < 1) return cudaErrorInvalidValue;
+    if (t_step < 1 || taper < 0 || taper > 1) return cudaErrorInvalidValue;
     switch (n) {
-        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
-        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
-        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
-        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, rect, s);
+        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
+        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
+        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
+        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -4,6 +4,13 @@ C ABI, plus central finite differences of the GPU forward and a weight-fitting r
 Tolerances (FP32 path): relative L2 <= 1e-5 for each step's adjoint.  The sign of each
 center-surround difference (a kink of |.|) is an integer-valued decision: the step tests feed
 both sides the same FP32 features and FP32 weights, so both take it on identical numbers.
+
+The oracle takes the zero subgradient of |F| only where F = 0 up to FP64 rounding (2^-40 of the
+window L1 norm).  The inputs below hold, by construction of the border extension and by chance,
+many cubes with bins between that level and 2^-17 L1, where FP32 has no usable direction F/|F|:
+the FP32 adjoint resolves those bins exactly (integer test for the bins that vanish for every
+input, FP64 recompute for the rest), and the tests assert from the oracle that such bins are
+present, so the 1e-5 bar is met on ill-conditioned cubes, not around them.
 """
 import numpy as np
 import pytest
@@ -70,6 +77,36 @@ def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
         eng.close()
     ref = oracle.features_adjoint(V, gE, n, boundary=boundary)
     assert rel_l2(got, ref) <= RTOL, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("n,shape,boundary,source", [
+    (8, (9, 7, 33), "symmetric", "seismic"),
+    (8, (16, 16, 40), "symmetric", "seismic"),
+    (16, (6, 5, 21), "symmetric", "seismic"),
+    (16, (20, 20, 40), "symmetric", "seismic"),
+    (16, (9, 8, 24), "symmetric", "random"),
+    (16, (17, 18, 40), "periodic", "seismic"),
+])
+def test_spectral_adjoint_ill_conditioned_cubes(sal, n, shape, boundary, source):
+    """Inputs the oracle shows to hold cubes with small non-zero bins (2^-40 < |F| / L1 <= 2^-17) and,
+    under the symmetric extension, bins that vanish for every input: the whole gradient at 1e-5."""
+    if source == "seismic":
+        V, _ = synth.volume(synth.small_spec(shape, seed=3, faults=1))
+    else:
+        V = synth.random_volume(shape, seed=0)
+    small = oracle.band_count(V, n, boundary)
+    assert small.sum() > 0, "the input holds no ill-conditioned cube"
+    gE = synth.random_volume((3,) + shape, seed=n + 9)
+    eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary))
+    try:
+        gV = torch.empty(shape, dtype=torch.float32, device="cuda")
+        sal.sal_local_spectra_project_backward(eng.h, _cuda(V), _cuda(gE), gV)
+        torch.cuda.synchronize()
+        got = gV.cpu().numpy()
+    finally:
+        eng.close()
+    ref = oracle.features_adjoint(V, gE, n, boundary=boundary)
+    assert rel_l2(got, ref) <= RTOL, (rel_l2(got, ref), int((small > 0).sum()))
 
 
 @pytest.mark.parametrize("n,shape,taper,prec,tol", [
