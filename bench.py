@@ -10,7 +10,10 @@ Prints one JSON line.  Multi-GPU (torchrun): every rank processes its own volume
 shards into independent volumes, no collective on the data path), the timed region is
 bracketed by barriers and the max over ranks is taken; value = all voxels / that time.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload salt128] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload full462x951x651] [--impl ours|reference]
+
+The default workload is the full-scale volume (462 x 951 x 651, 286 M voxels, window 16^3, BF16
+tensor-core local DFT): the largest configuration of the method that fits one GPU.
 """
 import argparse
 import json
@@ -44,13 +47,34 @@ WORKLOADS = {
                            "body, folds, noise 0.1 rms), passed as a volume [1][462][951] (one plane), window 16^2, "
                            "the in-plane t, x, t-x window, weights (0, 1/2, 1/2)",
                            cpu_sample=256, ref_sample=80),   # one plane: sample x sample voxels
-    "full462x951x651": dict(spec="full462x951x651", n=16, desc="462x951x651 synthetic seismic volume (20 faults, "
-                            "3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3", cpu_sample=40,
-                            ref_sample=20),
+    "full462x951x651": dict(spec="full462x951x651", n=16, desc="config 5: 462x951x651 synthetic seismic volume "
+                            "(20 faults, 3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3",
+                            cpu_sample=40, ref_sample=20, e2e_steps=5, side_steps=3),
 }
-# Peak of the binding pipe of K1 (FP32 SIMT form): 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-FMA_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12   # FMA-pipe operations per second (an FFMA counts once)
+DEFAULT_WORKLOAD = "full462x951x651"   # the largest configuration that fits one GPU
+# Peaks of the ALU pipes, set by set_alu_peaks() from the device: the FP32 FMA pipe from its unit count
+# (128 lanes per SM), the SM count of the device and its maximum SM clock; the MUFU pipe measured live
+# (sal_measure_mufu_rate).  The values below are the nominal GB300 figures, used only until then.
+PEAKS = {"sms": 152, "sm_ghz": 2.070, "fp32_tflops": 152 * 128 * 2 * 2.070e9 / 1e12,
+         "fma_tops": 152 * 128 * 2.070e9 / 1e12, "mufu": {}, "mufu_note": "nominal 16/clk/SM (not measured)"}
+
+
+def set_alu_peaks(sal, sms: int, sm_max_mhz):
+    """FP32 FMA peak = SMs x 128 lanes x 2 flop x max SM clock (unit counts and clocks); MUFU peak =
+    the measured issue rate of sqrt.approx / rsqrt.approx over the whole device."""
+    ghz = (sm_max_mhz or 2070.0) / 1e3
+    PEAKS.update(sms=sms, sm_ghz=ghz, fp32_tflops=sms * 128 * 2 * ghz * 1e9 / 1e12,
+                 fma_tops=sms * 128 * ghz * 1e9 / 1e12)
+    for op in ("sqrt", "rsqrt"):
+        rate, _ = sal.sal_measure_mufu_rate(op)
+        PEAKS["mufu"][op] = rate / 1e12
+    PEAKS["mufu_note"] = (f"measured in this run: {op_rates()} (sal_measure_mufu_rate: 8 CTAs x 256 threads per SM, "
+                          f"16 independent chains per thread); {sms} SMs")
+
+
+def op_rates():
+    return ", ".join(f"{k} {v:.3f} T/s ({v * 1e12 / (PEAKS['sms'] * PEAKS['sm_ghz'] * 1e9):.1f}/clk/SM at the max clock)"
+                     for k, v in PEAKS["mufu"].items())
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
 K1_TRAFFIC = {("salt128", 16, "fp32"): 8711168,   # sliding, 32-output form; profiles/salt128_n16_fp32_fwd_bwd.md
@@ -68,9 +92,6 @@ def measured_peaks():
         return {}
 
 
-# MUFU (XU) pipe: 16 ops / clk / SM x 152 SMs x 2.07 GHz (derived from unit counts and the max clock)
-MUFU_PEAK_TOPS = 16 * 152 * 2.070e9 / 1e12
-
 
 def bins_per_voxel(n: int) -> int:
     """abs(F) bins per voxel of the half spectrum (k_t in [0, n/2]): h n^2, one sqrt each."""
@@ -87,25 +108,27 @@ def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt", fea
     bin: |F|^2 and its share of the weighted sums) on the FMA pipe binds."""
     fpv = k1_flops_per_voxel(n) if flops_per_voxel is None else flops_per_voxel
     flops = flops_mult * fpv * nvox / (ms / 1e3) / 1e12
+    fp32_note = (f"FP32 FMA peak {PEAKS['sms']} SM x 128 lanes x 2 x {PEAKS['sm_ghz']:.2f} GHz (unit counts and "
+                 "the max SM clock)")
     if prec == "fp32":
-        return {"kernel": kernel, "bound": "alu", "pipe": "fp32 fma", "achieved": flops, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": flops / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
+        pk = PEAKS["fp32_tflops"]
+        return {"kernel": kernel, "bound": "alu", "pipe": "fp32 fma", "achieved": flops, "peak": pk,
+                "unit": "TFLOP/s", "frac": flops / pk, "traffic": traffic, "peak_note": fp32_note}
     bins = bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     tpk = measured_peaks().get("bf16_tflops", 1900.0)
     tensor = {"achieved_tflops": flops, "peak_tflops": tpk, "frac": flops / tpk,
               "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); fp16 dense rate is equal"}
     if feature == "energy":
         ops = 4.0 * bins
+        pk = PEAKS["fma_tops"]
         return {"kernel": kernel, "bound": "alu", "pipe": "FP32 FMA (energy epilogue: ~4 operations per bin)",
-                "achieved": ops, "peak": FMA_OPS_PEAK, "unit": "Tops/s", "frac": ops / FMA_OPS_PEAK,
-                "traffic": traffic, "peak_note": "FMA pipe 128 ops/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
-                "tensor": tensor}
+                "achieved": ops, "peak": pk, "unit": "Tops/s", "frac": ops / pk, "traffic": traffic,
+                "peak_note": fp32_note.replace("x 2 x", "x"), "tensor": tensor}
     what = "abs(F) epilogue: one sqrt per bin" if mufu_op == "sqrt" else "Gamma epilogue: one rsqrt per bin"
+    pk = PEAKS["mufu"].get(mufu_op, 16 * PEAKS["sms"] * PEAKS["sm_ghz"] * 1e9 / 1e12)
     return {"kernel": kernel, "bound": "alu", "pipe": f"MUFU ({what})", "achieved": bins,
-            "peak": MUFU_PEAK_TOPS, "unit": f"T{mufu_op}/s", "frac": bins / MUFU_PEAK_TOPS, "traffic": traffic,
-            "peak_note": "MUFU 16/clk/SM x 152 SM x 2.07 GHz (derived, not measured)",
-            "tensor": tensor}
+            "peak": pk, "unit": f"T{mufu_op}/s", "frac": bins / pk, "traffic": traffic,
+            "peak_note": PEAKS["mufu_note"], "tensor": tensor}
 
 
 def max_over_ranks(values, dist=None, device="cpu"):
@@ -146,6 +169,18 @@ def k1_flops_per_voxel_sliding(n: int) -> int:
     and the direct sum (8hn^3) for one output of each run."""
     h = n // 2 + 1
     return 4 * h * n + 8 * h * n * n + 8 * h * n * n + 8 * h * n ** 3 // K1_F32_SLIDING_RUN[n]
+
+
+def max_sm_clock_mhz(gpu_id):
+    """The device's maximum SM clock (nvidia-smi clocks.max.sm), or None."""
+    cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
+    if gpu_id:
+        cmd += ["-i", gpu_id]
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=30).stdout.strip().splitlines()
+        return float(out[0]) if out else None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
 
 
 class ClockSampler:
@@ -243,7 +278,8 @@ def _workload_volume(wl):
     import numpy as np
 
     import synth
-    V, _ = synth.volume(wl["spec"], with_mask=False)
+    # X slabs made in spawned processes (the generator is slab-invariant: same volume bit for bit)
+    V, _ = synth.volume(wl["spec"], with_mask=False, workers=min(16, os.cpu_count() or 1))
     if wl.get("section"):
         V = np.ascontiguousarray(V[:, :, V.shape[2] // 2])[None]
     return V
@@ -292,7 +328,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="salt128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp32"],
                     help="arithmetic of the local-DFT contraction (bf16/fp16: tensor cores)")
@@ -305,7 +341,19 @@ def main():
                          "cube of |IDFT(F_m)| (spatial reading: FP32, n <= 8, --form fwd)")
     ap.add_argument("--stride", type=int, default=1,
                     help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2)")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print the measured MUFU issue rates (the roofline denominators of the |F| epilogues) "
+                         "and exit")
     args = ap.parse_args()
+    if args.measure_peaks:
+        import torch
+
+        import paper_2201_06174_gb300 as sal
+        props = torch.cuda.get_device_properties(0)
+        set_alu_peaks(sal, props.multi_processor_count, max_sm_clock_mhz(""))
+        print(json.dumps({"mufu_tops": PEAKS["mufu"], "sms": PEAKS["sms"], "sm_ghz": PEAKS["sm_ghz"],
+                          "fp32_tflops": PEAKS["fp32_tflops"], "note": PEAKS["mufu_note"]}), flush=True)
+        return
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:
         wl["n"] = args.n
@@ -379,14 +427,15 @@ def main():
         for _, c in calls:
             c()
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    barrier()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
     dev_props = torch.cuda.get_device_properties(local_rank)
     gpu_id = str(getattr(dev_props, "uuid", "") or "")
     if gpu_id and not gpu_id.startswith("GPU-"):
         gpu_id = "GPU-" + gpu_id
+    set_alu_peaks(sal, dev_props.multi_processor_count, max_sm_clock_mhz(gpu_id))
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
     clocks = ClockSampler(gpu_id)
     clocks.start()
     barrier()
@@ -435,24 +484,30 @@ def main():
         if args.form == "fwdbwd":
             gVh.copy_(gV, non_blocking=True)
 
-    def e2e_rate(fused_backward):
-        for _ in range(max(args.warmup, 3)):
+    # the end-to-end and side measurements of a large workload take fewer steps than the headline
+    e2e_steps = min(args.steps, wl.get("e2e_steps", args.steps))
+    side_steps = min(args.steps, wl.get("side_steps", args.steps))
+
+    def e2e_rate(fused_backward, steps):
+        for _ in range(3):
             e2e_step(fused_backward)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             e2e_step(fused_backward)
         e1.record()
         barrier()
         ms = max_over_ranks([e0.elapsed_time(e1)], dist, dev)[0]
-        return job_throughput(world, nvox, args.steps, ms)
+        return job_throughput(world, nvox, steps, ms)
 
-    e2e_value = e2e_rate(False)
-    e2e_fused_value = e2e_rate(True) if args.form == "fwdbwd" else None
+    e2e_value = e2e_rate(False, e2e_steps)
+    e2e_fused_value = e2e_rate(True, side_steps) if args.form == "fwdbwd" else None
+    S_prec = S.clone()   # the map of this precision form, weights Wd (from the last e2e step's forward)
 
     # the plain FP32 form of K1 on the same volume (forward comparison of the precision forms)
     k1_fp32_ms = None
+    s_vs_fp32 = None
     if args.prec != "fp32":
         eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature, stride=args.stride))
         E32 = torch.empty_like(E)
@@ -460,7 +515,7 @@ def main():
             sal.sal_local_spectra_project(eng32.h, Vd, E32)
         barrier()
         tot = 0.0
-        for i in range(args.steps):
+        for i in range(side_steps):
             flush.fill_(i & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
@@ -468,7 +523,16 @@ def main():
             b.record()
             b.synchronize()
             tot += a.elapsed_time(b)
-        k1_fp32_ms = tot / args.steps
+        k1_fp32_ms = tot / side_steps
+        # the map of the FP32 form (oracle-pinned) with the same weights, against this form's map
+        S32 = torch.empty_like(S)
+        sal.sal_saliency(eng32.h, Vd, None, Wd, S32, None, None, W)
+        torch.cuda.synchronize()
+        dS = (S_prec.double() - S32.double())
+        s_vs_fp32 = {"max_abs": float(dS.abs().max()), "rel_l2": float(dS.norm() / S32.double().norm()),
+                     "voxels": nvox, "what": "normalised [0,1] map S of this form against the FP32 form's S, "
+                                              "every voxel, same weights"}
+        del E32, S32, dS
         eng32.close()
 
     n = wl["n"]
@@ -529,16 +593,18 @@ def main():
                     "ms_per_step": fwd_ms / args.steps},
         "ms_per_call": {nm: v / args.steps for nm, v in zip(names, per_call)},
         "k1_vs_fp32": None if k1_fp32_ms is None else {
-            "k1_ms": k1_ms, "k1_fp32_ms": k1_fp32_ms, "speedup": k1_fp32_ms / k1_ms,
+            "k1_ms": k1_ms, "k1_fp32_ms": k1_fp32_ms, "speedup": k1_fp32_ms / k1_ms, "fp32_steps": side_steps,
             "forward_fp32_Mvoxel_s": world * nvox / ((k1_fp32_ms + sum(per_call[1:3]) / args.steps) / 1e3) / 1e6},
         "roofline": rl,
-        "e2e": {"value": e2e_value, "unit": "Mvoxel/s",
+        "max_abs_S": None if s_vs_fp32 is None else s_vs_fp32["max_abs"],
+        "S_vs_fp32": s_vs_fp32,
+        "e2e": {"value": e2e_value, "unit": "Mvoxel/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes,
                 "d2h_bytes_per_step": (2 if args.form == "fwdbwd" else 1) * V.nbytes,
                 "calls": "sal_saliency (with E, S3 out)" + (" + sal_combine_backward + sal_center_surround_backward + "
                                                             "sal_local_spectra_project_backward"
                                                             if args.form == "fwdbwd" else ""),
-                "fused_backward_value": e2e_fused_value},
+                "fused_backward_value": e2e_fused_value, "fused_backward_steps": side_steps},
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": wall,

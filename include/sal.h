@@ -79,17 +79,38 @@ typedef struct {
                                the backward calls return SAL_ERR_UNSUPPORTED)           */
     /* Directional center-surround window (Eq. 3, Fig. 4): Q = n_offsets neighbours
        o = (dt,dx,dy), |dt|,|dx|,|dy| <= 8, with weight w_o = alpha[dir_id[o]] * gauss_w[o].
-       Host pointers; copied by sal_create. */
-    int n_offsets;          /* Q, 1 <= Q <= 64                                         */
+       Host pointers; copied by sal_create.  n_offsets = 0: sal_create builds the window
+       itself from the direction fields at the end of this struct (sal_directional_window);
+       offsets, gauss_w, dir_id and n_dirs are then ignored. */
+    int n_offsets;          /* Q, 0 or 1 <= Q <= 64                                    */
     const int* offsets;     /* [Q][3]                                                  */
     const float* gauss_w;   /* [Q]  Gaussian factor of each neighbour                  */
     const int* dir_id;      /* [Q]  direction group of each neighbour, < n_dirs        */
     int n_dirs;             /* 1 <= n_dirs <= 16                                       */
-    const float* alpha;     /* [n_dirs] per-direction weights (host)                   */
+    const float* alpha;     /* [n_dirs] per-direction weights (host); with n_offsets = 0
+                               it may be NULL (all 1)                                   */
     int prec;               /* sal_precision of the local DFT contraction              */
     double ls_delta;        /* ridge delta of the template fit (G + delta I)^-1 b      */
     size_t hbm_budget_bytes;/* upper bound on the handle's device scratch (0 = none)   */
+    /* Used when n_offsets = 0 (see sal_directional_window): */
+    int n_directions;       /* 0 with directions NULL: the three directions of Fig. 4  */
+    const int* directions;  /* [n_directions][3] direction vectors (host)              */
+    int radius;             /* R: neighbours s d for s = +-1 .. +-R                    */
+    double sigma;           /* sigma of the Gaussian factors                           */
 } sal_params;
+
+/* The directional window of Eq. 3 and Fig. 4 (host only, no device work).  For each direction
+ * vector d_i (directions [n_directions][3]; with n_directions = 0 and directions NULL, the three
+ * directions of Fig. 4: t (1,0,0), x (0,1,0) and t-x (1,1,0)), the neighbours o = s d_i for
+ * s = -R .. -1, 1 .. R in that order, with Gaussian factor gauss_w = exp(-|o|^2 / (2 sigma^2))
+ * (Eq. 3's w before the per-direction weight alpha) and direction id i.  Q = 2 R n_directions
+ * neighbours are written to offsets [Q][3], gauss_w [Q] and dir_id [Q] (host arrays of capacity
+ * `cap` neighbours) and Q to *n_offsets.  SAL_ERR_INVALID_ARG if R < 1, sigma is not finite and
+ * positive, n_directions is not in [1, 16] (or 0 with directions NULL), a direction is zero, a
+ * component of some o exceeds +-8, or Q exceeds cap or 64.  sal_create calls it when
+ * sal_params.n_offsets is 0. */
+sal_status sal_directional_window(int n_directions, const int* directions, int radius, double sigma, int cap,
+                                  int* n_offsets, int* offsets, float* gauss_w, int* dir_id);
 
 /* Creates a handle for volumes of size T x X x Y on the current CUDA device.
  * Validates `p`, builds the DFT tables and allocates scratch (E, S_m and gradient
@@ -147,15 +168,18 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
  * that runs under a caller-owned memory pool or arena, inside a region where new allocations
  * are forbidden, or on a path where an allocation and the synchronisation it may bring are not
  * acceptable.  It needs no handle (sal_create allocates) and calls no cudaMalloc or cudaFree.
- * The paper has no counterpart: this is a deployment form of the step 5 combination above,
- * with the same arguments and results (ls_delta as in sal_params).
+ * The paper has no counterpart.  It computes what sal_combine computes, with the same arguments
+ * and results (ls_delta as in sal_params), on the current device: S3, S and the non-NULL D, W_in,
+ * W_out must be device memory of that device (else SAL_ERR_INVALID_ARG before any work).
  * Its reduction scratch is one file-scope device array of about 0.6 MiB that every GPU that
  * loads the library holds until the process exits.  Limit: T*X*Y <= 16,777,216 voxels; larger
  * volumes return SAL_ERR_UNSUPPORTED before any work.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current: make that first call
- * before any stream capture.  All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race and give wrong results.  Errors are reported by
- * sal_last_error(NULL). */
+ * array's device address (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process: make that first call before any stream capture, and do not call it on a device after
+ * a cudaDeviceReset of that device in the same process (the kept address would be stale).  All
+ * calls share the array: calls that overlap on the GPU (other streams, other threads) race and
+ * give wrong results.  Errors are reported by sal_last_error(NULL), which a successful call
+ * clears. */
 sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
                                double ls_delta, float* W_out, float* S, void* stream);
 
@@ -205,6 +229,24 @@ sal_status sal_center_surround_backward(sal_handle* h, const float* E, const flo
  * gW (nullable, device [3]).  S3, gS3: [3][T][X][Y]; W: device [3]; gS: [T][X][Y]. */
 sal_status sal_combine_backward(sal_handle* h, const float* S3, const float* W, const float* gS, float* gS3,
                                 float* gW, void* stream);
+
+/* Check of the failure detection (the paper has no counterpart).  The tensor-core kernels bound every
+ * wait on an mbarrier; a wait that gives up sets the handle's error word, the CTA leaves, and the next
+ * call on the handle returns SAL_ERR_TIMEOUT and clears the word.  This call makes such a wait give
+ * up on purpose: one CTA waits on an mbarrier to which no arrival is ever made, through the same
+ * bounded helper, with `tries` tries (1 <= tries <= 2^20; SAL_ERR_INVALID_ARG otherwise), then sets
+ * the error word and returns.  Nothing faults, traps or spins without bound, and the CUDA context and
+ * the handle stay usable.  Enqueued on `stream`; returns SAL_OK once enqueued. */
+sal_status sal_check_bounded_wait(sal_handle* h, unsigned tries, void* stream);
+
+/* Measured issue rate of the MUFU pipe (the paper has no counterpart: the roofline denominator of the
+ * |F| epilogues).  op 0: sqrt.approx.f32, op 1: rsqrt.approx.f32, the instructions those epilogues
+ * issue once per bin.  Runs 8 CTAs of 256 threads per SM of the current device, each thread 16
+ * independent chains of 2048 operations, on the legacy default stream, synchronously, after one
+ * warm-up launch, timed with CUDA events; allocates and frees a small output buffer.
+ * *ops_per_second receives operations per second over the whole device, *sm_count (nullable) the
+ * device's SM count.  Errors are reported by sal_last_error(NULL). */
+sal_status sal_measure_mufu_rate(int op, double* ops_per_second, int* sm_count);
 
 /* Number of kernels this library has launched in the process so far (all handles and
  * entry points), for accounting; host pointer `count`. */

@@ -647,7 +647,7 @@ cudaError_t backward_weights_launch(const float* S3, const float* gS, long long 
 
 // The tiled kernel holds one block per tile for all its planes; with fewer tiles than two waves of
 // resident blocks (3 per SM) it leaves SMs idle, and the row kernel, whose warps cover every row, is faster.
-static int g_tiled_min_blocks = 2 * 152 * 3;
+static int g_tiled_min_blocks = 2 * 3 * 152;   // set from the device's SM count by dcs_adjoint_prepare
 
 cudaError_t dcs_adjoint_prepare() {
     int dev = 0, sms = 0;
@@ -697,7 +697,8 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
     const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count, t_step);
     const long long rows1 = e_total / (g.XH * g.YH);   // (plane, brick) rows, a warp each
     long long b1 = (rows1 + kThreads / 32 - 1) / (kThreads / 32);
-    if (b1 > 152 * 8) b1 = 152 * 8;
+    const long long cap1 = 8LL * device_sms();   // grid-stride: 8 blocks per SM
+    if (b1 > cap1) b1 = cap1;
     if (b1 < 1) b1 = 1;
     k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count, t_step);
     // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_step (t_count - 1) + n/2); a slab

@@ -268,10 +268,21 @@ constexpr int kNoAllocMaxDevices = 64;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
+// True when p is device (or managed) memory that the current device dev can address as its own.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, const float* D, const float* W_in,
                                           double ls_delta, float* W_out, float* S, void* stream) {
+    sal::set_unbound_error("");
     if (T < 1 || X < 1 || Y < 1) {
         sal::set_unbound_error("sal_combine_noalloc: T, X, Y must be >= 1");
         return SAL_ERR_INVALID_ARG;
@@ -300,6 +311,15 @@ extern "C" sal_status sal_combine_noalloc(int T, int X, int Y, const float* S3, 
         sal::set_unbound_error("sal_combine_noalloc: device ordinal beyond 63");
         return SAL_ERR_UNSUPPORTED;
     }
+    // every buffer must live on the current device: the kernels launch there
+    const void* bufs[5] = {S3, S, D, W_in, W_out};
+    const char* names[5] = {"S3", "S", "D", "W_in", "W_out"};
+    for (int i = 0; i < 5; ++i)
+        if (bufs[i] && !on_device(bufs[i], dev)) {
+            sal::set_unbound_error(std::string("sal_combine_noalloc: ") + names[i] +
+                                   " is not device memory of the current device " + std::to_string(dev));
+            return SAL_ERR_INVALID_ARG;
+        }
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);

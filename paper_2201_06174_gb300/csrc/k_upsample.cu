@@ -102,7 +102,8 @@ cudaError_t upsample_adjoint_launch(const float* gE, float* gEl, int T, int X, i
     const long long NVc = (long long)((T + stride - 1) / stride) * ((X + stride - 1) / stride) *
                           ((Y + stride - 1) / stride);
     long long nb = (NVc + kThreads - 1) / kThreads;
-    if (nb > 152 * 32) nb = 152 * 32;
+    const long long cap = 32LL * device_sms();   // grid-stride: 32 blocks per SM
+    if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;
     k5_upsample_adjoint<<<(int)nb, kThreads, 0, s>>>(gE, gEl, T, X, Y, stride);
     note_launches(1);

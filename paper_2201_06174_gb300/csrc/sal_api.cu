@@ -139,16 +139,87 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
 
 void sal::set_unbound_error(const std::string& msg) { g_create_error = msg; }
 
+int sal::device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+        return 1;
+    return sms;
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 void sal::note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 extern "C" {
 
-sal_status sal_create(const sal_params* p, int T, int X, int Y, sal_handle** out) {
+sal_status sal_directional_window(int n_directions, const int* directions, int radius, double sigma, int cap,
+                                  int* n_offsets, int* offsets, float* gauss_w, int* dir_id) {
+    // the t, x and t-x directions of Fig. 4
+    static const int kFig4[3][3] = {{1, 0, 0}, {0, 1, 0}, {1, 1, 0}};
+    if (!n_offsets || !offsets || !gauss_w || !dir_id)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "window output arrays must not be NULL");
+    if (n_directions == 0 && directions == nullptr) {
+        n_directions = 3;
+        directions = &kFig4[0][0];
+    }
+    if (n_directions < 1 || n_directions > sal::kMaxDirs || !directions)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "n_directions must be in [1, 16] with directions given");
+    if (radius < 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "radius must be >= 1");
+    if (!(sigma > 0.0) || !std::isfinite(sigma))
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    const long long Q = 2LL * radius * n_directions;
+    if (Q > sal::kMaxOffsets || Q > cap)
+        return fail(nullptr, SAL_ERR_INVALID_ARG, "the window holds " + std::to_string(Q) + " neighbours (limit " +
+                                                      std::to_string(std::min(cap, sal::kMaxOffsets)) + ")");
+    int q = 0;
+    for (int d = 0; d < n_directions; ++d) {
+        const int* v = directions + 3 * d;
+        if (v[0] == 0 && v[1] == 0 && v[2] == 0) return fail(nullptr, SAL_ERR_INVALID_ARG, "a direction is zero");
+        for (int sgn = -radius; sgn <= radius; ++sgn) {
+            if (sgn == 0) continue;
+            long long r2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const long long c = (long long)sgn * v[a];
+                if (c < -sal::kMaxHalo || c > sal::kMaxHalo)
+                    return fail(nullptr, SAL_ERR_INVALID_ARG, "a neighbour component exceeds +-8");
+                offsets[3 * q + a] = (int)c;
+                r2 += c * c;
+            }
+            gauss_w[q] = (float)std::exp(-(double)r2 / (2.0 * sigma * sigma));
+            dir_id[q] = d;
+            ++q;
+        }
+    }
+    *n_offsets = q;
+    g_create_error.clear();
+    return SAL_OK;
+}
+
+sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** out) {
     g_create_error.clear();
     if (!out) return fail(nullptr, SAL_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!p) return fail(nullptr, SAL_ERR_INVALID_ARG, "params is NULL");
+    if (!p_in) return fail(nullptr, SAL_ERR_INVALID_ARG, "params is NULL");
+    // n_offsets = 0: the window of Eq. 3 / Fig. 4 is built here from the direction fields
+    sal_params pw = *p_in;
+    int w_offs[3 * sal::kMaxOffsets], w_dir[sal::kMaxOffsets];
+    float w_g[sal::kMaxOffsets];
+    std::vector<float> w_alpha;
+    if (p_in->n_offsets == 0) {
+        const sal_status ws = sal_directional_window(p_in->n_directions, p_in->directions, p_in->radius,
+                                                     p_in->sigma, sal::kMaxOffsets, &pw.n_offsets, w_offs, w_g,
+                                                     w_dir);
+        if (ws != SAL_OK) return ws;
+        pw.offsets = w_offs;
+        pw.gauss_w = w_g;
+        pw.dir_id = w_dir;
+        pw.n_dirs = p_in->n_directions == 0 && p_in->directions == nullptr ? 3 : p_in->n_directions;
+        if (!p_in->alpha) {
+            w_alpha.assign(pw.n_dirs, 1.0f);
+            pw.alpha = w_alpha.data();
+        }
+    }
+    const sal_params* p = &pw;
     if (T < 1 || X < 1 || Y < 1) return fail(nullptr, SAL_ERR_INVALID_ARG, "T, X, Y must be >= 1");
     if (T > 65535 || X > 65535) return fail(nullptr, SAL_ERR_UNSUPPORTED, "T and X must be <= 65535");
     if (p->n < 2 || (p->n & 1) || p->n > sal::kMaxN)
@@ -353,6 +424,15 @@ sal_status sal_destroy(sal_handle* h) {
 sal_status sal_workspace_size(const sal_handle* h, size_t* bytes) {
     if (!h || !bytes) return SAL_ERR_INVALID_ARG;
     *bytes = h->bytes;
+    return SAL_OK;
+}
+
+sal_status sal_check_bounded_wait(sal_handle* h, unsigned tries, void* stream) {
+    sal_status st = check_handle(h);
+    if (st != SAL_OK) return st;
+    if (tries < 1 || tries > (1u << 20)) return fail(h, SAL_ERR_INVALID_ARG, "tries must be in [1, 2^20]");
+    cudaError_t e = sal::wait_check_launch(h->err_dev, tries, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "wait check launch");
     return SAL_OK;
 }
 

@@ -14,7 +14,8 @@ constexpr int kMaxOffsets = 64;
 constexpr int kMaxDirs = 16;
 constexpr int kMaxHalo = 8;      // |dt|,|dx|,|dy| bound of a center-surround offset
 constexpr int kMaxN = 32;        // largest DFT side the tables hold
-constexpr int kRedBlocks = 1216; // 152 SMs x 8: grid of the grid-stride reduction kernels
+constexpr int kRedBlocks = 1216; // fixed fan-in of the grid-stride reductions (8 blocks per SM of a
+                                 // 152-SM part); the results do not depend on the device
 
 // Center-surround window of Eq. 3, passed by value as a kernel parameter.
 struct Stencil {
@@ -161,6 +162,13 @@ cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS
 size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count, int t_step);
 cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
                               SpectraAdjointGeometry g, int t_begin, int t_count, int t_step, cudaStream_t s);
+
+// One CTA waits, through the tensor-core kernels' bounded mbarrier wait, on a barrier that nobody
+// arrives at, gives up after `tries` tries and sets the error word (failure-detection check).
+cudaError_t wait_check_launch(int* err, unsigned tries, cudaStream_t s);
+
+// SM count of the current device (cudaDevAttrMultiProcessorCount; 1 if the query fails).
+int device_sms();
 
 // Process-wide count of kernels launched by the library (sal_launch_count).
 void note_launches(int k);

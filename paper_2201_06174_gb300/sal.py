@@ -12,7 +12,6 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
-import math
 import os
 from typing import Dict, Optional, Sequence, Tuple
 
@@ -35,7 +34,8 @@ TAPER = {"rect": 0, "hann": 1}
 ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alpha", "sal_local_spectra_project",
                 "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
                 "sal_combine_noalloc", "sal_local_spectra_project_backward", "sal_center_surround_backward",
-                "sal_combine_backward", "sal_launch_count", "sal_adapt_weights")
+                "sal_combine_backward", "sal_launch_count", "sal_adapt_weights", "sal_directional_window",
+                "sal_check_bounded_wait", "sal_measure_mufu_rate")
 
 
 class SalError(RuntimeError):
@@ -50,7 +50,9 @@ class sal_params(ctypes.Structure):
                 ("offsets", ctypes.POINTER(ctypes.c_int)), ("gauss_w", ctypes.POINTER(ctypes.c_float)),
                 ("dir_id", ctypes.POINTER(ctypes.c_int)), ("n_dirs", ctypes.c_int),
                 ("alpha", ctypes.POINTER(ctypes.c_float)), ("prec", ctypes.c_int),
-                ("ls_delta", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("ls_delta", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("n_directions", ctypes.c_int), ("directions", ctypes.POINTER(ctypes.c_int)),
+                ("radius", ctypes.c_int), ("sigma", ctypes.c_double)]
 
 
 class sal_adapt_params(ctypes.Structure):
@@ -90,6 +92,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_combine_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.sal_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
     L.sal_adapt_weights.argtypes = [vp, vp, vp, ctypes.POINTER(sal_adapt_params), vp, vp, vp]
+    ip, fp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    L.sal_directional_window.argtypes = [i, ip, i, ctypes.c_double, i, ip, ip, fp, ip]
+    L.sal_check_bounded_wait.argtypes = [vp, ctypes.c_uint, vp]
+    L.sal_measure_mufu_rate.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -111,18 +117,21 @@ def _check(status: int, handle=None):
 
 def directional_window(directions: Sequence[Sequence[int]] = ((1, 0, 0), (0, 1, 0), (1, 1, 0)), R: int = 3,
                        sigma: float = 1.5):
-    """Neighbour offsets s*d for s in +-1..+-R along each direction d, their Gaussian factors
-    exp(-|o|^2 / (2 sigma^2)) and direction ids."""
-    offs, g, did = [], [], []
-    for di, d in enumerate(directions):
-        for s in range(-R, R + 1):
-            if s == 0:
-                continue
-            o = [s * int(c) for c in d]
-            offs.append(o)
-            g.append(math.exp(-float(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) / (2.0 * sigma * sigma)))
-            did.append(di)
-    return np.asarray(offs, np.int32), np.asarray(g, np.float32), np.asarray(did, np.int32)
+    """The library's directional window (sal_directional_window): neighbour offsets s*d for s in
+    +-1..+-R along each direction d, their Gaussian factors and direction ids."""
+    L = load()
+    d = np.ascontiguousarray(directions, np.int32).reshape(-1, 3)
+    cap = 64
+    offs = np.zeros((cap, 3), np.int32)
+    g = np.zeros(cap, np.float32)
+    did = np.zeros(cap, np.int32)
+    q = ctypes.c_int()
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(L.sal_directional_window(len(d), d.ctypes.data_as(ip), int(R), float(sigma), cap, ctypes.byref(q),
+                                    offs.ctypes.data_as(ip), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    did.ctypes.data_as(ip)), None)
+    Q = q.value
+    return offs[:Q].copy(), g[:Q].copy(), did[:Q].copy()
 
 
 @dataclasses.dataclass
@@ -143,26 +152,41 @@ class Params:
     gauss_w: Optional[np.ndarray] = None
     dir_id: Optional[np.ndarray] = None
 
-    def window(self):
+    def n_dirs(self) -> int:
         if self.offsets is not None:
-            return (np.ascontiguousarray(self.offsets, np.int32).reshape(-1, 3),
-                    np.ascontiguousarray(self.gauss_w, np.float32), np.ascontiguousarray(self.dir_id, np.int32))
-        return directional_window(self.directions, self.R, self.sigma)
+            did = np.asarray(self.dir_id)
+            return int(did.max()) + 1 if did.size else 0
+        return len(self.directions)
 
 
 def sal_create(params: Params, shape: Sequence[int]):
-    """Creates a handle on the current CUDA device and returns it."""
+    """Creates a handle on the current CUDA device and returns it.  Without an explicit window the
+    library builds the directional window from params.directions, R and sigma."""
     L = load()
-    offs, g, did = params.window()
-    ndirs = int(did.max()) + 1 if len(did) else 0
-    alpha = np.ones(ndirs, np.float32) if params.alpha is None else np.ascontiguousarray(params.alpha, np.float32)
+    ip, fp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    keep = []
+    alpha = None if params.alpha is None else np.ascontiguousarray(params.alpha, np.float32)
     p = sal_params(n=params.n, stride=params.stride, taper=TAPER[params.taper], boundary=BOUNDARY[params.boundary],
-                   feature=FEATURE[params.feature],
-                   n_offsets=len(g), offsets=offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                   gauss_w=g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                   dir_id=did.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n_dirs=len(alpha),
-                   alpha=alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), prec=PRECISION[params.prec],
-                   ls_delta=params.ls_delta, hbm_budget_bytes=params.hbm_budget_bytes)
+                   feature=FEATURE[params.feature], prec=PRECISION[params.prec], ls_delta=params.ls_delta,
+                   hbm_budget_bytes=params.hbm_budget_bytes)
+    if params.offsets is not None:
+        offs = np.ascontiguousarray(params.offsets, np.int32).reshape(-1, 3)
+        g = np.ascontiguousarray(params.gauss_w, np.float32)
+        did = np.ascontiguousarray(params.dir_id, np.int32)
+        if alpha is None:
+            alpha = np.ones(params.n_dirs(), np.float32)
+        keep += [offs, g, did]
+        p.n_offsets, p.offsets, p.gauss_w, p.dir_id = len(g), offs.ctypes.data_as(ip), g.ctypes.data_as(fp), \
+            did.ctypes.data_as(ip)
+        p.n_dirs = len(alpha)
+    else:
+        d = np.ascontiguousarray(params.directions, np.int32).reshape(-1, 3)
+        keep.append(d)
+        p.n_offsets, p.n_directions, p.directions = 0, len(d), d.ctypes.data_as(ip)
+        p.radius, p.sigma = int(params.R), float(params.sigma)
+    if alpha is not None:
+        keep.append(alpha)
+        p.alpha = alpha.ctypes.data_as(fp)
     h = ctypes.c_void_p()
     T, X, Y = (int(s) for s in shape)
     _check(L.sal_create(ctypes.byref(p), T, X, Y, ctypes.byref(h)), None)
@@ -219,10 +243,26 @@ def sal_combine_backward(h, S3, W, gS, gS3, gW=None, stream=None):
 
 
 def sal_combine_noalloc(S3, D, W_in, W_out, S, ls_delta: float = 1e-6, stream=None):
-    """Allocation-free combination (no handle, no device allocation); S3 is [3][T][X][Y]."""
-    T, X, Y = (int(v) for v in S3.shape[1:])
-    _check(load().sal_combine_noalloc(T, X, Y, _ptr(S3), _ptr(D), _ptr(W_in), float(ls_delta), _ptr(W_out), _ptr(S),
-                                      _stream(stream)), None)
+    """Allocation-free combination (no handle, no device allocation); S3 is [3][T][X][Y].  Runs on S3's
+    device (made current for the call); every tensor must be float32, contiguous and on that device."""
+    import torch
+    if S3.dim() != 4 or S3.shape[0] != 3:
+        raise SalError(SAL_ERR_INVALID_ARG, "S3 must be [3][T][X][Y]")
+    shape = tuple(S3.shape[1:])
+    want = {"S3": (S3, (3,) + shape), "S": (S, shape), "D": (D, shape), "W_in": (W_in, (3,)), "W_out": (W_out, (3,))}
+    for name, (t, shp) in want.items():
+        if t is None:
+            if name in ("S3", "S"):
+                raise SalError(SAL_ERR_INVALID_ARG, f"{name} must be given")
+            continue
+        if t.device != S3.device or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise SalError(SAL_ERR_INVALID_ARG, f"{name} must be a contiguous float32 tensor of shape {shp} on "
+                                                f"{S3.device}")
+    T, X, Y = (int(v) for v in shape)
+    with torch.cuda.device(S3.device):
+        st = stream if stream is not None else torch.cuda.current_stream(S3.device)
+        _check(load().sal_combine_noalloc(T, X, Y, _ptr(S3), _ptr(D), _ptr(W_in), float(ls_delta), _ptr(W_out),
+                                          _ptr(S), _stream(st)), None)
 
 
 def sal_adapt_weights(h, S3, D, W_out, method: str = "nlms", sections: int = 0, mu: float = 0.5, eps: float = 1e-8,
@@ -232,6 +272,20 @@ def sal_adapt_weights(h, S3, D, W_out, method: str = "nlms", sections: int = 0, 
     p = sal_adapt_params(ADAPT_METHODS[method], float(mu), float(eps), float(lam), float(delta), int(sections))
     _check(load().sal_adapt_weights(h, _ptr(S3), _ptr(D), ctypes.byref(p), _ptr(W_out), _ptr(err2), _stream(stream)),
            h)
+
+
+def sal_check_bounded_wait(h, tries: int = 1000, stream=None):
+    """Makes one bounded mbarrier wait give up on purpose (failure-detection check): the next call on
+    the handle returns SAL_ERR_TIMEOUT."""
+    _check(load().sal_check_bounded_wait(h, int(tries), _stream(stream)), h)
+
+
+def sal_measure_mufu_rate(op: str = "sqrt"):
+    """Measured MUFU issue rate of the current device: (operations per second, SM count)."""
+    r = ctypes.c_double()
+    sms = ctypes.c_int()
+    _check(load().sal_measure_mufu_rate({"sqrt": 0, "rsqrt": 1}[op], ctypes.byref(r), ctypes.byref(sms)), None)
+    return float(r.value), int(sms.value)
 
 
 def sal_launch_count() -> int:
@@ -320,8 +374,7 @@ class Saliency:
         import torch
         gV = self._empty()
         gW = torch.empty(3, dtype=torch.float32, device=self.device)
-        nd = len(self.params.window()[2]) and int(self.params.window()[2].max()) + 1
-        galpha = torch.empty(nd, dtype=torch.float32, device=self.device)
+        galpha = torch.empty(self.params.n_dirs(), dtype=torch.float32, device=self.device)
         sal_saliency_backward(self.h, self._in(V), self._in(W), self._in(gS), gV, gW, galpha)
         return gV, gW, galpha
 

@@ -171,12 +171,11 @@ def _fault_offsets(spec: VolumeSpec):
     return [(f.normal(), np.asarray(f.point, dtype=np.float64), f.throw) for f in spec.faults]
 
 
-def make_volume(spec: VolumeSpec, with_mask: bool = True):
-    """Returns (V, D): V float32 [T][X][Y]; D float32 {0,1} template mask (or None).
-
-    D is 1 within one sample of any fault plane or on a salt shell.
-    """
+def _chunk(spec: VolumeSpec, c0: int, with_mask: bool):
+    """The noise-free volume (and mask) of the X slab [c0, c0 + CHUNK_X): every random draw of a slab
+    comes from its own generator, so slabs can be made in any order or in parallel."""
     T, X, Y = spec.shape
+    c1 = min(X, c0 + CHUNK_X)
     rng = np.random.default_rng(spec.seed)
     pad = RICKER_HALF_TAPS
     max_shift = int(math.ceil(spec.fold_amp + sum(f.throw for f in spec.faults))) + 2
@@ -185,75 +184,106 @@ def make_volume(spec: VolumeSpec, with_mask: bool = True):
     w = ricker()
     faults = _fault_offsets(spec)
     shell_thick = [1.0 / min(s.semi_axes) for s in spec.salts]
-
-    clean = np.empty((T, X, Y), dtype=np.float32)
-    mask = np.zeros((T, X, Y), dtype=np.float32) if with_mask else None
     t_ext = np.arange(-pad, T + pad, dtype=np.float64)[:, None, None]
     y_idx = np.arange(Y, dtype=np.float64)[None, None, :]
-    for c0 in range(0, X, CHUNK_X):
-        c1 = min(X, c0 + CHUNK_X)
-        crng = np.random.default_rng([spec.seed, 7, c0])
-        x_idx = np.arange(c0, c1, dtype=np.float64)[None, :, None]
-        tau = np.broadcast_to(t_ext, (T + 2 * pad, c1 - c0, Y)).copy()
-        if spec.fold_amp:
-            k = 2.0 * math.pi / spec.fold_wavelength
-            tau -= spec.fold_amp * np.sin(k * x_idx) * np.sin(k * y_idx)
-        for nrm, p0, throw in faults:
-            d = (nrm[0] * (t_ext - p0[0]) + nrm[1] * (x_idx - p0[1]) + nrm[2] * (y_idx - p0[2]))
-            tau -= throw * (d > 0.0)
-        # linear interpolation of the 1-D reflectivity at the deformed depth
-        pos = tau + base
-        i0 = np.floor(pos).astype(np.int64)
-        fr = pos - i0
-        R = (1.0 - fr) * r1d[i0] + fr * r1d[i0 + 1]
+    crng = np.random.default_rng([spec.seed, 7, c0])
+    x_idx = np.arange(c0, c1, dtype=np.float64)[None, :, None]
+    tau = np.broadcast_to(t_ext, (T + 2 * pad, c1 - c0, Y)).copy()
+    if spec.fold_amp:
+        k = 2.0 * math.pi / spec.fold_wavelength
+        tau -= spec.fold_amp * np.sin(k * x_idx) * np.sin(k * y_idx)
+    for nrm, p0, throw in faults:
+        d = (nrm[0] * (t_ext - p0[0]) + nrm[1] * (x_idx - p0[1]) + nrm[2] * (y_idx - p0[2]))
+        tau -= throw * (d > 0.0)
+    # linear interpolation of the 1-D reflectivity at the deformed depth
+    pos = tau + base
+    i0 = np.floor(pos).astype(np.int64)
+    fr = pos - i0
+    R = (1.0 - fr) * r1d[i0] + fr * r1d[i0 + 1]
+    for s, thick in zip(spec.salts, shell_thick):
+        rho = np.sqrt(((t_ext - s.center[0]) / s.semi_axes[0]) ** 2
+                      + ((x_idx - s.center[1]) / s.semi_axes[1]) ** 2
+                      + ((y_idx - s.center[2]) / s.semi_axes[2]) ** 2)
+        inside = rho < 1.0
+        R = np.where(inside, spec.salt_fill_sigma * crng.standard_normal(R.shape), R)
+        R = np.where(np.abs(rho - 1.0) <= thick, spec.salt_shell_value, R)
+    for ch in spec.channels:
+        xc = ch.x0 + ch.amp * np.sin(2.0 * math.pi * y_idx / ch.wavelength)
+        inband = np.abs(x_idx - xc) <= ch.width / 2
+        top = np.round(ch.t_top)
+        R = np.where(inband & (t_ext == top), -1.5, R)
+        R = np.where(inband & (t_ext > top) & (t_ext < top + ch.thick), 0.0, R)
+        R = np.where(inband & (t_ext == top + ch.thick), 1.5, R)
+    # convolve along t with the Ricker wavelet ('valid' part = T samples)
+    out = np.zeros((T, c1 - c0, Y), dtype=np.float64)
+    for k in range(2 * pad + 1):
+        out += w[k] * R[k:k + T]
+    clean = out.astype(np.float32)
+    m = None
+    if with_mask:
+        tt = t_ext[pad:pad + T]
+        m = np.zeros((T, c1 - c0, Y), dtype=bool)
+        for nrm, p0, _ in faults:
+            d = (nrm[0] * (tt - p0[0]) + nrm[1] * (x_idx - p0[1]) + nrm[2] * (y_idx - p0[2]))
+            m |= np.abs(d) <= 1.0
         for s, thick in zip(spec.salts, shell_thick):
-            rho = np.sqrt(((t_ext - s.center[0]) / s.semi_axes[0]) ** 2
+            rho = np.sqrt(((tt - s.center[0]) / s.semi_axes[0]) ** 2
                           + ((x_idx - s.center[1]) / s.semi_axes[1]) ** 2
                           + ((y_idx - s.center[2]) / s.semi_axes[2]) ** 2)
-            inside = rho < 1.0
-            R = np.where(inside, spec.salt_fill_sigma * crng.standard_normal(R.shape), R)
-            R = np.where(np.abs(rho - 1.0) <= thick, spec.salt_shell_value, R)
-        for ch in spec.channels:
-            xc = ch.x0 + ch.amp * np.sin(2.0 * math.pi * y_idx / ch.wavelength)
-            inband = np.abs(x_idx - xc) <= ch.width / 2
-            top = np.round(ch.t_top)
-            R = np.where(inband & (t_ext == top), -1.5, R)
-            R = np.where(inband & (t_ext > top) & (t_ext < top + ch.thick), 0.0, R)
-            R = np.where(inband & (t_ext == top + ch.thick), 1.5, R)
-        # convolve along t with the Ricker wavelet ('valid' part = T samples)
-        out = np.zeros((T, c1 - c0, Y), dtype=np.float64)
-        for k in range(2 * pad + 1):
-            out += w[k] * R[k:k + T]
-        clean[:, c0:c1, :] = out.astype(np.float32)
-        if with_mask:
-            tt = t_ext[pad:pad + T]
-            m = np.zeros((T, c1 - c0, Y), dtype=bool)
-            for nrm, p0, _ in faults:
-                d = (nrm[0] * (tt - p0[0]) + nrm[1] * (x_idx - p0[1]) + nrm[2] * (y_idx - p0[2]))
-                m |= np.abs(d) <= 1.0
-            for s, thick in zip(spec.salts, shell_thick):
-                rho = np.sqrt(((tt - s.center[0]) / s.semi_axes[0]) ** 2
-                              + ((x_idx - s.center[1]) / s.semi_axes[1]) ** 2
-                              + ((y_idx - s.center[2]) / s.semi_axes[2]) ** 2)
-                m |= np.abs(rho - 1.0) <= thick
-            mask[:, c0:c1, :] = m
-    rms = float(np.sqrt(np.mean(clean.astype(np.float64) ** 2)))
+            m |= np.abs(rho - 1.0) <= thick
+        m = m.astype(np.float32)
+    return c0, clean, m, float(np.sum(clean.astype(np.float64) ** 2))
+
+
+def make_volume(spec: VolumeSpec, with_mask: bool = True, workers: int = 0):
+    """Returns (V, D): V float32 [T][X][Y]; D float32 {0,1} template mask (or None).
+
+    D is 1 within one sample of any fault plane or on a salt shell.  workers > 1 makes the X slabs in
+    that many spawned processes (start them before any CUDA work in the caller); the result is the
+    same bit for bit, since every slab has its own generators and the rms is summed in slab order.
+    """
+    T, X, Y = spec.shape
+    clean = np.empty((T, X, Y), dtype=np.float32)
+    mask = np.zeros((T, X, Y), dtype=np.float32) if with_mask else None
+    starts = list(range(0, X, CHUNK_X))
+    sumsq = {}
+    if workers > 1 and len(starts) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            results = ex.map(_chunk, [spec] * len(starts), starts, [with_mask] * len(starts))
+            for c0, cl, m, ss in results:
+                clean[:, c0:c0 + cl.shape[1], :] = cl
+                if with_mask:
+                    mask[:, c0:c0 + cl.shape[1], :] = m
+                sumsq[c0] = ss
+    else:
+        for c0 in starts:
+            _, cl, m, ss = _chunk(spec, c0, with_mask)
+            clean[:, c0:c0 + cl.shape[1], :] = cl
+            if with_mask:
+                mask[:, c0:c0 + cl.shape[1], :] = m
+            sumsq[c0] = ss
+    total = 0.0
+    for c0 in starts:
+        total += sumsq[c0]
+    rms = math.sqrt(total / clean.size)
     if spec.snr_db is not None:
         sigma = rms * 10.0 ** (-spec.snr_db / 20.0)
     else:
         sigma = (spec.noise_rel or 0.0) * rms
     V = clean
     if sigma > 0:
-        for c0 in range(0, X, CHUNK_X):
+        for c0 in starts:
             c1 = min(X, c0 + CHUNK_X)
             nrng = np.random.default_rng([spec.seed, 11, c0])
             V[:, c0:c1, :] += (sigma * nrng.standard_normal((T, c1 - c0, Y))).astype(np.float32)
     return V, mask
 
 
-def volume(name_or_spec, with_mask: bool = True):
+def volume(name_or_spec, with_mask: bool = True, workers: int = 0):
     spec = spec_for(name_or_spec) if isinstance(name_or_spec, str) else name_or_spec
-    return make_volume(spec, with_mask=with_mask)
+    return make_volume(spec, with_mask=with_mask, workers=workers)
 
 
 def random_volume(shape: Sequence[int], seed: int, dist: str = "normal") -> np.ndarray:

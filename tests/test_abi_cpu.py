@@ -73,6 +73,7 @@ def test_null_handle_calls():
                         ("sal_saliency", 9), ("sal_saliency_backward", 8), ("sal_local_spectra_project_backward", 5),
                         ("sal_center_surround_backward", 6), ("sal_combine_backward", 7)]:
         assert getattr(L, name)(*([None] * nargs)) == salmod.SAL_ERR_INVALID_ARG
+    assert L.sal_check_bounded_wait(None, 1, None) == salmod.SAL_ERR_INVALID_ARG
     assert L.sal_destroy(None) == salmod.SAL_OK
     assert L.sal_workspace_size(None, None) == salmod.SAL_ERR_INVALID_ARG
 
@@ -82,5 +83,48 @@ def test_product_window_matches_oracle_window():
     import oracle
     offs, g, did = sal.directional_window()
     o2, g2, d2, w2 = oracle.dcs_stencil()
+    assert np.array_equal(offs, o2) and np.array_equal(did, d2)
+    assert np.allclose(g, g2, rtol=1e-7)
+
+
+def test_library_window_argument_checks():
+    """sal_directional_window (host only) rejects bad radii, sigmas, zero directions, neighbours beyond
+    +-8 and windows larger than the capacity."""
+    L = sal.load()
+    ip = ctypes.POINTER(ctypes.c_int)
+    offs = np.zeros((64, 3), np.int32)
+    g = np.zeros(64, np.float32)
+    did = np.zeros(64, np.int32)
+    q = ctypes.c_int()
+
+    def call(dirs, R, sigma, cap=64):
+        d = np.ascontiguousarray(dirs, np.int32).reshape(-1, 3)
+        return L.sal_directional_window(len(d), d.ctypes.data_as(ip), R, sigma, cap, ctypes.byref(q),
+                                        offs.ctypes.data_as(ip), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        did.ctypes.data_as(ip))
+    assert call([[1, 0, 0]], 3, 1.5) == salmod.SAL_OK and q.value == 6
+    assert call([[1, 0, 0]], 0, 1.5) == salmod.SAL_ERR_INVALID_ARG
+    assert call([[1, 0, 0]], 2, 0.0) == salmod.SAL_ERR_INVALID_ARG
+    assert call([[1, 0, 0]], 2, float("nan")) == salmod.SAL_ERR_INVALID_ARG
+    assert call([[0, 0, 0]], 2, 1.0) == salmod.SAL_ERR_INVALID_ARG
+    assert call([[3, 0, 0]], 3, 1.0) == salmod.SAL_ERR_INVALID_ARG        # 9 > 8
+    assert call([[1, 0, 0]] * 11, 3, 1.0) == salmod.SAL_ERR_INVALID_ARG   # 66 > 64
+    assert call([[1, 0, 0]], 3, 1.5, cap=5) == salmod.SAL_ERR_INVALID_ARG
+    # the default (NULL directions) is the three directions of Fig. 4
+    assert L.sal_directional_window(0, None, 3, 1.5, 64, ctypes.byref(q), offs.ctypes.data_as(ip),
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), did.ctypes.data_as(ip)) == 0
+    import oracle
+    o2, g2, d2, _ = oracle.dcs_stencil()
+    assert q.value == len(g2) and np.array_equal(offs[:q.value], o2) and np.array_equal(did[:q.value], d2)
+    assert np.allclose(g[:q.value], g2, rtol=1e-7)
+
+
+@pytest.mark.parametrize("dirs,R,sigma", [(((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)), 2, 0.8),
+                                         (((0, 1, 0), (0, 0, 1), (0, 1, 1)), 3, 1.5),
+                                         (((1, -1, 0), (2, 0, 1)), 4, 2.5)])
+def test_library_window_matches_oracle_window_any_directions(dirs, R, sigma):
+    import oracle
+    offs, g, did = sal.directional_window(dirs, R, sigma)
+    o2, g2, d2, _ = oracle.dcs_stencil(dirs, R, sigma)
     assert np.array_equal(offs, o2) and np.array_equal(did, d2)
     assert np.allclose(g, g2, rtol=1e-7)

@@ -31,7 +31,7 @@ def test_fp32_roofline_fraction():
     rl = bench.roofline("k", "fp32", n, nvox, ms, 1, 123)
     achieved = bench.k1_flops_per_voxel(n) * nvox / (ms / 1e3) / 1e12
     assert rl["achieved"] == pytest.approx(achieved)
-    assert rl["frac"] == pytest.approx(achieved / bench.FP32_PEAK_TFLOPS)
+    assert rl["frac"] == pytest.approx(achieved / bench.PEAKS["fp32_tflops"])
     assert rl["unit"] == "TFLOP/s" and rl["traffic"] == 123 and rl["bound"] == "alu"
     sl = bench.roofline("k", "fp32", n, nvox, ms, 1, None, flops_per_voxel=bench.k1_flops_per_voxel_sliding(n))
     assert sl["achieved"] == pytest.approx(achieved * bench.k1_flops_per_voxel_sliding(n) / bench.k1_flops_per_voxel(n))
@@ -41,18 +41,29 @@ def test_tensor_form_roofline_is_the_mufu_epilogue():
     n, nvox, ms = 16, 128 ** 3, 2.7
     rl = bench.roofline("k", "bf16", n, nvox, ms, 1, None)
     bins = bench.bins_per_voxel(n) * nvox / (ms / 1e3) / 1e12
-    assert rl["achieved"] == pytest.approx(bins) and rl["peak"] == bench.MUFU_PEAK_TOPS
-    assert rl["frac"] == pytest.approx(bins / bench.MUFU_PEAK_TOPS)
+    nominal = 16 * bench.PEAKS["sms"] * bench.PEAKS["sm_ghz"] * 1e9 / 1e12   # before a measured rate is set
+    assert rl["achieved"] == pytest.approx(bins) and rl["peak"] == pytest.approx(nominal)
+    assert rl["frac"] == pytest.approx(bins / nominal)
     assert "tensor" in rl and rl["tensor"]["frac"] == pytest.approx(rl["tensor"]["achieved_tflops"] /
                                                                      rl["tensor"]["peak_tflops"])
     en = bench.roofline("k", "bf16", n, nvox, ms, 1, None, feature="energy")
-    assert en["peak"] == bench.FMA_OPS_PEAK and en["achieved"] == pytest.approx(4 * bins)
+    assert en["peak"] == bench.PEAKS["fma_tops"] and en["achieved"] == pytest.approx(4 * bins)
 
 
-def test_peaks_derived_from_unit_counts():
-    assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
-    assert bench.MUFU_PEAK_TOPS == pytest.approx(16 * 152 * 2.070e9 / 1e12)
-    assert bench.FMA_OPS_PEAK == pytest.approx(bench.FP32_PEAK_TFLOPS / 2)
+def test_peaks_derived_from_unit_counts_and_the_measured_mufu_rate(monkeypatch):
+    """The FP32 peak follows the device's SM count and max clock; the MUFU peak is the measured rate."""
+    monkeypatch.setattr(bench, "PEAKS", dict(bench.PEAKS, mufu={}))
+
+    class FakeSal:
+        @staticmethod
+        def sal_measure_mufu_rate(op):
+            return (5.5e12 if op == "sqrt" else 6.0e12), 150
+    bench.set_alu_peaks(FakeSal, 150, 2000.0)
+    assert bench.PEAKS["fp32_tflops"] == pytest.approx(150 * 128 * 2 * 2.0e9 / 1e12)
+    assert bench.PEAKS["fma_tops"] == pytest.approx(bench.PEAKS["fp32_tflops"] / 2)
+    assert bench.PEAKS["mufu"] == {"sqrt": pytest.approx(5.5), "rsqrt": pytest.approx(6.0)}
+    rl = bench.roofline("k", "bf16", 16, 128 ** 3, 2.0, 1, None, mufu_op="rsqrt")
+    assert rl["peak"] == pytest.approx(6.0) and "measured" in rl["peak_note"]
 
 
 def test_reference_arm_on_a_section_counts_its_plane_and_uses_its_window(monkeypatch, capsys):
