@@ -6,7 +6,8 @@
 //     brick by brick, never stored;
 //   Gamma (epilogue from tensor memory): Gamma[k] = (sum_m gE_m wt_m(k)) F[k]/|F[k]| -- the gradient of
 //     L = sum gE . E with respect to (Re F, Im F) -- with the zero subgradient where |F| <= 2^-19 of the
-//     window's L1 norm (the energy reading: Gamma[k] = 2 (sum_m gE_m wt_m(k)) F[k], wt holding r_m^2);
+//     window's L1 norm (FP16 operands put the direction of smaller bins at the level of their rounding;
+//     the 16-bit forms answer to the 1e-2 bar) (the energy reading: Gamma[k] = 2 (sum_m gE_m wt_m(k)) F[k], wt holding r_m^2);
 //     rounded to FP16 (scaled by sigma = n^3 / (8 max|gE|)) into the operand [(x0, k_x)][(re | im, k_y)]
 //     of one output;
 //   adjoint of stage 3 (y): Gamma of bins k and n - k folded into pair coefficients (A = G[k] + G[n-k],
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                       int T, int X, int Y, int bnd, int t_begin, int t_step,
                       const unsigned char* __restrict__ tables,
-                      const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
+                      const __grid_constant__ Tw<N> tw, int* __restrict__ err,
+                      const __grid_constant__ CUtensorMap tmap, int smode) {
     using G = BtGeo<N>;
     constexpr int H = G::H, P = G::P, XH = G::XH, YH = G::YH, YP = G::YP;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -152,7 +154,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     // mbarriers (arrival counts): [0], [1] forward buffer full (MMA commit); [2], [3] forward buffer read
     // (16 warps); [4] stage-3 A written (16); [5] stage-2 B tiles written (16); [6], [7] Gamma set written
     // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete, B_c | B_s read
-    // (commit); [11] unused; [12] constant operands landed (bulk copy); [13] the brick's gV block complete
+    // (commit); [11] the brick's TMA copies landed; [12] constant operands landed (bulk copy); [13] the
+    // brick's gV block complete
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 112);
     int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 116);
@@ -169,12 +172,16 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
     if (tid == 0) {
         const uint32_t counts[14] = {1, 1, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, 1,
-                                     kConsumers, 1, kConsumers, 1, 1};
+                                     kConsumers, 1, 1, 1, 1};
         for (int b = 0; b < 14; ++b) tc::mbar_init(tc::smem_u32(&s_mbar[b]), counts[b]);
         *s_fail = 0;
         tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[12]), (uint32_t)G::TAB5_B);
         tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB5_B, tc::smem_u32(&s_mbar[12]));
     }
+    // an interior brick: its copies go to the TMA unit first (warp 0), the rest of the set-up overlaps them
+    const bool tma = tcs::tma_brick<N>(smode, T, X, Y, t0, xb, yb);
+    if (tma && warp == 0)
+        tcs::stage_issue<N>(smode, &tmap, V, X, Y, t0, xb, yb, smem + G::STG_OFF, tc::smem_u32(&s_mbar[11]), lane);
     for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < (int)(G::A1_B / 16); i += kThreads)       // K rows 2..15 of A_t stay zero
@@ -190,7 +197,10 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     if (lane == 0) s_red[32 + warp] = gmax;
-    const float scale = tcs::stage_brick<N, kFmt, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid);
+    __syncthreads();   // mbarriers initialised before anyone waits on them
+    const float scale = tcs::stage_brick<N, kFmt, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid, tma,
+                                                            smem + G::STG_OFF, smode, tc::smem_u32(&s_mbar[11]), err,
+                                                            s_fail);
     // the direction F/|F| does not depend on the brick scale; the energy's Gamma = 2 rho F does (F of the
     // unscaled brick = scale x F of the staged one): that factor is applied to the block at the end
     float bgmax = 0.f;
@@ -587,12 +597,14 @@ cudaError_t launch_n(const TwiddleTable& t, const void* tables, const float* V, 
     using G = BtGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, t_count);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
+    CUtensorMap tmap;
+    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, false);
     if (feat == 1)
         k5_spectra_adjoint_tc<N, true><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, t_step,
-                                                                       tab, f32::make_tw<N>(t), err);
+                                                                       tab, f32::make_tw<N>(t), err, tmap, smode);
     else
         k5_spectra_adjoint_tc<N, false><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, t_step,
-                                                                        tab, f32::make_tw<N>(t), err);
+                                                                        tab, f32::make_tw<N>(t), err, tmap, smode);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -31,7 +31,7 @@ template <int N> struct TcGeo : tcs::FwdGeo<N> {
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + F::TAB_B;
     static constexpr size_t OFF_MISC = OFF_A3 + 2 * F::A3_B;
-    static constexpr size_t SMEM = OFF_MISC + 64 + 16 * 4;
+    static constexpr size_t SMEM = OFF_MISC + 80 + 16 * 4;
     static_assert(F::NB1 * 16 <= (int)kTmemCols, "tensor memory");
     static_assert(F::PASSES * F::OPC * 2 == 8, "accumulator slots");
     static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
@@ -46,7 +46,8 @@ __global__ void k1_tc_tables(const __grid_constant__ Tw<N> tw, unsigned char* __
 template <int N, int FMT, bool EN>
 __global__ void __launch_bounds__(kThreads, 2)
 k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, int Y, int bnd, int stride,
-              const unsigned char* __restrict__ tables, int* __restrict__ err) {
+              const unsigned char* __restrict__ tables, int* __restrict__ err,
+              const __grid_constant__ CUtensorMap tmap, int smode) {
     using G = TcGeo<N>;
     constexpr int H = G::H, P = G::P;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -57,11 +58,12 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;       // stage-3 A, imaginary part
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);   // [k_t][|k_x|][|k_y|][3]
     // mbarriers: [0], [1] buffer full (MMA commit); [2], [3] buffer empty (one arrival per consumer warp);
-    // [4] stage-3 A written, [5] stage-2 B tiles written (one arrival per consumer warp); [6] constants
+    // [4] stage-3 A written, [5] stage-2 B tiles written (one arrival per consumer warp); [6] constants;
+    // [7] the brick's TMA copies landed
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 56);
-    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 60);
-    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 64);   // [warps]
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 64);
+    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 68);
+    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 80);   // [warps]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int yb = blockIdx.x * kBY;
@@ -78,16 +80,24 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
         tc::mbar_init(tc::smem_u32(&s_mbar[4]), kConsumers);
         tc::mbar_init(tc::smem_u32(&s_mbar[5]), kConsumers);
         tc::mbar_init(tc::smem_u32(&s_mbar[6]), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[7]), 1);
         *s_fail = 0;
         tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[6]), (uint32_t)G::TAB_B);
         tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB_B, tc::smem_u32(&s_mbar[6]));
     }
+    // an interior brick: its copies go to the TMA unit first (warp 0), the rest of the set-up overlaps them
+    const bool tma = tcs::tma_brick<N>(smode, T, X, Y, t0, xb, yb);
+    if (tma && warp == 0)
+        tcs::stage_issue<N>(smode, &tmap, V, X, Y, t0, xb, yb, smem + G::STG_OFF, tc::smem_u32(&s_mbar[7]), lane);
     // stage-3 A rows beyond the halo (read by the last windows, multiplied by zero twiddles) stay zero
     for (int i = tid; i < (int)(2 * G::A3_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();   // mbarriers initialised before anyone waits on them
 
     // ---- the halo brick as the 16-bit stage-1 A operand ----------------------------------------------
-    const float scale = tcs::stage_brick<N, FMT, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid);
+    const float scale = tcs::stage_brick<N, FMT, kThreads>(V, T, X, Y, bnd, t0, xb, yb, s_a1, s_red, tid, tma,
+                                                           smem + G::STG_OFF, smode, tc::smem_u32(&s_mbar[7]), err,
+                                                           s_fail);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -324,10 +334,12 @@ cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X
     using G = TcGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, (T + stride - 1) / stride);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
+    CUtensorMap tmap;
+    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, true);
     if (feat == 1)
-        k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err);
+        k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err, tmap, smode);
     else
-        k1_spectra_tc<N, FMT, false><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err);
+        k1_spectra_tc<N, FMT, false><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err, tmap, smode);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -165,5 +165,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uin
         : "memory");
 }
 
+// Tiled tensor copy global -> shared of one 3-D box (TMA), completion counted on an mbarrier; no
+// multicast.  tmap: the generic address of a CUtensorMap kernel parameter (__grid_constant__); c0 is the
+// innermost coordinate (its byte offset must be a multiple of 16), dst 128-byte aligned.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst_smem, const void* tmap, int c0, int c1, int c2,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst_smem),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace sal

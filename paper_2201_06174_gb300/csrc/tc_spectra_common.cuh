@@ -19,6 +19,8 @@
 //            B3a = [c | -s], B3b = [s | c] over all k_y: the accumulator holds Re F and Im F.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -66,12 +68,27 @@ template <int N> struct FwdGeo {
     static constexpr size_t TAB_B = TAB_WT + WT_B;
     static constexpr size_t A3_B = (size_t)16 * SBO_A3;
     static constexpr int STAGE_ITEMS = 16 * NB1 * 16;   // (u, 8-position group) items of the A1 fill
+    // FP32 landing area of an interior brick's TMA copies, at the end of region 0 (the stage-1 A operand,
+    // written after every thread has read its samples, may overlap it): one tensor box [u][x][YP y], or
+    // one bulk copy per (u, x) row of RB = YP + 4 floats from the 16-byte boundary at or below its start
+    static constexpr int RB = YP + 4;
+    static constexpr size_t STG_TENSOR_B = (size_t)N * XH * YP * 4;
+    static constexpr size_t STG_ROWS_B = (size_t)N * XH * RB * 4;
+    static constexpr size_t STG_B = STG_TENSOR_B > STG_ROWS_B ? STG_TENSOR_B : STG_ROWS_B;
+    static constexpr size_t STG_OFF = (R0_B - STG_B) / 128 * 128;
     static_assert(XH <= kXHP && YH <= 32 && YP <= 32, "halo");
     static_assert(2 * H - 2 <= 16, "stage-1 columns");
     static_assert(N2 <= 128, "stage-2 accumulator");
     static_assert(PASSES * OPP == kBY && PASSES % 2 == 0, "passes");
     static_assert(TAB_B % 16 == 0 && A3_B % 16 == 0, "bulk copy alignment");
+    static_assert(STG_B <= R0_B && (RB * 4) % 16 == 0 && (YP * 4) % 16 == 0, "TMA landing area");
 };
+
+// How the interior bricks of a launch reach shared memory (bricks whose halo leaves the volume always take
+// the SIMT loads, which apply the border extension): SIMT loads; one tiled tensor copy per brick (a 3-D
+// tensor map over V, usable when a row of V is a multiple of 16 bytes); or one bulk copy per (u_t, x)
+// row of the brick (any row length).  Both copies run on the TMA unit, plain (no multicast).
+enum : int { kStageSimt = 0, kStageTensor = 1, kStageRows = 2 };
 
 template <int FMT> struct Pack;
 template <> struct Pack<1> {  // BF16
@@ -156,19 +173,103 @@ __device__ void build_fwd_tables(const Tw<N>& tw, unsigned char* out, int tid, i
     }
 }
 
+// Host: the staging mode of a launch over V [T][X][Y] and, for kStageTensor, its tensor map (3-D, dims
+// {Y, X, T}, box {YP, XH, n} floats, no swizzle, no multicast).  A tensor map needs 16-byte row strides
+// (Y a multiple of 4); other row lengths take the row copies; a V not 16-byte aligned the SIMT loads.
+// allow_rows = false: a kernel whose brick staging is not hidden by a second CTA on the SM (the adjoint)
+// takes the SIMT loads instead of the row copies, whose many small transfers cost it more than the loads.
+template <int N>
+inline int brick_stage_mode(const float* V, int T, int X, int Y, CUtensorMap* tmap, bool allow_rows) {
+    using G = FwdGeo<N>;
+    *tmap = CUtensorMap{};
+    const int rows = allow_rows ? kStageRows : kStageSimt;
+    if ((reinterpret_cast<uintptr_t>(V) & 15) != 0) return kStageSimt;
+    if ((Y & 3) != 0) return rows;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return rows;
+    const cuuint64_t dims[3] = {(cuuint64_t)Y, (cuuint64_t)X, (cuuint64_t)T};
+    const cuuint64_t strides[2] = {(cuuint64_t)Y * 4, (cuuint64_t)X * Y * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)G::YP, (cuuint32_t)G::XH, (cuuint32_t)N};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? kStageTensor : rows;
+}
+
+// Whether the brick at (t0, xb, yb) is staged by the TMA unit in mode `smode`: its halo (YP samples per
+// row) lies inside the volume; the row copies also must not read past the end of V (each reads up to
+// 3 samples beyond its row's halo).
+template <int N>
+__device__ __forceinline__ bool tma_brick(int smode, int T, int X, int Y, int t0, int xb, int yb) {
+    using G = FwdGeo<N>;
+    const int ty = yb - N / 2;
+    const bool inside = t0 - N / 2 >= 0 && t0 + N / 2 <= T && xb - N / 2 >= 0 && xb - N / 2 + G::XH <= X &&
+                        ty >= 0 && ty + G::YP <= Y;
+    if (smode == kStageTensor) return inside;
+    if (smode != kStageRows || !inside) return false;
+    const size_t last = ((size_t)(t0 + N / 2 - 1) * X + (xb - N / 2 + G::XH - 1)) * Y + ty + G::YP + 3;
+    return last < (size_t)T * X * Y;
+}
+
+// Issue of an interior brick's TMA copies into s_stage, completion counted on mbar (initialised with one
+// arrival); one warp, all lanes.  Lane 0 sets the expected byte count before any copy is issued.
+template <int N>
+__device__ void stage_issue(int smode, const CUtensorMap* tmap, const float* __restrict__ V, int X, int Y, int t0,
+                            int xb, int yb, unsigned char* s_stage, uint32_t mbar, int lane) {
+    using G = FwdGeo<N>;
+    const int ty = yb - N / 2;
+    if (lane == 0)
+        tc::mbar_arrive_expect_tx(mbar, (uint32_t)(smode == kStageTensor ? G::STG_TENSOR_B : G::STG_ROWS_B));
+    __syncwarp();
+    if (smode == kStageTensor) {
+        if (lane == 0) tc::tma_load_3d(tc::smem_u32(s_stage), tmap, ty, xb - N / 2, t0 - N / 2, mbar);
+    } else {
+        for (int r = lane; r < N * G::XH; r += 32) {
+            const int u = r / G::XH, x = r % G::XH;
+            const size_t f = ((size_t)(t0 - N / 2 + u) * X + (xb - N / 2 + x)) * Y + ty;
+            tc::bulk_g2s(tc::smem_u32(s_stage + (size_t)r * G::RB * 4), V + (f & ~(size_t)3), (uint32_t)(G::RB * 4),
+                         mbar);
+        }
+    }
+}
+
 // The halo brick as the 16-bit stage-1 A operand, scaled by 1/max|V|; returns max|V| (1 for an all-zero
 // brick).  item = (u, g): 8 positions pos = 8g .. 8g+7 (x = g / YG, y = 8 (g % YG) + i) at tap u.
-// Interior bricks (no border extension) load with 16-byte vector loads.  Contains one __syncthreads.
+// Bricks staged by the TMA unit (tma_brick; stage_issue has issued their copies) read their samples from
+// s_stage once mbar completes (a bounded wait: on timeout the error word and *s_fail are set and the
+// brick is taken as zero); the others load them from V, applying the border extension.  Contains one
+// __syncthreads.
 template <int N, int FMT, int NT>
 __device__ float stage_brick(const float* __restrict__ V, int T, int X, int Y, int bnd, int t0, int xb, int yb,
-                             unsigned char* s_a1, float* s_red, int tid) {
+                             unsigned char* s_a1, float* s_red, int tid, bool tma, const unsigned char* s_stage,
+                             int smode, uint32_t mbar, int* err, int* s_fail) {
     using G = FwdGeo<N>;
     constexpr int XH = G::XH, YH = G::YH, YG = G::YG, YP = G::YP;
     constexpr int PER = (G::STAGE_ITEMS + NT - 1) / NT;
     const int lane = tid & 31, warp = tid >> 5;
     const int ty = yb - N / 2;
+    bool landed = false;
+    if (tma) {
+        landed = tc::mbar_wait(mbar, 0, kWaitLimit);
+        if (!landed) {
+            atomicOr(err, 1);
+            atomicExch(s_fail, 1);
+        }
+    }
+    const float* stg = reinterpret_cast<const float*>(s_stage);
     const bool interior = t0 - N / 2 >= 0 && t0 + N / 2 <= T && xb - N / 2 >= 0 && xb - N / 2 + XH <= X && ty >= 0 &&
-                          ty + YP <= Y && (Y & 3) == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0;
+                          ty + YP <= Y;
     float vals[PER][8];
     float vmax = 0.f;
 #pragma unroll
@@ -179,13 +280,27 @@ __device__ float stage_brick(const float* __restrict__ V, int T, int X, int Y, i
         const bool live = item < G::STAGE_ITEMS && u < N && x < XH;
 #pragma unroll
         for (int i = 0; i < 8; ++i) vals[r][i] = 0.f;
-        if (interior) {
+        if (tma) {
+            if (live && landed) {
+                if (smode == kStageTensor) {
+                    // rows of YP floats from a 128-byte aligned base: two 16-byte reads
+                    const float4* row = reinterpret_cast<const float4*>(stg + (size_t)(u * XH + x) * YP + y8);
+                    const float4 a = row[0], b = row[1];
+                    vals[r][0] = a.x; vals[r][1] = a.y; vals[r][2] = a.z; vals[r][3] = a.w;
+                    vals[r][4] = b.x; vals[r][5] = b.y; vals[r][6] = b.z; vals[r][7] = b.w;
+                } else {
+                    const size_t f = ((size_t)(t0 - N / 2 + u) * X + (xb - N / 2 + x)) * Y + ty;
+                    const float* row = stg + (size_t)(u * XH + x) * G::RB + (f & 3);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) vals[r][i] = row[y8 + i];
+                }
+            }
+        } else if (interior) {
+            // the halo inside the volume: direct loads, no border extension
             if (live) {
                 const float* src = V + ((size_t)(t0 - N / 2 + u) * X + (xb - N / 2 + x)) * Y + ty + y8;
-                const float4 a = __ldg(reinterpret_cast<const float4*>(src));
-                const float4 b = __ldg(reinterpret_cast<const float4*>(src + 4));
-                vals[r][0] = a.x; vals[r][1] = a.y; vals[r][2] = a.z; vals[r][3] = a.w;
-                vals[r][4] = b.x; vals[r][5] = b.y; vals[r][6] = b.z; vals[r][7] = b.w;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) vals[r][i] = __ldg(src + i);
             }
         } else {
             const int gt = ext_index(t0 - N / 2 + u, T, bnd);
