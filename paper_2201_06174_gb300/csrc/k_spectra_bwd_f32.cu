@@ -11,13 +11,13 @@
 // The direction F / |F| is ill-conditioned for small |F|: FP32 computes F to about 2^-26 of the window's
 // L1 norm A_p = sum_u |h(u) Vext[p + u - n/2]| (which bounds every |F_p[k]|), so a bin with |F| near that
 // level has no usable FP32 direction.  Such bins are resolved exactly:
-//   - bins that are zero for every input, because the border extension makes the coefficient of every
+//   - bins that vanish for every input, because the border extension makes the coefficient of every
 //     source sample of one axis vanish (a mirror-symmetric window along an axis zeroes its Nyquist bin,
-//     a window folded onto few samples zeroes more), are found by integer arithmetic on the window's
-//     index map (axis_bin_vanishes) and take Gamma = 0;
-//   - every other bin with FP32 |F| <= 2^-16 A_p and a non-zero weight is recomputed as a direct FP64
-//     sum over its cube by one warp (resolve_small_bins), and takes Gamma = 0 only if |F| <= 2^-40 A_p
-//     (zero up to FP64 rounding), else its FP64 direction.
+//     a window folded onto few samples zeroes more), are found on the host by integer arithmetic on the
+//     window's index map (axis_vanish_mask) and take Gamma = 0;
+//   - every other bin with FP32 |F| <= 2^-16 A_p and a non-zero weight is recomputed by one warp as a
+//     direct sum over its cube in float-float arithmetic (pairs of FP32 values, error about 2^-46 A_p;
+//     resolve_small_bins), and takes Gamma = 0 if |F| <= 2^-36 A_p, else its float-float direction.
 // Bins above 2^-16 A_p carry an FP32 direction error of at most about 2^-10.
 // Spectra are recomputed brick by brick (the forward stages of K1), never stored.
 //
@@ -36,49 +36,105 @@ namespace {
 
 using f32::Tw;
 
-constexpr float kSmallBin = 1.0f / 65536.0f;     // FP32 |F| / A_p at or below which a bin is resolved in FP64
-constexpr double kZeroBin = 1.0 / 1099511627776.0;  // FP64 |F| / A_p at or below which F = 0 (2^-40)
+constexpr float kSmallBin = 1.0f / 65536.0f;       // FP32 |F| / A_p at or below which a bin is resolved exactly
+constexpr float kZeroBin = 1.0f / 68719476736.0f;  // float-float max(|Re F|, |Im F|) / A_p at or below which F = 0
 
-// FP64 constants of the exact recompute: cos, sin of 2 pi m / n and the taper h(u).
-template <int N> struct Exact64 {
-    double c[N], s[N], h[N];
+// Float-float constants of the exact recompute: cos, sin of 2 pi m / n and the taper h(u), each as a pair
+// (hi, lo) of FP32 values whose sum is the double-precision value.
+template <int N> struct Exact2f {
+    float ch[N], cl[N], sh[N], sl[N], hh[N], hl[N];
 };
 
-// Does bin k of the one-axis cube at position p (samples p - n/2 .. p + n/2 - 1 of an axis of length L,
-// through the border extension) vanish for every input?  The bin is sum_m h(m) w^(k m) x[src(m)]
-// (w = exp(-2 pi i / n)), so it vanishes for all x iff, for each source sample j, the coefficient
-// sum_{m: src(m) = j} h(m) w^(k m) is 0.  With n a power of two, w has minimal polynomial w^(n/2) + 1, so
-// the coefficient is zero iff its coordinates on w^0 .. w^(n/2-1) (w^(e + n/2) = -w^e) are; they are
-// integers for the rect taper (h = 1) and, scaled by 4, for the periodic Hann taper
-// (4 h(m) w^(km) = 2 w^(km) - w^(km+m) - w^(km-m)).  Exact: no rounding enters.
-template <int N>
-__device__ bool axis_bin_vanishes(int p, int L, int bnd, int taper, int k) {
-    if (p - N / 2 >= 0 && p + N / 2 - 1 < L) return false;   // distinct in-volume samples: never
-    int src[N];
-#pragma unroll
-    for (int m = 0; m < N; ++m) src[m] = ext_index(p - N / 2 + m, L, bnd);
-    for (int m = 0; m < N; ++m) {
+// Masks of the bins that vanish for every input, per axis (t, x, y): bit k of the mask of position p
+// (the cube's samples p - n/2 .. p + n/2 - 1 of that axis) is set when bin k of that axis vanishes.
+// Positions whose cube lies inside the axis never vanish; the others are p < n (entries 0 .. n-1) and
+// p >= L - n (entries n .. 2n-1).
+struct VanishTab {
+    uint16_t m[3][32];
+    int L[3];
+};
+
+__device__ __forceinline__ uint32_t vanish_mask(const VanishTab& v, int a, int p, int n) {
+    const int L = v.L[a];
+    if (p - n / 2 >= 0 && p + n / 2 - 1 < L) return 0u;
+    return p < n ? v.m[a][p] : v.m[a][n + (p - (L - n))];
+}
+
+// Host: does bin k of the one-axis cube at position p (axis length L) vanish for every input?  The bin is
+// sum_m h(m) w^(k m) x[src(m)] (w = exp(-2 pi i / n)), so it vanishes for all x iff, for each source
+// sample j, the coefficient sum_{m: src(m) = j} h(m) w^(k m) is 0.  With n a power of two, w has minimal
+// polynomial w^(n/2) + 1, so the coefficient is zero iff its coordinates on w^0 .. w^(n/2-1)
+// (w^(e + n/2) = -w^e) are; they are integers for the rect taper (h = 1) and, scaled by 4, for the
+// periodic Hann taper (4 h(m) w^(km) = 2 w^(km) - w^(km+m) - w^(km-m)).  Exact: no rounding enters.
+inline bool axis_bin_vanishes(int n, int p, int L, int bnd, int taper, int k) {
+    if (p - n / 2 >= 0 && p + n / 2 - 1 < L) return false;
+    int src[32];
+    for (int m = 0; m < n; ++m) src[m] = ext_index(p - n / 2 + m, L, bnd);
+    for (int m = 0; m < n; ++m) {
         if (src[m] < 0) continue;
         bool first = true;
         for (int q = 0; q < m; ++q) first = first && src[q] != src[m];
         if (!first) continue;
-        int a[N / 2];
-#pragma unroll
-        for (int e = 0; e < N / 2; ++e) a[e] = 0;
-        for (int q = m; q < N; ++q) {
+        int a[16] = {0};
+        for (int q = m; q < n; ++q) {
             if (src[q] != src[m]) continue;
-            const int e0 = (k * q) % N;
-            const int es[3] = {e0, (e0 + q) % N, (e0 - q % N + N) % N};
+            const int e0 = (k * q) % n;
+            const int es[3] = {e0, (e0 + q) % n, (e0 - q + n) % n};
             const int vs[3] = {taper ? 2 : 1, taper ? -1 : 0, taper ? -1 : 0};
             for (int r = 0; r < 3; ++r) {
-                if (es[r] < N / 2) a[es[r]] += vs[r];
-                else a[es[r] - N / 2] -= vs[r];
+                if (es[r] < n / 2) a[es[r]] += vs[r];
+                else a[es[r] - n / 2] -= vs[r];
             }
         }
-        for (int e = 0; e < N / 2; ++e)
+        for (int e = 0; e < n / 2; ++e)
             if (a[e] != 0) return false;
     }
     return true;
+}
+
+inline uint16_t axis_vanish_mask(int n, int p, int L, int bnd, int taper) {
+    uint16_t mk = 0;
+    for (int k = 0; k < n; ++k)
+        if (axis_bin_vanishes(n, p, L, bnd, taper, k)) mk = (uint16_t)(mk | (1u << k));
+    return mk;
+}
+
+inline VanishTab make_vanish_tab(int n, int T, int X, int Y, int bnd, int taper) {
+    VanishTab v{};
+    const int L[3] = {T, X, Y};
+    for (int a = 0; a < 3; ++a) {
+        v.L[a] = L[a];
+        for (int p = 0; p < n && p < L[a]; ++p) v.m[a][p] = axis_vanish_mask(n, p, L[a], bnd, taper);
+        for (int p = L[a] - n > 0 ? L[a] - n : 0; p < L[a]; ++p)
+            v.m[a][n + (p - (L[a] - n))] = axis_vanish_mask(n, p, L[a], bnd, taper);
+    }
+    return v;
+}
+
+// Float-float arithmetic (an unevaluated sum hi + lo of two FP32 values): the error-free transformations
+// two-sum (Knuth) and the FMA product residual, with the usual renormalisation.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return ff_fast_two_sum(s, e + a.lo + b.lo);
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_mul1(float a, FF b) {   // a exact in FP32
+    const float p = a * b.hi;
+    return ff_fast_two_sum(p, fmaf(a, b.lo, fmaf(a, b.hi, -p)));
 }
 
 template <int N> struct BCfg;
@@ -102,25 +158,34 @@ template <int N> struct BGeo {
     static constexpr size_t A0 = IN_BYTES + G_BYTES;
     static constexpr size_t A_BYTES = A0 > WIN_BYTES ? A0 : WIN_BYTES;   // s_in+s_g1 | windows | Gamma_G1
     static constexpr size_t SMALL_OFF = A_BYTES + G_BYTES + (size_t)4 * BY * 4 + (size_t)YH * 4;
-    // [2 + BY] uint32 masks of bins that vanish for every input (k_t, k_x, then k_y per output), then
-    // [YC][NT] uint16 masks of the small bins each thread leaves to the FP64 recompute
-    static constexpr size_t SMEM = SMALL_OFF + (size_t)(2 + BY) * 4 + (size_t)YC * NT * 2;
-    static_assert(H + N + BY * N <= NT, "one thread per (axis position, bin) of the vanishing masks");
+    // [YC][NT] uint16 masks of the small bins each thread leaves to the exact recompute, then the source
+    // rows of the cube along t and x ([N] + [N] ints, -1 outside a zero-extended volume)
+    static constexpr size_t IDX_OFF = (SMALL_OFF + (size_t)YC * NT * 2 + 15) / 16 * 16;
+    static constexpr size_t SMEM = IDX_OFF + (size_t)2 * N * 4;
     static_assert(N <= 16, "16-bit masks of small bins");
     static constexpr int BLOCK_FLOATS = N * N * YH;              // scratch block per CTA
     static_assert(BY % YC == 0 && NT <= 1024, "geometry");
 };
 
 // The small bins left by step 2 (s_small[yi][owner] bit k_y: output yi of the owner's run, bin k_y of its
-// (k_t, k_x) row), one warp at a time per owner: the lanes split the n^3 terms of the direct FP64 sum
-// F = sum_u h(u) Vext[p + u - n/2] w^(k.u) and reduce it; Gamma = rho F / |F| (0 if |F| <= 2^-40 A_p)
-// and its inverse DFT along y, h(u) Gamma exp(+2 pi i k_y u / n), go into the owner's private window.
+// (k_t, k_x) row), one warp at a time per owner: the lanes split the n^3 terms of the direct sum
+// F = sum_u h(u) Vext[p + u - n/2] w^(k.u) (each lane a fixed u_y, four independent float-float
+// accumulators, the loads of four terms issued before their arithmetic) and reduce it; Gamma = rho F / |F|
+// (0 if max(|Re F|, |Im F|) <= 2^-36 A_p) and its inverse DFT along y, h(u) Gamma exp(+2 pi i k_y u / n),
+// go into the owner's private window.
 template <int N, int NT, int YC, int BY, int H, int ROWS>
-__device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int T, int X, int Y, int bnd, int t0,
-                                                int x0, int y_start, const uint16_t* s_small, float2* s_win,
-                                                const float* s_ge, const float* s_l1, const float* __restrict__ wtab,
-                                                const Tw<N>& tw, const Exact64<N>& ex) {
+__device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int X, int Y, int bnd, int y_start,
+                                                int taper, const uint16_t* s_small, const int* s_src, float2* s_win,
+                                                const float* s_ge, const float* s_l1,
+                                                const float* __restrict__ wtab, const Tw<N>& tw,
+                                                const Exact2f<N>& ex) {
+    constexpr int N3 = N * N * N, PER = N3 >= 32 ? N3 / 32 : 1, STEP = 32 / N;   // terms per lane, (ut, ux) step
+    constexpr int U = PER >= 4 ? 4 : PER;                                          // independent accumulators
     const int tid = threadIdx.x, lane = tid & 31;
+    // lane's fixed u_y and its first (u_t, u_x) pair: term e = lane + 32 i has u_y = lane % N and
+    // (u_t, u_x) = divmod(lane / N + STEP i, N)
+    const int uy = lane % N, r0 = lane / N;
+    const bool live = lane < N3;   // n = 2: 8 terms, lanes 8.. idle
     bool mine = false;
     for (int yi = 0; yi < YC; ++yi) mine = mine || s_small[yi * NT + tid] != 0;
     unsigned todo = __ballot_sync(0xffffffffu, mine);
@@ -130,34 +195,61 @@ __device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int
         const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
         for (int yi = 0; yi < YC; ++yi) {
             unsigned msk = s_small[yi * NT + o];
-            const int yl = ych * YC + yi, y = y_start + yl;
+            const int yl = ych * YC + yi;
+            const int gy = ext_index(y_start + yl - N / 2 + uy, Y, bnd);
             while (msk) {
                 const int ky = __ffs(msk) - 1;
                 msk &= msk - 1;
-                double re = 0.0, im = 0.0;
-                for (int e = lane; e < N * N * N; e += 32) {
-                    const int ut = e / (N * N), ux = (e / N) % N, uy = e % N;
-                    const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-                    const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
-                    const int gy = ext_index(y - N / 2 + uy, Y, bnd);
-                    if ((gt | gx | gy) < 0) continue;
-                    const double v = (double)__ldg(V + ((size_t)gt * X + gx) * Y + gy) * ex.h[ut] * ex.h[ux] * ex.h[uy];
-                    const int ph = (kt * ut + kx * ux + ky * uy) % N;
-                    re = fma(v, ex.c[ph], re);
-                    im = fma(-v, ex.s[ph], im);
+                FF re[U], im[U];
+#pragma unroll
+                for (int a = 0; a < U; ++a) re[a] = im[a] = FF{0.f, 0.f};
+                const FF hy = {ex.hh[uy], ex.hl[uy]};
+                for (int i0 = 0; i0 < PER; i0 += U) {
+                    float v[U];
+                    int ph[U];
+                    FF h2[U];
+#pragma unroll
+                    for (int a = 0; a < U; ++a) {   // loads first, then the arithmetic
+                        const int rr = live ? r0 + STEP * (i0 + a) : 0, ut = rr / N, ux = rr % N;
+                        const int gt = s_src[ut], gx = s_src[N + ux];
+                        v[a] = (live && (gt | gx | gy) >= 0) ? __ldg(V + ((size_t)gt * X + gx) * Y + gy) : 0.f;
+                        ph[a] = (kt * ut + kx * ux + ky * uy) % N;
+                        h2[a] = taper ? ff_mul(FF{ex.hh[ut], ex.hl[ut]}, FF{ex.hh[ux], ex.hl[ux]}) : FF{1.f, 0.f};
+                    }
+#pragma unroll
+                    for (int a = 0; a < U; ++a) {
+                        FF c = {ex.ch[ph[a]], ex.cl[ph[a]]}, sn = {-ex.sh[ph[a]], -ex.sl[ph[a]]};
+                        if (taper) {
+                            const FF h3 = ff_mul(h2[a], hy);
+                            c = ff_mul(h3, c);
+                            sn = ff_mul(h3, sn);
+                        }
+                        re[a] = ff_add(re[a], ff_mul1(v[a], c));
+                        im[a] = ff_add(im[a], ff_mul1(v[a], sn));
+                    }
                 }
 #pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    re += __shfl_xor_sync(0xffffffffu, re, d);
-                    im += __shfl_xor_sync(0xffffffffu, im, d);
+                for (int a = 1; a < U; ++a) {
+                    re[0] = ff_add(re[0], re[a]);
+                    im[0] = ff_add(im[0], im[a]);
                 }
-                const double mag = sqrt(re * re + im * im);
-                if (mag > kZeroBin * (double)s_l1[yl] && lane < N) {
+                FF fre = re[0], fim = im[0];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    const FF r2 = {__shfl_xor_sync(0xffffffffu, fre.hi, d), __shfl_xor_sync(0xffffffffu, fre.lo, d)};
+                    const FF i2 = {__shfl_xor_sync(0xffffffffu, fim.hi, d), __shfl_xor_sync(0xffffffffu, fim.lo, d)};
+                    fre = ff_add(fre, r2);
+                    fim = ff_add(fim, i2);
+                }
+                const float mx = fmaxf(fabsf(fre.hi), fabsf(fim.hi));
+                if (mx > kZeroBin * s_l1[yl] && lane < N) {
                     const int k = ky <= N / 2 ? ky : N - ky;
                     const float rho = fmaf(s_ge[yl], __ldg(wtab + k * ROWS + row),
                                            fmaf(s_ge[BY + yl], __ldg(wtab + (H + k) * ROWS + row),
                                                 s_ge[2 * BY + yl] * __ldg(wtab + (2 * H + k) * ROWS + row)));
-                    const float gr = (float)(rho * re / mag), gi = (float)(rho * im / mag);
+                    const float fr = fre.hi / mx, fi = fim.hi / mx;      // scaled first: no underflow
+                    const float sc = rho / sqrtf(fmaf(fr, fr, fi * fi));
+                    const float gr = sc * fr, gi = sc * fi;
                     const int u = lane;
                     const float c = tw.c[k][u], sn = ky <= N / 2 ? tw.s[k][u] : -tw.s[k][u];
                     float2* w = s_win + (yi + u) * NT + o;
@@ -181,7 +273,8 @@ template <int N, bool EN, bool SL>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                        int T, int X, int Y, int bnd, int t_begin, int t_step, const float* __restrict__ wtab,
-                       int taper, const __grid_constant__ Tw<N> tw, const __grid_constant__ Exact64<N> ex) {
+                       int taper, const __grid_constant__ Tw<N> tw, const __grid_constant__ Exact2f<N> ex,
+                       const __grid_constant__ VanishTab vt) {
     using G = BGeo<N>;
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT, WIN = G::WIN;
@@ -194,8 +287,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     float* s_ge = reinterpret_cast<float*>(smem_raw + G::A_BYTES + G::G_BYTES);  // [3][BY]
     float* s_l1 = s_ge + 3 * BY;                                                 // [BY] window L1 norms
     float* s_col = s_l1 + BY;                                                    // [YH] column sums
-    unsigned* s_vanish = reinterpret_cast<unsigned*>(smem_raw + G::SMALL_OFF);   // [2 + BY] (k_t, k_x, k_y)
-    uint16_t* s_small = reinterpret_cast<uint16_t*>(s_vanish + 2 + BY);          // [YC][NT]
+    uint16_t* s_small = reinterpret_cast<uint16_t*>(smem_raw + G::SMALL_OFF);    // [YC][NT]
+    int* s_src = reinterpret_cast<int*>(smem_raw + G::IDX_OFF);                   // [2][N] cube rows along t, x
 
     const int tid = threadIdx.x;
     const int y_start = blockIdx.x * BY;
@@ -204,7 +297,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const size_t NV = (size_t)T * X * Y;
 
     if (!EN)
-        for (int i = tid; i < 2 + BY; i += NT) s_vanish[i] = 0u;
+        for (int i = tid; i < 2 * N; i += NT)
+            s_src[i] = i < N ? ext_index(t0 - N / 2 + i, T, bnd) : ext_index(x0 - N / 2 + i - N, X, bnd);
     B::stage_brick(V, s_in, T, X, Y, bnd, t0, x0, y_start);
     for (int i = tid; i < 3 * BY; i += NT) {
         const int m = i / BY, yl = i % BY, y = y_start + yl;
@@ -216,23 +310,6 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
         float a = 0.f;
         for (int r = 0; r < N * N; ++r) a = fmaf(tw.c[0][r / N] * tw.c[0][r % N], fabsf(s_in[r * YH + yy]), a);
         s_col[yy] = a;
-    }
-    if (!EN) {
-        // bins that vanish for every input under the border extension: one thread per (axis position, bin)
-        int word = -1, k = 0;
-        bool z = false;
-        if (tid < H) {
-            word = 0; k = tid;
-            z = axis_bin_vanishes<N>(t0, T, bnd, taper, k);
-        } else if (tid < H + N) {
-            word = 1; k = tid - H;
-            z = axis_bin_vanishes<N>(x0, X, bnd, taper, k);
-        } else if (tid < H + N + BY * N) {
-            const int i = tid - H - N;
-            word = 2 + i / N; k = i % N;
-            z = axis_bin_vanishes<N>(y_start + i / N, Y, bnd, taper, k);
-        }
-        if (z) atomicOr(s_vanish + word, 1u << k);
     }
     B::stage1(s_in, s_g1, tw);
     __syncthreads();
@@ -255,7 +332,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const float2* grow = s_g2 + (size_t)row * YH;
     float fr[N], fi[N];   // F[k_y] of the current output, all n bins
     // the whole row vanishes when its k_t or its k_x does
-    const bool row_vanishes = !EN && (((s_vanish[0] >> (row / N)) | (s_vanish[1] >> (row % N))) & 1u);
+    const bool row_vanishes =
+        !EN && (((vanish_mask(vt, 0, t0, N) >> (row / N)) | (vanish_mask(vt, 1, x0, N) >> (row % N))) & 1u);
     for (int yi = 0; yi < YC; ++yi) {
         const int yl = ych * YC + yi;
         if (!SL || yi == 0) {
@@ -335,7 +413,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
         if (!EN) {
             // bins that vanish for every input keep Gamma = 0; so does an all-zero cube (A_p = 0)
             if (small != 0u && (row_vanishes || !(s_l1[yl] > 0.f))) small = 0u;
-            if (small != 0u) small &= ~s_vanish[2 + yl];
+            if (small != 0u) small &= ~vanish_mask(vt, 2, y_start + yl, N);
             s_small[yi * NT + tid] = (uint16_t)small;
         }
 #pragma unroll
@@ -357,8 +435,8 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             *w = acc;
         }
     }
-    if (!EN) resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, T, X, Y, bnd, t0, x0, y_start, s_small, s_win, s_ge, s_l1,
-                                                        wtab, tw, ex);
+    if (!EN) resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge,
+                                                        s_l1, wtab, tw, ex);
     __syncthreads();
 
     // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
@@ -453,16 +531,21 @@ cudaError_t prepare_n() {
     return e;
 }
 
-// The FP64 constants of the exact recompute of small bins: cos, sin (2 pi m / n) and the taper (rect, or
-// the periodic Hann window 1/2 - cos(2 pi u / n) / 2), from the host's double-precision libm.
+// The float-float constants of the exact recompute of small bins: cos, sin (2 pi m / n) and the taper
+// (rect, or the periodic Hann window 1/2 - cos(2 pi u / n) / 2), from the host's double-precision libm,
+// each split into an FP32 head and the FP32 rounding of the remainder.
 template <int N>
-Exact64<N> make_exact64(int taper) {
-    Exact64<N> e;
+Exact2f<N> make_exact2f(int taper) {
+    Exact2f<N> e;
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
     for (int m = 0; m < N; ++m) {
         const double a = 2.0 * 3.14159265358979323846 * m / N;
-        e.c[m] = cos(a);
-        e.s[m] = sin(a);
-        e.h[m] = taper ? 0.5 - 0.5 * cos(a) : 1.0;
+        split(cos(a), e.ch[m], e.cl[m]);
+        split(sin(a), e.sh[m], e.sl[m]);
+        split(taper ? 0.5 - 0.5 * cos(a) : 1.0, e.hh[m], e.hl[m]);
     }
     return e;
 }
@@ -473,10 +556,12 @@ void launch_sl(const TwiddleTable& t, const float* wtab, dim3 grid, const float*
     using G = BGeo<N>;
     if (feat == 1)
         k5_spectra_adjoint_f32<N, true, SL><<<grid, G::NT, G::SMEM, s>>>(
-            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact64<N>(taper));
+            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact2f<N>(taper),
+            VanishTab{});
     else
         k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(
-            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact64<N>(taper));
+            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact2f<N>(taper),
+            make_vanish_tab(N, T, X, Y, bnd, taper));
 }
 
 template <int N>

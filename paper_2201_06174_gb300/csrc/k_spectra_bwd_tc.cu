@@ -74,9 +74,10 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr int BLOCK_FLOATS = N * F::XH * F::YH;
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + TAB5_B;
-    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets; B_c | B_s in set 1
-    static constexpr size_t G_B = 2 * GSET_B > 2 * BDG_B ? 2 * GSET_B : 2 * BDG_B;
-    static constexpr size_t OFF_AT = OFF_G + G_B;                // t-adjoint A operand [pos][16], MN-major
+    static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets
+    static constexpr size_t G_B = 2 * GSET_B;
+    static constexpr size_t OFF_BC = OFF_G + G_B;                // B_c | B_s (their own region)
+    static constexpr size_t OFF_AT = OFF_BC + 2 * BDG_B;         // t-adjoint A operand [pos][16], MN-major
     static constexpr size_t OFF_GE = OFF_AT + F::A1_B;
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * F::P * kBY * 4;
     static constexpr size_t OFF_MISC = (OFF_L1 + (size_t)F::P * kBY * 4 + 15) / 16 * 16;
@@ -84,7 +85,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static_assert((size_t)(kXHP * F::YP + F::XH * kBY) * 4 <= G_B, "L1 sums fit in the Gamma region");
     static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
     static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
-    static_assert(GSET_B >= 2 * BDG_B, "B_c | B_s fit in Gamma set 1");
+    static_assert(OFF_BC % 128 == 0, "B_c | B_s alignment");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -144,7 +145,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     unsigned char* s_are = smem + G::OFF_A3;
     unsigned char* s_aim = smem + G::OFF_A3 + G::A3_B;
     unsigned char* s_g = smem + G::OFF_G;                        // Gamma operands, two sets
-    unsigned char* s_bc = smem + G::OFF_G + G::GSET_B;           // B_c = [dG2r | dG2i] (after the y adjoint)
+    unsigned char* s_bc = smem + G::OFF_BC;                      // B_c = [dG2r | dG2i] (after the y adjoint)
     unsigned char* s_bs = s_bc + G::BDG_B;                       // B_s = [-dG2i | dG2r]
     float* s_col = reinterpret_cast<float*>(smem + G::OFF_G);    // L1 column sums (set-up only)
     unsigned char* s_at = smem + G::OFF_AT;                      // t-adjoint A operand
@@ -153,8 +154,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     const float* s_wt = reinterpret_cast<const float*>(s_tab + G::TAB_WT);
     // mbarriers (arrival counts): [0], [1] forward buffer full (MMA commit); [2], [3] forward buffer read
     // (16 warps); [4] stage-3 A written (16); [5] stage-2 B tiles written (16); [6], [7] Gamma set written
-    // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete, B_c | B_s read
-    // (commit); [11] the brick's TMA copies landed; [12] constant operands landed (bulk copy); [13] the
+    // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete (commit; the
+    // producer alone waits on it); [11] the brick's TMA copies landed; [12] constant operands landed (bulk copy); [13] the
     // brick's gV block complete
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 112);
@@ -342,12 +343,62 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 issue_s3(0);
                 issue_s3(1);
             }
+            // ---- dG1 of tile ktp -> the t-adjoint operand, then the t-adjoint MMAs.  Deferred until the
+            // adjoint-y MMAs of the next tile's first pass are issued, so the wait for the adjoint-x MMAs does
+            // not hold back the producer; it still precedes the next adjoint-x (which rewrites dG1) and the
+            // next conversion (which rewrites the operand), both later in program order.
+            auto finish_t = [&](int ktp) -> bool {
+                // ---- dG1 (rows x = lane) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) -------------------
+                // (the t-adjoint MMAs of tile ktp - 1 precede the adjoint-x MMAs of ktp: complete once dG1 is)
+                if (!pwait(10)) return false;
+                uint32_t d0[32], d1[32];      // columns 0..31: re over y; 32..63: im over y
+                tc::tmem_ld32_async(tmem + kColX, d0);
+                tc::tmem_ld32_async(tmem + kColX + 32u, d1);
+                tc::tmem_wait_ld(d0);
+                tc::tmem_wait_ld(d1);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {   // columns 16 c ..: re over y (c = 0, 1), im over y (c = 2, 3)
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float((c < 2 ? d0 : d1)[16 * (c & 1) + i]);
+                    const int k = c >> 1;
+                    if (lane < kXHP) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int y8 = 16 * (c & 1) + 8 * h;
+                            if (y8 < YP) {
+                                // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
+                                uint4 w;
+                                w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
+                                w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
+                                w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
+                                w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
+                                *reinterpret_cast<uint4*>(s_at + ((lane * YP + y8) / 8) * 256 + k * 16) = w;
+                            }
+                        }
+                    }
+                }
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                __syncwarp();
+                tc::fence_after_sync();
+                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
+                if (leader) {
+                    const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * ktp), 128, 256);
+                    const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
+#pragma unroll
+                    for (int i = 0; i < G::NB1; ++i)
+                        tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, ktp > 0 ? 1u : 0u);
+                }
+                return true;
+            };
             for (int kt = 0; kt < H && alive; ++kt) {
 #pragma unroll
                 for (int pass = 0; pass < G::PASSES; ++pass) {
                     const int b = pass & 1;
                     if (!(alive = pwait(6 + b))) break;     // Gamma of this pass written
                     issue_inv_y(pass);
+                    if (pass == 0 && kt > 0 && !(alive = finish_t(kt - 1))) break;
                     if (pass == G::PASSES - 1) commit(8);
                     if (pass + 2 < G::PASSES) {
                         if (!(alive = pwait(2 + b))) break; // the pass read buffer b
@@ -378,43 +429,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                     }
                 }
                 commit(10);
-                // ---- dG1 (rows x = lane) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) -------------------
-                // (the t-adjoint MMAs of k_t - 1, issued before, are complete once dG1 of k_t is)
-                if (!(alive = pwait(10))) break;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {   // columns 16 c ..: re over y (c = 0, 1), im over y (c = 2, 3)
-                    float v[16];
-                    tc::tmem_ld16(tmem + kColX + (uint32_t)(16 * c), v);
-                    const int k = c >> 1;
-                    if (lane < kXHP) {
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int y8 = 16 * (c & 1) + 8 * h;
-                            if (y8 < YP) {
-                                // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
-                                uint4 w;
-                                w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
-                                w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
-                                w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
-                                w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
-                                *reinterpret_cast<uint4*>(s_at + ((lane * YP + y8) / 8) * 256 + k * 16) = w;
-                            }
-                        }
-                    }
-                }
-                tc::fence_async_smem();
-                tc::fence_before_sync();
-                __syncwarp();
-                tc::fence_after_sync();
-                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
-                if (leader) {
-                    const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * kt), 128, 256);
-                    const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
-#pragma unroll
-                    for (int i = 0; i < G::NB1; ++i)
-                        tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, kt > 0 ? 1u : 0u);
-                }
             }
+            if (alive) alive = finish_t(H - 1);
             if (alive) commit(13);
         }
         __syncwarp();
@@ -459,8 +475,8 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
             for (int pass = 0; pass < G::PASSES; ++pass) {
                 const int b = pass & 1;
-                // Gamma set 1 holds B_c | B_s of k_t - 1 until its adjoint-x MMAs complete
-                if (pass == 1 && kt > 0) cwait(10);
+                // a Gamma set is free again once the buffer b of this pass is full: the stage-3 MMAs behind
+                // it were issued after the adjoint-y MMAs that read the set (one thread, completion in order)
                 if (cwait(b)) {
                     float v[32];
                     tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * grp), v);
@@ -476,15 +492,23 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
 #pragma unroll
                         for (int k = 0; k < H; ++k)
                             rho[k] = sigma_op * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
+                        // bins (2j, 2j+1) in packed FP32 pairs (two rounded operations per instruction)
                         float gr[N], gim[N];
 #pragma unroll
-                        for (int ky = 0; ky < N; ++ky) {
-                            const float re = v[o * G::N3 + ky], im = v[o * G::N3 + N + ky];
-                            const float m2 = fmaf(re, re, im * im);
-                            const float r = rho[ky <= N / 2 ? ky : N - ky];
-                            const float sc = EN ? r : (m2 > thr2 ? r * fast_rsqrt(m2) : 0.f);
-                            gr[ky] = sc * re;
-                            gim[ky] = sc * im;
+                        for (int j = 0; j < N / 2; ++j) {
+                            const int k0 = 2 * j, k1 = 2 * j + 1;
+                            const float2 re = make_float2(v[o * G::N3 + k0], v[o * G::N3 + k1]);
+                            const float2 im = make_float2(v[o * G::N3 + N + k0], v[o * G::N3 + N + k1]);
+                            const float2 m2 = __ffma2_rn(re, re, __fmul2_rn(im, im));
+                            const float r0 = rho[k0 <= N / 2 ? k0 : N - k0], r1 = rho[k1 <= N / 2 ? k1 : N - k1];
+                            const float2 sc = EN ? make_float2(r0, r1)
+                                                 : make_float2(m2.x > thr2 ? r0 * fast_rsqrt(m2.x) : 0.f,
+                                                               m2.y > thr2 ? r1 * fast_rsqrt(m2.y) : 0.f);
+                            const float2 a = __fmul2_rn(sc, re), c = __fmul2_rn(sc, im);
+                            gr[k0] = a.x;
+                            gr[k1] = a.y;
+                            gim[k0] = c.x;
+                            gim[k1] = c.y;
                         }
                         // pair coefficients of bins k and n - k (same twiddles up to the sign of the sine):
                         // re part [A_r | B_i], im part [A_i | B_r], A = G[k] + G[n-k], B = G[k] - G[n-k]
@@ -518,7 +542,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                     }
                 }
                 tc::fence_async_smem();
-                arrive(2 + b);   // buffer b read
+                arrive(2 + b);   // buffer b read (released only now: an earlier release costs registers)
                 arrive(6 + b);   // Gamma set b written
             }
             if (kt + 1 < H) {

@@ -245,18 +245,34 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
                         tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * (half + 2 * cc)), v);
 #pragma unroll
                         for (int o = 0; o < G::OPC; ++o) {
-                            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+                            // |F|^2 of bins (2j, 2j+1) with packed FP32 pairs (two rounded FMAs per
+                            // instruction), then |F| per bin, bins k and n - k summed (same Eq. 1 ratios)
+                            float mg[N];
 #pragma unroll
-                            for (int k = 0; k < H; ++k) {
-                                const float re = v[o * G::N3 + k], im = v[o * G::N3 + N + k];
-                                float sm = bin_mag<EN>(fmaf(re, re, im * im));
-                                if (k != 0 && 2 * k != N) {
-                                    const float re2 = v[o * G::N3 + N - k], im2 = v[o * G::N3 + 2 * N - k];
-                                    sm += bin_mag<EN>(fmaf(re2, re2, im2 * im2));
-                                }
-                                e0 = fmaf(wt[0][k], sm, e0);
-                                e1 = fmaf(wt[1][k], sm, e1);
-                                e2 = fmaf(wt[2][k], sm, e2);
+                            for (int j = 0; j < N / 2; ++j) {
+                                const float2 re = make_float2(v[o * G::N3 + 2 * j], v[o * G::N3 + 2 * j + 1]);
+                                const float2 im = make_float2(v[o * G::N3 + N + 2 * j], v[o * G::N3 + N + 2 * j + 1]);
+                                const float2 m2 = __ffma2_rn(re, re, __fmul2_rn(im, im));
+                                mg[2 * j] = bin_mag<EN>(m2.x);
+                                mg[2 * j + 1] = bin_mag<EN>(m2.y);
+                            }
+                            float sm[H];
+#pragma unroll
+                            for (int k = 0; k < H; ++k) sm[k] = (k == 0 || 2 * k == N) ? mg[k] : mg[k] + mg[N - k];
+                            // the weighted sums over |k_y|, two partial sums per map in one packed pair
+                            float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
+#pragma unroll
+                            for (int k = 0; k + 1 < H; k += 2) {
+                                const float2 s2 = make_float2(sm[k], sm[k + 1]);
+                                a0 = __ffma2_rn(make_float2(wt[0][k], wt[0][k + 1]), s2, a0);
+                                a1 = __ffma2_rn(make_float2(wt[1][k], wt[1][k + 1]), s2, a1);
+                                a2 = __ffma2_rn(make_float2(wt[2][k], wt[2][k + 1]), s2, a2);
+                            }
+                            float e0 = a0.x + a0.y, e1 = a1.x + a1.y, e2 = a2.x + a2.y;
+                            if (H & 1) {
+                                e0 = fmaf(wt[0][H - 1], sm[H - 1], e0);
+                                e1 = fmaf(wt[1][H - 1], sm[H - 1], e1);
+                                e2 = fmaf(wt[2][H - 1], sm[H - 1], e2);
                             }
                             const int slot = (pass * 2 + cc) * G::OPC + o;
                             acc[slot][0] += e0;
