@@ -239,8 +239,9 @@ def make_volume(spec: VolumeSpec, with_mask: bool = True, workers: int = 0):
     """Returns (V, D): V float32 [T][X][Y]; D float32 {0,1} template mask (or None).
 
     D is 1 within one sample of any fault plane or on a salt shell.  workers > 1 makes the X slabs in
-    that many spawned processes (start them before any CUDA work in the caller); the result is the
-    same bit for bit, since every slab has its own generators and the rms is summed in slab order.
+    that many spawned processes (the caller's main module must be safe to import, i.e. its work sits
+    under `if __name__ == "__main__"`, as spawned processes import it); the result is the same bit for
+    bit, since every slab has its own generators and the rms is summed in slab order.
     """
     T, X, Y = spec.shape
     clean = np.empty((T, X, Y), dtype=np.float32)
