@@ -509,7 +509,8 @@ def main():
     k1_fp32_ms = None
     s_vs_fp32 = None
     if args.prec != "fp32":
-        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature, stride=args.stride))
+        eng32 = sal.Saliency(V.shape, sal.Params(n=wl["n"], prec="fp32", feature=args.feature, stride=args.stride,
+                                                 **({"directions": wl["directions"]} if "directions" in wl else {})))
         E32 = torch.empty_like(E)
         for _ in range(3):
             sal.sal_local_spectra_project(eng32.h, Vd, E32)
