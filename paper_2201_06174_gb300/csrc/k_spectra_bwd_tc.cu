@@ -26,9 +26,10 @@
 //     A operand [pos][(re, im, 0...)] and D_t[pos][u_t] += A_t B_t(k_t), B_t = [c | -s](k_t, u_t),
 //     accumulates the brick's block of gVext over all k_t in tensor memory; at the end it is written to
 //     scratch [u_t][x][y] and the fixed-order gather kernel sums the overlapping blocks.
-// Warp-specialised: one producer warp issues every MMA, sixteen consumer warps compute Gamma and move
-// the adjoint operands; they meet only on mbarriers, and the stage-3 MMAs of the next k_t tile are issued
-// while the consumers still read back the adjoint of the current one.
+// Warp-specialised: two issuing warps (one for the forward recompute's MMAs, one for the adjoint's MMAs and
+// the dG1 moves, so that neither chain of waits holds back the other), sixteen consumer warps compute Gamma
+// and move the adjoint operands; they meet only on mbarriers, and the stage-3 MMAs of the next k_t tile are
+// issued while the consumers still read back the adjoint of the current one.
 // FP16 operands in both 16-bit forms (3 more mantissa bits than BF16: the direction F/|F| of small bins
 // amplifies operand rounding).  Every wait on the tensor cores is bounded; on timeout the CTA sets the
 // error word, skips the remaining MMAs and writes a zero block.
@@ -47,7 +48,8 @@ using tcs::Pack;
 
 constexpr int kFmt = 0;                   // FP16 operands
 constexpr int kConsumers = 16;            // consumer warps: 4 per tensor-memory lane quarter
-constexpr int kThreads = 32 * (kConsumers + 1);   // + one producer warp
+constexpr int kThreads = 32 * (kConsumers + 2);   // + the adjoint and the forward issuing warps
+constexpr int kBars = 16;                 // mbarriers
 constexpr uint32_t kTmemCols = 512;       // [0,256) forward buffers; [256,320) dG2; [320,384) dG1; [384,480) gV
 constexpr uint32_t kColY = 256;
 constexpr uint32_t kColX = 320;
@@ -81,7 +83,7 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr size_t OFF_GE = OFF_AT + F::A1_B;
     static constexpr size_t OFF_L1 = OFF_GE + (size_t)3 * F::P * kBY * 4;
     static constexpr size_t OFF_MISC = (OFF_L1 + (size_t)F::P * kBY * 4 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_MISC + 128 + 2 * 32 * 4;
+    static constexpr size_t SMEM = OFF_MISC + 8 * kBars + 16 + 2 * 32 * 4;
     static_assert((size_t)(kXHP * F::YP + F::XH * kBY) * 4 <= G_B, "L1 sums fit in the Gamma region");
     static_assert(TAB5_B % 16 == 0 && OFF_A3 % 16 == 0 && OFF_AT % 16 == 0, "alignment");
     static_assert(kColT + 16 * F::NB1 <= kTmemCols, "tensor memory");
@@ -155,12 +157,13 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     // mbarriers (arrival counts): [0], [1] forward buffer full (MMA commit); [2], [3] forward buffer read
     // (16 warps); [4] stage-3 A written (16); [5] stage-2 B tiles written (16); [6], [7] Gamma set written
     // (16); [8] dG2 complete (commit); [9] B_c | B_s written (16); [10] dG1 complete (commit; the
-    // producer alone waits on it); [11] the brick's TMA copies landed; [12] constant operands landed (bulk copy); [13] the
-    // brick's gV block complete
+    // adjoint issuing warp alone waits on it); [11] the brick's TMA copies landed; [12] constant operands landed
+    // (bulk copy); [13] the brick's gV block complete; [14], [15] the adjoint-y MMAs that read Gamma set 0 / 1
+    // complete (commit: the set may be rewritten)
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MISC);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 112);
-    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 116);
-    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 128);  // [2][32]
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC + 8 * kBars);
+    int* s_fail = reinterpret_cast<int*>(smem + G::OFF_MISC + 8 * kBars + 4);
+    float* s_red = reinterpret_cast<float*>(smem + G::OFF_MISC + 8 * kBars + 16);  // [2][32]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = warp & 3, grp = (warp >> 2) & 3;
@@ -172,9 +175,9 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     // ---- set-up ------------------------------------------------------------------------------------
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kTmemCols);
     if (tid == 0) {
-        const uint32_t counts[14] = {1, 1, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, 1,
-                                     kConsumers, 1, 1, 1, 1};
-        for (int b = 0; b < 14; ++b) tc::mbar_init(tc::smem_u32(&s_mbar[b]), counts[b]);
+        const uint32_t counts[kBars] = {1, 1, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers, kConsumers,
+                                        1, kConsumers, 1, 1, 1, 1, 1, 1};
+        for (int b = 0; b < kBars; ++b) tc::mbar_init(tc::smem_u32(&s_mbar[b]), counts[b]);
         *s_fail = 0;
         tc::mbar_arrive_expect_tx(tc::smem_u32(&s_mbar[12]), (uint32_t)G::TAB5_B);
         tc::bulk_g2s(tc::smem_u32(s_tab), tables, (uint32_t)G::TAB5_B, tc::smem_u32(&s_mbar[12]));
@@ -253,10 +256,12 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
     };
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
 
-    if (warp == kConsumers) {
-        // ====== producer warp: lane 0 issues every MMA; the warp (lane quarter 0 of tensor memory) also moves
-        // dG1 into the t-adjoint operand, so the consumers never wait for the adjoint of stage 2 ======
+    if (warp >= kConsumers) {
+        // ====== issuing warps: in each, one elected lane issues the MMAs.  The adjoint warp (lane quarter 0 of
+        // tensor memory) also moves dG1 into the t-adjoint operand, so the consumers never wait for the
+        // adjoint of stage 2 ======
         {
+            const bool adjoint = warp == kConsumers;
             const bool leader = lane == 0;
             const uint32_t idesc1 = tc::idesc_f16(kFmt, 128, 16, 1, 0);
             const uint32_t idesc2 = tc::idesc_f16(kFmt, 128, G::N2, 0, 0);
@@ -270,11 +275,12 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             const uint32_t at = tc::smem_u32(s_at);
             const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
             const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
-            uint32_t ph[14];
+            uint32_t ph[kBars];
 #pragma unroll
-            for (int b = 0; b < 14; ++b) ph[b] = 0;
+            for (int b = 0; b < kBars; ++b) ph[b] = 0;
             auto commit = [&](int b) {
-                if (leader) tc::mma_commit(tc::smem_u32(&s_mbar[b]));
+                if (tc::elect_one()) tc::mma_commit(tc::smem_u32(&s_mbar[b]));
+                __syncwarp();
             };
             // warp-uniform bounded wait; a give-up (here or in a consumer) stops all further issue
             auto pwait = [&](int b) -> bool {
@@ -294,151 +300,175 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             const uint64_t tred = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TRE, G::TI_LBO, 128);
             const uint64_t timd = tc::desc_noswizzle(tab + (uint32_t)G::TAB_TIM, G::TI_LBO, 128);
             auto issue_s2 = [&](int kt) {
-                if (!leader) return;
                 const uint64_t b2 = tc::desc_add(b2d, (uint32_t)(kt * G::B2_B));
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int s = 0; s < kK2 / 16; ++s)
-                    tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2, s > 0 ? 1u : 0u);
-                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                    for (int s = 0; s < kK2 / 16; ++s)
+                        tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2,
+                                    s > 0 ? 1u : 0u);
+                    tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                }
+                __syncwarp();
             };
             auto issue_s3 = [&](int pass) {
-                if (!leader) return;
                 const uint32_t col = (uint32_t)(128 * (pass & 1));
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int j = 0; j < G::OPP; ++j) {
-                    const uint32_t y0 = pass * G::OPP + j;
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
+                    for (int j = 0; j < G::OPP; ++j) {
+                        const uint32_t y0 = pass * G::OPP + j;
+                        tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
+                        tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
+                    }
+                    tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
                 }
-                tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
+                __syncwarp();
             };
             // adjoint of stage 3 for the outputs of one pass (Gamma set pass % 2), accumulating into kColY
             auto issue_inv_y = [&](int pass) {
-                if (!leader) return;
                 const uint32_t set = (uint32_t)((pass & 1) * G::GSET_B);
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int j = 0; j < G::OPP; ++j) {
-                    const uint32_t y0 = pass * G::OPP + j;
-                    const uint32_t slot = set + (uint32_t)(j * G::SLOT_B);
-                    const uint32_t shift = (15u - y0) * 16u;
-                    const uint32_t accum = y0 > 0 ? 1u : 0u;
-                    tc::mma_f16(tmem + kColY, tc::desc_add(gd, slot), tc::desc_add(tred, shift), idescy, accum);
-                    tc::mma_f16(tmem + kColY + 32, tc::desc_add(gd, slot + G::IM_OFF), tc::desc_add(timd, shift),
-                                idescy, accum);
+                    for (int j = 0; j < G::OPP; ++j) {
+                        const uint32_t y0 = pass * G::OPP + j;
+                        const uint32_t slot = set + (uint32_t)(j * G::SLOT_B);
+                        const uint32_t shift = (15u - y0) * 16u;
+                        const uint32_t accum = y0 > 0 ? 1u : 0u;
+                        tc::mma_f16(tmem + kColY, tc::desc_add(gd, slot), tc::desc_add(tred, shift), idescy, accum);
+                        tc::mma_f16(tmem + kColY + 32, tc::desc_add(gd, slot + G::IM_OFF), tc::desc_add(timd, shift),
+                                    idescy, accum);
+                    }
                 }
+                __syncwarp();
             };
-            bool alive = pwait(12);
-            if (alive && leader) {   // stage 1, all k_t at once
-                const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+            if (!adjoint) {
+                // ---- forward issue: stage 1 once, then stage 2 per k_t and stage 3 per pass ----------------
+                bool alive = pwait(12);
+                if (alive) {   // stage 1, all k_t at once
+                    const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+                    const uint64_t a1 = tc::desc_noswizzle(tc::smem_u32(s_a1), 128, 256);
+                    if (tc::elect_one()) {
 #pragma unroll
-                for (int i = 0; i < G::NB1; ++i)
-                    tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1,
-                                idesc1, 0);
-                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
-            }
-            alive = alive && pwait(5);
-            if (alive) issue_s2(0);
-            alive = alive && pwait(4);
-            if (alive) {
-                issue_s3(0);
-                issue_s3(1);
-            }
-            // ---- dG1 of tile ktp -> the t-adjoint operand, then the t-adjoint MMAs.  Deferred until the
-            // adjoint-y MMAs of the next tile's first pass are issued, so the wait for the adjoint-x MMAs does
-            // not hold back the producer; it still precedes the next adjoint-x (which rewrites dG1) and the
-            // next conversion (which rewrites the operand), both later in program order.
-            auto finish_t = [&](int ktp) -> bool {
-                // ---- dG1 (rows x = lane) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) -------------------
-                // (the t-adjoint MMAs of tile ktp - 1 precede the adjoint-x MMAs of ktp: complete once dG1 is)
-                if (!pwait(10)) return false;
-                uint32_t d0[32], d1[32];      // columns 0..31: re over y; 32..63: im over y
-                tc::tmem_ld32_async(tmem + kColX, d0);
-                tc::tmem_ld32_async(tmem + kColX + 32u, d1);
-                tc::tmem_wait_ld(d0);
-                tc::tmem_wait_ld(d1);
+                        for (int i = 0; i < G::NB1; ++i)
+                            tc::mma_f16(tmem + 16 * i, tc::desc_add(a1, 4096 * i), b1, idesc1, 0);
+                        tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                    }
+                    __syncwarp();
+                }
+                alive = alive && pwait(5);
+                if (alive) issue_s2(0);
+                alive = alive && pwait(4);
+                if (alive) {
+                    issue_s3(0);
+                    issue_s3(1);
+                }
+                for (int kt = 0; kt < H && alive; ++kt) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {   // columns 16 c ..: re over y (c = 0, 1), im over y (c = 2, 3)
-                    float v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float((c < 2 ? d0 : d1)[16 * (c & 1) + i]);
-                    const int k = c >> 1;
-                    if (lane < kXHP) {
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int y8 = 16 * (c & 1) + 8 * h;
-                            if (y8 < YP) {
-                                // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
-                                uint4 w;
-                                w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
-                                w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
-                                w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
-                                w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
-                                *reinterpret_cast<uint4*>(s_at + ((lane * YP + y8) / 8) * 256 + k * 16) = w;
+                    for (int pass = 0; pass < G::PASSES; ++pass) {
+                        const int b = pass & 1;
+                        if (pass + 2 < G::PASSES) {
+                            if (!(alive = pwait(2 + b))) break;   // the pass read buffer b
+                            issue_s3(pass + 2);
+                        } else if (pass + 2 == G::PASSES && kt + 1 < H) {
+                            if (!(alive = pwait(2))) break;       // buffer 0 released
+                            issue_s2(kt + 1);
+                        }
+                    }
+                    if (!alive || kt + 1 == H) break;
+                    if (!(alive = pwait(4))) break;               // A3(kt + 1) written (buffer 0's D2 read)
+                    issue_s3(0);
+                    if (!(alive = pwait(3))) break;               // buffer 1 released by the last pass of kt
+                    issue_s3(1);
+                }
+            } else {
+                // ---- adjoint issue: y per pass, x per k_t, t per k_t (with the dG1 moves) ------------------
+                // ---- dG1 of tile ktp -> the t-adjoint operand, then the t-adjoint MMAs.  Run after the adjoint-y
+                // MMAs of the next tile's first pass are issued, so the wait for the adjoint-x MMAs does not hold them
+                // back; it still precedes the next adjoint-x (which rewrites dG1) and the next conversion (which
+                // rewrites the operand), both later in this warp's program order.
+                auto finish_t = [&](int ktp) -> bool {
+                    // ---- dG1 (rows x = lane) -> the t-adjoint A operand, K rows 0 (re) and 1 (im) -------------------
+                    // (the t-adjoint MMAs of tile ktp - 1 precede the adjoint-x MMAs of ktp: complete once dG1 is)
+                    if (!pwait(10)) return false;
+                    uint32_t d0[32], d1[32];      // columns 0..31: re over y; 32..63: im over y
+                    tc::tmem_ld32_async(tmem + kColX, d0);
+                    tc::tmem_ld32_async(tmem + kColX + 32u, d1);
+                    tc::tmem_wait_ld(d0);
+                    tc::tmem_wait_ld(d1);
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c) {   // columns 16 c ..: re over y (c = 0, 1), im over y (c = 2, 3)
+                        float v[16];
+    #pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float((c < 2 ? d0 : d1)[16 * (c & 1) + i]);
+                        const int k = c >> 1;
+                        if (lane < kXHP) {
+    #pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int y8 = 16 * (c & 1) + 8 * h;
+                                if (y8 < YP) {
+                                    // MN-major: byte(pos, k) = (pos/8) 256 + (k/8) 128 + (k%8) 16 + (pos%8) 2, pos = x YP + y
+                                    uint4 w;
+                                    w.x = Pack<kFmt>::two(kDxScale * v[8 * h + 0], kDxScale * v[8 * h + 1]);
+                                    w.y = Pack<kFmt>::two(kDxScale * v[8 * h + 2], kDxScale * v[8 * h + 3]);
+                                    w.z = Pack<kFmt>::two(kDxScale * v[8 * h + 4], kDxScale * v[8 * h + 5]);
+                                    w.w = Pack<kFmt>::two(kDxScale * v[8 * h + 6], kDxScale * v[8 * h + 7]);
+                                    *reinterpret_cast<uint4*>(s_at + ((lane * YP + y8) / 8) * 256 + k * 16) = w;
+                                }
                             }
                         }
                     }
-                }
-                tc::fence_async_smem();
-                tc::fence_before_sync();
-                __syncwarp();
-                tc::fence_after_sync();
-                // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
-                if (leader) {
+                    tc::fence_async_smem();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    // ---- adjoint of stage 1: gV block += A_t B_t(k_t), accumulated over k_t in tensor memory ----
                     const uint64_t btd = tc::desc_noswizzle(tab + (uint32_t)(G::TAB_BT + 512 * ktp), 128, 256);
                     const uint64_t atd = tc::desc_noswizzle(at, 128, 256);
-#pragma unroll
-                    for (int i = 0; i < G::NB1; ++i)
-                        tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, ktp > 0 ? 1u : 0u);
-                }
-                return true;
-            };
-            for (int kt = 0; kt < H && alive; ++kt) {
-#pragma unroll
-                for (int pass = 0; pass < G::PASSES; ++pass) {
-                    const int b = pass & 1;
-                    if (!(alive = pwait(6 + b))) break;     // Gamma of this pass written
-                    issue_inv_y(pass);
-                    if (pass == 0 && kt > 0 && !(alive = finish_t(kt - 1))) break;
-                    if (pass == G::PASSES - 1) commit(8);
-                    if (pass + 2 < G::PASSES) {
-                        if (!(alive = pwait(2 + b))) break; // the pass read buffer b
-                        issue_s3(pass + 2);
-                    } else if (pass + 2 == G::PASSES) {
-                        if (!(alive = pwait(2))) break;     // buffer 0 released
-                        if (kt + 1 < H) issue_s2(kt + 1);
+                    if (tc::elect_one()) {
+    #pragma unroll
+                        for (int i = 0; i < G::NB1; ++i)
+                            tc::mma_f16(tmem + kColT + 16 * i, tc::desc_add(atd, 4096 * i), btd, idesct, ktp > 0 ? 1u : 0u);
                     }
-                }
-                if (!alive) break;
-                if (kt + 1 < H) {
-                    if (!(alive = pwait(4))) break;          // A3(kt + 1) written (buffer 0's D2 read)
-                    issue_s3(0);
-                    if (!(alive = pwait(3))) break;          // buffer 1 released by the last pass of kt
-                    issue_s3(1);
-                }
-                // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) ---------------
-                if (!(alive = pwait(9))) break;
-                if (leader) {
+                    __syncwarp();
+                    return true;
+                };
+                bool alive = pwait(12);
+                for (int kt = 0; kt < H && alive; ++kt) {
+#pragma unroll
+                    for (int pass = 0; pass < G::PASSES; ++pass) {
+                        const int b = pass & 1;
+                        if (!(alive = pwait(6 + b))) break;       // Gamma of this pass written
+                        issue_inv_y(pass);
+                        commit(14 + b);                           // Gamma set b read once these complete
+                        if (pass == G::PASSES - 1) commit(8);
+                        if (pass == 0 && kt > 0 && !(alive = finish_t(kt - 1))) break;
+                    }
+                    if (!alive) break;
+                    // ---- adjoint of stage 2: dG1 = A2_cos^T B_c + A2_sin^T B_s (A2 read MN-major) -----------
+                    if (!(alive = pwait(9))) break;
                     const uint64_t a2t = tc::desc_noswizzle(tab, G::SBO_K2, 128);   // A2 read MN-major: A2^T
                     const uint64_t bcd = tc::desc_noswizzle(bc, 128, 2048), bsd = tc::desc_noswizzle(bs, 128, 2048);
+                    if (tc::elect_one()) {
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        tc::mma_f16(tmem + kColX, tc::desc_add(a2t, 1536 * s), tc::desc_add(bcd, 256 * s), idescx,
-                                    s > 0 ? 1u : 0u);
-                        tc::mma_f16(tmem + kColX, tc::desc_add(a2t, (kXHP / 8) * 128 + 1536 * s),
-                                    tc::desc_add(bsd, 256 * s), idescx, 1u);
+                        for (int s = 0; s < 8; ++s) {
+                            tc::mma_f16(tmem + kColX, tc::desc_add(a2t, 1536 * s), tc::desc_add(bcd, 256 * s), idescx,
+                                        s > 0 ? 1u : 0u);
+                            tc::mma_f16(tmem + kColX, tc::desc_add(a2t, (kXHP / 8) * 128 + 1536 * s),
+                                        tc::desc_add(bsd, 256 * s), idescx, 1u);
+                        }
+                        tc::mma_commit(tc::smem_u32(&s_mbar[10]));
                     }
+                    __syncwarp();
                 }
-                commit(10);
+                if (alive) alive = finish_t(H - 1);
+                if (alive) commit(13);
             }
-            if (alive) alive = finish_t(H - 1);
-            if (alive) commit(13);
         }
         __syncwarp();
     } else {
         // ================================ consumer warps ===============================================
-        uint32_t ph[14];
+        uint32_t ph[kBars];
 #pragma unroll
-        for (int b = 0; b < 14; ++b) ph[b] = 0;
+        for (int b = 0; b < kBars; ++b) ph[b] = 0;
         // warp-uniform bounded wait
         auto cwait = [&](int b) -> bool {
             bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
@@ -464,20 +494,24 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
         arrive(4);
         for (int kt = 0; kt < H; ++kt) {
-            float wt[3][H];
+            // this lane's Eq. 1 weights for (k_t, |k_x|), in pairs of |k_y| (2 kk, 2 kk + 1) for packed FP32
+            constexpr int HP = (H + 1) / 2;
+            float2 wt[3][HP];
 #pragma unroll
-            for (int k = 0; k < H; ++k) {
-                const float* w = s_wt + ((kt * H + ajx) * H + k) * 3;
-                wt[0][k] = w[0];
-                wt[1][k] = w[1];
-                wt[2][k] = w[2];
+            for (int kk = 0; kk < HP; ++kk) {
+                const float* w = s_wt + ((kt * H + ajx) * H + 2 * kk) * 3;
+                const bool two = 2 * kk + 1 < H;
+                wt[0][kk] = make_float2(w[0], two ? w[3] : 0.f);
+                wt[1][kk] = make_float2(w[1], two ? w[4] : 0.f);
+                wt[2][kk] = make_float2(w[2], two ? w[5] : 0.f);
             }
 #pragma unroll
             for (int pass = 0; pass < G::PASSES; ++pass) {
                 const int b = pass & 1;
-                // a Gamma set is free again once the buffer b of this pass is full: the stage-3 MMAs behind
-                // it were issued after the adjoint-y MMAs that read the set (one thread, completion in order)
-                if (cwait(b)) {
+                // Gamma set b is rewritten only once the adjoint-y MMAs that read it two passes ago completed
+                const bool full = cwait(b);
+                const bool set_free = kt * G::PASSES + pass < 2 || cwait(14 + b);
+                if (full && set_free) {
                     float v[32];
                     tc::tmem_ld32(tmem + lane_base + (uint32_t)(128 * b + 32 * grp), v);
 #pragma unroll
@@ -488,22 +522,35 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                         const float g0 = s_ge[gi], g1 = s_ge[P * kBY + gi], g2 = s_ge[2 * P * kBY + gi];
                         const float thr = kKinkTau * s_l1[gi];
                         const float thr2 = fmaxf(thr * thr, 1e-30f);
-                        float rho[H];
+                        // rho of |k_y| = 2 kk, 2 kk + 1 (packed; sigma folded into the three gE factors)
+                        const float2 gs0 = make_float2(sigma_op * g0, sigma_op * g0);
+                        const float2 gs1 = make_float2(sigma_op * g1, sigma_op * g1);
+                        const float2 gs2 = make_float2(sigma_op * g2, sigma_op * g2);
+                        float2 rho[HP];
 #pragma unroll
-                        for (int k = 0; k < H; ++k)
-                            rho[k] = sigma_op * fmaf(g0, wt[0][k], fmaf(g1, wt[1][k], g2 * wt[2][k]));
-                        // bins (2j, 2j+1) in packed FP32 pairs (two rounded operations per instruction)
+                        for (int kk = 0; kk < HP; ++kk)
+                            rho[kk] = __ffma2_rn(gs0, wt[0][kk], __ffma2_rn(gs1, wt[1][kk], __fmul2_rn(gs2, wt[2][kk])));
+                        auto rho_of = [&](int k) -> float {
+                            const int a = k <= N / 2 ? k : N - k;
+                            return (a & 1) ? rho[a / 2].y : rho[a / 2].x;
+                        };
+                        // bins (2j, 2j+1) in packed FP32 pairs (two rounded operations per instruction).  The
+                        // kink band as a 0/1 factor: |F|^2 carries 1e-30 (far below every band) so that the
+                        // reciprocal square root stays finite where the factor is 0
+                        const float2 tiny = make_float2(1e-30f, 1e-30f);
                         float gr[N], gim[N];
 #pragma unroll
                         for (int j = 0; j < N / 2; ++j) {
                             const int k0 = 2 * j, k1 = 2 * j + 1;
                             const float2 re = make_float2(v[o * G::N3 + k0], v[o * G::N3 + k1]);
                             const float2 im = make_float2(v[o * G::N3 + N + k0], v[o * G::N3 + N + k1]);
-                            const float2 m2 = __ffma2_rn(re, re, __fmul2_rn(im, im));
-                            const float r0 = rho[k0 <= N / 2 ? k0 : N - k0], r1 = rho[k1 <= N / 2 ? k1 : N - k1];
-                            const float2 sc = EN ? make_float2(r0, r1)
-                                                 : make_float2(m2.x > thr2 ? r0 * fast_rsqrt(m2.x) : 0.f,
-                                                               m2.y > thr2 ? r1 * fast_rsqrt(m2.y) : 0.f);
+                            const float2 r = make_float2(rho_of(k0), rho_of(k1));
+                            float2 sc = r;
+                            if (!EN) {
+                                const float2 m2 = __ffma2_rn(re, re, __ffma2_rn(im, im, tiny));
+                                const float2 on = make_float2(m2.x > thr2 ? 1.f : 0.f, m2.y > thr2 ? 1.f : 0.f);
+                                sc = __fmul2_rn(__fmul2_rn(r, on), make_float2(fast_rsqrt(m2.x), fast_rsqrt(m2.y)));
+                            }
                             const float2 a = __fmul2_rn(sc, re), c = __fmul2_rn(sc, im);
                             gr[k0] = a.x;
                             gr[k1] = a.y;

@@ -113,8 +113,8 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
 
     if (warp == kConsumers) {
-        // ================================ producer warp: one lane issues every MMA ============================
-        if (lane == 0) {
+        // ============================ producer warp: one elected lane issues every MMA ========================
+        {
             const uint32_t idesc1 = tc::idesc_f16(FMT, 128, 16, 1, 0);
             const uint32_t idesc2 = tc::idesc_f16(FMT, 128, G::N2, 0, 0);
             const uint32_t idesc3 = tc::idesc_f16(FMT, 128, G::N3, 1, 0);
@@ -122,11 +122,11 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
             const uint32_t are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
             const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
             const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
-            // bounded wait; a give-up (here or in a consumer) stops all further issue
+            // warp-uniform bounded wait; a give-up (here or in a consumer) stops all further issue
             auto pwait = [&](int b, uint32_t parity) -> bool {
-                if (*v_fail) return false;
-                const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
-                if (!ok) give_up();
+                bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), parity, kWaitLimit);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok && lane == 0 && !*v_fail) give_up();
                 tc::fence_after_sync();
                 return ok;
             };
@@ -137,29 +137,38 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
             const uint64_t aimd = tc::desc_noswizzle(aim, 128, G::SBO_A3);
             auto issue_s2 = [&](int kt) {
                 const uint64_t b2 = tc::desc_add(b2d, (uint32_t)(kt * G::B2_B));
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int s = 0; s < kK2 / 16; ++s)
-                    tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2, s > 0 ? 1u : 0u);
-                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                    for (int s = 0; s < kK2 / 16; ++s)
+                        tc::mma_f16(tmem, tc::desc_add(a2d, 256 * s), tc::desc_add(b2, 256 * s), idesc2,
+                                    s > 0 ? 1u : 0u);
+                    tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                }
+                __syncwarp();
             };
             auto issue_s3 = [&](int pass) {
                 const uint32_t col = (uint32_t)(128 * (pass & 1));
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int j = 0; j < G::OPP; ++j) {
-                    const uint32_t y0 = pass * G::OPP + j;
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
-                    tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
+                    for (int j = 0; j < G::OPP; ++j) {
+                        const uint32_t y0 = pass * G::OPP + j;
+                        tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(ared, y0 * 16), b3a, idesc3, 0);
+                        tc::mma_f16(tmem + col + j * G::N3, tc::desc_add(aimd, y0 * 16), b3b, idesc3, 1);
+                    }
+                    tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
                 }
-                tc::mma_commit(tc::smem_u32(&s_mbar[pass & 1]));
+                __syncwarp();
             };
             bool alive = pwait(6, 0);
             if (alive) {   // stage 1, all k_t at once
                 const uint64_t b1 = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B1, 128, 256);
+                const uint64_t a1 = tc::desc_noswizzle(tc::smem_u32(s_a1), 128, 256);
+                if (tc::elect_one()) {
 #pragma unroll
-                for (int i = 0; i < G::NB1; ++i)
-                    tc::mma_f16(tmem + 16 * i, tc::desc_noswizzle(tc::smem_u32(s_a1) + 4096 * i, 128, 256), b1,
-                                idesc1, 0);
-                tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                    for (int i = 0; i < G::NB1; ++i) tc::mma_f16(tmem + 16 * i, tc::desc_add(a1, 4096 * i), b1, idesc1, 0);
+                    tc::mma_commit(tc::smem_u32(&s_mbar[0]));
+                }
+                __syncwarp();
             }
             alive = alive && pwait(5, 0);             // the stage-2 B tiles are written
             if (alive) issue_s2(0);
