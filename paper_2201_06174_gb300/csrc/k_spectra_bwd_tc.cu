@@ -275,17 +275,15 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             const uint32_t at = tc::smem_u32(s_at);
             const uint64_t b3a = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3A, 128, 256);
             const uint64_t b3b = tc::desc_noswizzle(tab + (uint32_t)G::TAB_B3B, 128, 256);
-            uint32_t ph[kBars];
-#pragma unroll
-            for (int b = 0; b < kBars; ++b) ph[b] = 0;
+            uint32_t ph = 0;   // expected phase parity of each mbarrier, one bit each
             auto commit = [&](int b) {
                 if (tc::elect_one()) tc::mma_commit(tc::smem_u32(&s_mbar[b]));
                 __syncwarp();
             };
             // warp-uniform bounded wait; a give-up (here or in a consumer) stops all further issue
             auto pwait = [&](int b) -> bool {
-                bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
-                ph[b] ^= 1u;
+                bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), (ph >> b) & 1u, kWaitLimit);
+                ph ^= 1u << b;
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok && leader && !*v_fail) give_up();
                 tc::fence_after_sync();
@@ -466,13 +464,11 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         __syncwarp();
     } else {
         // ================================ consumer warps ===============================================
-        uint32_t ph[kBars];
-#pragma unroll
-        for (int b = 0; b < kBars; ++b) ph[b] = 0;
+        uint32_t ph = 0;   // expected phase parity of each mbarrier, one bit each
         // warp-uniform bounded wait
         auto cwait = [&](int b) -> bool {
-            bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), ph[b], kWaitLimit);
-            ph[b] ^= 1u;
+            bool ok = !*v_fail && tc::mbar_wait(tc::smem_u32(&s_mbar[b]), (ph >> b) & 1u, kWaitLimit);
+            ph ^= 1u << b;
             ok = __all_sync(0xffffffffu, ok);
             if (!ok && lane == 0 && !*v_fail) give_up();
             tc::fence_after_sync();
