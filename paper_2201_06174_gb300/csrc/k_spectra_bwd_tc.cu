@@ -659,13 +659,13 @@ cudaError_t tables_n(const TwiddleTable& t, int feat, void* dst, cudaStream_t s)
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const void* tables, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, int* err,
-                     cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, const float* Vt, int Yt,
+                     int* err, cudaStream_t s) {
     using G = BtGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, t_count);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
     CUtensorMap tmap;
-    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, false);
+    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, false, Vt, Yt);
     if (feat == 1)
         k5_spectra_adjoint_tc<N, true><<<grid, kThreads, G::SMEM, s>>>(V, gE, blocks, T, X, Y, bnd, t_begin, t_step,
                                                                        tab, f32::make_tw<N>(t), err, tmap, smode);
@@ -705,10 +705,13 @@ SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n) {
 
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                      int t_begin, int t_step, int t_count, int* err, cudaStream_t s) {
+                                      int t_begin, int t_step, int t_count, const float* Vt, int Yt, int* err,
+                                      cudaStream_t s) {
     if (fmt != 0 || t_step < 1) return cudaErrorInvalidValue;
-    if (n == 8) return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, err, s);
-    if (n == 16) return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, err, s);
+    if (n == 8)
+        return launch_n<8>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, Vt, Yt, err, s);
+    if (n == 16)
+        return launch_n<16>(tw, tables, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, Vt, Yt, err, s);
     return cudaErrorInvalidValue;
 }
 

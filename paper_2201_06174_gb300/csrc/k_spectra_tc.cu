@@ -355,12 +355,12 @@ cudaError_t tables_nf(const TwiddleTable& t, int feat, void* dst, cudaStream_t s
 
 template <int N, int FMT>
 cudaError_t launch_nf(const void* tables, const float* V, float* E, int T, int X, int Y, int bnd, int feat, int stride,
-                      int* err, cudaStream_t s) {
+                      const float* Vt, int Yt, int* err, cudaStream_t s) {
     using G = TcGeo<N>;
     dim3 grid((Y + kBY - 1) / kBY, (X + G::P - 1) / G::P, (T + stride - 1) / stride);
     const unsigned char* tab = static_cast<const unsigned char*>(tables);
     CUtensorMap tmap;
-    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, true);
+    const int smode = tcs::brick_stage_mode<N>(V, T, X, Y, &tmap, true, Vt, Yt);
     if (feat == 1)
         k1_spectra_tc<N, FMT, true><<<grid, kThreads, G::SMEM, s>>>(V, E, T, X, Y, bnd, stride, tab, err, tmap, smode);
     else
@@ -392,12 +392,12 @@ cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int 
 }
 
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int feat, int stride, int* err, cudaStream_t s) {
+                              int bnd, int feat, int stride, const float* Vt, int Yt, int* err, cudaStream_t s) {
     if (stride < 1) return cudaErrorInvalidConfiguration;
-    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, feat, stride, err, s)
-                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, feat, stride, err, s);
-    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, feat, stride, err, s)
-                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, feat, stride, err, s);
+    if (n == 8) return fmt == 1 ? launch_nf<8, 1>(tables, V, E, T, X, Y, bnd, feat, stride, Vt, Yt, err, s)
+                                : launch_nf<8, 0>(tables, V, E, T, X, Y, bnd, feat, stride, Vt, Yt, err, s);
+    if (n == 16) return fmt == 1 ? launch_nf<16, 1>(tables, V, E, T, X, Y, bnd, feat, stride, Vt, Yt, err, s)
+                                 : launch_nf<16, 0>(tables, V, E, T, X, Y, bnd, feat, stride, Vt, Yt, err, s);
     return cudaErrorInvalidValue;
 }
 

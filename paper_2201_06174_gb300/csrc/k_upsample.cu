@@ -110,6 +110,28 @@ cudaError_t upsample_adjoint_launch(const float* gE, float* gEl, int T, int X, i
     return cudaGetLastError();
 }
 
+// One warp per row of V, lanes along y (coalesced on both sides); HBM-bound, 8 B per voxel.
+__global__ void __launch_bounds__(kThreads)
+k_pad_rows(const float* __restrict__ V, float* __restrict__ Vp, long long rows, int Y, int Ypad) {
+    constexpr int kWarps = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long r = (long long)blockIdx.x * kWarps + wid; r < rows; r += (long long)gridDim.x * kWarps) {
+        const float* src = V + r * Y;
+        float* dst = Vp + r * Ypad;
+        for (int y = lane; y < Y; y += 32) dst[y] = __ldg(src + y);
+    }
+}
+
+cudaError_t pad_rows_launch(const float* V, float* Vp, long long rows, int Y, int Ypad, cudaStream_t s) {
+    if (Y < 1 || Ypad < Y || rows < 1) return cudaErrorInvalidValue;
+    long long nb = (rows + kThreads / 32 - 1) / (kThreads / 32);
+    const long long cap = 16LL * device_sms();
+    if (nb > cap) nb = cap;
+    k_pad_rows<<<(int)nb, kThreads, 0, s>>>(V, Vp, rows, Y, Ypad);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s) {
     if (stride < 1) return cudaErrorInvalidValue;
     const long long rows = (long long)T * X;

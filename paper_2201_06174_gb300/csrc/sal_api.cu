@@ -30,6 +30,8 @@ struct sal_handle {
     void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
     float* f32_wt = nullptr;    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
     float* sp_tab = nullptr;    // spatial-domain reading: kernels h_m and the taper
+    float* vpad = nullptr;      // V with rows padded to ypad floats (tensor-core forms, Y not a multiple of 4)
+    int ypad = 0;
     // backward scratch, allocated by the first sal_saliency_backward call
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
@@ -69,6 +71,8 @@ void free_scratch(sal_handle* h) {
     h->f32_wt = nullptr;
     if (h->sp_tab) cudaFree(h->sp_tab);
     h->sp_tab = nullptr;
+    if (h->vpad) cudaFree(h->vpad);
+    h->vpad = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
     h->err_host = nullptr;
     h->err_dev = nullptr;
@@ -110,6 +114,15 @@ sal_status check_handle(sal_handle* h) {
     return SAL_OK;
 }
 
+// The row-padded copy of V the tensor-core kernels' TMA staging reads (one tensor copy per interior brick),
+// refreshed from V on every call; null (and no work) when V's rows are already a multiple of 16 bytes.
+const float* padded_copy(sal_handle* h, const float* V, cudaStream_t st, cudaError_t& e) {
+    e = cudaSuccess;
+    if (!h->vpad) return nullptr;
+    e = sal::pad_rows_launch(V, h->vpad, (long long)h->T * h->X, h->Y, h->ypad, st);
+    return e == cudaSuccess ? h->vpad : nullptr;
+}
+
 // K1 in the handle's precision: FP32 on the SIMT pipes, or BF16/FP16 on the tensor cores.  With stride
 // s > 1 the cubes sit on the lattice of multiples of s (into the handle's lattice scratch) and E is
 // interpolated from them.
@@ -128,8 +141,10 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
         e = sal::spectra_f32_launch(h->n, h->tw, h->f32_wt, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s,
                                     h->taper, st);
     } else {
-        e = sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, out, h->T, h->X, h->Y,
-                                   h->boundary, h->feature, s, h->err_dev, st);
+        const float* vt = padded_copy(h, V, st, e);
+        if (e == cudaSuccess)
+            e = sal::spectra_tc_launch(h->n, h->prec == SAL_BF16 ? 1 : 0, h->tc_tables, V, out, h->T, h->X, h->Y,
+                                       h->boundary, h->feature, s, vt, h->ypad, h->err_dev, st);
     }
     if (e != cudaSuccess || s == 1) return e;
     return sal::upsample_launch(h->Ec, E, h->T, h->X, h->Y, s, st);
@@ -312,14 +327,18 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
     const size_t ec_bytes = sc > 1 ? (size_t)3 * ((T + sc - 1) / sc) * ((X + sc - 1) / sc) * ((Y + sc - 1) / sc) *
                                          sizeof(float)
                                    : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + sp_bytes;
+    // the tensor-core forms stage interior bricks by TMA from a row-padded copy when rows are not 16-byte multiples
+    const int ypad = (Y + 3) & ~3;
+    const size_t vpad_bytes = tc_fwd && h->feature != 2 && ypad != Y ? (size_t)T * X * ypad * sizeof(float) : 0;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + sp_bytes + vpad_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
     }
     if ((e = cudaMalloc(&h->E, plane3)) != cudaSuccess || (e = cudaMalloc(&h->S3, plane3)) != cudaSuccess ||
         (e = cudaMalloc(&h->small, small)) != cudaSuccess ||
-        (ec_bytes && (e = cudaMalloc(&h->Ec, ec_bytes)) != cudaSuccess)) {
+        (ec_bytes && (e = cudaMalloc(&h->Ec, ec_bytes)) != cudaSuccess) ||
+        (vpad_bytes && (e = cudaMalloc(&h->vpad, vpad_bytes)) != cudaSuccess)) {
         free_scratch(h);
         delete h;
         cudaGetLastError();
@@ -337,6 +356,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
         h->err_host = static_cast<volatile int*>(hp);
         *h->err_host = 0;
     }
+    h->ypad = h->vpad ? ypad : 0;
     char* b = static_cast<char*>(h->small);
     h->red.g_part = reinterpret_cast<double*>(b);
     b += (size_t)sal::kRedBlocks * 16 * sizeof(double);
@@ -557,6 +577,11 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     }
     const sal::SpectraAdjointGeometry g = adjoint_geometry(h);
     const int planes = (h->T + sc - 1) / sc;
+    const float* vt = nullptr;
+    if (h->prec != SAL_FP32) {
+        vt = padded_copy(h, V, st, e);
+        if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint: padded copy");
+    }
     for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->prec == SAL_FP32
@@ -565,7 +590,8 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,
-                                                 h->boundary, h->feature, t_begin, sc, cnt, h->err_dev, st);
+                                                 h->boundary, h->feature, t_begin, sc, cnt, vt, h->ypad, h->err_dev,
+                                                 st);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint");
         if ((e = sal::gather_add_launch(h->blocks, h->gext, gV, h->T, h->X, h->Y, h->boundary, h->n, g, t_begin, cnt,
                                         sc, st)) != cudaSuccess)

@@ -83,6 +83,8 @@ void f32_weight_table_fill(int n, int feat, float* out);   // host
 // and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.
 cudaError_t upsample_launch(const float* Ec, float* E, int T, int X, int Y, int stride, cudaStream_t s);
 cudaError_t upsample_adjoint_launch(const float* gE, float* gEl, int T, int X, int Y, int stride, cudaStream_t s);
+// V [rows][Y] -> Vp [rows][Ypad] (Ypad >= Y; the padding columns are not written)
+cudaError_t pad_rows_launch(const float* V, float* Vp, long long rows, int Y, int Ypad, cudaStream_t s);
 
 // K1 for the 32^3 window: FP32 on the SIMT pipes, or on the tensor cores (BF16 fmt = 1, FP16 fmt = 0)
 cudaError_t spectra_f32_n32_prepare();
@@ -99,8 +101,10 @@ bool spectra_tc_supported(int n);
 size_t spectra_tc_tables_bytes(int n);
 cudaError_t spectra_tc_prepare(int n, int fmt);
 cudaError_t spectra_tc_tables_build(int n, int fmt, const TwiddleTable& tw, int feat, void* tables, cudaStream_t s);
+// Vt (nullable): a copy of V with rows of Yt >= Y floats, Yt a multiple of 4, which the TMA staging of interior
+// bricks reads through one tensor copy per brick when V's own rows are not a multiple of 16 bytes.
 cudaError_t spectra_tc_launch(int n, int fmt, const void* tables, const float* V, float* E, int T, int X, int Y,
-                              int bnd, int feat, int stride, int* err, cudaStream_t s);
+                              int bnd, int feat, int stride, const float* Vt, int Yt, int* err, cudaStream_t s);
 
 // ---- K3a: sequential adaptive weights (LMS / NLMS / RLS) over inline-section blocks -------------
 // Per-map bounds of S3 into r.norm (lo at 0..2, 1/(hi-lo) at 3..5; 0 for a flat map).
@@ -144,7 +148,8 @@ cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, int f
 SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                      int t_begin, int t_step, int t_count, int* err, cudaStream_t s);
+                                      int t_begin, int t_step, int t_count, const float* Vt, int Yt, int* err,
+                                      cudaStream_t s);
 cudaError_t backward_weights_launch(const float* S3, const float* gS, long long N, const Reduce& r, double* part,
                                     float* coef, float* gW, cudaStream_t s);
 // gS with map stride gms: the raw-map gradient of map m at p is coef[m] * gS[m * gms + p].  Windows whose

@@ -178,13 +178,20 @@ __device__ void build_fwd_tables(const Tw<N>& tw, unsigned char* out, int tid, i
 // (Y a multiple of 4); other row lengths take the row copies; a V not 16-byte aligned the SIMT loads.
 // allow_rows = false: a kernel whose brick staging is not hidden by a second CTA on the SM (the adjoint)
 // takes the SIMT loads instead of the row copies, whose many small transfers cost it more than the loads.
+// Vt, Yt: a row-padded copy of V (Yt >= Y, a multiple of 4): the tensor map then reads the copy, and every
+// interior brick takes one tensor copy whatever Y is (the border bricks keep the SIMT loads from V).
 template <int N>
-inline int brick_stage_mode(const float* V, int T, int X, int Y, CUtensorMap* tmap, bool allow_rows) {
+inline int brick_stage_mode(const float* V, int T, int X, int Y, CUtensorMap* tmap, bool allow_rows,
+                            const float* Vt = nullptr, int Yt = 0) {
     using G = FwdGeo<N>;
     *tmap = CUtensorMap{};
     const int rows = allow_rows ? kStageRows : kStageSimt;
-    if ((reinterpret_cast<uintptr_t>(V) & 15) != 0) return kStageSimt;
-    if ((Y & 3) != 0) return rows;
+    // the tensor map reads the row-padded copy when there is one (same samples, rows of Yt floats)
+    const float* src = Vt ? Vt : V;
+    const int ys = Vt ? Yt : Y;
+    if (Vt && (ys < Y || (ys & 3) != 0)) return kStageSimt;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) != 0) return kStageSimt;
+    if ((ys & 3) != 0) return rows;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
@@ -198,10 +205,10 @@ inline int brick_stage_mode(const float* V, int T, int X, int Y, CUtensorMap* tm
     }();
     if (!encode) return rows;
     const cuuint64_t dims[3] = {(cuuint64_t)Y, (cuuint64_t)X, (cuuint64_t)T};
-    const cuuint64_t strides[2] = {(cuuint64_t)Y * 4, (cuuint64_t)X * Y * 4};
+    const cuuint64_t strides[2] = {(cuuint64_t)ys * 4, (cuuint64_t)X * ys * 4};
     const cuuint32_t box[3] = {(cuuint32_t)G::YP, (cuuint32_t)G::XH, (cuuint32_t)N};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode(tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides, box,
+    const CUresult r = encode(tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(src), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? kStageTensor : rows;
