@@ -489,10 +489,11 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
         ok = cwait(0);
         if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
         arrive(4);
-        for (int kt = 0; kt < H; ++kt) {
-            // this lane's Eq. 1 weights for (k_t, |k_x|), in pairs of |k_y| (2 kk, 2 kk + 1) for packed FP32
-            constexpr int HP = (H + 1) / 2;
-            float2 wt[3][HP];
+        // this lane's Eq. 1 weights for (k_t, |k_x|), in pairs of |k_y| (2 kk, 2 kk + 1) for packed FP32; those
+        // of the next tile are read before the tile boundary's waits, which then cover the loads
+        constexpr int HP = (H + 1) / 2;
+        float2 wt[3][HP];
+        auto load_wt = [&](int kt) {
 #pragma unroll
             for (int kk = 0; kk < HP; ++kk) {
                 const float* w = s_wt + ((kt * H + ajx) * H + 2 * kk) * 3;
@@ -501,6 +502,9 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 wt[1][kk] = make_float2(w[1], two ? w[4] : 0.f);
                 wt[2][kk] = make_float2(w[2], two ? w[5] : 0.f);
             }
+        };
+        load_wt(0);
+        for (int kt = 0; kt < H; ++kt) {
 #pragma unroll
             for (int pass = 0; pass < G::PASSES; ++pass) {
                 const int b = pass & 1;
@@ -589,6 +593,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
                 arrive(6 + b);   // Gamma set b written
             }
             if (kt + 1 < H) {
+                load_wt(kt + 1);
                 // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
                 ok = cwait(0);
                 if (ok && grp < 2) tcs::d2_to_a3<N, kFmt>(tmem, s_are, s_aim, q, lane, grp);
