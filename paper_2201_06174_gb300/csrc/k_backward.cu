@@ -301,10 +301,16 @@ __device__ __forceinline__ void dcs_adjoint_border_tile(const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3)   // 3 blocks per SM: 59 KB of ring each for the default window
+// GW: also the per-tile partials of the per-offset weight gradients (the sums of k4_gw_partial, for windows of
+// at most kGwMax offsets): each thread sums its voxels' terms over the tile's planes in registers, a fixed
+// shuffle tree sums the warp, the warps are summed in order in FP64 into tpart[tile][o].
+constexpr int kGwMax = 18;
+
+template <bool GW>
+__global__ void __launch_bounds__(kThreads, GW ? 2 : 3)   // 3 blocks per SM: 59 KB of ring each (default window)
 k4_dcs_adjoint_tiled(const float* __restrict__ E, const float* __restrict__ gS, long long gms,
                      const float* __restrict__ coef, float* __restrict__ gE, int T, int X, int Y, int bnd,
-                     const __grid_constant__ Stencil st) {
+                     const __grid_constant__ Stencil st, double* __restrict__ tpart) {
     extern __shared__ float s_ring[];   // [2 h_t + 1][6][TXH][TYH]: E_t, E_x, E_y, gS_t, gS_x, gS_y
     __shared__ float s_w[kMaxOffsets];
     __shared__ int s_d[kMaxOffsets][3];
@@ -324,6 +330,10 @@ k4_dcs_adjoint_tiled(const float* __restrict__ E, const float* __restrict__ gS, 
     const int x = x0 + lx, y = y0 + ly;
     const float c0 = coef[0], c1 = coef[1], c2 = coef[2];
     const int Q = st.Q;
+    float gw[GW ? kGwMax : 1];
+#pragma unroll
+    for (int o = 0; o < (GW ? kGwMax : 1); ++o) gw[o] = 0.f;
+    const float cm[3] = {c0, c1, c2};
     const bool col_ok = x < X && y < Y;
     const bool col_inner = x >= hx && x < X - hx && y >= hy && y < Y - hy;
     // global index of element i (< PE) of extended plane gt, or -1 outside a zero-extended volume
@@ -387,31 +397,61 @@ k4_dcs_adjoint_tiled(const float* __restrict__ E, const float* __restrict__ gS, 
                 eq[m] = here[m * PE];
                 gq[m] = here[(3 + m) * PE];
             }
-            if (col_inner && t >= ht && t < T - ht) {
-                // the neighbour is q + o and the only preimage of q under offset o is q - o
-#pragma unroll 2
-                for (int o = 0; o < Q; ++o) {
-                    const int dt = s_d[o][0], dx = s_d[o][1], dy = s_d[o][2];
-                    const float w = s_w[o];
-                    // slots of planes t + dt and t - dt (|dt| <= h_t < R: one wrap at most)
-                    int sn = b + dt, sp = b - dt;
-                    sn += sn < 0 ? R : 0;
-                    sn -= sn >= R ? R : 0;
-                    sp += sp < 0 ? R : 0;
-                    sp -= sp >= R ? R : 0;
-                    const float* nb_p = s_ring + (size_t)sn * PL + (lx + hx + dx) * TYH + (ly + hy + dy);
-                    const float* pr_p = s_ring + (size_t)sp * PL + (lx + hx - dx) * TYH + (ly + hy - dy);
+            // one offset of the interior path: the neighbour is q + o and the only preimage of q under offset
+            // o is q - o; returns this voxel's term of the weight gradient of o (GW)
+            auto interior = [&](int o) -> float {
+                const int dt = s_d[o][0], dx = s_d[o][1], dy = s_d[o][2];
+                const float w = s_w[o];
+                // slots of planes t + dt and t - dt (|dt| <= h_t < R: one wrap at most)
+                int sn = b + dt, sp = b - dt;
+                sn += sn < 0 ? R : 0;
+                sn -= sn >= R ? R : 0;
+                sp += sp < 0 ? R : 0;
+                sp -= sp >= R ? R : 0;
+                const float* nb_p = s_ring + (size_t)sn * PL + (lx + hx + dx) * TYH + (ly + hy + dy);
+                const float* pr_p = s_ring + (size_t)sp * PL + (lx + hx - dx) * TYH + (ly + hy - dy);
+                float g = 0.f;
 #pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        const float nb = nb_p[m * PE];
-                        const float pe = pr_p[m * PE], pg = pr_p[(3 + m) * PE];
-                        acc[m] += sgnf(fmaf(-w, nb, eq[m])) * gq[m];
-                        acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
-                    }
+                for (int m = 0; m < 3; ++m) {
+                    const float nb = nb_p[m * PE];
+                    const float pe = pr_p[m * PE], pg = pr_p[(3 + m) * PE];
+                    const float own = sgnf(fmaf(-w, nb, eq[m])) * gq[m];
+                    acc[m] += own;
+                    acc[m] -= w * sgnf(fmaf(-w, eq[m], pe)) * pg;
+                    if (GW) g = fmaf(own * cm[m], nb, g);
+                }
+                return g;
+            };
+            if (col_inner && t >= ht && t < T - ht) {
+                if (GW) {
+#pragma unroll
+                    for (int o = 0; o < kGwMax; ++o)
+                        if (o < Q) gw[o] += interior(o);
+                } else {
+#pragma unroll 2
+                    for (int o = 0; o < Q; ++o) interior(o);
                 }
             } else {
                 const TileRing tr{s_ring, R, PL, PE, TXH, TYH, ht, hx, hy, x0, y0};
                 dcs_adjoint_border_tile(E, gS, gms, T, X, Y, bnd, tr, s_d, s_w, Q, b, t, x, y, eq, gq, acc);
+                if (GW) {
+                    // the weight-gradient terms take the extended neighbour ext(q + o), staged for every voxel
+#pragma unroll
+                    for (int o = 0; o < kGwMax; ++o) {
+                        if (o < Q) {
+                            const float w = s_w[o];
+                            const float* nb_p = s_ring + (size_t)tr.slot(b, s_d[o][0]) * PL +
+                                                (lx + hx + s_d[o][1]) * TYH + (ly + hy + s_d[o][2]);
+                            float g = 0.f;
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) {
+                                const float nb = nb_p[m * PE];
+                                g = fmaf(sgnf(fmaf(-w, nb, eq[m])) * gq[m] * cm[m], nb, g);
+                            }
+                            gw[o] += g;
+                        }
+                    }
+                }
             }
             gE[q] = acc[0] * c0 * st.invQ;
             gE[NV + q] = acc[1] * c1 * st.invQ;
@@ -420,6 +460,43 @@ k4_dcs_adjoint_tiled(const float* __restrict__ E, const float* __restrict__ gS, 
         __syncthreads();   // plane t - h_t is no longer read: its slot takes plane t + 1 + h_t
         if (more) store(t + 1 + ht);
         __syncthreads();
+    }
+    if (GW) {
+        __shared__ double s_gw[kThreads / 32][kGwMax];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 0; o < kGwMax; ++o) {
+            float v = gw[o];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) s_gw[wid][o] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < Q) {
+            double a = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) a += s_gw[w][threadIdx.x];
+            tpart[(size_t)blockIdx.x * Q + threadIdx.x] = a;
+        }
+    }
+}
+
+// Sums of the per-tile weight-gradient partials, one block per offset (fixed order: strided threads, then a
+// tree), into part[o] (the single partial the finalize kernel then reads).
+__global__ void __launch_bounds__(kThreads)
+k4_gw_tiles_sum(const double* __restrict__ tpart, long long ntiles, int Q, double* __restrict__ part) {
+    __shared__ double red[kThreads / 32];
+    const int o = blockIdx.x;
+    double a = 0.0;
+    for (long long i = threadIdx.x; i < ntiles; i += kThreads) a += tpart[i * Q + o];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        part[o] = t;
     }
 }
 
@@ -655,7 +732,11 @@ cudaError_t dcs_adjoint_prepare() {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     g_tiled_min_blocks = 2 * 3 * sms;
-    return cudaFuncSetAttribute(k4_dcs_adjoint_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+    e = cudaFuncSetAttribute(k4_dcs_adjoint_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTileSmemMax);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k4_dcs_adjoint_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTileSmemMax);
 }
 
 cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE, int T,
@@ -666,12 +747,31 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
     // the tiled kernel when its plane ring fits (dcs_adjoint_prepare), its tiles fill the GPU and their
     // count fits a one-dimensional grid; the row kernel otherwise
     if (smem <= kTileSmemMax && nblk >= g_tiled_min_blocks && nblk <= 0x7fffffffLL) {
-        k4_dcs_adjoint_tiled<<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
+        k4_dcs_adjoint_tiled<false><<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st, nullptr);
         note_launches(1);
         return cudaGetLastError();
     }
     k4_dcs_adjoint<<<red_blocks(NV), kThreads, 0, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st);
     note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dcs_adjoint_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE,
+                                      int T, int X, int Y, int bnd, const Stencil& st, double* tile_part,
+                                      size_t tile_part_bytes, double* part, float* galpha, cudaStream_t s) {
+    const size_t smem = dcs_tile_smem_bytes(st.halo[0], st.halo[1], st.halo[2]);
+    const long long nblk = (long long)((T + kTileT - 1) / kTileT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
+    const bool fused = smem <= kTileSmemMax && nblk >= g_tiled_min_blocks && nblk <= 0x7fffffffLL &&
+                       st.Q <= kGwMax && tile_part && (size_t)nblk * st.Q * sizeof(double) <= tile_part_bytes;
+    if (!fused) {
+        cudaError_t e = dcs_galpha_launch(E, gS, gms, coef, T, X, Y, bnd, st, part, galpha, s);
+        if (e != cudaSuccess) return e;
+        return dcs_adjoint_launch(E, gS, gms, coef, gE, T, X, Y, bnd, st, s);
+    }
+    k4_dcs_adjoint_tiled<true><<<(int)nblk, kThreads, smem, s>>>(E, gS, gms, coef, gE, T, X, Y, bnd, st, tile_part);
+    k4_gw_tiles_sum<<<st.Q, kThreads, 0, s>>>(tile_part, nblk, st.Q, part);
+    k4_galpha_finalize<<<1, kThreads, 0, s>>>(part, 1, st, galpha);
+    note_launches(3);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ struct sal_handle {
     float* gE = nullptr;     // [3][N]
     double* bpart = nullptr; // [kRedBlocks][64]
     float* blocks = nullptr; // brick blocks of the spectral adjoint for one slab of t0
+    size_t blocks_bytes = 0; //   (also the per-tile partials of the center-surround adjoint, which runs before)
     float* gext = nullptr;   // the blocks summed along t, per extended plane of the slab
     float* gEl = nullptr;    // stride > 1: the feature gradient gathered onto the lattice voxels (zero elsewhere)
     int slab_t = 0;
@@ -557,6 +558,7 @@ sal_status ensure_backward_scratch(sal_handle* h) {
         return fail(h, SAL_ERR_OOM, std::string("backward scratch cudaMalloc: ") + cudaGetErrorString(e));
     }
     h->slab_t = slab;   // lattice planes per slab
+    h->blocks_bytes = per_t * slab;
     h->bytes += plane3 + lat3 + bpart + per_t * slab + ext_bytes;
     return SAL_OK;
 }
@@ -622,6 +624,14 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
     float* coef = h->red.norm + 12;
     if ((e = sal::backward_weights_launch(h->S3, gS, h->N, h->red, h->bpart, coef, gW, st)) != cudaSuccess)
         return cuda_fail(h, e, "backward: weights");
+    if (galpha && gV) {
+        // one pass for both gradients (the brick scratch holds the per-tile partials until K5 needs it)
+        if ((e = sal::dcs_adjoint_galpha_launch(h->E, gS, 0, coef, h->gE, h->T, h->X, h->Y, h->boundary, h->st,
+                                                reinterpret_cast<double*>(h->blocks), h->blocks_bytes, h->bpart,
+                                                galpha, st)) != cudaSuccess)
+            return cuda_fail(h, e, "backward: center_surround adjoint and alpha");
+        return spectral_adjoint(h, V, h->gE, gV, st);
+    }
     if (galpha &&
         (e = sal::dcs_galpha_launch(h->E, gS, 0, coef, h->T, h->X, h->Y, h->boundary, h->st, h->bpart, galpha, st)) !=
             cudaSuccess)
@@ -652,6 +662,13 @@ sal_status sal_center_surround_backward(sal_handle* h, const float* E, const flo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const float* ones = h->red.norm + 16;
+    if (galpha && gE) {
+        if ((e = sal::dcs_adjoint_galpha_launch(E, gS3, h->N, ones, gE, h->T, h->X, h->Y, h->boundary, h->st,
+                                                reinterpret_cast<double*>(h->blocks), h->blocks_bytes, h->bpart,
+                                                galpha, st)) != cudaSuccess)
+            return cuda_fail(h, e, "center_surround_backward");
+        return SAL_OK;
+    }
     if (galpha && (e = sal::dcs_galpha_launch(E, gS3, h->N, ones, h->T, h->X, h->Y, h->boundary, h->st, h->bpart,
                                              galpha, st)) != cudaSuccess)
         return cuda_fail(h, e, "center_surround_backward: alpha");

@@ -161,6 +161,12 @@ cudaError_t dcs_adjoint_launch(const float* E, const float* gS, long long gms, c
                                int X, int Y, int bnd, const Stencil& st, cudaStream_t s);
 cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, int T, int X, int Y,
                               int bnd, const Stencil& st, double* part, float* galpha, cudaStream_t s);
+// Both at once: the tiled kernel also sums the weight-gradient terms (one FP64 partial per tile and offset into
+// tile_part, tile_part_bytes long) when the window has at most 18 offsets and the partials fit; otherwise the
+// two launches above.  gE and galpha must both be given.
+cudaError_t dcs_adjoint_galpha_launch(const float* E, const float* gS, long long gms, const float* coef, float* gE,
+                                      int T, int X, int Y, int bnd, const Stencil& st, double* tile_part,
+                                      size_t tile_part_bytes, double* part, float* galpha, cudaStream_t s);
 cudaError_t expand_gradient_launch(const float* gS, const float* coef, float* gS3, long long N, cudaStream_t s);
 // Overlap-add of one slab's brick blocks into gV through the scratch `ext` (gather_ext_floats floats):
 // first along t (contiguous slices), then across the bricks that overlap each voxel.

@@ -144,10 +144,11 @@ def test_center_surround_adjoint_matches_oracle(sal, boundary, shape):
     _check_center_surround_adjoint(sal, boundary, shape, sal.Params(n=4, boundary=boundary, alpha=[1.0, 0.7, 1.3]))
 
 
-@pytest.mark.parametrize("boundary", ["symmetric", "periodic"])
+@pytest.mark.parametrize("boundary", ["symmetric", "periodic", "zero"])
 def test_center_surround_adjoint_tiled_kernel(sal, boundary):
     """A volume whose 16 x 16 x 8 tiles fill two waves of the GPU (smaller ones take the row kernel), with
-    ragged tiles on every axis; E and gS random (the adjoint takes any E)."""
+    ragged tiles on every axis; E and gS random (the adjoint takes any E).  gE and the direction gradients
+    together: the tiled kernel also sums the weight-gradient terms (one pass over E and gS)."""
     shape = (100, 130, 150)
     E32 = np.abs(synth.random_volume((3,) + shape, seed=21)).astype(np.float32)
     gS3 = synth.random_volume((3,) + shape, seed=22)
