@@ -312,6 +312,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
         if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
         if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_adjoint_tc_prepare(h->n, 0);
     }
+    if (e == cudaSuccess) e = sal::dcs_prepare();
     if (e == cudaSuccess) e = sal::dcs_adjoint_prepare();
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
 

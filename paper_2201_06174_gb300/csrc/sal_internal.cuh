@@ -116,6 +116,8 @@ cudaError_t adapt_launch(const float* S3, const float* D, int T, int X, int Y, i
                          cudaStream_t s);
 
 // ---- K2: directional center-surround ----------------------------------------------------------
+// Once per device: the shared-memory size limit of the ring-staged K2 (windows whose ring fits 96 KB).
+cudaError_t dcs_prepare();
 cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, const Stencil& st,
                        float* mm_part, cudaStream_t s);
 
