@@ -68,6 +68,8 @@ def set_alu_peaks(sal, sms: int, sm_max_mhz):
     for op in ("sqrt", "rsqrt"):
         rate, _ = sal.sal_measure_mufu_rate(op)
         PEAKS["mufu"][op] = rate / 1e12
+    # the tensor pipe's cost per MMA (M = 128, K = 16) at the widths the local-spectrum kernels issue
+    PEAKS["mma_cycles"] = {nc: sal.sal_measure_mma_rate(nc)[0] for nc in (16, 32, 64)}
     PEAKS["mufu_note"] = (f"measured in this run: {op_rates()} (sal_measure_mufu_rate: 8 CTAs x 256 threads per SM, "
                           f"16 independent chains per thread); {sms} SMs")
 
@@ -78,8 +80,15 @@ def op_rates():
 # K1 DRAM traffic per launch (bytes) from an ncu capture of the same kernel and workload;
 # None until captured for the current kernel.
 K1_TRAFFIC = {("salt128", 16, "fp32"): 8711168,   # sliding, 32-output form; profiles/salt128_n16_fp32_fwd_bwd.md
-              ("salt128", 16, "bf16"): 8597163}   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
-K5_TRAFFIC = {("salt128", 16, "bf16"): 717391437}  # K5 alone: 34.2 MB read + 683.2 MB written (brick blocks)
+              ("salt128", 16, "bf16"): 8546816,   # profiles/salt128_n16_bf16_fwd_bwd.md (per launch)
+              # one-pass capture of the full-scale launch (1.56 GB read + 3.39 GB written: ncu's 3-digit
+              # figures); profiles/full462x951x651_n16_bf16_fwd_bwd.md
+              ("full462x951x651", 16, "bf16"): 4950000000}
+# K5 alone (the brick blocks it writes dominate): 34.7 MB read + 689.5 MB written per 128^3 launch of 16,384
+# bricks (profiles/salt128_n16_bf16_fwd_bwd.md); a brick's traffic does not depend on the volume, so the
+# full-scale call (2,254,098 bricks over its t-slab launches) is that per-brick figure times its bricks.
+K5_TRAFFIC = {("salt128", 16, "bf16"): 724247040,
+              ("full462x951x651", 16, "bf16"): 99641345482}
 
 
 def measured_peaks():
@@ -96,6 +105,35 @@ def measured_peaks():
 def bins_per_voxel(n: int) -> int:
     """abs(F) bins per voxel of the half spectrum (k_t in [0, n/2]): h n^2, one sqrt each."""
     return (n // 2 + 1) * n * n
+
+
+def mma_per_brick(kind: str, n: int):
+    """(MMAs per brick, N) of the tensor-core kernels at window n (8, 16), from their geometry: a brick is
+    one t0, 128/n positions x0 and 16 outputs y0; stage 1 one MMA per 128 halo positions (24 x YP),
+    per k_t tile stage 2 three K steps, stage 3 two per output; the adjoint adds per tile two adjoint-y
+    MMAs per output, 16 adjoint-x MMAs and one t-adjoint MMA per 128 halo positions."""
+    h = n // 2 + 1
+    yp = 8 * -(-(16 + n - 1) // 8)
+    nb1 = -(-(24 * yp) // 128)
+    fwd = [(nb1, 16), (3 * h, 2 * yp), (32 * h, 2 * n)]
+    return fwd if kind == "k1" else fwd + [(32 * h, 32), (16 * h, 64), (nb1 * h, 16)]
+
+
+def tensor_issue(kind: str, n: int, shape, ms: float):
+    """The tensor pipe's instruction floor of a tensor-core kernel: its MMAs per brick at the measured cost per
+    MMA of each width (sal_measure_mma_rate; a width above 64 taken at the 64-column cost), the bricks spread
+    evenly over the SMs at the max SM clock; frac = floor / measured time."""
+    cyc = PEAKS.get("mma_cycles")
+    if not cyc or n not in (8, 16):
+        return None
+    T, X, Y = shape
+    bricks = -(-Y // 16) * -(-X // (128 // n)) * T
+    per_brick = sum(c * cyc[min((w for w in cyc if w >= nc), default=64)] for c, nc in mma_per_brick(kind, n))
+    floor_ms = bricks / PEAKS["sms"] * per_brick / (PEAKS["sm_ghz"] * 1e6)
+    return {"mma_per_brick": sum(c for c, _ in mma_per_brick(kind, n)), "cycles_per_brick": per_brick,
+            "cycles_per_mma": {str(k): round(v, 1) for k, v in cyc.items()}, "floor_ms": floor_ms,
+            "frac": floor_ms / ms,
+            "note": "tensor-pipe instruction rate measured in this run (sal_measure_mma_rate), bricks over the SMs"}
 
 
 def roofline(kernel, prec, n, nvox, ms, flops_mult, traffic, mufu_op="sqrt", feature="abs", flops_per_voxel=None):
@@ -561,6 +599,8 @@ def main():
         k1_rl["form"] = "spatial reading: the circulant of h_m = IDFT(r_m) applied directly (flops of that form)"
     if sc > 1:
         k1_rl["cubes_per_launch"] = ncubes
+    if args.prec != "fp32" and sc == 1 and not spatial and n in (8, 16):
+        k1_rl["tensor_issue"] = tensor_issue("k1", n, V.shape, k1_ms)
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
@@ -573,6 +613,8 @@ def main():
                       flops_per_voxel=k1_flops_per_voxel_sliding(n) + k1_flops_per_voxel(n) if k5_sliding else None)
         if k5_sliding:
             rl["form"] = "forward recompute by the sliding DFT along y (flops of that form)"
+        if args.prec != "fp32" and sc == 1 and n in (8, 16):
+            rl["tensor_issue"] = tensor_issue("k5", n, V.shape, k5_ms)
         rl["k1"] = k1_rl
     else:
         rl = k1_rl

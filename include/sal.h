@@ -248,6 +248,19 @@ sal_status sal_check_bounded_wait(sal_handle* h, unsigned tries, void* stream);
  * device's SM count.  Errors are reported by sal_last_error(NULL). */
 sal_status sal_measure_mufu_rate(int op, double* ops_per_second, int* sm_count);
 
+/* Measured cost of one tensor-core MMA (tcgen05.mma, kind::f16, M = 128, K = 16, FP16 operands, FP32
+ * accumulation) with n_cols = 16, 32, 64, 128 or 256 columns, in SM clock cycles: the instruction
+ * rate of the tensor pipe, which bounds the local-spectrum kernels' narrow MMAs (N = 16 .. 64) rather
+ * than their flops.  Not part of the paper's method (the measurement behind the tensor-core kernels'
+ * roofline).  One CTA per SM of the current device; one elected thread issues 4096 MMAs back to back on
+ * constant operands in shared memory into one tensor-memory accumulator, commits them and waits
+ * (bounded); runs on the legacy default stream, synchronously, after one warm-up launch, and allocates
+ * and frees two small device buffers.  *cycles_per_mma receives the mean over the SMs of the cycles
+ * from the first issue to completion divided by 4096, *sm_count (nullable) the device's SM count.
+ * SAL_ERR_UNSUPPORTED on a device without 5th-generation tensor cores; SAL_ERR_TIMEOUT if the bounded
+ * wait gave up.  Errors are reported by sal_last_error(NULL). */
+sal_status sal_measure_mma_rate(int n_cols, double* cycles_per_mma, int* sm_count);
+
 /* Number of kernels this library has launched in the process so far (all handles and
  * entry points), for accounting; host pointer `count`. */
 sal_status sal_launch_count(unsigned long long* count);

@@ -35,7 +35,7 @@ ENTRY_POINTS = ("sal_create", "sal_destroy", "sal_workspace_size", "sal_set_alph
                 "sal_center_surround", "sal_combine", "sal_saliency", "sal_saliency_backward", "sal_last_error",
                 "sal_combine_noalloc", "sal_local_spectra_project_backward", "sal_center_surround_backward",
                 "sal_combine_backward", "sal_launch_count", "sal_adapt_weights", "sal_directional_window",
-                "sal_check_bounded_wait", "sal_measure_mufu_rate")
+                "sal_check_bounded_wait", "sal_measure_mufu_rate", "sal_measure_mma_rate")
 
 
 class SalError(RuntimeError):
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sal_directional_window.argtypes = [i, ip, i, ctypes.c_double, i, ip, ip, fp, ip]
     L.sal_check_bounded_wait.argtypes = [vp, ctypes.c_uint, vp]
     L.sal_measure_mufu_rate.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    L.sal_measure_mma_rate.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.sal_last_error.argtypes = [vp]
     L.sal_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -285,6 +286,15 @@ def sal_measure_mufu_rate(op: str = "sqrt"):
     r = ctypes.c_double()
     sms = ctypes.c_int()
     _check(load().sal_measure_mufu_rate({"sqrt": 0, "rsqrt": 1}[op], ctypes.byref(r), ctypes.byref(sms)), None)
+    return float(r.value), int(sms.value)
+
+
+def sal_measure_mma_rate(n_cols: int):
+    """Measured cost of one tensor-core MMA (M = 128, K = 16) with n_cols columns on the current device:
+    (SM cycles per MMA, SM count)."""
+    r = ctypes.c_double()
+    sms = ctypes.c_int()
+    _check(load().sal_measure_mma_rate(int(n_cols), ctypes.byref(r), ctypes.byref(sms)), None)
     return float(r.value), int(sms.value)
 
 

@@ -58,6 +58,10 @@ def test_peaks_derived_from_unit_counts_and_the_measured_mufu_rate(monkeypatch):
         @staticmethod
         def sal_measure_mufu_rate(op):
             return (5.5e12 if op == "sqrt" else 6.0e12), 150
+
+        @staticmethod
+        def sal_measure_mma_rate(nc):
+            return {16: 44.0, 32: 44.0, 64: 48.0}[nc], 150
     bench.set_alu_peaks(FakeSal, 150, 2000.0)
     assert bench.PEAKS["fp32_tflops"] == pytest.approx(150 * 128 * 2 * 2.0e9 / 1e12)
     assert bench.PEAKS["fma_tops"] == pytest.approx(bench.PEAKS["fp32_tflops"] / 2)
@@ -114,3 +118,17 @@ def test_spatial_reading_flops_and_guard():
     r = subprocess.run([sys.executable, bench.__file__, "--feature", "spatial", "--prec", "bf16", "--form", "fwd",
                         "--workload", "fault48"], capture_output=True, text=True, timeout=120)
     assert r.returncode != 0 and "--feature spatial runs in FP32" in r.stderr
+
+
+def test_tensor_issue_floor_counts_the_kernels_mmas(monkeypatch):
+    """The MMA counts per brick follow the kernels' geometry (n = 16: 6 stage-1 MMAs, per k_t tile 3 stage-2
+    and 32 stage-3 MMAs, the adjoint 32 + 16 + 6 more), and the floor spreads the bricks over the SMs."""
+    monkeypatch.setattr(bench, "PEAKS", dict(bench.PEAKS, sms=100, sm_ghz=2.0, mma_cycles={16: 40.0, 32: 40.0, 64: 50.0}))
+    assert sum(c for c, _ in bench.mma_per_brick("k1", 16)) == 6 + 9 * 35
+    assert sum(c for c, _ in bench.mma_per_brick("k5", 16)) == 6 + 9 * 89
+    ti = bench.tensor_issue("k5", 16, (100, 80, 160), 10.0)
+    bricks = 10 * 10 * 100
+    cyc = 6 * 40 + 9 * (3 * 50 + 32 * 40 + 32 * 40 + 16 * 50 + 6 * 40)
+    assert ti["cycles_per_brick"] == cyc
+    assert ti["floor_ms"] == pytest.approx(bricks / 100 * cyc / 2.0e6)
+    assert ti["frac"] == pytest.approx(ti["floor_ms"] / 10.0)
