@@ -381,7 +381,7 @@ def main():
                     help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print the measured MUFU issue rates (the roofline denominators of the |F| epilogues) "
-                         "and exit")
+                         "and the tensor pipe's cost per MMA by width, and exit")
     args = ap.parse_args()
     if args.measure_peaks:
         import torch
@@ -389,8 +389,12 @@ def main():
         import paper_2201_06174_gb300 as sal
         props = torch.cuda.get_device_properties(0)
         set_alu_peaks(sal, props.multi_processor_count, max_sm_clock_mhz(""))
+        mma = {str(nc): sal.sal_measure_mma_rate(nc)[0] for nc in (16, 32, 64, 128, 256)}
         print(json.dumps({"mufu_tops": PEAKS["mufu"], "sms": PEAKS["sms"], "sm_ghz": PEAKS["sm_ghz"],
-                          "fp32_tflops": PEAKS["fp32_tflops"], "note": PEAKS["mufu_note"]}), flush=True)
+                          "fp32_tflops": PEAKS["fp32_tflops"], "note": PEAKS["mufu_note"],
+                          "mma_cycles_per_mma": mma,
+                          "mma_note": "tcgen05.mma kind::f16, M = 128, K = 16, by N; back-to-back issue on every SM"}),
+              flush=True)
         return
     wl = dict(WORKLOADS[args.workload])
     if args.n is not None:

@@ -3,9 +3,10 @@
 // in compensated FP32: each difference is formed by one FMA (fmaf(-w, e_nb, e_c): the product is
 // not rounded before the subtraction) and the Q distances are summed with Kahan compensation.
 // HBM-class: 12 B read + 12 B written per voxel.  Two forms with the same per-voxel sums: k2_dcs_tiled
-// (every window whose plane ring fits 96 KB of shared memory, the default among them) stages E in tiles
-// with their halos; k2_dcs, one warp per 128 voxels of a (t, x) row, reads the neighbours from L1/L2
-// (voxels the halo away from every border at linear offsets, the others through the border extension).
+// (windows whose plane ring fits 96 KB of shared memory, the default among them, on volumes with at least
+// a wave of tiles) stages E in tiles with their halos; k2_dcs, one warp per 128 voxels of a (t, x) row,
+// reads the neighbours from L1/L2 (voxels the halo away from every border at linear offsets, the others
+// through the border extension).
 // Both fuse the per-block min/max of each S_m for the normalisation in K3.
 #include <algorithm>
 #include <cfloat>
@@ -276,15 +277,17 @@ cudaError_t dcs_launch(const float* E, float* S3, int T, int X, int Y, int bnd, 
     const long long NV = (long long)T * X * Y;
     const int nparts = red_blocks(NV);  // K3 reduces exactly this many min/max partials
     const size_t smem = ring_bytes(st.halo[0], st.halo[1], st.halo[2]);
+    int per_sm = 0;
     if (smem <= kRingMax) {
-        int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_dcs_tiled, kThreads, smem);
         if (e != cudaSuccess) return e;
-        const long long ntiles =
-            (long long)((T + kTT - 1) / kTT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
-        long long grid = std::min<long long>((long long)std::max(per_sm, 1) * device_sms(), nparts);
-        grid = std::min(grid, ntiles);
-        if (grid < 1) grid = 1;
+    }
+    const long long ntiles = (long long)((T + kTT - 1) / kTT) * ((X + kTX - 1) / kTX) * ((Y + kTY - 1) / kTY);
+    const long long wave = (long long)std::max(per_sm, 1) * device_sms();
+    // the ring kernel when its tiles fill at least one wave of resident blocks; with fewer it would leave
+    // SMs idle, and the row kernel, whose warps cover every row, is faster
+    if (smem <= kRingMax && per_sm > 0 && ntiles >= wave) {
+        long long grid = std::min<long long>(wave, nparts);
         k2_dcs_tiled<<<(int)grid, kThreads, smem, s>>>(E, S3, T, X, Y, bnd, st, mm_part, nparts);
         note_launches(1);
         return cudaGetLastError();
