@@ -610,31 +610,37 @@ k4_galpha_finalize(const double* __restrict__ part, int nparts, const __grid_con
 //   pass 2 (across bricks): gV[q] += sum of ext over the extended positions (t_ext, x_ext, y_ext) that
 //     map to q and the bricks that hold them.
 // Both passes sum in a fixed order, so the result is deterministic.
-// Pass 1: one warp per (plane i, brick) row of `slice` contiguous floats, lanes along the row.
+// Pass 1: one warp per (plane i, brick) row of `slice` contiguous floats (slice4 = slice / 4 16-byte groups:
+// the blocks' slices are padded to a multiple of 4 floats), lanes along the row.
 __global__ void __launch_bounds__(kThreads)
-k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, int nb, int slice, int t_count,
+k5_gather_t(const float4* __restrict__ blocks, float4* __restrict__ ext, int n, int nb, int slice4, int t_count,
             int t_step) {
     constexpr int kWarps = kThreads / 32;
     const int lane = threadIdx.x & 31;
-    const long long bsz = (long long)n * slice;
+    const long long bsz = (long long)n * slice4;
     const long long rows = (long long)(t_step * (t_count - 1) + n) * nb;
     // from the slice of brick r to that of brick r + 1 on the same plane: the next t0's block, u_t - t_step
-    const long long rstep = (long long)nb * bsz - (long long)t_step * slice;
+    const long long rstep = (long long)nb * bsz - (long long)t_step * slice4;
     for (long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); w < rows;
          w += (long long)gridDim.x * kWarps) {
         const int brick = (int)(w % nb), i = (int)(w / nb);
         // the bricks r whose slice u_t = i - t_step r (< n) lands on plane i, in increasing r
         const int r_lo = i >= n ? (i - n + t_step) / t_step : 0;
         const int nr = min(t_count - 1, i / t_step) - r_lo + 1;   // at most 16 (n <= 16)
-        const float* src = blocks + ((long long)r_lo * nb + brick) * bsz + (long long)(i - t_step * r_lo) * slice;
-        float* dst = ext + w * slice;
-        for (int e = lane; e < slice; e += 32) {
-            float v[16];
+        const float4* src = blocks + ((long long)r_lo * nb + brick) * bsz + (long long)(i - t_step * r_lo) * slice4;
+        float4* dst = ext + w * slice4;
+        for (int e = lane; e < slice4; e += 32) {
+            float4 v[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = j < nr ? __ldg(src + j * rstep + e) : 0.f;
-            float sum = 0.f;
+            for (int j = 0; j < 16; ++j) v[j] = j < nr ? __ldg(src + j * rstep + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sum += v[j];
+            for (int j = 0; j < 16; ++j) {
+                sum.x += v[j].x;
+                sum.y += v[j].y;
+                sum.z += v[j].z;
+                sum.w += v[j].w;
+            }
             dst[e] = sum;
         }
     }
@@ -643,12 +649,11 @@ k5_gather_t(const float* __restrict__ blocks, float* __restrict__ ext, int n, in
 // Pass 2: one thread per voxel; block (32 y, 8 x) of plane t = t_lo + blockIdx.z.
 __global__ void __launch_bounds__(kThreads)
 k5_gather_xy(const float* __restrict__ ext, float* __restrict__ gV, int T, int X, int Y, int bnd, int n, int BX,
-             int XH, int BY, int YH, int t_begin, int t_count, int t_step, int t_lo) {
+             int XH, int BY, int YH, int slice, int t_begin, int t_count, int t_step, int t_lo) {
     const int h2 = n / 2;
     const int nseg = (Y + BY - 1) / BY;
     const int nxs = (X + BX - 1) / BX;
     const int nb = nxs * nseg;
-    const int slice = XH * YH;
     const int te_lo = t_begin - h2, te_hi = t_begin + t_step * (t_count - 1) + h2;   // extended planes of this slab
     const int t = t_lo + blockIdx.z, x = blockIdx.y * 8 + threadIdx.y, y = blockIdx.x * 32 + threadIdx.x;
     if (x >= X || y >= Y) return;
@@ -660,10 +665,26 @@ k5_gather_xy(const float* __restrict__ ext, float* __restrict__ gV, int T, int X
         const int sa = max(0, ceildiv(y + h2 - YH + 1, BY)), sb = min(nseg - 1, floordiv(y + h2, BY));
         const float* plane = ext + (long long)(t - te_lo) * nb * slice;
         float sum = 0.f;
-        for (int xs = xa; xs <= xb; ++xs)
-            for (int sg = sa; sg <= sb; ++sg)
-                sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
-                             (y - sg * BY + h2));
+        if (xb - xa < 4 && sb - sa < 2) {
+            // up to 4 x 2 bricks (the tensor-core geometries): every load issued before the sums, which run in
+            // the loop order below (x brick outer, y segment inner)
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int xs = xa + k / 2, sg = sa + k % 2;
+                v[k] = xs <= xb && sg <= sb ? __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
+                                                   (y - sg * BY + h2))
+                                            : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (xa + k / 2 <= xb && sa + k % 2 <= sb) sum += v[k];
+        } else {
+            for (int xs = xa; xs <= xb; ++xs)
+                for (int sg = sa; sg <= sb; ++sg)
+                    sum += __ldg(plane + (long long)(xs * nseg + sg) * slice + (x - xs * BX + h2) * YH +
+                                 (y - sg * BY + h2));
+        }
         gV[q] += sum;
         return;
     }
@@ -787,7 +808,7 @@ cudaError_t dcs_galpha_launch(const float* E, const float* gS, long long gms, co
 
 size_t gather_ext_floats(int n, SpectraAdjointGeometry g, int X, int Y, int t_count, int t_step) {
     const size_t nb = (size_t)((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
-    return (size_t)(t_step * (t_count - 1) + n) * nb * g.XH * g.YH;
+    return (size_t)(t_step * (t_count - 1) + n) * nb * g.slice;
 }
 
 cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T, int X, int Y, int bnd, int n,
@@ -795,12 +816,14 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
     if (n > 16 || t_step < 1) return cudaErrorInvalidValue;   // pass 1 unrolls up to 16 bricks per plane
     const int nb = ((X + g.BX - 1) / g.BX) * ((Y + g.BY - 1) / g.BY);
     const long long e_total = (long long)gather_ext_floats(n, g, X, Y, t_count, t_step);
-    const long long rows1 = e_total / (g.XH * g.YH);   // (plane, brick) rows, a warp each
+    if (g.slice % 4 != 0) return cudaErrorInvalidValue;   // pass 1 moves 16-byte groups
+    const long long rows1 = e_total / g.slice;   // (plane, brick) rows, a warp each
     long long b1 = (rows1 + kThreads / 32 - 1) / (kThreads / 32);
     const long long cap1 = 8LL * device_sms();   // grid-stride: 8 blocks per SM
     if (b1 > cap1) b1 = cap1;
     if (b1 < 1) b1 = 1;
-    k5_gather_t<<<(int)b1, kThreads, 0, s>>>(blocks, ext, n, nb, g.XH * g.YH, t_count, t_step);
+    k5_gather_t<<<(int)b1, kThreads, 0, s>>>(reinterpret_cast<const float4*>(blocks), reinterpret_cast<float4*>(ext),
+                                             n, nb, g.slice / 4, t_count, t_step);
     // planes the slab reaches: extended t in [t_begin - n/2, t_begin + t_step (t_count - 1) + n/2); a slab
     // whose extension leaves the volume may wrap (periodic) or reflect (symmetric) onto any edge plane
     const int h2 = n / 2;
@@ -811,8 +834,8 @@ cudaError_t gather_add_launch(const float* blocks, float* ext, float* gV, int T,
     }
     static_assert(kThreads == 32 * 8, "pass 2 blocks are 32 y x 8 x");
     const dim3 grid2((Y + 31) / 32, (X + 7) / 8, t_hi - t_lo);   // T, X <= 65535 (checked at create)
-    k5_gather_xy<<<grid2, dim3(32, 8), 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, t_begin, t_count,
-                                              t_step, t_lo);
+    k5_gather_xy<<<grid2, dim3(32, 8), 0, s>>>(ext, gV, T, X, Y, bnd, n, g.BX, g.XH, g.BY, g.YH, g.slice, t_begin,
+                                              t_count, t_step, t_lo);
     note_launches(2);
     return cudaGetLastError();
 }

@@ -163,7 +163,8 @@ template <int N> struct BGeo {
     static constexpr size_t IDX_OFF = (SMALL_OFF + (size_t)YC * NT * 2 + 15) / 16 * 16;
     static constexpr size_t SMEM = IDX_OFF + (size_t)2 * N * 4;
     static_assert(N <= 16, "16-bit masks of small bins");
-    static constexpr int BLOCK_FLOATS = N * N * YH;              // scratch block per CTA
+    static constexpr int SLICE = (N * YH + 3) / 4 * 4;           // u_t slices of the block, 16-byte aligned
+    static constexpr int BLOCK_FLOATS = N * SLICE;               // scratch block per CTA
     static_assert(BY % YC == 0 && NT <= 1024, "geometry");
 };
 
@@ -506,7 +507,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
                 z = fmaf(g[k].x, tw.c[k][u], z);
                 if (k != 0 && 2 * k != N) z = fmaf(-g[k].y, tw.s[k][u], z);
             }
-            blk[((size_t)u * N + ux) * YH + y] = z;
+            blk[(size_t)u * G::SLICE + ux * YH + y] = z;
         }
     }
 }
@@ -593,11 +594,11 @@ cudaError_t spectra_adjoint_f32_prepare(int n) {
 
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
     switch (n) {
-        case 2: return {BGeo<2>::BY, BGeo<2>::YH, 1, 2, BGeo<2>::BLOCK_FLOATS};
-        case 4: return {BGeo<4>::BY, BGeo<4>::YH, 1, 4, BGeo<4>::BLOCK_FLOATS};
-        case 8: return {BGeo<8>::BY, BGeo<8>::YH, 1, 8, BGeo<8>::BLOCK_FLOATS};
-        case 16: return {BGeo<16>::BY, BGeo<16>::YH, 1, 16, BGeo<16>::BLOCK_FLOATS};
-        default: return {0, 0, 0, 0, 0};
+        case 2: return {BGeo<2>::BY, BGeo<2>::YH, 1, 2, BGeo<2>::BLOCK_FLOATS, BGeo<2>::SLICE};
+        case 4: return {BGeo<4>::BY, BGeo<4>::YH, 1, 4, BGeo<4>::BLOCK_FLOATS, BGeo<4>::SLICE};
+        case 8: return {BGeo<8>::BY, BGeo<8>::YH, 1, 8, BGeo<8>::BLOCK_FLOATS, BGeo<8>::SLICE};
+        case 16: return {BGeo<16>::BY, BGeo<16>::YH, 1, 16, BGeo<16>::BLOCK_FLOATS, BGeo<16>::SLICE};
+        default: return {0, 0, 0, 0, 0, 0};
     }
 }
 

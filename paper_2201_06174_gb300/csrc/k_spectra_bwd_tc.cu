@@ -73,7 +73,8 @@ template <int N> struct BtGeo : tcs::FwdGeo<N> {
     static constexpr size_t TAB_BT = TAB_TIM + TI_B;          // B_t per k_t: [u][(re, im, 0...)], 512 B each
     static constexpr size_t TAB5_B = TAB_BT + (size_t)F::H * 512;
     static constexpr size_t BDG_B = (size_t)8 * 2048;         // one dG2 operand [K = 128][N = 64], MN-major
-    static constexpr int BLOCK_FLOATS = N * F::XH * F::YH;
+    static constexpr int SLICE = (F::XH * F::YH + 3) / 4 * 4;   // u_t slices of the block, 16-byte aligned
+    static constexpr int BLOCK_FLOATS = N * SLICE;
     static constexpr size_t OFF_TAB = F::R0_B;
     static constexpr size_t OFF_A3 = OFF_TAB + TAB5_B;
     static constexpr size_t OFF_G = (OFF_A3 + 2 * F::A3_B + 127) / 128 * 128;   // two Gamma sets
@@ -637,7 +638,7 @@ k5_spectra_adjoint_tc(const float* __restrict__ V, const float* __restrict__ gE,
             const int pos = 128 * i + m, x = pos / YP, y = pos % YP;
             if (x < XH && y < YH) {
 #pragma unroll
-                for (int u = 0; u < N; ++u) blk[(u * XH + x) * YH + y] = ok ? v[u] * out_scale : 0.f;
+                for (int u = 0; u < N; ++u) blk[u * G::SLICE + x * YH + y] = ok ? v[u] * out_scale : 0.f;
             }
         }
     }
@@ -703,9 +704,9 @@ cudaError_t spectra_adjoint_tc_tables_build(int n, const TwiddleTable& tw, int f
 }
 
 SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n) {
-    if (n == 8) return {kBY, BtGeo<8>::YH, BtGeo<8>::P, BtGeo<8>::XH, BtGeo<8>::BLOCK_FLOATS};
-    if (n == 16) return {kBY, BtGeo<16>::YH, BtGeo<16>::P, BtGeo<16>::XH, BtGeo<16>::BLOCK_FLOATS};
-    return {0, 0, 0, 0, 0};
+    if (n == 8) return {kBY, BtGeo<8>::YH, BtGeo<8>::P, BtGeo<8>::XH, BtGeo<8>::BLOCK_FLOATS, BtGeo<8>::SLICE};
+    if (n == 16) return {kBY, BtGeo<16>::YH, BtGeo<16>::P, BtGeo<16>::XH, BtGeo<16>::BLOCK_FLOATS, BtGeo<16>::SLICE};
+    return {0, 0, 0, 0, 0, 0};
 }
 
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,

@@ -134,7 +134,8 @@ struct SpectraAdjointGeometry {
     int YH;            // y extent of a brick's block
     int BX;            // outputs per brick along x
     int XH;            // x extent of a brick's block
-    int block_floats;  // n * XH * YH: scratch floats per brick
+    int block_floats;  // n * slice: scratch floats per brick
+    int slice;         // floats per u_t slice of a block: XH * YH rounded up to a multiple of 4 (16-byte rows)
 };
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);

@@ -61,7 +61,7 @@ def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
     budget = 0
     if slabs > 1:
         nseg = -(-shape[2] // _BY[n])
-        per_t = shape[1] * nseg * n * n * (_BY[n] + n - 1) * 4
+        per_t = shape[1] * nseg * n * (-(-n * (_BY[n] + n - 1) // 4) * 4) * 4   # slices padded to 4 floats
         base = sal.Saliency(shape, sal.Params(n=n, boundary=boundary))
         created = sal.sal_workspace_size(base.h)
         base.close()
