@@ -190,10 +190,12 @@ def k1_flops_per_voxel(n: int) -> int:
     return 4 * h * n + 8 * h * n * n + 8 * h * n ** 3
 
 
-def k1_flops_per_voxel_spatial(n: int) -> int:
-    """Flops per voxel of the spatial reading's kernel: for each of the 3 maps and n^3 outputs, an n^3-term
-    circular convolution (one FMA, 2 flops, per term)."""
-    return 3 * 2 * n ** 6
+def k1_flops_per_voxel_spatial(n: int, adjoint: bool = False) -> int:
+    """Flops per voxel of the spatial reading's kernels: per window 9 n^2 line FFTs (forward: three passes
+    of the forward transform, three of the two inverse transforms) or 18 n^2 (adjoint), each a radix-2 FFT
+    of n points at 5 n log2 n flops."""
+    lines = (18 if adjoint else 9) * n * n
+    return lines * 5 * n * (n.bit_length() - 1)
 
 
 # Outputs per thread of the FP32 K1's sliding form (rect taper, stride 1): the first of each run by the
@@ -376,7 +378,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--feature", default="abs", choices=["abs", "energy", "spatial"],
                     help="E_m: mean of |F_m| (the paper's step 3), of |F_m|^2 (energy reading), or over the "
-                         "cube of |IDFT(F_m)| (spatial reading: FP32, n <= 8, --form fwd)")
+                         "cube of |IDFT(F_m)| (spatial reading: FP32, n <= 16)")
     ap.add_argument("--stride", type=int, default=1,
                     help="cubes at voxels whose indices are multiples of the stride (1 < stride < n/2)")
     ap.add_argument("--measure-peaks", action="store_true",
@@ -403,8 +405,8 @@ def main():
     if wl["n"] >= 32:  # the FP64 oracle costs 12 n^4 flop per voxel: keep its sample to ~30 s
         wl["cpu_sample"], wl["ref_sample"] = 16, 12
     if args.feature == "spatial":
-        if args.prec != "fp32" or wl["n"] > 8 or args.stride != 1 or args.form != "fwd":
-            ap.error("--feature spatial runs in FP32 with n <= 8, stride 1 and --form fwd")
+        if args.prec != "fp32" or wl["n"] > 16 or args.stride != 1:
+            ap.error("--feature spatial runs in FP32 with n <= 16 and stride 1")
         # the oracle's spatial reading goes one voxel at a time through numpy's FFTs
         wl["cpu_sample"], wl["ref_sample"] = min(wl["cpu_sample"], 16), min(wl["ref_sample"], 12)
     if args.impl == "reference":
@@ -600,7 +602,7 @@ def main():
     if sliding:
         k1_rl["form"] = "sliding DFT along y (flops of that form)"
     if spatial:
-        k1_rl["form"] = "spatial reading: the circulant of h_m = IDFT(r_m) applied directly (flops of that form)"
+        k1_rl["form"] = "spatial reading: per-window separable radix-2 FFTs in shared memory (flops of that form)"
     if sc > 1:
         k1_rl["cubes_per_launch"] = ncubes
     if args.prec != "fp32" and sc == 1 and not spatial and n in (8, 16):
@@ -610,14 +612,18 @@ def main():
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
         # the FP32 adjoint at n = 16 recomputes the forward stage 3 by the sliding recursion: its flops are
         # the sliding forward's plus the direct adjoint's; otherwise twice the direct forward's
-        k5_sliding = args.prec == "fp32" and n == 16
-        rl = roofline(f"k5_spectra_adjoint_{tag} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
-                      1 if k5_sliding else 2, K5_TRAFFIC.get(trk), mufu_op="rsqrt" if args.prec != "fp32" else "sqrt",
-                      feature=args.feature,
-                      flops_per_voxel=k1_flops_per_voxel_sliding(n) + k1_flops_per_voxel(n) if k5_sliding else None)
+        k5_sliding = args.prec == "fp32" and n == 16 and not spatial
+        k5_name = "k5_spatial_adjoint_f32" if spatial else f"k5_spectra_adjoint_{tag}"
+        rl = roofline(f"{k5_name} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
+                      1 if k5_sliding or spatial else 2, K5_TRAFFIC.get(trk),
+                      mufu_op="rsqrt" if args.prec != "fp32" else "sqrt", feature=args.feature,
+                      flops_per_voxel=(k1_flops_per_voxel_spatial(n, adjoint=True) if spatial else
+                                       k1_flops_per_voxel_sliding(n) + k1_flops_per_voxel(n) if k5_sliding else None))
+        if spatial:
+            rl["form"] = "spatial reading's adjoint: forward recompute, signs, combined inverse (flops of that form)"
         if k5_sliding:
             rl["form"] = "forward recompute by the sliding DFT along y (flops of that form)"
-        if args.prec != "fp32" and sc == 1 and n in (8, 16):
+        if args.prec != "fp32" and sc == 1 and n in (8, 16) and not spatial:
             rl["tensor_issue"] = tensor_issue("k5", n, V.shape, k5_ms)
         rl["k1"] = k1_rl
     else:

@@ -558,9 +558,13 @@ def features_adjoint(V, gE, n: int, boundary="symmetric", taper="rect", threads:
                      feature="abs", stride: int = 1) -> np.ndarray:
     """gV = (dE/dV)^T gE through the extension (adjoint of the feature step).  stride s > 1: the
     gradient of the interpolated features goes back to the lattice (upsample_adjoint) and from there
-    through the cubes of the lattice voxels."""
+    through the cubes of the lattice voxels.  Feature "spatial": spatial_features_adjoint (stride 1)."""
     V64 = _f64(V)
     gE = _f64(gE)
+    if feature == "spatial":
+        if stride != 1:
+            raise ValueError("the spatial-domain reading is defined here for stride 1")
+        return spatial_features_adjoint(V64, gE, n, boundary, taper)
     if stride > 1:
         gEc = upsample_adjoint(gE, stride)
         lat = np.zeros_like(gE)

@@ -29,7 +29,6 @@ struct sal_handle {
     void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
     void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
     float* f32_wt = nullptr;    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
-    float* sp_tab = nullptr;    // spatial-domain reading: kernels h_m and the taper
     float* vpad = nullptr;      // V with rows padded to ypad floats (tensor-core forms, Y not a multiple of 4)
     int ypad = 0;
     // backward scratch, allocated by the first sal_saliency_backward call
@@ -70,8 +69,6 @@ void free_scratch(sal_handle* h) {
     h->tc_tables = h->adj_tables = nullptr;
     if (h->f32_wt) cudaFree(h->f32_wt);
     h->f32_wt = nullptr;
-    if (h->sp_tab) cudaFree(h->sp_tab);
-    h->sp_tab = nullptr;
     if (h->vpad) cudaFree(h->vpad);
     h->vpad = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
@@ -132,7 +129,7 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
     float* out = s > 1 ? h->Ec : E;
     cudaError_t e;
     if (h->feature == 2) {
-        e = sal::spatial_f32_launch(h->n, h->sp_tab, V, E, h->T, h->X, h->Y, h->boundary, h->taper, st);
+        e = sal::spatial_f32_launch(h->n, V, E, h->T, h->X, h->Y, h->boundary, h->taper, st);
     } else if (h->n == 32) {
         e = h->prec == SAL_FP32
                 ? sal::spectra_f32_n32_launch(h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, h->taper, st)
@@ -248,7 +245,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
         return fail(nullptr, SAL_ERR_INVALID_ARG,
                     "feature must be 0 (mean of |F_m|), 1 (mean of |F_m|^2) or 2 (mean of |IDFT(F_m)|)");
     if (p->feature == 2 && (p->prec != SAL_FP32 || !sal::spatial_f32_supported(p->n) || p->stride != 1))
-        return fail(nullptr, SAL_ERR_UNSUPPORTED, "feature 2 is built for FP32, n in {2, 4, 8}, stride 1");
+        return fail(nullptr, SAL_ERR_UNSUPPORTED, "feature 2 is built for FP32, n in {2, 4, 8, 16}, stride 1");
     if (p->prec < 0 || p->prec > 2) return fail(nullptr, SAL_ERR_INVALID_ARG, "bad precision");
     if (!sal::spectra_f32_supported(p->n) && p->n != 32)
         return fail(nullptr, SAL_ERR_UNSUPPORTED, "FP32 path is built for n in {2,4,8,16,32}");
@@ -312,6 +309,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
         if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_tc_prepare(h->n, h->prec == SAL_BF16 ? 1 : 0);
         if (e == cudaSuccess && h->prec != SAL_FP32) e = sal::spectra_adjoint_tc_prepare(h->n, 0);
     }
+    if (e == cudaSuccess && h->feature == 2) e = sal::spatial_f32_prepare();
     if (e == cudaSuccess) e = sal::dcs_prepare();
     if (e == cudaSuccess) e = sal::dcs_adjoint_prepare();
     if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "kernel attributes"); }
@@ -324,7 +322,6 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
     const size_t adj_bytes = tc_fwd ? sal::spectra_adjoint_tc_tables_bytes(h->n) : 0;
     const bool f32_tab = h->prec == SAL_FP32 && sal::spectra_f32_supported(h->n) && h->feature != 2;
     const size_t wt_bytes = f32_tab ? sal::f32_weight_table_floats(h->n) * sizeof(float) : 0;
-    const size_t sp_bytes = h->feature == 2 ? sal::spatial_table_floats(h->n) * sizeof(float) : 0;
     const int sc = p->stride;
     const size_t ec_bytes = sc > 1 ? (size_t)3 * ((T + sc - 1) / sc) * ((X + sc - 1) / sc) * ((Y + sc - 1) / sc) *
                                          sizeof(float)
@@ -332,7 +329,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
     // the tensor-core forms stage interior bricks by TMA from a row-padded copy when rows are not 16-byte multiples
     const int ypad = (Y + 3) & ~3;
     const size_t vpad_bytes = tc_fwd && h->feature != 2 && ypad != Y ? (size_t)T * X * ypad * sizeof(float) : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + sp_bytes + vpad_bytes;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + vpad_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
@@ -409,21 +406,6 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
             return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
         if ((e = cudaMemcpy(h->f32_wt, wt.data(), wt_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
-            free_scratch(h);
-            delete h;
-            return cuda_fail(nullptr, e, "cudaMemcpy");
-        }
-    }
-    if (sp_bytes) {
-        std::vector<float> tab(sal::spatial_table_floats(h->n));
-        sal::spatial_table_fill(h->n, h->taper, tab.data());
-        if ((e = cudaMalloc(&h->sp_tab, sp_bytes)) != cudaSuccess) {
-            free_scratch(h);
-            delete h;
-            cudaGetLastError();
-            return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        }
-        if ((e = cudaMemcpy(h->sp_tab, tab.data(), sp_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
             free_scratch(h);
             delete h;
             return cuda_fail(nullptr, e, "cudaMemcpy");
@@ -517,6 +499,7 @@ constexpr size_t kBlocksCap = (size_t)2 << 30;  // brick-block scratch of the sp
 
 // Brick geometry of the spectral adjoint in the handle's precision.
 sal::SpectraAdjointGeometry adjoint_geometry(const sal_handle* h) {
+    if (h->feature == 2) return sal::spatial_adjoint_f32_geometry(h->n);
     return h->prec == SAL_FP32 ? sal::spectra_adjoint_f32_geometry(h->n) : sal::spectra_adjoint_tc_geometry(h->n);
 }
 
@@ -587,7 +570,10 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     }
     for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
-        e = h->prec == SAL_FP32
+        e = h->feature == 2
+                ? sal::spatial_adjoint_f32_launch(h->n, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary, t_begin, cnt,
+                                                  h->taper, st)
+            : h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, h->f32_wt, V, gE, h->blocks, h->T, h->X, h->Y,
                                                   h->boundary, h->feature, t_begin, sc, cnt, h->taper, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
@@ -610,7 +596,6 @@ sal_status sal_saliency_backward(sal_handle* h, const float* V, const float* W, 
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !W || !gS) return fail(h, SAL_ERR_INVALID_ARG, "V, W and gS must not be NULL");
-    if (h->feature == 2) return fail(h, SAL_ERR_UNSUPPORTED, "the spatial-domain reading has no backward");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
@@ -649,7 +634,6 @@ sal_status sal_local_spectra_project_backward(sal_handle* h, const float* V, con
     sal_status s = check_handle(h);
     if (s != SAL_OK) return s;
     if (!V || !gE || !gV) return fail(h, SAL_ERR_INVALID_ARG, "V, gE and gV must not be NULL");
-    if (h->feature == 2) return fail(h, SAL_ERR_UNSUPPORTED, "the spatial-domain reading has no backward");
     if ((s = ensure_backward_scratch(h)) != SAL_OK) return s;
     return spectral_adjoint(h, V, gE, gV, static_cast<cudaStream_t>(stream));
 }

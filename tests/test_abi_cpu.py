@@ -47,9 +47,9 @@ def _create(**kw):
     (dict(offsets=np.array([[1, 0, 0]]), gauss_w=np.array([np.nan]), dir_id=np.array([0])), salmod.SAL_ERR_INVALID_ARG),
     (dict(alpha=[np.inf, 1, 1]), salmod.SAL_ERR_INVALID_ARG),
     (dict(ls_delta=-1.0), salmod.SAL_ERR_INVALID_ARG),
-    # the spatial-domain reading of the feature step: FP32, n in {2, 4, 8}, stride 1
+    # the spatial-domain reading of the feature step: FP32, n in {2, 4, 8, 16}, stride 1
     (dict(n=8, feature="spatial", prec="bf16"), salmod.SAL_ERR_UNSUPPORTED),
-    (dict(n=16, feature="spatial"), salmod.SAL_ERR_UNSUPPORTED),
+    (dict(n=32, feature="spatial"), salmod.SAL_ERR_UNSUPPORTED),
     (dict(n=8, feature="spatial", stride=2), salmod.SAL_ERR_UNSUPPORTED),
 ])
 def test_create_rejects_bad_arguments_before_device_work(kw, status):

@@ -110,11 +110,12 @@ def test_reference_arm_on_a_section_counts_its_plane_and_uses_its_window(monkeyp
 
 
 def test_spatial_reading_flops_and_guard():
-    """The spatial reading's kernel applies the n^3 x n^3 circulant per map: 6 n^6 flop per voxel; the bench
-    runs it only in the form the library provides."""
+    """The spatial reading's kernels: 9 n^2 (forward) or 18 n^2 (adjoint) radix-2 line FFTs of 5 n log2 n
+    flops per window; the bench runs them only in the form the library provides."""
     import subprocess
     import sys
-    assert [bench.k1_flops_per_voxel_spatial(n) for n in (2, 4, 8)] == [384, 24576, 1572864]
+    assert [bench.k1_flops_per_voxel_spatial(n) for n in (2, 4, 8, 16)] == [360, 5760, 69120, 737280]
+    assert bench.k1_flops_per_voxel_spatial(16, adjoint=True) == 2 * 737280
     r = subprocess.run([sys.executable, bench.__file__, "--feature", "spatial", "--prec", "bf16", "--form", "fwd",
                         "--workload", "fault48"], capture_output=True, text=True, timeout=120)
     assert r.returncode != 0 and "--feature spatial runs in FP32" in r.stderr
