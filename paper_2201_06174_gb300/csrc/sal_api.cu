@@ -28,7 +28,8 @@ struct sal_handle {
     void* small = nullptr;   // one allocation holding the reduction scratch
     void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
     void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
-    float* f32_wt = nullptr;    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
+    float* f32_wt = nullptr;
+    float* sp_tab = nullptr;    // spatial-domain reading: the Eq. 1 ratio table    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
     float* vpad = nullptr;      // V with rows padded to ypad floats (tensor-core forms, Y not a multiple of 4)
     int ypad = 0;
     // backward scratch, allocated by the first sal_saliency_backward call
@@ -69,6 +70,8 @@ void free_scratch(sal_handle* h) {
     h->tc_tables = h->adj_tables = nullptr;
     if (h->f32_wt) cudaFree(h->f32_wt);
     h->f32_wt = nullptr;
+    if (h->sp_tab) cudaFree(h->sp_tab);
+    h->sp_tab = nullptr;
     if (h->vpad) cudaFree(h->vpad);
     h->vpad = nullptr;
     if (h->err_host) cudaFreeHost((void*)h->err_host);
@@ -129,7 +132,7 @@ cudaError_t launch_k1(sal_handle* h, const float* V, float* E, cudaStream_t st) 
     float* out = s > 1 ? h->Ec : E;
     cudaError_t e;
     if (h->feature == 2) {
-        e = sal::spatial_f32_launch(h->n, V, E, h->T, h->X, h->Y, h->boundary, h->taper, st);
+        e = sal::spatial_f32_launch(h->n, h->sp_tab, V, E, h->T, h->X, h->Y, h->boundary, h->taper, st);
     } else if (h->n == 32) {
         e = h->prec == SAL_FP32
                 ? sal::spectra_f32_n32_launch(h->tw, V, out, h->T, h->X, h->Y, h->boundary, h->feature, s, h->taper, st)
@@ -322,6 +325,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
     const size_t adj_bytes = tc_fwd ? sal::spectra_adjoint_tc_tables_bytes(h->n) : 0;
     const bool f32_tab = h->prec == SAL_FP32 && sal::spectra_f32_supported(h->n) && h->feature != 2;
     const size_t wt_bytes = f32_tab ? sal::f32_weight_table_floats(h->n) * sizeof(float) : 0;
+    const size_t sp_bytes = h->feature == 2 ? sal::spatial_weight_table_floats(h->n) * sizeof(float) : 0;
     const int sc = p->stride;
     const size_t ec_bytes = sc > 1 ? (size_t)3 * ((T + sc - 1) / sc) * ((X + sc - 1) / sc) * ((Y + sc - 1) / sc) *
                                          sizeof(float)
@@ -329,7 +333,7 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
     // the tensor-core forms stage interior bricks by TMA from a row-padded copy when rows are not 16-byte multiples
     const int ypad = (Y + 3) & ~3;
     const size_t vpad_bytes = tc_fwd && h->feature != 2 && ypad != Y ? (size_t)T * X * ypad * sizeof(float) : 0;
-    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + vpad_bytes;
+    const size_t need = 2 * plane3 + small + tab_bytes + adj_bytes + ec_bytes + wt_bytes + sp_bytes + vpad_bytes;
     if (h->budget && need > h->budget) {
         delete h;
         return fail(nullptr, SAL_ERR_OOM, "scratch (" + std::to_string(need) + " B) exceeds hbm_budget_bytes");
@@ -406,6 +410,21 @@ sal_status sal_create(const sal_params* p_in, int T, int X, int Y, sal_handle** 
             return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
         if ((e = cudaMemcpy(h->f32_wt, wt.data(), wt_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            return cuda_fail(nullptr, e, "cudaMemcpy");
+        }
+    }
+    if (sp_bytes) {
+        std::vector<float> rt(sal::spatial_weight_table_floats(h->n));
+        sal::spatial_weight_table_fill(h->n, rt.data());
+        if ((e = cudaMalloc(&h->sp_tab, sp_bytes)) != cudaSuccess) {
+            free_scratch(h);
+            delete h;
+            cudaGetLastError();
+            return fail(nullptr, SAL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        if ((e = cudaMemcpy(h->sp_tab, rt.data(), sp_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
             free_scratch(h);
             delete h;
             return cuda_fail(nullptr, e, "cudaMemcpy");
@@ -571,7 +590,7 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
     for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->feature == 2
-                ? sal::spatial_adjoint_f32_launch(h->n, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary, t_begin, cnt,
+                ? sal::spatial_adjoint_f32_launch(h->n, h->sp_tab, V, gE, h->blocks, h->T, h->X, h->Y, h->boundary, t_begin, cnt,
                                                   h->taper, st)
             : h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, h->f32_wt, V, gE, h->blocks, h->T, h->X, h->Y,

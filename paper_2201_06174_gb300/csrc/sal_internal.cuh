@@ -72,11 +72,14 @@ cudaError_t spectra_f32_launch(int n, const TwiddleTable& tw, const float* wtab,
                                int X, int Y, int bnd, int feat, int stride, int taper, cudaStream_t s);
 size_t f32_weight_table_floats(int n);
 // The spatial-domain reading of the feature step (FP32, n in {2, 4, 8, 16}, stride 1): per-window separable
-// FFTs in shared memory (spatial_f32_prepare sets their shared-memory limits; once per device).
+// FFTs in shared memory (spatial_f32_prepare sets their shared-memory limits; once per device).  rtab: the
+// Eq. 1 ratio table (spatial_weight_table_fill, host; 16-byte aligned device copy).
 bool spatial_f32_supported(int n);
+size_t spatial_weight_table_floats(int n);
+void spatial_weight_table_fill(int n, float* out);
 cudaError_t spatial_f32_prepare();
-cudaError_t spatial_f32_launch(int n, const float* V, float* E, int T, int X, int Y, int bnd, int taper,
-                               cudaStream_t s);
+cudaError_t spatial_f32_launch(int n, const float* rtab, const float* V, float* E, int T, int X, int Y, int bnd,
+                               int taper, cudaStream_t s);
 void f32_weight_table_fill(int n, int feat, float* out);   // host
 // The lattice features of stride s to every voxel of E [3][T][X][Y] (trilinear, held past the last point),
 // and its adjoint: the lattice points of gEl (full-size, zero elsewhere) gather the gradients gE.
@@ -151,8 +154,9 @@ SpectraAdjointGeometry spectra_adjoint_tc_geometry(int n);
 // The adjoint of the spatial-domain reading: brick blocks of the same layout as K5's (geometry below), bricks
 // of the planes t_begin .. t_begin + t_count - 1 (stride 1)
 SpectraAdjointGeometry spatial_adjoint_f32_geometry(int n);
-cudaError_t spatial_adjoint_f32_launch(int n, const float* V, const float* gE, float* blocks, int T, int X, int Y,
-                                       int bnd, int t_begin, int t_count, int taper, cudaStream_t s);
+cudaError_t spatial_adjoint_f32_launch(int n, const float* rtab, const float* V, const float* gE, float* blocks,
+                                       int T, int X, int Y, int bnd, int t_begin, int t_count, int taper,
+                                       cudaStream_t s);
 cudaError_t spectra_adjoint_tc_launch(int n, int fmt, const TwiddleTable& tw, const void* tables, const float* V,
                                       const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
                                       int t_begin, int t_step, int t_count, const float* Vt, int Yt, int* err,
