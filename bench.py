@@ -211,6 +211,21 @@ def k1_flops_per_voxel_sliding(n: int) -> int:
     return 4 * h * n + 8 * h * n * n + 8 * h * n * n + 8 * h * n ** 3 // K1_F32_SLIDING_RUN[n]
 
 
+K5_F32_SLIDING_RUN = {8: 4, 16: 8}   # outputs per thread run of the FP32 adjoint (its YC)
+
+
+def k5_flops_per_voxel_sliding(n: int) -> int:
+    """Algorithmic flops per voxel of the FP32 adjoint with both y-passes sliding (rect taper, n = 8, 16), run
+    of r outputs per (k_t, k_x) row: the forward recompute (stages t, x; along y the direct sum for the
+    run's first output and one complex multiply-add per bin for the others), then the adjoints of the three
+    stages: along y per output one complex add per bin (the prefix sums) and, per run, r - 1 + n point
+    evaluations of n bins (8n flops each); along x 8hn^2, along t 4hn."""
+    h, r = n // 2 + 1, K5_F32_SLIDING_RUN[n]
+    fwd = 4 * h * n + 8 * h * n * n + 8 * h * n * n + 8 * h * n ** 3 // r
+    inv_y = h * n * (2 * n + 8 * n * (r - 1 + n) // r)
+    return fwd + inv_y + 8 * h * n * n + 4 * h * n
+
+
 def max_sm_clock_mhz(gpu_id):
     """The device's maximum SM clock (nvidia-smi clocks.max.sm), or None."""
     cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
@@ -610,19 +625,19 @@ def main():
     if args.form == "fwdbwd":
         k5_ms = per_call[names.index("k5_local_spectra_project_backward")] / args.steps
         # the timed call is memset + K5 + the overlap-add gather; the traffic entry is K5's own
-        # the FP32 adjoint at n = 16 recomputes the forward stage 3 by the sliding recursion: its flops are
-        # the sliding forward's plus the direct adjoint's; otherwise twice the direct forward's
-        k5_sliding = args.prec == "fp32" and n == 16 and not spatial
+        # the FP32 adjoint at n = 8, 16 runs both y-passes as sliding recursions (k5_flops_per_voxel_sliding);
+        # otherwise its flops are twice the direct forward's
+        k5_sliding = args.prec == "fp32" and n in K5_F32_SLIDING_RUN and not spatial
         k5_name = "k5_spatial_adjoint_f32" if spatial else f"k5_spectra_adjoint_{tag}"
         rl = roofline(f"{k5_name} (call incl. memset and the two overlap-add passes)", args.prec, n, nvox, k5_ms,
                       1 if k5_sliding or spatial else 2, K5_TRAFFIC.get(trk),
                       mufu_op="rsqrt" if args.prec != "fp32" else "sqrt", feature=args.feature,
                       flops_per_voxel=(k1_flops_per_voxel_spatial(n, adjoint=True) if spatial else
-                                       k1_flops_per_voxel_sliding(n) + k1_flops_per_voxel(n) if k5_sliding else None))
+                                       k5_flops_per_voxel_sliding(n) if k5_sliding else None))
         if spatial:
             rl["form"] = "spatial reading's adjoint: forward recompute, signs, combined inverse (flops of that form)"
         if k5_sliding:
-            rl["form"] = "forward recompute by the sliding DFT along y (flops of that form)"
+            rl["form"] = "forward recompute and inverse along y by sliding recursions (flops of that form)"
         if args.prec != "fp32" and sc == 1 and n in (8, 16) and not spatial:
             rl["tensor_issue"] = tensor_issue("k5", n, V.shape, k5_ms)
         rl["k1"] = k1_rl

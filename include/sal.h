@@ -74,9 +74,9 @@ typedef struct {
                                r_m(k)^2 |F[k]|^2 (the mean of |F_m|^2, the energy reading of
                                that garbled step); both forward and backward, all precisions;
                                2 = E_m = (1/n^3) sum_u |f_m[u]|, f_m the inverse DFT of F_m (its
-                               spatial-domain reading): FP32, n in {2, 4, 8}, stride 1, forward
-                               only (other combinations: SAL_ERR_UNSUPPORTED at sal_create, and
-                               the backward calls return SAL_ERR_UNSUPPORTED)           */
+                               spatial-domain reading): FP32, n in {2, 4, 8, 16}, stride 1,
+                               forward and backward (other combinations:
+                               SAL_ERR_UNSUPPORTED at sal_create)                        */
     /* Directional center-surround window (Eq. 3, Fig. 4): Q = n_offsets neighbours
        o = (dt,dx,dy), |dt|,|dx|,|dy| <= 8, with weight w_o = alpha[dir_id[o]] * gauss_w[o].
        Host pointers; copied by sal_create.  n_offsets = 0: sal_create builds the window

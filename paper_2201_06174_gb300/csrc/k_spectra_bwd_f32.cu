@@ -265,10 +265,16 @@ __device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int
     }
 }
 
-// EN: the energy reading of the feature (Gamma = 2 rho F, no kink band); SL: the forward stage 3 by the
-// sliding recursion along y (rect taper, n = 16; at n = 8 the direct sum is as fast, with 30 fewer
-// registers): the first output of each thread's run by the direct sum,
-// then F_{y0+1}[k] = e^{2 pi i k/n} (F_{y0}[k] - G2[y0 - n/2] + G2[y0 + n/2]) (the forward kernel's form).
+// EN: the energy reading of the feature (Gamma = 2 rho F, no kink band).  SL: both y-passes slide (rect
+// taper, n = 8, 16).  With the phase anchored at the start y_r of the thread's run,
+//   Ft_j[k] = F_{y_r + j}[k] w^(k j) = sum_{y = j}^{j + n - 1} G2[y_r + y] w^(k y),   w = e^(-2 pi i / n),
+// the forward recompute is Ft_0 by the direct sum, then Ft_{j+1} = Ft_j + (G2[y_r + j + n] - G2[y_r + j]) w^(k j),
+// and |Ft| = |F|, so Gamma~_j = Gamma(Ft_j) = Gamma_j w^(k j) (the direction and the energy reading alike).
+// The inverse along y of the run, dG2[y_r + p] = sum_{j <= p < j + n} sum_k Gamma_j[k] e^(2 pi i k (p - j)/n),
+// is then z(P, p) = sum_k P[k] e^(2 pi i k p / n) of the sum P of Gamma~_j over the outputs j whose window
+// holds p: for a run of YC <= n outputs, with the prefix sums P_i = sum_{j <= i} Gamma~_j,
+//   p < YC - 1:  z(P_p, p);     YC - 1 <= p < n:  z(P_{YC-1}, p);     p = n + i:  z(P_{YC-1}, i) - z(P_i, i),
+// (z has period n in p): YC + n - 1 point evaluations of n bins per run instead of YC n.
 // The brick is staged as is: the small-bin level below is relative to the raw window's L1 norm.
 template <int N, bool EN, bool SL>
 __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
@@ -328,10 +334,31 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     const int ych = tid / ROWS;
     float wt[3][H];
     B::row_weights(wtab, row, wt);
+    if constexpr (!SL) {   // the sliding inverse writes every window position itself
 #pragma unroll
-    for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
+        for (int j = 0; j < WIN; ++j) s_win[j * NT + tid] = make_float2(0.f, 0.f);
+    }
+    static_assert(!SL || YC <= N, "the sliding inverse needs runs of at most n outputs");
     const float2* grow = s_g2 + (size_t)row * YH;
-    float fr[N], fi[N];   // F[k_y] of the current output, all n bins
+    float fr[N], fi[N];   // F[k_y] of the current output, all n bins (SL: Ft, the run-anchored phase)
+    // SL: prefix sums over the run's outputs of the pair coefficients below (the pairing is linear)
+    float par[H], pai[H], pbr[H], pbi[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) par[k] = pai[k] = pbr[k] = pbi[k] = 0.f;
+    // z(P, p): sum_k P[k] e^(2 pi i k p / n) from the pair coefficients of P, at run position p (mod n)
+    auto z_at = [&](int p, float& zr, float& zi) {
+        zr = 0.f;
+        zi = 0.f;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            zr = fmaf(par[k], tw.c[k][p], zr);
+            zi = fmaf(pai[k], tw.c[k][p], zi);
+            if (k != 0 && 2 * k != N) {
+                zr = fmaf(pbr[k], tw.s[k][p], zr);
+                zi = fmaf(pbi[k], tw.s[k][p], zi);
+            }
+        }
+    };
     // the whole row vanishes when its k_t or its k_x does
     const bool row_vanishes =
         !EN && (((vanish_mask(vt, 0, t0, N) >> (row / N)) | (vanish_mask(vt, 1, x0, N) >> (row % N))) & 1u);
@@ -367,15 +394,16 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
                 }
             }
         } else {
+            // Ft_yi = Ft_{yi-1} + (entering - leaving) w^(k (yi - 1)), w^(k m) = c - i sn
             const float2 a = grow[yl - 1], b = grow[yl - 1 + N];   // sample leaving, sample entering
             const float dr = b.x - a.x, di = b.y - a.y;
+            const int m = yi - 1;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-                const float c = k <= N / 2 ? tw.c[k][1] : tw.c[N - k][1];
-                const float sn = k <= N / 2 ? tw.s[k][1] : -tw.s[N - k][1];
-                const float xr = fr[k] + dr, xi = fi[k] + di;
-                fr[k] = fmaf(c, xr, -sn * xi);
-                fi[k] = fmaf(sn, xr, c * xi);
+                const float c = k <= N / 2 ? tw.c[k][m] : tw.c[N - k][m];
+                const float sn = k <= N / 2 ? tw.s[k][m] : -tw.s[N - k][m];
+                fr[k] = fmaf(dr, c, fmaf(di, sn, fr[k]));
+                fi[k] = fmaf(di, c, fmaf(-dr, sn, fi[k]));
             }
         }
         const float g0 = s_ge[yl], g1 = s_ge[BY + yl], g2 = s_ge[2 * BY + yl];
@@ -417,23 +445,58 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             if (small != 0u) small &= ~vanish_mask(vt, 2, y_start + yl, N);
             s_small[yi * NT + tid] = (uint16_t)small;
         }
-#pragma unroll
-        for (int u = 0; u < N; ++u) {
-            float zr = 0.f, zi = 0.f;
+        if constexpr (SL) {
+            // P_yi = P_{yi-1} + Gamma~_yi; position yi takes z(P_yi, yi), position n + yi its negative (the
+            // full sum's value is added below)
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                zr = fmaf(ar[k], tw.c[k][u], zr);
-                zi = fmaf(ai[k], tw.c[k][u], zi);
-                if (k != 0 && 2 * k != N) {
-                    zr = fmaf(br[k], tw.s[k][u], zr);
-                    zi = fmaf(bi[k], tw.s[k][u], zi);
-                }
+                par[k] += ar[k];
+                pai[k] += ai[k];
+                pbr[k] += br[k];
+                pbi[k] += bi[k];
             }
-            float2* w = s_win + (yi + u) * NT + tid;
-            float2 acc = *w;
-            acc.x += zr;
-            acc.y += zi;
-            *w = acc;
+            if (yi < YC - 1) {
+                float zr, zi;
+                z_at(yi, zr, zi);
+                s_win[yi * NT + tid] = make_float2(zr, zi);
+                s_win[(N + yi) * NT + tid] = make_float2(-zr, -zi);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+                float zr = 0.f, zi = 0.f;
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    zr = fmaf(ar[k], tw.c[k][u], zr);
+                    zi = fmaf(ai[k], tw.c[k][u], zi);
+                    if (k != 0 && 2 * k != N) {
+                        zr = fmaf(br[k], tw.s[k][u], zr);
+                        zi = fmaf(bi[k], tw.s[k][u], zi);
+                    }
+                }
+                float2* w = s_win + (yi + u) * NT + tid;
+                float2 acc = *w;
+                acc.x += zr;
+                acc.y += zi;
+                *w = acc;
+            }
+        }
+    }
+    if constexpr (SL) {
+        // the full sum P_{YC-1}: positions YC - 1 .. n - 1 take z(P_{YC-1}, p); positions n + i add z(P_{YC-1}, i)
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            float zr, zi;
+            z_at(p, zr, zi);
+            if (p < YC - 1) {
+                float2* w = s_win + (N + p) * NT + tid;
+                float2 acc = *w;
+                acc.x += zr;
+                acc.y += zi;
+                *w = acc;
+            } else {
+                s_win[p * NT + tid] = make_float2(zr, zi);
+            }
         }
     }
     if (!EN) resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge,
@@ -512,7 +575,7 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
     }
 }
 
-template <int N> constexpr bool kAdjointSliding = N >= 16;
+template <int N> constexpr bool kAdjointSliding = N >= 8;
 
 template <int N>
 cudaError_t prepare_n() {

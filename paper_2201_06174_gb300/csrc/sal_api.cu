@@ -28,8 +28,8 @@ struct sal_handle {
     void* small = nullptr;   // one allocation holding the reduction scratch
     void* tc_tables = nullptr;  // constant tensor-core operands of K1 (BF16/FP16 forms)
     void* adj_tables = nullptr; // constant tensor-core operands of K5 (FP16)
-    float* f32_wt = nullptr;
-    float* sp_tab = nullptr;    // spatial-domain reading: the Eq. 1 ratio table    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
+    float* f32_wt = nullptr;    // Eq. 1 weight table of the FP32 K1 / K5 (n <= 16)
+    float* sp_tab = nullptr;    // spatial-domain reading: the Eq. 1 ratio table
     float* vpad = nullptr;      // V with rows padded to ypad floats (tensor-core forms, Y not a multiple of 4)
     int ypad = 0;
     // backward scratch, allocated by the first sal_saliency_backward call

@@ -22,6 +22,15 @@ def test_sliding_form_flops_per_voxel(n):
     assert tx < bench.k1_flops_per_voxel_sliding(n) < bench.k1_flops_per_voxel(n)
 
 
+@pytest.mark.parametrize("n,flops", [(8, 20_800), (16, 150_912)])
+def test_sliding_adjoint_flops_per_voxel(n, flops):
+    """The FP32 adjoint with both y-passes sliding, counted by hand at n = 16 (h = 9, runs of 8 outputs):
+    forward 576 + 18432 + 18432 + 36864; inverse along y 144 (32 + 8 16 23 / 8); along x 18432, along t 576.
+    Below the cost of two direct forward passes, which it replaces."""
+    assert bench.k5_flops_per_voxel_sliding(n) == flops
+    assert bench.k5_flops_per_voxel_sliding(n) < 2 * bench.k1_flops_per_voxel(n)
+
+
 def test_bins_per_voxel():
     assert [bench.bins_per_voxel(n) for n in (8, 16, 32)] == [320, 2304, 17408]
 

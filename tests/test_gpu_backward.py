@@ -60,13 +60,17 @@ def test_spectral_adjoint_matches_oracle(sal, n, shape, boundary, slabs):
     gE = synth.random_volume((3,) + shape, seed=n + 7)
     budget = 0
     if slabs > 1:
+        # gE (3 planes), the reduction partials, n - 1 fixed overlap-add planes, and per t-plane of a slab
+        # the brick blocks (n slices of n x (BY + n - 1) floats, padded to 4) plus one overlap-add plane
         nseg = -(-shape[2] // _BY[n])
-        per_t = shape[1] * nseg * n * (-(-n * (_BY[n] + n - 1) // 4) * 4) * 4   # slices padded to 4 floats
+        per_ext = shape[1] * nseg * (-(-n * (_BY[n] + n - 1) // 4) * 4) * 4
+        per_t = n * per_ext
         base = sal.Saliency(shape, sal.Params(n=n, boundary=boundary))
         created = sal.sal_workspace_size(base.h)
         base.close()
         N = int(np.prod(shape))
-        budget = created + 3 * N * 4 + 1216 * 64 * 8 + per_t * max(1, shape[0] // slabs)
+        budget = (created + 3 * N * 4 + 1216 * 64 * 8 + (n - 1) * per_ext
+                  + (per_t + per_ext) * max(1, shape[0] // slabs))
     eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, hbm_budget_bytes=budget))
     try:
         gV = torch.empty(shape, dtype=torch.float32, device="cuda")

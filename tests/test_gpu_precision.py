@@ -123,14 +123,20 @@ def test_tensor_core_spectral_adjoint_matches_oracle(sal, prec, n, shape, bounda
     gE = synth.random_volume((3,) + shape, seed=n + 9)
     budget = 0
     if slabs > 1:
+        # the backward's scratch: gE (3 planes), the reduction partials, and per t-plane of a slab the brick
+        # blocks (n slices per brick, each XH x YH floats padded to a multiple of 4) plus one overlap-add plane
+        # of brick slices; n - 1 more such planes are fixed.  The budget holds T // slabs planes of a slab.
         P = 128 // n
         nxs, nys = -(-shape[1] // P), -(-shape[2] // 16)
-        per_t = nxs * nys * n * (P + n - 1) * (16 + n - 1) * 4
+        slice_f = -(-(P + n - 1) * (16 + n - 1) // 4) * 4
+        per_ext = nxs * nys * slice_f * 4
+        per_t = n * per_ext
         base = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, prec=prec))
         created = sal.sal_workspace_size(base.h)
         base.close()
         N = int(np.prod(shape))
-        budget = created + 3 * N * 4 + 1216 * 64 * 8 + per_t * max(1, shape[0] // slabs)
+        budget = (created + 3 * N * 4 + 1216 * 64 * 8 + (n - 1) * per_ext
+                  + (per_t + per_ext) * max(1, shape[0] // slabs))
     eng = sal.Saliency(shape, sal.Params(n=n, boundary=boundary, prec=prec, hbm_budget_bytes=budget))
     try:
         gV = torch.empty(shape, dtype=torch.float32, device="cuda")
