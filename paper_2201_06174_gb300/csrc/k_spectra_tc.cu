@@ -247,6 +247,14 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
                 const int b = pass & 1;
                 const bool full = cwait(b, b ? pf1 : pf0);
                 if (b) pf1 ^= 1u; else pf0 ^= 1u;
+                if (pass == G::PASSES - 1 && kt + 1 < H) {
+                    // the last pass's buffer is full, so every stage-3 MMA of kt has completed and A3 is free: the
+                    // D2 of kt + 1 (its stage-2 MMAs followed this pass's) goes into A3 before this pass's
+                    // epilogue, and the first stage-3 MMAs of kt + 1 run under that epilogue
+                    if (cwait(0, pf0)) tcs::d2_to_a3<N, FMT>(tmem, s_are, s_aim, q, lane, half);
+                    pf0 ^= 1u;
+                    arrive(4);
+                }
                 if (full) {
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {   // chunks half and half + 2 of this buffer
@@ -291,12 +299,6 @@ k1_spectra_tc(const float* __restrict__ V, float* __restrict__ E, int T, int X, 
                     }
                 }
                 arrive(2 + b);                                 // this warp is done with buffer b
-            }
-            if (kt + 1 < H) {
-                // stage 2 of kt + 1 done (and with it every stage-3 MMA of kt): A3 may be rewritten
-                if (cwait(0, pf0)) tcs::d2_to_a3<N, FMT>(tmem, s_are, s_aim, q, lane, half);
-                pf0 ^= 1u;
-                arrive(4);
             }
         }
     }
