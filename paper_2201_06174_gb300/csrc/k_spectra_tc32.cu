@@ -1,10 +1,19 @@
 // K1-TC for the 32^3 window (Sec. 2 steps 1-3; Eq. 2, Eq. 1): stage 3 (the DFT along y of every
 // (k_t, k_x) row) on the tensor cores, as for the smaller windows, with the shapes of n = 32:
 //   rows m = (x0 - xb) * 32 + k_x, 4 positions x 32 k_x = 128;
-//   B = the 32 paired twiddle columns [cos k = 0..16 | sin k = 1..15] over 32 taps: two K steps;
-//   one output y0 = 64 TMEM columns (real part of A x B | imaginary part of A x B);
+//   B = the 32 twiddle columns over 32 taps (two K steps), each bin's cosine and sine side by side:
+//     column 0: cos k = 0, column 1: cos k = 16 (the self-paired bins), columns 2j, 2j + 1: cos j, sin j;
+//   one output y0 = 64 TMEM columns (real part of A x B | imaginary part of A x B), read back in halves of
+//     16 columns that hold whole (cos, sin) pairs;
 //   the halo brick is staged in FP16 after a per-brick 1/max|V| scale (the FP32 brick of a 32^3
-//   window exceeds shared memory); stages 1-2 accumulate in FP32 on the SIMT pipes.
+//   window exceeds shared memory);
+//   stage 1 (t) per k_t on the SIMT pipes (FP32 sums over the 32 taps), written as the stage-2 B operand
+//     B2[(re|im, y)][(cos|sin, x)] = [[G1r, G1i], [G1i, -G1r]] (16-bit, K-major, x over a 40-row halo);
+//   stage 2 (x) on the tensor cores as in the smaller windows: A2 = the Toeplitz twiddles
+//     h(x - x0) [cos | sin](2 pi k_x (x - x0) / n), built once per CTA, so one MMA chain (K = 80, N = 96)
+//     gives Re G2 and Im G2 of every (x0, k_x) row and halo column y; D2 is rounded into the stage-3 A.
+// 16 warps (one CTA per SM: the halo fills shared memory): the SIMT stage needs the warps to hide its
+// latency; in the epilogue the four warps of a tensor-memory lane quarter take two outputs of each pass.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -21,22 +30,31 @@ constexpr int N = 32, H = N / 2 + 1, P = 128 / N, BY = 16;
 constexpr int XH = P + N - 1, YH = BY + N - 1;
 constexpr int KROWS = BY + N - 1;                        // window start + 32 taps
 constexpr uint32_t SBO_A = KROWS * 16;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr uint32_t kTmemCols = 512;                      // 8 outputs x 64 columns
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+constexpr int XHP = 40;                                  // x halo rows of stage 2 (>= XH, multiple of 8)
+constexpr int YP = 48;                                   // y columns of stage 2 (>= YH, multiple of 8)
+constexpr int K2 = 2 * XHP;                              // stage-2 K: cos taps | sin taps
+constexpr int N2 = 2 * YP;                               // stage-2 N: re | im over y
+constexpr uint32_t SBO_K2 = K2 / 8 * 128;                // 8-row group stride of the K-major A2 / B2
 constexpr size_t IN_B = (size_t)N * XH * YH * 2;         // FP16 halo
-constexpr size_t G1_B = (size_t)XH * YH * 8;
+constexpr size_t B2_B = (size_t)N2 / 8 * SBO_K2;         // stage-2 B (one k_t)
+constexpr size_t A2_B = (size_t)16 * SBO_K2;             // stage-2 A (128 rows)
 constexpr size_t A_B = (size_t)16 * SBO_A;
 constexpr size_t B_B = 2048;
 constexpr size_t WT_B = (size_t)N * H * 3 * 4;
-constexpr size_t OFF_G1 = (IN_B + 127) / 128 * 128;
-constexpr size_t OFF_A = (OFF_G1 + G1_B + 127) / 128 * 128;
+constexpr size_t OFF_B2 = (IN_B + 127) / 128 * 128;
+constexpr size_t OFF_A2 = OFF_B2 + B2_B;
+constexpr size_t OFF_A = OFF_A2 + A2_B;
 constexpr size_t OFF_B = OFF_A + 2 * A_B;
 constexpr size_t OFF_WT = OFF_B + B_B;
 constexpr size_t OFF_MISC = OFF_WT + WT_B;
 constexpr size_t SMEM = OFF_MISC + 64 + (kThreads / 32) * 4;
 static_assert(SMEM <= 227 * 1024, "shared memory");
+static_assert(XH <= XHP && YH <= YP && N2 <= 256 && N2 % 16 == 0, "stage-2 shapes");
+static_assert(OFF_B2 % 128 == 0 && OFF_A2 % 128 == 0 && OFF_A % 16 == 0, "operand alignment");
 
 template <int FMT> struct Pack;
 template <> struct Pack<1> {
@@ -58,7 +76,8 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
                 const __grid_constant__ Tw<N> tw, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __half* s_in = reinterpret_cast<__half*>(smem);                     // [N][XH][YH], scaled
-    float2* s_g1 = reinterpret_cast<float2*>(smem + OFF_G1);            // [XH][YH]
+    unsigned char* s_b2 = smem + OFF_B2;                                // stage-2 B (K-major)
+    unsigned char* s_a2 = smem + OFF_A2;                                // stage-2 A (K-major)
     unsigned char* s_are = smem + OFF_A;
     unsigned char* s_aim = smem + OFF_A + A_B;
     unsigned char* s_b = smem + OFF_B;                                  // [32 n][32 k], K-major
@@ -78,14 +97,28 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     }
     for (int i = tid; i < 32 * 32; i += kThreads) {
         const int n = i / 32, k = i % 32;
-        float v = 0.f;
-        if (n < H) v = tw.c[n][k];
-        else v = tw.s[n - H + 1][k];
+        const float v = n == 0 ? tw.c[0][k] : n == 1 ? tw.c[N / 2][k] : (n & 1) ? tw.s[n / 2][k] : tw.c[n / 2][k];
         *reinterpret_cast<uint16_t*>(s_b + (n / 8) * 512 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2) =
             Pack<FMT>::one(v);
     }
     for (int i = tid; i < (int)(2 * A_B / 16); i += kThreads)
         reinterpret_cast<uint4*>(s_are)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // B2 rows and columns past the halo stay zero (A2 is zero there too, but 0 x garbage could be NaN)
+    for (int i = tid; i < (int)(B2_B / 16); i += kThreads)
+        reinterpret_cast<uint4*>(s_b2)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // A2[(x0l, k_x)][k2]: k2 < XHP: cos, else sin, of (k_x, x - x0l), x = k2 % XHP; zero outside the window
+    for (int i = tid; i < 128 * K2; i += kThreads) {
+        const int mm = i / K2, k2 = i % K2;
+        const int x0 = mm / N, kxx = mm % N, u = k2 % XHP - x0;
+        float v = 0.f;
+        if (u >= 0 && u < N) {
+            const bool lo = kxx <= N / 2;
+            const int kk = lo ? kxx : N - kxx;
+            v = k2 < XHP ? tw.c[kk][u] : (lo ? tw.s[kk][u] : -tw.s[kk][u]);
+        }
+        *reinterpret_cast<uint16_t*>(s_a2 + (mm / 8) * SBO_K2 + (k2 / 8) * 128 + (mm % 8) * 16 + (k2 % 8) * 2) =
+            Pack<FMT>::one(v);
+    }
     // the halo's maximum first (two passes over global memory; the second converts to FP16)
     float vmax = 0.f;
     for (int r = tid; r < N * XH * YH; r += kThreads) {
@@ -117,12 +150,12 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
         s_in[r] = __float2half_rn(v * inv_scale);
     }
 
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, sub = warp >> 2;   // lane quarter; outputs sub and sub + 4 of each pass
     const int m = 32 * q + lane;
     const int x0l = m / N, kx = m % N;
-    float acc[8][3];
+    float acc[4][3];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
     const uint32_t idesc = tc::idesc_f16(FMT, 128, 32, 1, 0);
     const uint32_t bsm = tc::smem_u32(s_b), are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
     uint32_t phase = 0;
@@ -134,7 +167,7 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             cr[u] = tw.c[kt][u];
             sr[u] = tw.s[kt][u];
         }
-        __syncthreads();   // the halo is staged; the previous tile is done with s_g1 and s_wt
+        __syncthreads();   // the halo is staged; the previous tile is done with B2, A3 and s_wt
         for (int i = tid; i < N * H; i += kThreads) {
             const int k = i % H, x = i / H;
             const int ii = kt, j = x < N / 2 ? x : x - N;
@@ -145,6 +178,8 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             s_wt[i * 3 + 1] = w1;
             s_wt[i * 3 + 2] = w2;
         }
+        // stage 1 (t): G1 = P - iQ of every halo position, into B2 (K-major: byte(ncol, k2) = (ncol/8) SBO_K2 +
+        // (k2/8) 128 + (ncol%8) 16 + (k2%8) 2; ncol = y (re) or YP + y (im), k2 = x (cos) or XHP + x (sin))
         for (int it = tid; it < XH * YH; it += kThreads) {
             float Pv = 0.f, Qv = 0.f;
 #pragma unroll
@@ -153,42 +188,58 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
                 Pv = fmaf(v, cr[u], Pv);
                 Qv = fmaf(v, sr[u], Qv);
             }
-            s_g1[it] = make_float2(Pv, -Qv);
-        }
-        __syncthreads();
-        // stage 2 -> A operand: row m = xl * 32 + k_x at K row y (2-byte stores)
-        for (int it = tid; it < P * YH; it += kThreads) {
-            const int xl = it / YH, y = it % YH;
-            float2 g[N];
-#pragma unroll
-            for (int u = 0; u < N; ++u) g[u] = s_g1[(xl + u) * YH + y];
-            unsigned char* rowre = s_are + (size_t)(xl * 4) * SBO_A + (size_t)y * 16;
-            unsigned char* rowim = s_aim + (size_t)(xl * 4) * SBO_A + (size_t)y * 16;
-#pragma unroll
-            for (int k = 0; k < H; ++k) {
-                float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    pr = fmaf(g[u].x, tw.c[k][u], pr);
-                    pi = fmaf(g[u].y, tw.c[k][u], pi);
-                    if (k != 0 && 2 * k != N) {
-                        qr = fmaf(g[u].x, tw.s[k][u], qr);
-                        qi = fmaf(g[u].y, tw.s[k][u], qi);
-                    }
-                }
-                const size_t oa = (size_t)(k / 8) * SBO_A + (k % 8) * 2;
-                *reinterpret_cast<uint16_t*>(rowre + oa) = Pack<FMT>::one(pr + qi);
-                *reinterpret_cast<uint16_t*>(rowim + oa) = Pack<FMT>::one(pi - qr);
-                if (k != 0 && 2 * k != N) {
-                    const int kb = N - k;
-                    const size_t ob = (size_t)(kb / 8) * SBO_A + (kb % 8) * 2;
-                    *reinterpret_cast<uint16_t*>(rowre + ob) = Pack<FMT>::one(pr - qi);
-                    *reinterpret_cast<uint16_t*>(rowim + ob) = Pack<FMT>::one(pi + qr);
-                }
-            }
+            const int x = it / YH, y = it % YH;
+            const size_t o_re = (size_t)(y / 8) * SBO_K2 + (y % 8) * 16;
+            const size_t o_im = (size_t)((YP + y) / 8) * SBO_K2 + ((YP + y) % 8) * 16;
+            const size_t k_c = (size_t)(x / 8) * 128 + (x % 8) * 2;
+            const size_t k_s = (size_t)((XHP + x) / 8) * 128 + ((XHP + x) % 8) * 2;
+            *reinterpret_cast<uint16_t*>(s_b2 + o_re + k_c) = Pack<FMT>::one(Pv);
+            *reinterpret_cast<uint16_t*>(s_b2 + o_re + k_s) = Pack<FMT>::one(-Qv);
+            *reinterpret_cast<uint16_t*>(s_b2 + o_im + k_c) = Pack<FMT>::one(-Qv);
+            *reinterpret_cast<uint16_t*>(s_b2 + o_im + k_s) = Pack<FMT>::one(-Pv);
         }
         tc::fence_async_smem();
+        tc::fence_before_sync();
         __syncthreads();
+        // stage 2 (x) on the tensor cores: D2[(x0, k_x)][(re | im, y)] = A2 B2 in tensor-memory columns [0, N2)
+        {
+            if (tid == 0 && !*s_fail) {
+                tc::fence_after_sync();
+                const uint32_t idesc2 = tc::idesc_f16(FMT, 128, N2, 0, 0);
+                const uint64_t a2d = tc::desc_noswizzle(tc::smem_u32(s_a2), 128, SBO_K2);
+                const uint64_t b2d = tc::desc_noswizzle(tc::smem_u32(s_b2), 128, SBO_K2);
+#pragma unroll
+                for (int ks = 0; ks < K2 / 16; ++ks)
+                    tc::mma_f16(tmem, tc::desc_add(a2d, 256 * ks), tc::desc_add(b2d, 256 * ks), idesc2, ks > 0 ? 1u : 0u);
+                tc::mma_commit(tc::smem_u32(s_mbar));
+            }
+            const int failed_before = *s_fail;
+            const bool ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(s_mbar), phase, kWaitLimit);
+            const int bad = __syncthreads_or(!ok);
+            if (bad && tid == 0 && !failed_before) {
+                atomicOr(err, 1);
+                *s_fail = 1;
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
+            // D2 -> the stage-3 A operands (row m at K row y, 2-byte stores): three warps per lane quarter, one
+            // 32-column chunk each (columns [0, YP): real part over y, [YP, 2 YP): imaginary part)
+            if (!bad && sub < 3) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * sub), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = 32 * sub + i, part = c / YP, y = c % YP;
+                    if (y < YH) {
+                        unsigned char* dst = (part ? s_aim : s_are) + (size_t)(m / 8) * SBO_A + (size_t)y * 16 + (m % 8) * 2;
+                        *reinterpret_cast<uint16_t*>(dst) = Pack<FMT>::one(v[i]);
+                    }
+                }
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+        }
         float wt[3][H];
 #pragma unroll
         for (int k = 0; k < H; ++k) {
@@ -225,30 +276,36 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             tc::fence_after_sync();
             if (!bad) {
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int j = half + 2 * jj;
-                    float vr[32], vi[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * 64), vr);
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * 64 + 32), vi);
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int j = sub + 4 * jj;
                     float e0 = 0.f, e1 = 0.f, e2 = 0.f;
 #pragma unroll
-                    for (int k = 0; k < H; ++k) {
-                        const float pr = vr[k], pi = vi[k];
-                        float a;
-                        if (k == 0 || 2 * k == N) {
-                            a = bin_mag<EN>(fmaf(pr, pr, pi * pi));
-                        } else {
-                            const float qr = vr[H + k - 1], qi = vi[H + k - 1];
-                            const float ar = pr + qi, ai = pi - qr, br = pr - qi, bi = pi + qr;
-                            a = bin_mag<EN>(fmaf(ar, ar, ai * ai)) + bin_mag<EN>(fmaf(br, br, bi * bi));
+                    for (int h = 0; h < 2; ++h) {   // columns 16 h .. 16 h + 15: bins k = 8 h .. 8 h + 7
+                        float vr[16], vi[16];
+                        tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * 64 + 16 * h), vr);
+                        tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * 64 + 32 + 16 * h), vi);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const int k = 8 * h + c;
+                            const float pr = vr[2 * c], pi = vi[2 * c], qr = vr[2 * c + 1], qi = vi[2 * c + 1];
+                            if (k == 0) {   // columns 0, 1: the self-paired bins 0 and n/2
+                                const float a0 = bin_mag<EN>(fmaf(pr, pr, pi * pi));
+                                const float a1 = bin_mag<EN>(fmaf(qr, qr, qi * qi));
+                                e0 = fmaf(wt[0][0], a0, fmaf(wt[0][H - 1], a1, e0));
+                                e1 = fmaf(wt[1][0], a0, fmaf(wt[1][H - 1], a1, e1));
+                                e2 = fmaf(wt[2][0], a0, fmaf(wt[2][H - 1], a1, e2));
+                            } else {        // bins k and n - k: P = pr + i pi, Q = qr + i qi
+                                const float ar = pr + qi, ai = pi - qr, br = pr - qi, bi = pi + qr;
+                                const float a = bin_mag<EN>(fmaf(ar, ar, ai * ai)) + bin_mag<EN>(fmaf(br, br, bi * bi));
+                                e0 = fmaf(wt[0][k], a, e0);
+                                e1 = fmaf(wt[1][k], a, e1);
+                                e2 = fmaf(wt[2][k], a, e2);
+                            }
                         }
-                        e0 = fmaf(wt[0][k], a, e0);
-                        e1 = fmaf(wt[1][k], a, e1);
-                        e2 = fmaf(wt[2][k], a, e2);
                     }
-                    acc[pass * 4 + jj][0] += e0;
-                    acc[pass * 4 + jj][1] += e1;
-                    acc[pass * 4 + jj][2] += e2;
+                    acc[pass * 2 + jj][0] += e0;
+                    acc[pass * 2 + jj][1] += e1;
+                    acc[pass * 2 + jj][2] += e2;
                 }
             }
             tc::fence_before_sync();
@@ -262,8 +319,8 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     const int x = xb + x0l;
     const float out_scale = EN ? scale * scale : scale;   // the features of the unscaled brick
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int y0 = (i / 4) * 8 + half + 2 * (i % 4);
+    for (int i = 0; i < 4; ++i) {
+        const int y0 = (i / 2) * 8 + sub + 4 * (i % 2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float s = acc[i][c];
