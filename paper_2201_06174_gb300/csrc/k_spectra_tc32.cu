@@ -50,7 +50,7 @@ constexpr size_t OFF_A2 = OFF_B2 + B2_B;
 constexpr size_t OFF_A = OFF_A2 + A2_B;
 constexpr size_t OFF_B = OFF_A + 2 * A_B;
 constexpr size_t OFF_WT = OFF_B + B_B;
-constexpr size_t OFF_MISC = OFF_WT + WT_B;
+constexpr size_t OFF_MISC = OFF_WT + 2 * WT_B;                 // the weight table, double-buffered by k_t
 constexpr size_t SMEM = OFF_MISC + 64 + (kThreads / 32) * 4;
 static_assert(SMEM <= 227 * 1024, "shared memory");
 static_assert(XH <= XHP && YH <= YP && N2 <= 256 && N2 % 16 == 0, "stage-2 shapes");
@@ -81,7 +81,7 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     unsigned char* s_are = smem + OFF_A;
     unsigned char* s_aim = smem + OFF_A + A_B;
     unsigned char* s_b = smem + OFF_B;                                  // [32 n][32 k], K-major
-    float* s_wt = reinterpret_cast<float*>(smem + OFF_WT);              // [k_x][k][3] of this tile
+    float* s_wt = reinterpret_cast<float*>(smem + OFF_WT);              // [2][k_x][k][3]: tiles k_t, k_t + 1
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + OFF_MISC);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + OFF_MISC + 8);
     int* s_fail = reinterpret_cast<int*>(smem + OFF_MISC + 16);
@@ -119,15 +119,36 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
         *reinterpret_cast<uint16_t*>(s_a2 + (mm / 8) * SBO_K2 + (k2 / 8) * 128 + (mm % 8) * 16 + (k2 % 8) * 2) =
             Pack<FMT>::one(v);
     }
-    // the halo's maximum first (two passes over global memory; the second converts to FP16)
+    // The halo brick, two passes over global memory (its maximum, then the scaled FP16 copy): a warp per
+    // (u_t, x) row of YH samples, each lane samples y = lane and lane + 32 (its two border-extended source
+    // columns fixed for the whole brick), RU rows in flight per warp.
+    constexpr int ROWS = N * XH, RU = 4;
+    const int gy0 = ext_index(yb - N / 2 + lane, Y, bnd);
+    const int gy1 = lane + 32 < YH ? ext_index(yb - N / 2 + lane + 32, Y, bnd) : -1;
+    auto halo_rows = [&](auto&& use) {
+        for (int r0 = warp * RU; r0 < ROWS; r0 += (kThreads / 32) * RU) {
+            float v0[RU], v1[RU];
+#pragma unroll
+            for (int a = 0; a < RU; ++a) {   // loads first
+                const int r = r0 + a;
+                v0[a] = v1[a] = 0.f;
+                if (r < ROWS) {
+                    const int gt = ext_index(t0 - N / 2 + r / XH, T, bnd);
+                    const int gx = ext_index(xb - N / 2 + r % XH, X, bnd);
+                    if ((gt | gx) >= 0) {
+                        const float* row = V + ((size_t)gt * X + gx) * Y;
+                        if (gy0 >= 0) v0[a] = __ldg(row + gy0);
+                        if (gy1 >= 0) v1[a] = __ldg(row + gy1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < RU; ++a)
+                if (r0 + a < ROWS) use(r0 + a, v0[a], v1[a]);
+        }
+    };
     float vmax = 0.f;
-    for (int r = tid; r < N * XH * YH; r += kThreads) {
-        const int yy = r % YH, xx = (r / YH) % XH, ut = r / (YH * XH);
-        const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-        const int gx = ext_index(xb - N / 2 + xx, X, bnd);
-        const int gy = ext_index(yb - N / 2 + yy, Y, bnd);
-        if ((gt | gx | gy) >= 0) vmax = fmaxf(vmax, fabsf(__ldg(V + ((size_t)gt * X + gx) * Y + gy)));
-    }
+    halo_rows([&](int, float a, float b) { vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b))); });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if (lane == 0) s_red[warp] = vmax;
@@ -140,15 +161,10 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     for (int w = 0; w < kThreads / 32; ++w) bmax = fmaxf(bmax, s_red[w]);
     const float scale = bmax > 0.f ? bmax : 1.f;
     const float inv_scale = 1.f / scale;
-    for (int r = tid; r < N * XH * YH; r += kThreads) {
-        const int yy = r % YH, xx = (r / YH) % XH, ut = r / (YH * XH);
-        const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-        const int gx = ext_index(xb - N / 2 + xx, X, bnd);
-        const int gy = ext_index(yb - N / 2 + yy, Y, bnd);
-        float v = 0.f;
-        if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-        s_in[r] = __float2half_rn(v * inv_scale);
-    }
+    halo_rows([&](int r, float a, float b) {   // s_in[u][x][y], row r = u XH + x
+        s_in[(size_t)r * YH + lane] = __float2half_rn(a * inv_scale);
+        if (lane + 32 < YH) s_in[(size_t)r * YH + lane + 32] = __float2half_rn(b * inv_scale);
+    });
 
     const int q = warp & 3, sub = warp >> 2;   // lane quarter; outputs sub and sub + 4 of each pass
     const int m = 32 * q + lane;
@@ -160,23 +176,25 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
     const uint32_t bsm = tc::smem_u32(s_b), are = tc::smem_u32(s_are), aim = tc::smem_u32(s_aim);
     uint32_t phase = 0;
 
-    for (int kt = 0; kt < H; ++kt) {
+    // The SIMT part of tile kt: its Eq. 1 weight table (buffer kt % 2) and stage 1 (t) into the stage-2 B
+    // operand.  Tile 0 runs before the loop; tile kt + 1 runs while the last stage-3 MMAs of tile kt execute.
+    auto prep_tile = [&](int kt) {
         float cr[N], sr[N];
 #pragma unroll
         for (int u = 0; u < N; ++u) {
             cr[u] = tw.c[kt][u];
             sr[u] = tw.s[kt][u];
         }
-        __syncthreads();   // the halo is staged; the previous tile is done with B2, A3 and s_wt
+        float* wtab = s_wt + (kt & 1) * (N * H * 3);
         for (int i = tid; i < N * H; i += kThreads) {
             const int k = i % H, x = i / H;
             const int ii = kt, j = x < N / 2 ? x : x - N;
             const float mult = (kt == 0 || 2 * kt == N) ? 1.f : 2.f;
             float w0, w1, w2;
             f32::bin_weights<EN>(ii, j, k, mult / (float)(N * N * N), w0, w1, w2);
-            s_wt[i * 3 + 0] = w0;
-            s_wt[i * 3 + 1] = w1;
-            s_wt[i * 3 + 2] = w2;
+            wtab[i * 3 + 0] = w0;
+            wtab[i * 3 + 1] = w1;
+            wtab[i * 3 + 2] = w2;
         }
         // stage 1 (t): G1 = P - iQ of every halo position, into B2 (K-major: byte(ncol, k2) = (ncol/8) SBO_K2 +
         // (k2/8) 128 + (ncol%8) 16 + (k2%8) 2; ncol = y (re) or YP + y (im), k2 = x (cos) or XHP + x (sin))
@@ -198,6 +216,12 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             *reinterpret_cast<uint16_t*>(s_b2 + o_im + k_c) = Pack<FMT>::one(-Qv);
             *reinterpret_cast<uint16_t*>(s_b2 + o_im + k_s) = Pack<FMT>::one(-Pv);
         }
+        tc::fence_async_smem();
+    };
+    __syncthreads();   // the halo is staged
+    prep_tile(0);
+
+    for (int kt = 0; kt < H; ++kt) {
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -240,14 +264,6 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             tc::fence_before_sync();
             __syncthreads();
         }
-        float wt[3][H];
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-            const float* w = s_wt + (kx * H + k) * 3;
-            wt[0][k] = w[0];
-            wt[1][k] = w[1];
-            wt[2][k] = w[2];
-        }
         for (int pass = 0; pass < 2; ++pass) {
             if (tid == 0 && !*s_fail) {
                 tc::fence_after_sync();
@@ -265,6 +281,9 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
                 }
                 tc::mma_commit(tc::smem_u32(s_mbar));
             }
+            // under the last MMAs of this tile: the next tile's weights and stage 1 (B2 and the other weight
+            // buffer are free: this tile's stage-2 MMAs have completed)
+            if (pass == 1 && kt + 1 < H) prep_tile(kt + 1);
             const int failed_before = *s_fail;
             const bool ok = failed_before ? false : tc::mbar_wait(tc::smem_u32(s_mbar), phase, kWaitLimit);
             const int bad = __syncthreads_or(!ok);
@@ -275,6 +294,15 @@ k1_spectra_tc32(const float* __restrict__ V, float* __restrict__ E, int T, int X
             phase ^= 1u;
             tc::fence_after_sync();
             if (!bad) {
+                float wt[3][H];   // this lane's Eq. 1 weights for (k_t, k_x), |k_y| = 0 .. n/2
+                const float* wtab = s_wt + (kt & 1) * (N * H * 3);
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    const float* w = wtab + (kx * H + k) * 3;
+                    wt[0][k] = w[0];
+                    wt[1][k] = w[1];
+                    wt[2][k] = w[2];
+                }
 #pragma unroll
                 for (int jj = 0; jj < 2; ++jj) {
                     const int j = sub + 4 * jj;
