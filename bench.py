@@ -49,7 +49,7 @@ WORKLOADS = {
                            cpu_sample=256, ref_sample=80),   # one plane: sample x sample voxels
     "full462x951x651": dict(spec="full462x951x651", n=16, desc="config 5: 462x951x651 synthetic seismic volume "
                             "(20 faults, 3 salt bodies, 4 sinuous channels, folds, noise 0.1 rms), window 16^3",
-                            cpu_sample=40, ref_sample=20, e2e_steps=5, side_steps=3),
+                            cpu_sample=40, ref_sample=20, e2e_steps=10, side_steps=3),
 }
 DEFAULT_WORKLOAD = "full462x951x651"   # the largest configuration that fits one GPU
 # Peaks of the ALU pipes, set by set_alu_peaks() from the device: the FP32 FMA pipe from its unit count

@@ -161,7 +161,8 @@ template <int N> struct BGeo {
     // [YC][NT] uint16 masks of the small bins each thread leaves to the exact recompute, then the source
     // rows of the cube along t and x ([N] + [N] ints, -1 outside a zero-extended volume)
     static constexpr size_t IDX_OFF = (SMALL_OFF + (size_t)YC * NT * 2 + 15) / 16 * 16;
-    static constexpr size_t SMEM = IDX_OFF + (size_t)2 * N * 4;
+    static constexpr size_t WB_OFF = IDX_OFF + (size_t)2 * N * 4;   // [NT / 32] owners of small bins, per warp
+    static constexpr size_t SMEM = WB_OFF + (size_t)(NT / 32) * 4;
     static_assert(N <= 16, "16-bit masks of small bins");
     static constexpr int SLICE = (N * YH + 3) / 4 * 4;           // u_t slices of the block, 16-byte aligned
     static constexpr int BLOCK_FLOATS = N * SLICE;               // scratch block per CTA
@@ -169,7 +170,8 @@ template <int N> struct BGeo {
 };
 
 // The small bins left by step 2 (s_small[yi][owner] bit k_y: output yi of the owner's run, bin k_y of its
-// (k_t, k_x) row), one warp at a time per owner: the lanes split the n^3 terms of the direct sum
+// (k_t, k_x) row), each owner's bins by one warp (the owners dealt round-robin to the CTA's warps in thread
+// order): the lanes split the n^3 terms of the direct sum
 // F = sum_u h(u) Vext[p + u - n/2] w^(k.u) (each lane a fixed u_y, four independent float-float
 // accumulators, the loads of four terms issued before their arithmetic) and reduce it; Gamma = rho F / |F|
 // (0 if max(|Re F|, |Im F|) <= 2^-36 A_p) and its inverse DFT along y, h(u) Gamma exp(+2 pi i k_y u / n),
@@ -179,7 +181,7 @@ __device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int
                                                 int taper, const uint16_t* s_small, const int* s_src, float2* s_win,
                                                 const float* s_ge, const float* s_l1,
                                                 const float* __restrict__ wtab, const Tw<N>& tw,
-                                                const Exact2f<N>& ex) {
+                                                const Exact2f<N>& ex, unsigned* s_wbits) {
     constexpr int N3 = N * N * N, PER = N3 >= 32 ? N3 / 32 : 1, STEP = 32 / N;   // terms per lane, (ut, ux) step
     constexpr int U = PER >= 4 ? 4 : PER;                                          // independent accumulators
     const int tid = threadIdx.x, lane = tid & 31;
@@ -187,79 +189,91 @@ __device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int
     // (u_t, u_x) = divmod(lane / N + STEP i, N)
     const int uy = lane % N, r0 = lane / N;
     const bool live = lane < N3;   // n = 2: 8 terms, lanes 8.. idle
+    // the owners (threads with small bins) in thread order, dealt round-robin to the CTA's warps: an owner's bins
+    // are processed by one warp in a fixed order (the same sums in the same order whichever warp it is), and
+    // owners that cluster in one warp no longer hold the rest of the CTA at the next barrier
+    constexpr int NW = NT / 32;
+    const int warp = tid >> 5;
     bool mine = false;
     for (int yi = 0; yi < YC; ++yi) mine = mine || s_small[yi * NT + tid] != 0;
-    unsigned todo = __ballot_sync(0xffffffffu, mine);
-    while (todo) {
-        const int o = (tid & ~31) + __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
-        for (int yi = 0; yi < YC; ++yi) {
-            unsigned msk = s_small[yi * NT + o];
-            const int yl = ych * YC + yi;
-            const int gy = ext_index(y_start + yl - N / 2 + uy, Y, bnd);
-            while (msk) {
-                const int ky = __ffs(msk) - 1;
-                msk &= msk - 1;
-                FF re[U], im[U];
-#pragma unroll
-                for (int a = 0; a < U; ++a) re[a] = im[a] = FF{0.f, 0.f};
-                const FF hy = {ex.hh[uy], ex.hl[uy]};
-                for (int i0 = 0; i0 < PER; i0 += U) {
-                    float v[U];
-                    int ph[U];
-                    FF h2[U];
-#pragma unroll
-                    for (int a = 0; a < U; ++a) {   // loads first, then the arithmetic
-                        const int rr = live ? r0 + STEP * (i0 + a) : 0, ut = rr / N, ux = rr % N;
-                        const int gt = s_src[ut], gx = s_src[N + ux];
-                        v[a] = (live && (gt | gx | gy) >= 0) ? __ldg(V + ((size_t)gt * X + gx) * Y + gy) : 0.f;
-                        ph[a] = (kt * ut + kx * ux + ky * uy) % N;
-                        h2[a] = taper ? ff_mul(FF{ex.hh[ut], ex.hl[ut]}, FF{ex.hh[ux], ex.hl[ux]}) : FF{1.f, 0.f};
-                    }
-#pragma unroll
-                    for (int a = 0; a < U; ++a) {
-                        FF c = {ex.ch[ph[a]], ex.cl[ph[a]]}, sn = {-ex.sh[ph[a]], -ex.sl[ph[a]]};
-                        if (taper) {
-                            const FF h3 = ff_mul(h2[a], hy);
-                            c = ff_mul(h3, c);
-                            sn = ff_mul(h3, sn);
+    const unsigned wb = __ballot_sync(0xffffffffu, mine);
+    if (lane == 0) s_wbits[warp] = wb;
+    __syncthreads();   // every owner's masks and every warp's owner bits visible
+    int idx = 0;   // index of the next owner in thread order
+    for (int w = 0; w < NW; ++w) {
+        unsigned todo = s_wbits[w];
+        while (todo) {
+            const int o = 32 * w + __ffs(todo) - 1;
+            todo &= todo - 1;
+            if (idx++ % NW != warp) continue;
+            const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
+            for (int yi = 0; yi < YC; ++yi) {
+                unsigned msk = s_small[yi * NT + o];
+                const int yl = ych * YC + yi;
+                const int gy = ext_index(y_start + yl - N / 2 + uy, Y, bnd);
+                while (msk) {
+                    const int ky = __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    FF re[U], im[U];
+    #pragma unroll
+                    for (int a = 0; a < U; ++a) re[a] = im[a] = FF{0.f, 0.f};
+                    const FF hy = {ex.hh[uy], ex.hl[uy]};
+                    for (int i0 = 0; i0 < PER; i0 += U) {
+                        float v[U];
+                        int ph[U];
+                        FF h2[U];
+    #pragma unroll
+                        for (int a = 0; a < U; ++a) {   // loads first, then the arithmetic
+                            const int rr = live ? r0 + STEP * (i0 + a) : 0, ut = rr / N, ux = rr % N;
+                            const int gt = s_src[ut], gx = s_src[N + ux];
+                            v[a] = (live && (gt | gx | gy) >= 0) ? __ldg(V + ((size_t)gt * X + gx) * Y + gy) : 0.f;
+                            ph[a] = (kt * ut + kx * ux + ky * uy) % N;
+                            h2[a] = taper ? ff_mul(FF{ex.hh[ut], ex.hl[ut]}, FF{ex.hh[ux], ex.hl[ux]}) : FF{1.f, 0.f};
                         }
-                        re[a] = ff_add(re[a], ff_mul1(v[a], c));
-                        im[a] = ff_add(im[a], ff_mul1(v[a], sn));
+    #pragma unroll
+                        for (int a = 0; a < U; ++a) {
+                            FF c = {ex.ch[ph[a]], ex.cl[ph[a]]}, sn = {-ex.sh[ph[a]], -ex.sl[ph[a]]};
+                            if (taper) {
+                                const FF h3 = ff_mul(h2[a], hy);
+                                c = ff_mul(h3, c);
+                                sn = ff_mul(h3, sn);
+                            }
+                            re[a] = ff_add(re[a], ff_mul1(v[a], c));
+                            im[a] = ff_add(im[a], ff_mul1(v[a], sn));
+                        }
                     }
+    #pragma unroll
+                    for (int a = 1; a < U; ++a) {
+                        re[0] = ff_add(re[0], re[a]);
+                        im[0] = ff_add(im[0], im[a]);
+                    }
+                    FF fre = re[0], fim = im[0];
+    #pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) {
+                        const FF r2 = {__shfl_xor_sync(0xffffffffu, fre.hi, d), __shfl_xor_sync(0xffffffffu, fre.lo, d)};
+                        const FF i2 = {__shfl_xor_sync(0xffffffffu, fim.hi, d), __shfl_xor_sync(0xffffffffu, fim.lo, d)};
+                        fre = ff_add(fre, r2);
+                        fim = ff_add(fim, i2);
+                    }
+                    const float mx = fmaxf(fabsf(fre.hi), fabsf(fim.hi));
+                    if (mx > kZeroBin * s_l1[yl] && lane < N) {
+                        const int k = ky <= N / 2 ? ky : N - ky;
+                        const float rho = fmaf(s_ge[yl], __ldg(wtab + k * ROWS + row),
+                                               fmaf(s_ge[BY + yl], __ldg(wtab + (H + k) * ROWS + row),
+                                                    s_ge[2 * BY + yl] * __ldg(wtab + (2 * H + k) * ROWS + row)));
+                        const float fr = fre.hi / mx, fi = fim.hi / mx;      // scaled first: no underflow
+                        const float sc = rho / sqrtf(fmaf(fr, fr, fi * fi));
+                        const float gr = sc * fr, gi = sc * fi;
+                        const int u = lane;
+                        const float c = tw.c[k][u], sn = ky <= N / 2 ? tw.s[k][u] : -tw.s[k][u];
+                        float2* w = s_win + (yi + u) * NT + o;
+                        float2 acc = *w;
+                        acc.x += gr * c - gi * sn;
+                        acc.y += gr * sn + gi * c;
+                        *w = acc;
+                    }
+                    __syncwarp();
                 }
-#pragma unroll
-                for (int a = 1; a < U; ++a) {
-                    re[0] = ff_add(re[0], re[a]);
-                    im[0] = ff_add(im[0], im[a]);
-                }
-                FF fre = re[0], fim = im[0];
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    const FF r2 = {__shfl_xor_sync(0xffffffffu, fre.hi, d), __shfl_xor_sync(0xffffffffu, fre.lo, d)};
-                    const FF i2 = {__shfl_xor_sync(0xffffffffu, fim.hi, d), __shfl_xor_sync(0xffffffffu, fim.lo, d)};
-                    fre = ff_add(fre, r2);
-                    fim = ff_add(fim, i2);
-                }
-                const float mx = fmaxf(fabsf(fre.hi), fabsf(fim.hi));
-                if (mx > kZeroBin * s_l1[yl] && lane < N) {
-                    const int k = ky <= N / 2 ? ky : N - ky;
-                    const float rho = fmaf(s_ge[yl], __ldg(wtab + k * ROWS + row),
-                                           fmaf(s_ge[BY + yl], __ldg(wtab + (H + k) * ROWS + row),
-                                                s_ge[2 * BY + yl] * __ldg(wtab + (2 * H + k) * ROWS + row)));
-                    const float fr = fre.hi / mx, fi = fim.hi / mx;      // scaled first: no underflow
-                    const float sc = rho / sqrtf(fmaf(fr, fr, fi * fi));
-                    const float gr = sc * fr, gi = sc * fi;
-                    const int u = lane;
-                    const float c = tw.c[k][u], sn = ky <= N / 2 ? tw.s[k][u] : -tw.s[k][u];
-                    float2* w = s_win + (yi + u) * NT + o;
-                    float2 acc = *w;
-                    acc.x += gr * c - gi * sn;
-                    acc.y += gr * sn + gi * c;
-                    *w = acc;
-                }
-                __syncwarp();
             }
         }
     }
@@ -499,8 +513,9 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             }
         }
     }
-    if (!EN) resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge,
-                                                        s_l1, wtab, tw, ex);
+    if (!EN)
+        resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge, s_l1,
+                                                   wtab, tw, ex, reinterpret_cast<unsigned*>(smem_raw + G::WB_OFF));
     __syncthreads();
 
     // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
