@@ -24,7 +24,8 @@
 // One CTA = one brick (t0, x0, y_start .. y_start+BY-1), same mapping as K1:
 //   1. stage brick, forward stages 1 and 2 (shared with K1);
 //   2. per (row, y0): forward stage 3 -> Gamma -> inverse DFT along y (pairing k, n-k), added
-//      into a private accumulation window of the thread (thread-interleaved shared memory);
+//      into a private accumulation window of the thread (thread-interleaved shared memory); for the rect
+//      cube at n = 8, 16 both y-passes slide over the thread's run of outputs (see SL below);
 //   3. windows of the y-chunks summed into Gamma_G2[k_t][k_x][y];
 //   4. adjoint of stage 2 (x) -> Gamma_G1[k_t][u_x][y];
 //   5. adjoint of stage 1 (t), real part -> the brick's block [u_t][u_x][y] of gVext, written to
