@@ -39,6 +39,13 @@ using f32::Tw;
 
 constexpr float kSmallBin = 1.0f / 65536.0f;       // FP32 |F| / A_p at or below which a bin is resolved exactly
 constexpr float kZeroBin = 1.0f / 68719476736.0f;  // float-float max(|Re F|, |Im F|) / A_p at or below which F = 0
+constexpr int kListQ = 32;   // small bins a CTA may hand to the listed-bin passes (more: it resolves them itself)
+// Layout of the listed-bin scratch of one launch of ncta CTAs (ints): [0] the number of listed bins, [4 ..)
+// the work list (cta << 5 | entry, in no particular order), then per CTA kListStride ints: [0] its count,
+// [1 .. Q] its entries (owner | output << 10 | bin << 14, in the in-kernel resolve's order), [1 + Q ..) the
+// (Re, Im) of each entry's Gamma, written by the exact pass.
+constexpr int kListStride = 1 + 3 * kListQ;
+__host__ __device__ constexpr size_t list_cta_offset(long long ncta) { return 4 + (size_t)ncta * kListQ; }
 
 // Float-float constants of the exact recompute: cos, sin of 2 pi m / n and the taper h(u), each as a pair
 // (hi, lo) of FP32 values whose sum is the double-precision value.
@@ -163,7 +170,7 @@ template <int N> struct BGeo {
     // rows of the cube along t and x ([N] + [N] ints, -1 outside a zero-extended volume)
     static constexpr size_t IDX_OFF = (SMALL_OFF + (size_t)YC * NT * 2 + 15) / 16 * 16;
     static constexpr size_t WB_OFF = IDX_OFF + (size_t)2 * N * 4;   // [NT / 32] owners of small bins, per warp
-    static constexpr size_t SMEM = WB_OFF + (size_t)(NT / 32) * 4;
+    static constexpr size_t SMEM = WB_OFF + (size_t)(NT / 32 + 1) * 4;   // + the CTA's list decision
     static_assert(N <= 16, "16-bit masks of small bins");
     static constexpr int SLICE = (N * YH + 3) / 4 * 4;           // u_t slices of the block, 16-byte aligned
     static constexpr int BLOCK_FLOATS = N * SLICE;               // scratch block per CTA
@@ -280,6 +287,219 @@ __device__ __noinline__ void resolve_small_bins(const float* __restrict__ V, int
     }
 }
 
+// The CTA's small bins as a list for the listed-bin pass: entries (owner, output, bin) in the order the
+// in-kernel resolve would take them (owners in thread order, then outputs, then bins), list[0] = their
+// count.  Returns (CTA-uniform) whether the list holds them all; a CTA with more than kListQ writes a count
+// of 0 and resolves its bins itself.  Contains one __syncthreads.
+template <int NT, int YC>
+__device__ bool list_small_bins(const uint16_t* s_small, unsigned* s_wbits, int* __restrict__ list,
+                                int* __restrict__ work, int* __restrict__ nwork, long long cta) {
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bool mine = false;
+    for (int yi = 0; yi < YC; ++yi) mine = mine || s_small[yi * NT + tid] != 0;
+    const unsigned wb = __ballot_sync(0xffffffffu, mine);
+    if (lane == 0) s_wbits[warp] = wb;
+    __syncthreads();
+    if (tid == 0) {
+        int cnt = 0;
+        for (int w = 0; w < NW; ++w) {
+            for (unsigned todo = s_wbits[w]; todo; todo &= todo - 1) {
+                const int o = 32 * w + __ffs(todo) - 1;
+                for (int yi = 0; yi < YC; ++yi)
+                    for (unsigned msk = s_small[yi * NT + o]; msk; msk &= msk - 1) {
+                        if (cnt < kListQ) list[1 + cnt] = o | (yi << 10) | ((__ffs(msk) - 1) << 14);
+                        ++cnt;
+                    }
+            }
+        }
+        const bool fits = cnt <= kListQ;
+        list[0] = fits ? cnt : 0;
+        s_wbits[NW] = fits ? 1u : 0u;
+        if (fits && cnt > 0) {   // the exact pass takes the bins in any order: each writes its own slot
+            const int base = atomicAdd(nwork, cnt);
+            for (int e = 0; e < cnt; ++e) work[base + e] = (int)(cta << 5) | e;
+        }
+    }
+    __syncthreads();
+    return s_wbits[NW] != 0u;
+}
+
+// The listed bins' exact pass: one warp per listed bin (a grid-stride loop over the work list).  Each is
+// recomputed exactly as the in-kernel resolve does (the direct sum F = sum_u h(u) Vext[...] w^(k.u) in
+// float-float arithmetic, lanes splitting the n^3 terms; A_p = sum_u h(u) |Vext| alongside), and its
+// Gamma = rho F / |F| (0 if max(|Re F|, |Im F|) <= 2^-36 A_p) is written to the bin's slot of its CTA's list.
+template <int N>
+__global__ void __launch_bounds__(256)
+k5_listed_exact_f32(const float* __restrict__ V, const float* __restrict__ gE, int* __restrict__ lists,
+                    long long ncta, int T, int X, int Y, int bnd, int t_begin, int t_step,
+                    const float* __restrict__ wtab, int taper, const __grid_constant__ Exact2f<N> ex) {
+    using G = BGeo<N>;
+    constexpr int H = G::H, BY = G::BY, YC = G::YC, ROWS = G::ROWS;
+    constexpr int N3 = N * N * N, PER = N3 >= 32 ? N3 / 32 : 1, STEP = 32 / N;
+    constexpr int U = PER >= 4 ? 4 : PER;   // terms whose loads are issued together
+    // the float-float constants in shared memory: the lanes index them by their own phase, which the
+    // parameter space would serve one distinct address at a time
+    __shared__ float s_ex[6][N];
+    __shared__ int s_rows[8][2][N];   // per warp: the cube's source rows along t and x of its current bin
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 6 * N; i += blockDim.x) {
+        const int a = i / N, m = i % N;
+        s_ex[a][m] = a == 0 ? ex.ch[m] : a == 1 ? ex.cl[m] : a == 2 ? ex.sh[m] : a == 3 ? ex.sl[m]
+                   : a == 4 ? ex.hh[m] : ex.hl[m];
+    }
+    __syncthreads();
+    const int nw = lists[0];
+    const int* work = lists + 4;
+    int* ctal = lists + list_cta_offset(ncta);
+    const int nseg = (Y + BY - 1) / BY;
+    const size_t NV = (size_t)T * X * Y;
+    const int uy = lane % N, r0 = lane / N;
+    const bool live = lane < N3;
+    const int wstride = gridDim.x * (blockDim.x / 32);
+    for (int w = blockIdx.x * (blockDim.x / 32) + wib; w < nw; w += wstride) {
+        const int item = work[w];
+        const long long cta = item >> 5;
+        const int e = item & 31;
+        int* L = ctal + cta * kListStride;
+        const int ent = L[1 + e];
+        const int y_start = (int)(cta % nseg) * BY;
+        const int x0 = (int)((cta / nseg) % X);
+        const int t0 = t_begin + (int)(cta / ((long long)nseg * X)) * t_step;
+        const int o = ent & 1023, yi = (ent >> 10) & 15, ky = (ent >> 14) & 15;
+        const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
+        const int yl = ych * YC + yi;
+        const int gy = ext_index(y_start + yl - N / 2 + uy, Y, bnd);
+        if (lane < 2 * N)
+            s_rows[wib][lane / N][lane % N] = lane < N ? ext_index(t0 - N / 2 + lane, T, bnd)
+                                                       : ext_index(x0 - N / 2 + lane - N, X, bnd);
+        __syncwarp();
+        const FF hy = {s_ex[4][uy], s_ex[5][uy]};
+        FF re = {0.f, 0.f}, im = {0.f, 0.f};
+        float a1 = 0.f;   // the window's L1 norm, FP32 (it only places the 2^-36 band)
+        for (int i0 = 0; i0 < PER; i0 += U) {
+            float v[U];
+            int tx[U];
+#pragma unroll
+            for (int a = 0; a < U; ++a) {   // loads first
+                const int rr = live ? r0 + STEP * (i0 + a) : 0, ut = rr / N, ux = rr % N;
+                const int gt = s_rows[wib][0][ut], gx = s_rows[wib][1][ux];
+                v[a] = (live && (gt | gx | gy) >= 0) ? __ldg(V + ((size_t)gt * X + gx) * Y + gy) : 0.f;
+                tx[a] = rr;
+            }
+#pragma unroll
+            for (int a = 0; a < U; ++a) {
+                const int ut = tx[a] / N, ux = tx[a] % N;
+                const int ph = (kt * ut + kx * ux + ky * uy) % N;
+                FF c = {s_ex[0][ph], s_ex[1][ph]}, sn = {-s_ex[2][ph], -s_ex[3][ph]};
+                if (taper) {
+                    const FF h3 = ff_mul(ff_mul(FF{s_ex[4][ut], s_ex[5][ut]}, FF{s_ex[4][ux], s_ex[5][ux]}), hy);
+                    c = ff_mul(h3, c);
+                    sn = ff_mul(h3, sn);
+                    a1 = fmaf(h3.hi, fabsf(v[a]), a1);
+                } else {
+                    a1 += fabsf(v[a]);
+                }
+                re = ff_add(re, ff_mul1(v[a], c));
+                im = ff_add(im, ff_mul1(v[a], sn));
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const FF r2 = {__shfl_xor_sync(0xffffffffu, re.hi, d), __shfl_xor_sync(0xffffffffu, re.lo, d)};
+            const FF i2 = {__shfl_xor_sync(0xffffffffu, im.hi, d), __shfl_xor_sync(0xffffffffu, im.lo, d)};
+            re = ff_add(re, r2);
+            im = ff_add(im, i2);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, d);
+        }
+        float gr = 0.f, gim = 0.f;
+        const float mx = fmaxf(fabsf(re.hi), fabsf(im.hi));
+        if (mx > kZeroBin * a1) {
+            const int k = ky <= N / 2 ? ky : N - ky;
+            const size_t gi = ((size_t)t0 * X + x0) * Y + y_start + yl;
+            const float rho = fmaf(__ldg(gE + gi), __ldg(wtab + k * ROWS + row),
+                                   fmaf(__ldg(gE + NV + gi), __ldg(wtab + (H + k) * ROWS + row),
+                                        __ldg(gE + 2 * NV + gi) * __ldg(wtab + (2 * H + k) * ROWS + row)));
+            const float fr = re.hi / mx, fi = im.hi / mx;      // scaled first: no underflow
+            const float sc = rho / sqrtf(fmaf(fr, fr, fi * fi));
+            gr = sc * fr;
+            gim = sc * fi;
+        }
+        if (lane == 0) {
+            float* gam = reinterpret_cast<float*>(L + 1 + kListQ);
+            gam[2 * e] = gr;
+            gam[2 * e + 1] = gim;
+        }
+        __syncwarp();   // the next bin rewrites this warp's source rows
+    }
+}
+
+// The listed bins' apply pass: one warp per CTA of the main kernel's launch adds its listed bins, in list
+// order, to the brick's block; the three adjoint stages of one bin are the outer product
+//   block[u_t][u_x][y_l + u_y] += Re( Gamma h(u_t) h(u_x) h(u_y) e^{+2 pi i (k_t u_t + k_x u_x + k_y u_y) / n} ).
+// Each block element is owned by one lane per bin; the warp syncs between bins (they overlap along y).
+template <int N>
+__global__ void __launch_bounds__(256)
+k5_listed_apply_f32(float* __restrict__ blocks, const int* __restrict__ lists, long long ncta,
+                    const __grid_constant__ Tw<N> tw) {
+    using G = BGeo<N>;
+    constexpr int YC = G::YC, YH = G::YH, ROWS = G::ROWS;
+    constexpr int N3 = N * N * N, PER = N3 >= 32 ? N3 / 32 : 1, STEP = 32 / N;
+    __shared__ float s_c[N / 2 + 1][N], s_s[N / 2 + 1][N];   // the lanes index them by their own taps
+    for (int i = threadIdx.x; i < (N / 2 + 1) * N; i += blockDim.x) {
+        s_c[i / N][i % N] = tw.c[i / N][i % N];
+        s_s[i / N][i % N] = tw.s[i / N][i % N];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long cta = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (cta >= ncta) return;
+    const int* L = lists + list_cta_offset(ncta) + cta * kListStride;
+    const int cnt = L[0];
+    if (cnt <= 0) return;
+    const float* gam = reinterpret_cast<const float*>(L + 1 + kListQ);
+    float* blk = blocks + cta * G::BLOCK_FLOATS;
+    const int uy = lane % N, r0 = lane / N;
+    const bool live = lane < N3;
+    for (int e = 0; e < cnt; ++e) {
+        const float gr = gam[2 * e], gim = gam[2 * e + 1];
+        if (gr != 0.f || gim != 0.f) {   // warp-uniform
+            const int ent = L[1 + e];
+            const int o = ent & 1023, yi = (ent >> 10) & 15, ky = (ent >> 14) & 15;
+            const int row = o % ROWS, kt = row / N, kx = row % N, ych = o / ROWS;
+            const int yl = ych * YC + yi;
+            // h(u) e^{+i theta} of each axis from the twiddle table (the taper is in it): bins above n/2 take the
+            // conjugate of their mirror
+            const int kxa = kx <= N / 2 ? kx : N - kx, kya = ky <= N / 2 ? ky : N - ky;
+            const float sx = kx <= N / 2 ? 1.f : -1.f, sy = ky <= N / 2 ? 1.f : -1.f;
+            const float eyr = s_c[kya][uy], eyi = sy * s_s[kya][uy];
+            const float gyr = gr * eyr - gim * eyi, gyi = gr * eyi + gim * eyr;   // Gamma e_y
+            constexpr int UB = PER >= 8 ? 8 : PER;   // block elements read, then written, together
+            for (int i0 = 0; i0 < PER; i0 += UB) {
+                float cur[UB];
+                size_t off[UB];
+#pragma unroll
+                for (int a = 0; a < UB; ++a) {
+                    const int rr = r0 + STEP * (i0 + a);
+                    off[a] = (size_t)(rr / N) * G::SLICE + (rr % N) * YH + yl + uy;
+                    cur[a] = (live && rr < N * N) ? blk[off[a]] : 0.f;
+                }
+#pragma unroll
+                for (int a = 0; a < UB; ++a) {
+                    const int rr = r0 + STEP * (i0 + a);
+                    if (!live || rr >= N * N) continue;
+                    const int ut = rr / N, ux = rr % N;
+                    const float etr = s_c[kt][ut], eti = s_s[kt][ut];
+                    const float exr = s_c[kxa][ux], exi = sx * s_s[kxa][ux];
+                    const float txr = etr * exr - eti * exi, txi = etr * exi + eti * exr;
+                    blk[off[a]] = cur[a] + (gyr * txr - gyi * txi);
+                }
+            }
+        }
+        __syncwarp();   // the next bin's window overlaps this one's along y
+    }
+}
+
 // EN: the energy reading of the feature (Gamma = 2 rho F, no kink band).  SL: both y-passes slide (rect
 // taper, n = 8, 16).  With the phase anchored at the start y_r of the thread's run,
 //   Ft_j[k] = F_{y_r + j}[k] w^(k j) = sum_{y = j}^{j + n - 1} G2[y_r + y] w^(k y),   w = e^(-2 pi i / n),
@@ -296,7 +516,7 @@ __global__ void __launch_bounds__(BGeo<N>::NT, BCfg<N>::MINB)
 k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE, float* __restrict__ blocks,
                        int T, int X, int Y, int bnd, int t_begin, int t_step, const float* __restrict__ wtab,
                        int taper, const __grid_constant__ Tw<N> tw, const __grid_constant__ Exact2f<N> ex,
-                       const __grid_constant__ VanishTab vt) {
+                       const __grid_constant__ VanishTab vt, int* __restrict__ lists) {
     using G = BGeo<N>;
     using B = typename G::B;
     constexpr int H = G::H, BY = G::BY, YC = G::YC, YH = G::YH, ROWS = G::ROWS, NT = G::NT, WIN = G::WIN;
@@ -514,9 +734,18 @@ k5_spectra_adjoint_f32(const float* __restrict__ V, const float* __restrict__ gE
             }
         }
     }
-    if (!EN)
-        resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge, s_l1,
-                                                   wtab, tw, ex, reinterpret_cast<unsigned*>(smem_raw + G::WB_OFF));
+    if (!EN) {
+        // the small bins go to the listed-bin pass when a list is given and they fit in it
+        unsigned* s_wbits = reinterpret_cast<unsigned*>(smem_raw + G::WB_OFF);
+        const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        const size_t ncta = (size_t)gridDim.x * gridDim.y * gridDim.z;
+        const bool listed = lists && list_small_bins<NT, YC>(s_small, s_wbits,
+                                                             lists + list_cta_offset(ncta) + cta * kListStride,
+                                                             lists + 4, lists, (long long)cta);
+        if (!listed)
+            resolve_small_bins<N, NT, YC, BY, H, ROWS>(V, X, Y, bnd, y_start, taper, s_small, s_src, s_win, s_ge,
+                                                       s_l1, wtab, tw, ex, s_wbits);
+    }
     __syncthreads();
 
     // ---- step 3: sum the y-chunk windows into Gamma_G2[row][y] ---------------------------------
@@ -632,28 +861,44 @@ Exact2f<N> make_exact2f(int taper) {
 
 template <int N, bool SL>
 void launch_sl(const TwiddleTable& t, const float* wtab, dim3 grid, const float* V, const float* gE, float* blocks,
-               int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int taper, cudaStream_t s) {
+               int T, int X, int Y, int bnd, int feat, int t_begin, int t_step, int taper, int* lists,
+               cudaStream_t s) {
     using G = BGeo<N>;
-    if (feat == 1)
+    if (feat == 1) {
         k5_spectra_adjoint_f32<N, true, SL><<<grid, G::NT, G::SMEM, s>>>(
             V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact2f<N>(taper),
-            VanishTab{});
-    else
-        k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(
-            V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact2f<N>(taper),
-            make_vanish_tab(N, T, X, Y, bnd, taper));
+            VanishTab{}, nullptr);
+        return;
+    }
+    k5_spectra_adjoint_f32<N, false, SL><<<grid, G::NT, G::SMEM, s>>>(
+        V, gE, blocks, T, X, Y, bnd, t_begin, t_step, wtab, taper, f32::make_tw<N>(t), make_exact2f<N>(taper),
+        make_vanish_tab(N, T, X, Y, bnd, taper), lists);
+    if (lists) {
+        const long long ncta = (long long)grid.x * grid.y * grid.z;
+        k5_listed_exact_f32<N><<<8 * device_sms(), 256, 0, s>>>(V, gE, lists, ncta, T, X, Y, bnd, t_begin, t_step,
+                                                                 wtab, taper, make_exact2f<N>(taper));
+        k5_listed_apply_f32<N><<<(unsigned)((ncta + 7) / 8), 256, 0, s>>>(blocks, lists, ncta, f32::make_tw<N>(t));
+        note_launches(2);
+    }
 }
 
 template <int N>
 cudaError_t launch_n(const TwiddleTable& t, const float* wtab, const float* V, const float* gE, float* blocks, int T,
-                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, int taper, cudaStream_t s) {
+                     int X, int Y, int bnd, int feat, int t_begin, int t_step, int t_count, int taper, int* lists,
+                     cudaStream_t s) {
     using G = BGeo<N>;
     dim3 grid((Y + G::BY - 1) / G::BY, X, t_count);
+    if (lists && feat != 1) {   // the work-list counter starts at zero
+        const cudaError_t e = cudaMemsetAsync(lists, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
     if constexpr (kAdjointSliding<N>) {
-        if (taper == 0) launch_sl<N, true>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
-        else launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
+        if (taper == 0)
+            launch_sl<N, true>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, lists, s);
+        else
+            launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, lists, s);
     } else {
-        launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, s);
+        launch_sl<N, false>(t, wtab, grid, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, taper, lists, s);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -681,15 +926,26 @@ SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n) {
     }
 }
 
+size_t spectra_adjoint_f32_list_bytes(int n, int X, int Y, int t_count) {
+    const int by = n == 16 ? BGeo<16>::BY : BGeo<8>::BY;   // 32 for n <= 8
+    const long long ncta = (long long)((Y + by - 1) / by) * X * t_count;
+    return (list_cta_offset(ncta) + (size_t)ncta * kListStride) * sizeof(int);
+}
+
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
                                        const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                       int t_begin, int t_step, int t_count, int taper, cudaStream_t s) {
+                                       int t_begin, int t_step, int t_count, int taper, int* lists, cudaStream_t s) {
     if (t_step < 1 || taper < 0 || taper > 1) return cudaErrorInvalidValue;
     switch (n) {
-        case 2: return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
-        case 4: return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
-        case 8: return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
-        case 16: return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, s);
+        case 2:
+            return launch_n<2>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, lists, s);
+        case 4:
+            return launch_n<4>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, lists, s);
+        case 8:
+            return launch_n<8>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, lists, s);
+        case 16:
+            return launch_n<16>(tw, wtab, V, gE, blocks, T, X, Y, bnd, feat, t_begin, t_step, t_count, taper, lists,
+                                s);
         default: return cudaErrorInvalidValue;
     }
 }

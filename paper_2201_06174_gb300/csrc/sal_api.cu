@@ -587,6 +587,12 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
         vt = padded_copy(h, V, st, e);
         if (e != cudaSuccess) return cuda_fail(h, e, "spectral adjoint: padded copy");
     }
+    // the FP32 adjoint lists its small bins in the overlap-add's plane buffer, free until the gather runs
+    const size_t ext_bytes = sal::gather_ext_floats(h->n, g, h->X, h->Y, h->slab_t, sc) * sizeof(float);
+    int* lists = h->prec == SAL_FP32 && h->feature == 0 &&
+                         sal::spectra_adjoint_f32_list_bytes(h->n, h->X, h->Y, h->slab_t) <= ext_bytes
+                     ? reinterpret_cast<int*>(h->gext)
+                     : nullptr;
     for (int p0 = 0; p0 < planes; p0 += h->slab_t) {
         const int cnt = std::min(h->slab_t, planes - p0), t_begin = p0 * sc;
         e = h->feature == 2
@@ -594,7 +600,7 @@ sal_status spectral_adjoint(sal_handle* h, const float* V, const float* gE, floa
                                                   h->taper, st)
             : h->prec == SAL_FP32
                 ? sal::spectra_adjoint_f32_launch(h->n, h->tw, h->f32_wt, V, gE, h->blocks, h->T, h->X, h->Y,
-                                                  h->boundary, h->feature, t_begin, sc, cnt, h->taper, st)
+                                                  h->boundary, h->feature, t_begin, sc, cnt, h->taper, lists, st)
                 // the adjoint's 16-bit operands are FP16 in both 16-bit forms: the direction F/|F| of
                 // small bins amplifies operand rounding, and FP16 carries 3 more mantissa bits
                 : sal::spectra_adjoint_tc_launch(h->n, 0, h->tw, h->adj_tables, V, gE, h->blocks, h->T, h->X, h->Y,

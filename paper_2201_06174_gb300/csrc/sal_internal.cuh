@@ -142,10 +142,13 @@ struct SpectraAdjointGeometry {
 cudaError_t spectra_adjoint_f32_prepare(int n);
 SpectraAdjointGeometry spectra_adjoint_f32_geometry(int n);
 // bricks of t0 = t_begin + r t_step, r < t_count (t_step s > 1: the lattice planes of stride-s windows)
-// taper 0 (rect) recomputes the forward stage 3 by the sliding recursion for n = 16
+// taper 0 (rect) runs both y-passes as sliding recursions for n = 8, 16.  lists (nullable; device scratch of
+// spectra_adjoint_f32_list_bytes): the small bins of the abs(F) reading are listed per CTA there and
+// resolved by a second, grid-wide pass; without it each CTA resolves its own.
+size_t spectra_adjoint_f32_list_bytes(int n, int X, int Y, int t_count);
 cudaError_t spectra_adjoint_f32_launch(int n, const TwiddleTable& tw, const float* wtab, const float* V,
                                        const float* gE, float* blocks, int T, int X, int Y, int bnd, int feat,
-                                       int t_begin, int t_step, int t_count, int taper, cudaStream_t s);
+                                       int t_begin, int t_step, int t_count, int taper, int* lists, cudaStream_t s);
 // K5 on the tensor cores (FP16 operands: fmt must be 0); its constant operands are built once per handle
 cudaError_t spectra_adjoint_tc_prepare(int n, int fmt);
 size_t spectra_adjoint_tc_tables_bytes(int n);
