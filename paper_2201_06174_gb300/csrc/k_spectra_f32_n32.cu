@@ -42,14 +42,32 @@ k1_spectra_f32_n32(const float* __restrict__ V, float* __restrict__ E, int T, in
     const int yb = blockIdx.x * BY, x0 = blockIdx.y * stride, t0 = blockIdx.z * stride;
 
     const float vshift = SL ? __ldg(V + ((size_t)t0 * X + x0) * Y + yb) : 0.f;
-    for (int r = tid; r < N * N * YH; r += NT) {
-        const int yy = r % YH, ux = (r / YH) % N, ut = r / (YH * N);
-        const int gt = ext_index(t0 - N / 2 + ut, T, bnd);
-        const int gx = ext_index(x0 - N / 2 + ux, X, bnd);
-        const int gy = ext_index(yb - N / 2 + yy, Y, bnd);
-        float v = 0.f;
-        if ((gt | gx | gy) >= 0) v = __ldg(V + ((size_t)gt * X + gx) * Y + gy);
-        s_in[r] = v - vshift;
+    // the halo brick a (u_t, u_x) row of YH samples per warp, RU rows in flight: each lane samples y = lane and
+    // lane + 32, its two border-extended source columns fixed for the brick
+    {
+        constexpr int ROWS = N * N, RU = 4;
+        const int gy0 = ext_index(yb - N / 2 + lane, Y, bnd);
+        const int gy1 = lane + 32 < YH ? ext_index(yb - N / 2 + lane + 32, Y, bnd) : -1;
+        for (int r0 = warp * RU; r0 < ROWS; r0 += (NT / 32) * RU) {
+            float v0[RU], v1[RU];
+#pragma unroll
+            for (int a = 0; a < RU; ++a) {   // loads first
+                const int r = r0 + a;
+                const int gt = ext_index(t0 - N / 2 + r / N, T, bnd);
+                const int gx = ext_index(x0 - N / 2 + r % N, X, bnd);
+                v0[a] = v1[a] = 0.f;
+                if ((gt | gx) >= 0) {
+                    const float* row = V + ((size_t)gt * X + gx) * Y;
+                    if (gy0 >= 0) v0[a] = __ldg(row + gy0);
+                    if (gy1 >= 0) v1[a] = __ldg(row + gy1);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < RU; ++a) {   // s_in[u_t][u_x][y], row r = u_t N + u_x
+                s_in[(r0 + a) * YH + lane] = v0[a] - vshift;
+                if (lane + 32 < YH) s_in[(r0 + a) * YH + lane + 32] = v1[a] - vshift;
+            }
+        }
     }
     float e0 = 0.f, e1 = 0.f, e2 = 0.f;       // direct form: this lane's (k_x) partial E of output y0 = warp
     float es[SL ? BY : 1][3];                 // sliding form: this lane's partial E of the 8 outputs
